@@ -1,0 +1,203 @@
+/*
+ * ricmrcc.h -- C ABI of the GB300 spin-free RIC-MRCCSD residual library.
+ *
+ * The library evaluates the spin-free many-body residual and energy of the
+ * renormalized internally contracted multireference coupled cluster method
+ * with singles and doubles (RIC-MRCCSD; arXiv 2511.03567, Sec. 2.2-2.3) and
+ * solves the amplitude equations with the flow-renormalized update
+ * (Eq. ric-update) on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions used by every call
+ * ------------------------------
+ *  - Orbitals are ordered [core | active | virtual]: n = n_core + n_act + n_virt
+ *    (Table 1: internal i,j; active t,u,v,...; virtual a,b).
+ *  - All floating point data are IEEE double, C (row-major) order.
+ *  - Spin-free RDMs use the E-operator convention of Sec. 2.3.1
+ *    (Eq. spinfree-spinsum): G1[P*a+Q] = <E^P_Q>, G2[P,Q,R,S] = <E^{PQ}_{RS}>,
+ *    G3[P,Q,R,S,T,U] = <E^{PQR}_{STU}>, E^{PQ}_{RS} = sum a+_P a+_Q a_S a_R.
+ *  - Spin-free amplitudes are the non-redundant components of Table 2:
+ *    singles are the alpha component t^{c}_{k}, doubles the alpha-beta
+ *    component t^{c d-bar}_{k l-bar}.  They are passed as one flat array per
+ *    rank, the class blocks concatenated in the order reported by
+ *    ricmrcc_amplitude_layout():
+ *      T1: IA[o][v], IT[o][a], TA[a][v]                (element [k][c] = t^c_k)
+ *      T2: IJAB[o][o][v][v], IJTA[o][o][a][v], IJTU[o][o][a][a],
+ *          ITAB[o][a][v][v], ITUA[o][a][a][v], ITAU[o][a][v][a],
+ *          ITUV[o][a][a][a], TUAB[a][a][v][v], TUVA[a][a][a][v]
+ *                                                    (element [k][l][c][d] = t^{cd}_{kl})
+ *    ITUA and ITAU are the two stored components of the ITUA class
+ *    (Sec. 3.2): t^{u a-bar}_{i t-bar} and t^{a u-bar}_{i t-bar}.
+ *    IJAB, IJTU and TUAB must obey t^{cd}_{kl} = t^{dc}_{lk}
+ *    (Eq. spinfree-perm-sym); the residual of these classes obeys it too.
+ *  - Host pointers are borrowed for the duration of the call and copied;
+ *    the handle owns all device memory.  Output buffers are caller-owned.
+ *  - *_dev variants take device pointers and run on the handle's stream
+ *    (ricmrcc_set_stream); they return after the work is enqueued unless
+ *    stated otherwise.
+ *  - Every call returns a status code; on failure ricmrcc_last_error()
+ *    gives a message owned by the handle (valid until the next call).
+ *    No call aborts the process or traps the GPU.
+ */
+#ifndef RICMRCC_H
+#define RICMRCC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RICMRCC_API __attribute__((visibility("default")))
+#else
+#define RICMRCC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RICMRCC_OK = 0,
+  RICMRCC_EINVAL = 1,        /* bad argument (size, null pointer, non-finite input) */
+  RICMRCC_ENOMEM = 2,        /* device allocation failed */
+  RICMRCC_ECUDA = 3,         /* CUDA runtime error */
+  RICMRCC_NOT_CONVERGED = 4, /* solve hit max_iter */
+  RICMRCC_DIVERGED = 5,      /* non-finite residual/energy or runaway update */
+  RICMRCC_ESTATE = 6,        /* call out of order (e.g. residual before set_rdms) */
+  RICMRCC_ENOTSUP = 7        /* valid request that this build does not support */
+};
+
+/* kind argument of ricmrcc_set_rdms */
+enum { RICMRCC_RDM = 0, RICMRCC_CUMULANT = 1 };
+
+/* precision of the dense contractions (ricmrcc_set_precision) */
+enum {
+  RICMRCC_FP64 = 0,  /* every contraction in FP64 */
+  RICMRCC_MIXED = 1  /* large contractions on BF16 tensor cores (split-precision
+                        products, FP32 accumulation), FP64 everything else */
+};
+
+typedef struct ricmrcc ricmrcc_t;
+
+#define RICMRCC_NCLASS1 3
+#define RICMRCC_NCLASS2 9
+
+typedef struct {
+  int64_t t1_size;                     /* elements of the flat T1 / R1 array */
+  int64_t t2_size;                     /* elements of the flat T2 / R2 array */
+  int64_t t1_offset[RICMRCC_NCLASS1];  /* IA, IT, TA */
+  int32_t t1_shape[RICMRCC_NCLASS1][2];
+  int64_t t2_offset[RICMRCC_NCLASS2];  /* IJAB..TUVA as listed above */
+  int32_t t2_shape[RICMRCC_NCLASS2][4];
+} ricmrcc_layout;
+
+typedef struct {
+  double s;          /* flow parameter s [Eh^-2] of Eq. ric-update; s >= 0 */
+  int max_iter;      /* iteration limit (default 100) */
+  double e_tol;      /* |E_n - E_{n-1}| threshold (default 1e-10) */
+  double t_tol;      /* max |t_new - t| threshold (default 1e-9) */
+  int diis_size;     /* DIIS subspace size, 0 disables (default 8) */
+  int diis_start;    /* first iteration that extrapolates (default 3) */
+  int precision;     /* RICMRCC_FP64 or RICMRCC_MIXED (default FP64) */
+  double refine_tol; /* mixed: switch to FP64 iterations once max|dt| < refine_tol */
+} ricmrcc_opts;
+
+typedef struct {
+  int iterations;     /* residual evaluations performed */
+  int converged;      /* 1 if both thresholds were met */
+  int fp64_iterations;
+  int mixed_iterations;
+  double energy;      /* E = E0 + Hbar_0 at the returned amplitudes */
+  double e0;          /* reference energy <Psi0|H|Psi0> */
+  double max_dt;      /* last max |t_new - t| */
+  double seconds;     /* wall time of the solve */
+} ricmrcc_stats;
+
+/* Create a handle for one problem size (Table 1 spaces) and an auxiliary
+ * basis of n_aux functions.  n_core, n_act, n_virt >= 0, n_aux >= 1.
+ * n_act = 0 is a single-determinant reference.  Uses the current CUDA device.
+ * Errors: EINVAL (negative sizes), ENOMEM, ECUDA. */
+RICMRCC_API int ricmrcc_create(int n_core, int n_act, int n_virt, int n_aux, ricmrcc_t** out);
+
+/* Release every resource of the handle (NULL is ignored). */
+RICMRCC_API void ricmrcc_destroy(ricmrcc_t* h);
+
+/* Last error message of the handle ("" if none).  Owned by the handle. */
+RICMRCC_API const char* ricmrcc_last_error(const ricmrcc_t* h);
+
+/* Stream (cudaStream_t) used by every later call; NULL = legacy default. */
+RICMRCC_API int ricmrcc_set_stream(ricmrcc_t* h, void* stream);
+
+/* Select the arithmetic of the dense contractions (RICMRCC_FP64 / MIXED). */
+RICMRCC_API int ricmrcc_set_precision(ricmrcc_t* h, int precision);
+
+/* One-electron integrals h[n][n] (symmetric) and the density-fitting factor
+ * B[n_aux][n][n] (symmetric in the orbital pair), so that the chemist-notation
+ * two-electron integral is (pq|rs) = sum_Q B[Q][p][q] B[Q][r][s] and the
+ * physicist <pq|rs> = (pr|qs) (Sec. 2.1).  Host pointers.  Rebuilds the
+ * integral tensor; if RDMs are already set, also the generalized Fock matrix
+ * f = h + sum_C v + sum_A v gamma and E0 (Sec. 2.1).  Errors: EINVAL (NULL
+ * or non-finite data). */
+RICMRCC_API int ricmrcc_set_integrals(ricmrcc_t* h, const double* hmat, const double* B);
+RICMRCC_API int ricmrcc_set_integrals_dev(ricmrcc_t* h, const double* hmat, const double* B);
+
+/* Spin-free reference densities of the CAS state (Sec. 2.3.2, Eq.
+ * spinfree-rdm).  kind = RICMRCC_RDM: g1 = Gamma1[a][a], g2 = Gamma2[a]^4,
+ * g3 = Gamma3[a]^6.  kind = RICMRCC_CUMULANT: g1 = Gamma1, g2 = Lambda2,
+ * g3 = Lambda3 (spin traces of the spin-orbital cumulants of Eq. cumulant and
+ * its three-body analogue).  Builds the cumulants used by the residual and,
+ * if integrals are set, f and E0.  With n_act = 0 the pointers may be NULL.
+ * Host pointers.  Errors: EINVAL. */
+RICMRCC_API int ricmrcc_set_rdms(ricmrcc_t* h, const double* g1, const double* g2, const double* g3,
+                     int kind);
+RICMRCC_API int ricmrcc_set_rdms_dev(ricmrcc_t* h, const double* g1, const double* g2, const double* g3,
+                         int kind);
+
+/* Rotate to semi-canonical orbitals (Sec. 2.2: f diagonal inside the core,
+ * active and virtual blocks).  Eigenvalues ascend inside each block; each
+ * eigenvector's largest-magnitude component is made positive.  Rotates h, B,
+ * the RDMs and any stored amplitudes' reference, and rebuilds f, E0.
+ * U_out (nullable, host [n][n]) receives new_orbital_j = sum_p U[p][j] old_p.
+ * Requires integrals and RDMs.  Errors: ESTATE. */
+RICMRCC_API int ricmrcc_semicanonicalize(ricmrcc_t* h, double* U_out);
+
+/* Sizes and offsets of the flat amplitude arrays (see the conventions). */
+RICMRCC_API int ricmrcc_amplitude_layout(const ricmrcc_t* h, ricmrcc_layout* out);
+
+/* Reference energy E0 = <Psi0|H|Psi0> (no nuclear repulsion) and the
+ * spin-free generalized Fock matrix F[n][n] (alpha component), host outputs;
+ * either pointer may be NULL.  Requires integrals and RDMs. */
+RICMRCC_API int ricmrcc_reference(ricmrcc_t* h, double* E0, double* F);
+
+/* Many-body residual and energy (Sec. 2.2, Eqs. for E_CC, r^c_k, r^{cd}_{kl}
+ * with H-bar truncated after the two-fold commutator and the RIC neglect
+ * rules): R = non-redundant spin-free components of H-bar^c_k, H-bar^{cd}_{kl}
+ * after Eq. antisym, E = E0 + H-bar_0.  T1/T2 in, R1/R2 out in the flat class
+ * layout; E_out (nullable) receives the energy.  Host pointers; blocks until
+ * done.  Requires integrals and RDMs.  Errors: ESTATE, EINVAL, ECUDA. */
+RICMRCC_API int ricmrcc_residual(ricmrcc_t* h, const double* T1, const double* T2, double* R1, double* R2,
+                     double* E_out);
+/* Same with device pointers (E_out is a device double, nullable). */
+RICMRCC_API int ricmrcc_residual_dev(ricmrcc_t* h, const double* T1, const double* T2, double* R1,
+                         double* R2, double* E_out);
+
+/* Fill opts with the defaults listed in ricmrcc_opts. */
+RICMRCC_API int ricmrcc_opts_default(ricmrcc_opts* opts);
+
+/* Solve the amplitude equations with the renormalized update of Eq.
+ * ric-update, t <- (t Delta + r)(1 - exp(-s Delta^2)) / Delta with
+ * Delta = sum eps(holes) - sum eps(particles), eps = diag f (Eq. cc-update),
+ * DIIS-accelerated (Sec. 2.2).  Starts from the stored amplitudes (zero after
+ * set_rdms, or those given by ricmrcc_set_amplitudes).  E_out (nullable) and
+ * stats (nullable) receive the result.  Returns OK, NOT_CONVERGED (max_iter
+ * reached; amplitudes and energy of the last iterate are kept) or DIVERGED
+ * (non-finite numbers). */
+RICMRCC_API int ricmrcc_solve(ricmrcc_t* h, const ricmrcc_opts* opts, double* E_out, ricmrcc_stats* stats);
+
+/* Copy the stored amplitudes out / in (flat class layout, host pointers);
+ * set_amplitudes allows warm starts and resuming an interrupted solve. */
+RICMRCC_API int ricmrcc_get_amplitudes(ricmrcc_t* h, double* T1, double* T2);
+RICMRCC_API int ricmrcc_set_amplitudes(ricmrcc_t* h, const double* T1, const double* T2);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RICMRCC_H */

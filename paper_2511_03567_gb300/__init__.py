@@ -1,0 +1,256 @@
+"""Python binding of the GB300 spin-free RIC-MRCCSD library (libricmrcc.so).
+
+Argument marshalling only: every step of the residual, energy and solver
+runs in the library's CUDA kernels.  Host arrays are numpy float64; device
+arrays are CUDA torch tensors (float64, contiguous) passed to the *_dev calls.
+Importing works without a GPU; creating a handle needs the built library and
+a CUDA device and raises if either is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libricmrcc.so")
+
+OK, EINVAL, ENOMEM, ECUDA, NOT_CONVERGED, DIVERGED, ESTATE, ENOTSUP = range(8)
+RDM, CUMULANT = 0, 1
+FP64, MIXED = 0, 1
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "NOT_CONVERGED",
+                5: "DIVERGED", 6: "ESTATE", 7: "ENOTSUP"}
+
+T1_NAMES = ("IA", "IT", "TA")
+T2_NAMES = ("IJAB", "IJTA", "IJTU", "ITAB", "ITUA", "ITAU", "ITUV", "TUAB", "TUVA")
+
+
+class Layout(ctypes.Structure):
+    _fields_ = [("t1_size", ctypes.c_int64), ("t2_size", ctypes.c_int64),
+                ("t1_offset", ctypes.c_int64 * 3), ("t1_shape", (ctypes.c_int32 * 2) * 3),
+                ("t2_offset", ctypes.c_int64 * 9), ("t2_shape", (ctypes.c_int32 * 4) * 9)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_double), ("max_iter", ctypes.c_int), ("e_tol", ctypes.c_double),
+                ("t_tol", ctypes.c_double), ("diis_size", ctypes.c_int),
+                ("diis_start", ctypes.c_int), ("precision", ctypes.c_int),
+                ("refine_tol", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("fp64_iterations", ctypes.c_int), ("mixed_iterations", ctypes.c_int),
+                ("energy", ctypes.c_double), ("e0", ctypes.c_double),
+                ("max_dt", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class RicMrccError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_LIB = None
+_DP = ctypes.POINTER(ctypes.c_double)
+
+
+def library_path():
+    return LIB_PATH
+
+
+def load_library():
+    """Load libricmrcc.so (raises if it has not been built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    sig = {
+        "ricmrcc_create": ([ctypes.c_int] * 4 + [ctypes.POINTER(vp)], ctypes.c_int),
+        "ricmrcc_destroy": ([vp], None),
+        "ricmrcc_last_error": ([vp], ctypes.c_char_p),
+        "ricmrcc_set_stream": ([vp, vp], ctypes.c_int),
+        "ricmrcc_set_precision": ([vp, ctypes.c_int], ctypes.c_int),
+        "ricmrcc_set_integrals": ([vp, vp, vp], ctypes.c_int),
+        "ricmrcc_set_integrals_dev": ([vp, vp, vp], ctypes.c_int),
+        "ricmrcc_set_rdms": ([vp, vp, vp, vp, ctypes.c_int], ctypes.c_int),
+        "ricmrcc_set_rdms_dev": ([vp, vp, vp, vp, ctypes.c_int], ctypes.c_int),
+        "ricmrcc_semicanonicalize": ([vp, vp], ctypes.c_int),
+        "ricmrcc_amplitude_layout": ([vp, ctypes.POINTER(Layout)], ctypes.c_int),
+        "ricmrcc_reference": ([vp, vp, vp], ctypes.c_int),
+        "ricmrcc_residual": ([vp] * 6, ctypes.c_int),
+        "ricmrcc_residual_dev": ([vp] * 6, ctypes.c_int),
+        "ricmrcc_opts_default": ([ctypes.POINTER(Opts)], ctypes.c_int),
+        "ricmrcc_solve": ([vp, ctypes.POINTER(Opts), vp, ctypes.POINTER(Stats)], ctypes.c_int),
+        "ricmrcc_get_amplitudes": ([vp, vp, vp], ctypes.c_int),
+        "ricmrcc_set_amplitudes": ([vp, vp, vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _LIB = lib
+    return lib
+
+
+def _ptr(x):
+    """Address of a contiguous float64 numpy array or CUDA torch tensor (or None)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.dtype == np.float64 and x.flags["C_CONTIGUOUS"], "need contiguous float64"
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous(), "need a contiguous tensor"
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+def _host(x):
+    return None if x is None else np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+class RicMrcc:
+    """One problem (sizes fixed at creation) on the current CUDA device."""
+
+    def __init__(self, n_core, n_act, n_virt, n_aux):
+        self.lib = load_library()
+        self.dims = (n_core, n_act, n_virt, n_aux)
+        h = ctypes.c_void_p()
+        rc = self.lib.ricmrcc_create(n_core, n_act, n_virt, n_aux, ctypes.byref(h))
+        if rc != OK:
+            raise RicMrccError(rc, "ricmrcc_create failed")
+        self.h = h
+        lay = Layout()
+        self._check(self.lib.ricmrcc_amplitude_layout(self.h, ctypes.byref(lay)))
+        self.layout = lay
+
+    def _check(self, rc, allow=(OK,)):
+        if rc not in allow:
+            msg = self.lib.ricmrcc_last_error(self.h).decode()
+            raise RicMrccError(rc, msg)
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.ricmrcc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ setup
+    def set_stream(self, stream_ptr):
+        self._check(self.lib.ricmrcc_set_stream(self.h, stream_ptr))
+
+    def set_precision(self, precision):
+        self._check(self.lib.ricmrcc_set_precision(self.h, precision))
+
+    def set_integrals(self, hmat, B):
+        if hasattr(hmat, "is_cuda") and hmat.is_cuda:
+            self._check(self.lib.ricmrcc_set_integrals_dev(self.h, _ptr(hmat), _ptr(B)))
+        else:
+            hm, b = _host(hmat), _host(B)
+            self._check(self.lib.ricmrcc_set_integrals(self.h, _ptr(hm), _ptr(b)))
+
+    def set_rdms(self, g1, g2, g3, kind=RDM):
+        if hasattr(g1, "is_cuda") and g1.is_cuda:
+            self._check(self.lib.ricmrcc_set_rdms_dev(self.h, _ptr(g1), _ptr(g2), _ptr(g3), kind))
+        else:
+            a, b, c = _host(g1), _host(g2), _host(g3)
+            self._check(self.lib.ricmrcc_set_rdms(self.h, _ptr(a), _ptr(b), _ptr(c), kind))
+
+    def semicanonicalize(self):
+        n = sum(self.dims[:3])
+        U = np.zeros((n, n))
+        self._check(self.lib.ricmrcc_semicanonicalize(self.h, _ptr(U)))
+        return U
+
+    def reference(self):
+        n = sum(self.dims[:3])
+        e0 = ctypes.c_double()
+        F = np.zeros((n, n))
+        self._check(self.lib.ricmrcc_reference(self.h, ctypes.byref(e0), _ptr(F)))
+        return e0.value, F
+
+    # ------------------------------------------------------------- amplitudes
+    def pack(self, T):
+        """{class: array} -> (flat T1, flat T2) in the library layout."""
+        lay = self.layout
+        t1 = np.zeros(lay.t1_size)
+        t2 = np.zeros(lay.t2_size)
+        for i, nm in enumerate(T1_NAMES):
+            shp = tuple(lay.t1_shape[i])
+            t1[lay.t1_offset[i]:lay.t1_offset[i] + int(np.prod(shp))] = np.asarray(T[nm]).ravel()
+        for i, nm in enumerate(T2_NAMES):
+            shp = tuple(lay.t2_shape[i])
+            t2[lay.t2_offset[i]:lay.t2_offset[i] + int(np.prod(shp))] = np.asarray(T[nm]).ravel()
+        return t1, t2
+
+    def unpack(self, t1, t2):
+        lay = self.layout
+        out = {}
+        for i, nm in enumerate(T1_NAMES):
+            shp = tuple(lay.t1_shape[i])
+            out[nm] = np.asarray(t1[lay.t1_offset[i]:lay.t1_offset[i] + int(np.prod(shp))]).reshape(shp)
+        for i, nm in enumerate(T2_NAMES):
+            shp = tuple(lay.t2_shape[i])
+            out[nm] = np.asarray(t2[lay.t2_offset[i]:lay.t2_offset[i] + int(np.prod(shp))]).reshape(shp)
+        return out
+
+    def residual(self, T):
+        """Residual class blocks and energy for amplitudes T (dict or flat pair)."""
+        t1, t2 = self.pack(T) if isinstance(T, dict) else (_host(T[0]), _host(T[1]))
+        r1 = np.zeros(self.layout.t1_size)
+        r2 = np.zeros(self.layout.t2_size)
+        e = ctypes.c_double()
+        self._check(self.lib.ricmrcc_residual(self.h, _ptr(t1), _ptr(t2), _ptr(r1), _ptr(r2),
+                                              ctypes.byref(e)))
+        return self.unpack(r1, r2), e.value
+
+    def residual_dev(self, t1, t2, r1, r2, e_out=None):
+        """Device-pointer variant: torch CUDA tensors, results written in place."""
+        self._check(self.lib.ricmrcc_residual_dev(self.h, _ptr(t1), _ptr(t2), _ptr(r1), _ptr(r2),
+                                                  _ptr(e_out)))
+
+    def get_amplitudes(self):
+        t1 = np.zeros(self.layout.t1_size)
+        t2 = np.zeros(self.layout.t2_size)
+        self._check(self.lib.ricmrcc_get_amplitudes(self.h, _ptr(t1), _ptr(t2)))
+        return self.unpack(t1, t2)
+
+    def set_amplitudes(self, T):
+        t1, t2 = self.pack(T)
+        self._check(self.lib.ricmrcc_set_amplitudes(self.h, _ptr(t1), _ptr(t2)))
+
+    # ------------------------------------------------------------------ solve
+    @staticmethod
+    def default_opts(**kw):
+        o = Opts()
+        load_library().ricmrcc_opts_default(ctypes.byref(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def solve(self, s=0.5, **kw):
+        o = self.default_opts(s=s, **kw)
+        st = Stats()
+        e = ctypes.c_double()
+        rc = self.lib.ricmrcc_solve(self.h, ctypes.byref(o), ctypes.byref(e), ctypes.byref(st))
+        self._check(rc, allow=(OK, NOT_CONVERGED))
+        return e.value, st
+
+
+def header_symbols(header=None):
+    """Entry points declared in include/ricmrcc.h."""
+    import re
+    header = header or os.path.join(os.path.dirname(HERE), "include", "ricmrcc.h")
+    return re.findall(r"RICMRCC_API [\w\s\*]*?\b(ricmrcc_\w+)\(", open(header).read())

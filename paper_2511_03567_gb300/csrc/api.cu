@@ -1,0 +1,675 @@
+// C ABI of the GB300 RIC-MRCCSD library (see include/ricmrcc.h).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <chrono>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/ricmrcc.h"
+#include "internal.h"
+#include "kernels.h"
+#include "planner.h"
+
+#include "ric_terms.inc"
+
+namespace {
+
+struct DevBuf {
+  double* p = nullptr;
+  int64_t n = 0;
+};
+
+}  // namespace
+
+struct ricmrcc {
+  Dims d{};
+  std::string err;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t s = nullptr;  // internal work stream
+  cudaEvent_t ev = nullptr;
+  int precision = RICMRCC_FP64;
+
+  // device data
+  double *h = nullptr, *B = nullptr, *eri = nullptr, *F = nullptr, *eps = nullptr;
+  double *g1 = nullptr, *g2 = nullptr, *g3 = nullptr, *L2 = nullptr, *D2 = nullptr, *G = nullptr,
+         *E = nullptr, *L3 = nullptr, *D3 = nullptr;
+  double *T = nullptr, *X = nullptr, *Tn = nullptr, *Err = nullptr;
+  double *scal = nullptr;  // [0] E0, [1] Eacc, [2] maxdt, [3] one, [4] energy out
+  double *hist_v = nullptr, *hist_e = nullptr, *gram = nullptr, *coef = nullptr, *dots = nullptr;
+  int* dstatus = nullptr;
+  int64_t *pack1 = nullptr, *pack2 = nullptr, *pack2b = nullptr;
+  double *flat1 = nullptr, *flat2 = nullptr, *rflat1 = nullptr, *rflat2 = nullptr;
+  double* arena = nullptr;
+  double* host_scal = nullptr;  // pinned, 8 doubles
+  int* d_sweeps = nullptr;
+
+  int64_t n2g = 0, n1g = 0, ng = 0, t1_size = 0, t2_size = 0;
+  int64_t t1_off[3], t2_off[9];
+  int t1_shape[3][2], t2_shape[9][4];
+  int diis_cap = 8;
+
+  Program res_prog, cum_prog;
+  bool have_ints = false, have_rdms = false, planned = false;
+  double E0 = 0.0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(ricmrcc_t* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(h, RICMRCC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+int dalloc(ricmrcc_t* h, T** p, int64_t n) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, RICMRCC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  h->allocs.push_back((void*)*p);
+  cudaMemsetAsync(*p, 0, sizeof(T) * (size_t)n, h->s);
+  return RICMRCC_OK;
+}
+
+#define TRY(x)                     \
+  do {                             \
+    int rc_ = (x);                 \
+    if (rc_ != RICMRCC_OK) return rc_; \
+  } while (0)
+
+bool finite_host(const double* x, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!isfinite(x[i])) return false;
+  return true;
+}
+
+// Enter / leave: order the internal stream after the user's stream and back.
+int enter(ricmrcc_t* h) {
+  h->err.clear();
+  if (h->user_stream) {
+    CK(cudaEventRecord(h->ev, h->user_stream));
+    CK(cudaStreamWaitEvent(h->s, h->ev, 0));
+  }
+  return RICMRCC_OK;
+}
+int leave(ricmrcc_t* h) {
+  CK(cudaGetLastError());
+  if (h->user_stream) {
+    CK(cudaEventRecord(h->ev, h->s));
+    CK(cudaStreamWaitEvent(h->user_stream, h->ev, 0));
+  }
+  return RICMRCC_OK;
+}
+
+// Flat class layout -> index in the general tensors (Table 2 classes).
+void build_layout(ricmrcc_t* h, std::vector<int64_t>& p1, std::vector<int64_t>& p2,
+                  std::vector<int64_t>& p2b) {
+  const Dims& d = h->d;
+  const int o = d.o, a = d.a, v = d.v, np = d.np, nh = d.nh;
+  // particle-local offsets: active 0, virtual a; hole-local: core 0, active o
+  struct C1 { int hsz, hoff, psz, poff; };
+  const C1 c1[3] = {{o, 0, v, a}, {o, 0, a, 0}, {a, o, v, a}};  // IA IT TA
+  int64_t off = 0;
+  for (int c = 0; c < 3; ++c) {
+    h->t1_off[c] = off;
+    h->t1_shape[c][0] = c1[c].hsz;
+    h->t1_shape[c][1] = c1[c].psz;
+    for (int k = 0; k < c1[c].hsz; ++k)
+      for (int p = 0; p < c1[c].psz; ++p) p1.push_back((int64_t)(c1[c].poff + p) * nh + c1[c].hoff + k);
+    off += (int64_t)c1[c].hsz * c1[c].psz;
+  }
+  h->t1_size = off;
+  // doubles: k, l hole spaces; c, d particle spaces
+  struct C2 { int k, l, c, d; };  // 0 core, 1 active, 2 virtual
+  const C2 c2[9] = {{0, 0, 2, 2}, {0, 0, 1, 2}, {0, 0, 1, 1}, {0, 1, 2, 2}, {0, 1, 1, 2},
+                    {0, 1, 2, 1}, {0, 1, 1, 1}, {1, 1, 2, 2}, {1, 1, 1, 2}};
+  auto hsz = [&](int s) { return s == 0 ? o : a; };
+  auto hof = [&](int s) { return s == 0 ? 0 : o; };
+  auto psz = [&](int s) { return s == 1 ? a : v; };
+  auto pof = [&](int s) { return s == 1 ? 0 : a; };
+  off = 0;
+  for (int c = 0; c < 9; ++c) {
+    const C2& q = c2[c];
+    h->t2_off[c] = off;
+    h->t2_shape[c][0] = hsz(q.k);
+    h->t2_shape[c][1] = hsz(q.l);
+    h->t2_shape[c][2] = psz(q.c);
+    h->t2_shape[c][3] = psz(q.d);
+    for (int k = 0; k < hsz(q.k); ++k)
+      for (int l = 0; l < hsz(q.l); ++l)
+        for (int x = 0; x < psz(q.c); ++x)
+          for (int y = 0; y < psz(q.d); ++y) {
+            const int64_t K = hof(q.k) + k, Lh = hof(q.l) + l, Cp = pof(q.c) + x, Dp = pof(q.d) + y;
+            p2.push_back(((Cp * np + Dp) * nh + K) * nh + Lh);
+            p2b.push_back(((Dp * np + Cp) * nh + Lh) * nh + K);
+          }
+    off += (int64_t)hsz(q.k) * hsz(q.l) * psz(q.c) * psz(q.d);
+  }
+  h->t2_size = off;
+}
+
+int plan(ricmrcc_t* h) {
+  if (h->planned) return RICMRCC_OK;
+  const Dims& d = h->d;
+  const int64_t n = d.n, np = d.np, nh = d.nh, a = d.a;
+  TensorView tv[NTENSOR], ov[NOUT];
+  auto set = [](TensorView& t, double* base, std::initializer_list<int> dom,
+                std::initializer_list<int64_t> st) {
+    t.base = base;
+    t.nax = (int)dom.size();
+    int i = 0;
+    for (int x : dom) t.dom[i++] = x;
+    i = 0;
+    for (int64_t x : st) t.stride[i++] = x;
+  };
+  set(tv[TF], h->F, {DOM_G, DOM_G}, {n, 1});
+  // <pq|rs> = (pr|qs): eri[p][r][q][s]
+  set(tv[TV], h->eri, {DOM_G, DOM_G, DOM_G, DOM_G}, {n * n * n, n, n * n, 1});
+  set(tv[TT1], h->T + h->n2g, {DOM_P, DOM_H}, {nh, 1});
+  set(tv[TT2], h->T, {DOM_P, DOM_P, DOM_H, DOM_H}, {np * nh * nh, nh * nh, nh, 1});
+  set(tv[TG], h->G, {DOM_A, DOM_A}, {a, 1});
+  set(tv[TE], h->E, {DOM_A, DOM_A}, {a, 1});
+  set(tv[TD2], h->D2, {DOM_A, DOM_A, DOM_A, DOM_A}, {a * a * a, a * a, a, 1});
+  set(tv[TD3], h->D3, {DOM_A, DOM_A, DOM_A, DOM_A, DOM_A, DOM_A},
+      {a * a * a * a * a, a * a * a * a, a * a * a, a * a, a, 1});
+  set(ov[OR1], h->X + h->n2g, {DOM_P, DOM_H}, {nh, 1});
+  set(ov[OX2], h->X, {DOM_P, DOM_P, DOM_H, DOM_H}, {np * nh * nh, nh * nh, nh, 1});
+  set(ov[OE], h->scal + 1, {}, {});
+  set(ov[OL3], h->L3, {DOM_A, DOM_A, DOM_A, DOM_A, DOM_A, DOM_A},
+      {a * a * a * a * a, a * a * a * a, a * a * a, a * a, a, 1});
+  Planner pl(d, tv, ov, h->scal + 3);
+  for (const auto& t : kResidualTerms)
+    if (!pl.add_term(t, &h->res_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad residual term");
+  for (const auto& t : kEnergyTerms)
+    if (!pl.add_term(t, &h->res_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad energy term");
+  for (const auto& t : kCumulant3Terms)
+    if (!pl.add_term(t, &h->cum_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad cumulant term");
+  TRY(dalloc(h, &h->arena, pl.arena_size()));
+  pl.finalize(&h->res_prog, h->arena);
+  pl.finalize(&h->cum_prog, h->arena);
+  for (Program* p : {&h->res_prog, &h->cum_prog}) {
+    TRY(dalloc(h, &p->d_table, (int64_t)p->table.size()));
+    CK(cudaMemcpyAsync(p->d_table, p->table.data(), sizeof(int64_t) * p->table.size(),
+                       cudaMemcpyHostToDevice, h->s));
+  }
+  h->planned = true;
+  if (getenv("RICMRCC_VERBOSE"))
+    fprintf(stderr,
+            "ricmrcc plan: o=%d a=%d v=%d X=%d | residual+energy %zu terms -> %zu ops, %.3e flop | "
+            "cumulant %zu ops | arena %.1f MB | cse hits %lld | tables %.1f MB\n",
+            d.o, d.a, d.v, d.X, h->res_prog.n_terms, h->res_prog.ops.size(), h->res_prog.flops,
+            h->cum_prog.ops.size(), pl.arena_size() * 8.0 / 1e6, (long long)pl.cse_hits(),
+            (h->res_prog.table.size() + h->cum_prog.table.size()) * 8.0 / 1e6);
+  return RICMRCC_OK;
+}
+
+void run_program(ricmrcc_t* h, const Program& p) {
+  for (const auto& op : p.ops) launch_contract(op, p.d_table, h->s);
+}
+
+int rebuild_reference(ricmrcc_t* h) {
+  if (!(h->have_ints && h->have_rdms)) return RICMRCC_OK;
+  const Dims& d = h->d;
+  launch_fock(h->F, h->h, h->eri, h->g1, d, h->s);
+  launch_e0(h->scal + 0, h->h, h->F, h->eri, h->g1, h->L2, d, h->s);
+  // eps = diag(F)
+  CK(cudaMemcpy2DAsync(h->eps, sizeof(double), h->F, sizeof(double) * (d.n + 1), sizeof(double),
+                       d.n, cudaMemcpyDeviceToDevice, h->s));
+  CK(cudaMemcpyAsync(h->host_scal, h->scal, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  h->E0 = h->host_scal[0];
+  return RICMRCC_OK;
+}
+
+// (pq|rs) = sum_Q B[Q][pq] B[Q][rs] with the generic contraction kernel
+int build_eri(ricmrcc_t* h) {
+  const Dims& d = h->d;
+  const int64_t n2 = (int64_t)d.n * d.n;
+  CK(cudaMemsetAsync(h->eri, 0, sizeof(double) * n2 * n2, h->s));
+  Program p;
+  ContractOp op{};
+  op.A = h->B;
+  op.B = h->B;
+  op.C = h->eri;
+  op.L = 1;
+  op.M = n2;
+  op.N = n2;
+  op.K = d.X;
+  op.alpha = 1.0;
+  op.tab = 0;
+  // tables: AL BL CL | AM CM | BN CN | AK BK
+  std::vector<int64_t>& t = p.table;
+  t.push_back(0);
+  t.push_back(0);
+  t.push_back(0);
+  for (int64_t i = 0; i < n2; ++i) t.push_back(i);
+  for (int64_t i = 0; i < n2; ++i) t.push_back(i * n2);
+  for (int64_t i = 0; i < n2; ++i) t.push_back(i);
+  for (int64_t i = 0; i < n2; ++i) t.push_back(i);
+  for (int64_t q = 0; q < d.X; ++q) t.push_back(q * n2);
+  for (int64_t q = 0; q < d.X; ++q) t.push_back(q * n2);
+  op.kind = n2 >= 64 ? 0 : 1;
+  op.ksplit = 1;
+  op.kchunk = d.X;
+  int64_t* dt = nullptr;
+  CK(cudaMalloc(&dt, sizeof(int64_t) * t.size()));
+  CK(cudaMemcpyAsync(dt, t.data(), sizeof(int64_t) * t.size(), cudaMemcpyHostToDevice, h->s));
+  launch_contract(op, dt, h->s);
+  CK(cudaStreamSynchronize(h->s));
+  CK(cudaFree(dt));
+  return RICMRCC_OK;
+}
+
+int cumulants(ricmrcc_t* h, int kind) {
+  const int a = h->d.a;
+  if (a == 0) return RICMRCC_OK;
+  const int64_t a6 = (int64_t)a * a * a * a * a * a;
+  launch_cumulant2(h->L2, h->D2, h->G, h->E, h->g1, h->g2, a, kind == RICMRCC_CUMULANT, h->s);
+  CK(cudaMemcpyAsync(h->L3, h->g3, sizeof(double) * a6, cudaMemcpyDeviceToDevice, h->s));
+  if (kind == RICMRCC_RDM) {
+    TRY(plan(h));
+    run_program(h, h->cum_prog);
+  }
+  launch_direct3(h->D3, h->L3, a, h->s);
+  return RICMRCC_OK;
+}
+
+int residual_device(ricmrcc_t* h) {
+  // X, E accumulators and intermediates start from zero
+  CK(cudaMemsetAsync(h->X, 0, sizeof(double) * h->ng, h->s));
+  CK(cudaMemsetAsync(h->scal + 1, 0, sizeof(double), h->s));
+  run_program(h, h->res_prog);
+  return RICMRCC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+static int create_impl(ricmrcc_t* h, int n_core, int n_act, int n_virt, int n_aux);
+
+int ricmrcc_create(int n_core, int n_act, int n_virt, int n_aux, ricmrcc_t** out) {
+  if (!out) return RICMRCC_EINVAL;
+  *out = nullptr;
+  if (n_core < 0 || n_act < 0 || n_virt < 0 || n_aux < 1 || n_core + n_act + n_virt < 1)
+    return RICMRCC_EINVAL;
+  ricmrcc_t* h = new ricmrcc();
+  const int rc = create_impl(h, n_core, n_act, n_virt, n_aux);
+  if (rc != RICMRCC_OK) {
+    ricmrcc_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return RICMRCC_OK;
+}
+
+static int create_impl(ricmrcc_t* h, int n_core, int n_act, int n_virt, int n_aux) {
+  {
+  }
+  Dims& d = h->d;
+  d.o = n_core;
+  d.a = n_act;
+  d.v = n_virt;
+  d.X = n_aux;
+  d.n = n_core + n_act + n_virt;
+  d.np = n_act + n_virt;
+  d.nh = n_core + n_act;
+  CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
+  const int64_t n = d.n, a = d.a;
+  h->n2g = (int64_t)d.np * d.np * d.nh * d.nh;
+  h->n1g = (int64_t)d.np * d.nh;
+  h->ng = h->n2g + h->n1g;
+  TRY(dalloc(h, &h->h, n * n));
+  TRY(dalloc(h, &h->B, (int64_t)d.X * n * n));
+  TRY(dalloc(h, &h->eri, n * n * n * n));
+  TRY(dalloc(h, &h->F, n * n));
+  TRY(dalloc(h, &h->eps, n));
+  TRY(dalloc(h, &h->g1, a * a));
+  TRY(dalloc(h, &h->g2, a * a * a * a));
+  TRY(dalloc(h, &h->g3, a * a * a * a * a * a));
+  TRY(dalloc(h, &h->L2, a * a * a * a));
+  TRY(dalloc(h, &h->D2, a * a * a * a));
+  TRY(dalloc(h, &h->G, a * a));
+  TRY(dalloc(h, &h->E, a * a));
+  TRY(dalloc(h, &h->L3, a * a * a * a * a * a));
+  TRY(dalloc(h, &h->D3, a * a * a * a * a * a));
+  TRY(dalloc(h, &h->T, h->ng));
+  TRY(dalloc(h, &h->X, h->ng));
+  TRY(dalloc(h, &h->Tn, h->ng));
+  TRY(dalloc(h, &h->Err, h->ng));
+  TRY(dalloc(h, &h->scal, 8));
+  TRY(dalloc(h, &h->gram, 16 * 16));
+  TRY(dalloc(h, &h->coef, 16));
+  TRY(dalloc(h, &h->dots, 16));
+  TRY(dalloc(h, &h->dstatus, 4));
+  TRY(dalloc(h, &h->d_sweeps, 4));
+  CK(cudaMallocHost(&h->host_scal, 8 * sizeof(double)));
+  std::vector<int64_t> p1, p2, p2b;
+  build_layout(h, p1, p2, p2b);
+  TRY(dalloc(h, &h->pack1, (int64_t)p1.size()));
+  TRY(dalloc(h, &h->pack2, (int64_t)p2.size()));
+  TRY(dalloc(h, &h->pack2b, (int64_t)p2b.size()));
+  CK(cudaMemcpyAsync(h->pack1, p1.data(), sizeof(int64_t) * p1.size(), cudaMemcpyHostToDevice, h->s));
+  CK(cudaMemcpyAsync(h->pack2, p2.data(), sizeof(int64_t) * p2.size(), cudaMemcpyHostToDevice, h->s));
+  CK(cudaMemcpyAsync(h->pack2b, p2b.data(), sizeof(int64_t) * p2b.size(), cudaMemcpyHostToDevice, h->s));
+  TRY(dalloc(h, &h->flat1, h->t1_size));
+  TRY(dalloc(h, &h->flat2, h->t2_size));
+  TRY(dalloc(h, &h->rflat1, h->t1_size));
+  TRY(dalloc(h, &h->rflat2, h->t2_size));
+  launch_fill(h->scal + 3, 1.0, 1, h->s);
+  TRY(plan(h));
+  CK(cudaStreamSynchronize(h->s));
+  return RICMRCC_OK;
+}
+
+void ricmrcc_destroy(ricmrcc_t* h) {
+  if (!h) return;
+  if (h->s) cudaStreamSynchronize(h->s);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->host_scal) cudaFreeHost(h->host_scal);
+  if (h->hist_v) cudaFree(h->hist_v);
+  if (h->hist_e) cudaFree(h->hist_e);
+  if (h->ev) cudaEventDestroy(h->ev);
+  if (h->s) cudaStreamDestroy(h->s);
+  delete h;
+}
+
+const char* ricmrcc_last_error(const ricmrcc_t* h) { return h ? h->err.c_str() : "null handle"; }
+
+int ricmrcc_set_stream(ricmrcc_t* h, void* stream) {
+  if (!h) return RICMRCC_EINVAL;
+  h->user_stream = (cudaStream_t)stream;
+  return RICMRCC_OK;
+}
+
+int ricmrcc_set_precision(ricmrcc_t* h, int precision) {
+  if (!h) return RICMRCC_EINVAL;
+  if (precision != RICMRCC_FP64 && precision != RICMRCC_MIXED)
+    return fail(h, RICMRCC_EINVAL, "precision must be RICMRCC_FP64 or RICMRCC_MIXED");
+  if (precision == RICMRCC_MIXED) return fail(h, RICMRCC_ENOTSUP, "mixed precision not built");
+  h->precision = precision;
+  return RICMRCC_OK;
+}
+
+static int set_integrals_impl(ricmrcc_t* h, const double* hm, const double* B, bool dev) {
+  if (!h || !hm || !B) return fail(h, RICMRCC_EINVAL, "null pointer");
+  const Dims& d = h->d;
+  const int64_t n2 = (int64_t)d.n * d.n;
+  if (!dev && (!finite_host(hm, n2) || !finite_host(B, n2 * d.X)))
+    return fail(h, RICMRCC_EINVAL, "non-finite integrals");
+  TRY(enter(h));
+  const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CK(cudaMemcpyAsync(h->h, hm, sizeof(double) * n2, k, h->s));
+  CK(cudaMemcpyAsync(h->B, B, sizeof(double) * n2 * d.X, k, h->s));
+  TRY(build_eri(h));
+  h->have_ints = true;
+  TRY(rebuild_reference(h));
+  return leave(h);
+}
+
+int ricmrcc_set_integrals(ricmrcc_t* h, const double* hm, const double* B) {
+  return set_integrals_impl(h, hm, B, false);
+}
+int ricmrcc_set_integrals_dev(ricmrcc_t* h, const double* hm, const double* B) {
+  return set_integrals_impl(h, hm, B, true);
+}
+
+static int set_rdms_impl(ricmrcc_t* h, const double* g1, const double* g2, const double* g3,
+                         int kind, bool dev) {
+  if (!h) return RICMRCC_EINVAL;
+  if (kind != RICMRCC_RDM && kind != RICMRCC_CUMULANT) return fail(h, RICMRCC_EINVAL, "bad kind");
+  const int64_t a = h->d.a;
+  if (a > 0 && (!g1 || !g2 || !g3)) return fail(h, RICMRCC_EINVAL, "null pointer");
+  if (!dev && a > 0 &&
+      (!finite_host(g1, a * a) || !finite_host(g2, a * a * a * a) || !finite_host(g3, a * a * a * a * a * a)))
+    return fail(h, RICMRCC_EINVAL, "non-finite RDMs");
+  TRY(enter(h));
+  const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (a > 0) {
+    CK(cudaMemcpyAsync(h->g1, g1, sizeof(double) * a * a, k, h->s));
+    CK(cudaMemcpyAsync(h->g2, g2, sizeof(double) * a * a * a * a, k, h->s));
+    CK(cudaMemcpyAsync(h->g3, g3, sizeof(double) * a * a * a * a * a * a, k, h->s));
+  }
+  TRY(cumulants(h, kind));
+  h->have_rdms = true;
+  CK(cudaMemsetAsync(h->T, 0, sizeof(double) * h->ng, h->s));
+  TRY(rebuild_reference(h));
+  return leave(h);
+}
+
+int ricmrcc_set_rdms(ricmrcc_t* h, const double* g1, const double* g2, const double* g3, int kind) {
+  return set_rdms_impl(h, g1, g2, g3, kind, false);
+}
+int ricmrcc_set_rdms_dev(ricmrcc_t* h, const double* g1, const double* g2, const double* g3,
+                         int kind) {
+  return set_rdms_impl(h, g1, g2, g3, kind, true);
+}
+
+int ricmrcc_amplitude_layout(const ricmrcc_t* h, ricmrcc_layout* out) {
+  if (!h || !out) return RICMRCC_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->t1_size = h->t1_size;
+  out->t2_size = h->t2_size;
+  for (int c = 0; c < 3; ++c) {
+    out->t1_offset[c] = h->t1_off[c];
+    out->t1_shape[c][0] = h->t1_shape[c][0];
+    out->t1_shape[c][1] = h->t1_shape[c][1];
+  }
+  for (int c = 0; c < 9; ++c) {
+    out->t2_offset[c] = h->t2_off[c];
+    for (int j = 0; j < 4; ++j) out->t2_shape[c][j] = h->t2_shape[c][j];
+  }
+  return RICMRCC_OK;
+}
+
+int ricmrcc_reference(ricmrcc_t* h, double* E0, double* F) {
+  if (!h) return RICMRCC_EINVAL;
+  if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
+  TRY(enter(h));
+  if (E0) *E0 = h->E0;
+  if (F) {
+    CK(cudaMemcpyAsync(F, h->F, sizeof(double) * h->d.n * h->d.n, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+  }
+  return leave(h);
+}
+
+static void scatter_amplitudes(ricmrcc_t* h, const double* f1, const double* f2) {
+  cudaMemsetAsync(h->T, 0, sizeof(double) * h->ng, h->s);
+  launch_scatter(h->T + h->n2g, f1, h->pack1, nullptr, h->t1_size, h->s);
+  launch_scatter(h->T, f2, h->pack2, h->pack2b, h->t2_size, h->s);
+}
+
+static int residual_impl(ricmrcc_t* h, const double* T1, const double* T2, double* R1, double* R2,
+                         double* E_out, bool dev) {
+  if (!h) return RICMRCC_EINVAL;
+  if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
+  if (!T1 || !T2 || !R1 || !R2) return fail(h, RICMRCC_EINVAL, "null pointer");
+  if (!dev && (!finite_host(T1, h->t1_size) || !finite_host(T2, h->t2_size)))
+    return fail(h, RICMRCC_EINVAL, "non-finite amplitudes");
+  TRY(enter(h));
+  const double *f1 = T1, *f2 = T2;
+  if (!dev) {
+    CK(cudaMemcpyAsync(h->flat1, T1, sizeof(double) * h->t1_size, cudaMemcpyHostToDevice, h->s));
+    CK(cudaMemcpyAsync(h->flat2, T2, sizeof(double) * h->t2_size, cudaMemcpyHostToDevice, h->s));
+    f1 = h->flat1;
+    f2 = h->flat2;
+  }
+  scatter_amplitudes(h, f1, f2);
+  TRY(residual_device(h));
+  double* r1 = dev ? R1 : h->rflat1;
+  double* r2 = dev ? R2 : h->rflat2;
+  launch_gather(r1, h->X + h->n2g, h->pack1, nullptr, h->t1_size, h->s);
+  // R2 = X + X^{pair swap}
+  launch_gather(r2, h->X, h->pack2, h->pack2b, h->t2_size, h->s);
+  if (!dev) {
+    CK(cudaMemcpyAsync(R1, r1, sizeof(double) * h->t1_size, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(R2, r2, sizeof(double) * h->t2_size, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaMemcpyAsync(h->host_scal + 1, h->scal + 1, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    if (E_out) *E_out = h->E0 + h->host_scal[1];
+  } else if (E_out) {
+    launch_energy_out(E_out, h->scal + 1, h->E0, h->s);
+  }
+  return leave(h);
+}
+
+int ricmrcc_residual(ricmrcc_t* h, const double* T1, const double* T2, double* R1, double* R2,
+                     double* E_out) {
+  return residual_impl(h, T1, T2, R1, R2, E_out, false);
+}
+int ricmrcc_residual_dev(ricmrcc_t* h, const double* T1, const double* T2, double* R1, double* R2,
+                         double* E_out) {
+  return residual_impl(h, T1, T2, R1, R2, E_out, true);
+}
+
+int ricmrcc_opts_default(ricmrcc_opts* o) {
+  if (!o) return RICMRCC_EINVAL;
+  o->s = 0.5;
+  o->max_iter = 100;
+  o->e_tol = 1e-10;
+  o->t_tol = 1e-9;
+  o->diis_size = 8;
+  o->diis_start = 3;
+  o->precision = RICMRCC_FP64;
+  o->refine_tol = 1e-5;
+  return RICMRCC_OK;
+}
+
+int ricmrcc_solve(ricmrcc_t* h, const ricmrcc_opts* opts, double* E_out, ricmrcc_stats* stats) {
+  if (!h) return RICMRCC_EINVAL;
+  ricmrcc_opts o;
+  ricmrcc_opts_default(&o);
+  if (opts) o = *opts;
+  if (!(o.s >= 0.0) || !isfinite(o.s) || o.max_iter < 1 || o.diis_size < 0 || o.diis_size > 16)
+    return fail(h, RICMRCC_EINVAL, "bad options (s >= 0, max_iter >= 1, 0 <= diis_size <= 16)");
+  if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
+  if (o.precision == RICMRCC_MIXED) return fail(h, RICMRCC_ENOTSUP, "mixed precision not built");
+  TRY(enter(h));
+  const auto t0 = std::chrono::steady_clock::now();
+  const int cap = o.diis_size > 0 ? o.diis_size : 1;
+  if (h->diis_cap != cap || !h->hist_v) {
+    if (h->hist_v) cudaFree(h->hist_v);
+    if (h->hist_e) cudaFree(h->hist_e);
+    h->hist_v = h->hist_e = nullptr;
+    CK(cudaMalloc(&h->hist_v, sizeof(double) * h->ng * cap));
+    CK(cudaMalloc(&h->hist_e, sizeof(double) * h->ng * cap));
+    h->diis_cap = cap;
+  }
+  double e_old = 0.0, E = 0.0, maxdt = 0.0;
+  bool have_old = false, converged = false, diverged = false;
+  int it = 0, nvec = 0;
+  std::vector<double> gram(16 * 16, 0.0);
+  for (it = 1; it <= o.max_iter; ++it) {
+    TRY(residual_device(h));
+    CK(cudaMemsetAsync(h->scal + 2, 0, sizeof(double), h->s));
+    launch_update(h->T, h->X, h->Tn, h->Err, h->eps, h->d, o.s, h->scal + 2, h->s);
+    CK(cudaMemcpyAsync(h->host_scal, h->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    E = h->E0 + h->host_scal[1];
+    maxdt = h->host_scal[2];
+    if (!isfinite(E) || !isfinite(maxdt) || maxdt > 1e100) {
+      diverged = true;
+      break;
+    }
+    if (have_old && fabs(E - e_old) < o.e_tol && maxdt < o.t_tol) {
+      converged = true;
+      break;
+    }
+    e_old = E;
+    have_old = true;
+    if (o.diis_size == 0) {
+      CK(cudaMemcpyAsync(h->T, h->Tn, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
+      continue;
+    }
+    // DIIS history (ring buffer; the extrapolation does not depend on order)
+    const int slot = nvec % cap;
+    CK(cudaMemcpyAsync(h->hist_v + (int64_t)slot * h->ng, h->Tn, sizeof(double) * h->ng,
+                       cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemcpyAsync(h->hist_e + (int64_t)slot * h->ng, h->Err, sizeof(double) * h->ng,
+                       cudaMemcpyDeviceToDevice, h->s));
+    ++nvec;
+    const int m = nvec < cap ? nvec : cap;
+    CK(cudaMemsetAsync(h->dots, 0, sizeof(double) * 16, h->s));
+    launch_dots(h->dots, h->Err, h->hist_e, h->ng, m, h->ng, h->s);
+    // place the new row/column of the Gram matrix
+    std::vector<double> dv(16, 0.0);
+    CK(cudaMemcpyAsync(dv.data(), h->dots, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    for (int j = 0; j < m; ++j) {
+      gram[slot * 16 + j] = dv[j];
+      gram[j * 16 + slot] = dv[j];
+    }
+    if (it >= o.diis_start && m >= 2) {
+      CK(cudaMemcpyAsync(h->gram, gram.data(), sizeof(double) * 256, cudaMemcpyHostToDevice, h->s));
+      launch_diis_solve(h->gram, h->coef, m, h->dstatus, h->s);
+      launch_extrapolate(h->T, h->hist_v, h->coef, h->dstatus, m, slot, h->ng, h->ng, h->s);
+    } else {
+      CK(cudaMemcpyAsync(h->T, h->Tn, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
+    }
+  }
+  if (it > o.max_iter) it = o.max_iter;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (E_out) *E_out = E;
+  if (stats) {
+    stats->iterations = it;
+    stats->converged = converged ? 1 : 0;
+    stats->fp64_iterations = it;
+    stats->mixed_iterations = 0;
+    stats->energy = E;
+    stats->e0 = h->E0;
+    stats->max_dt = maxdt;
+    stats->seconds = secs;
+  }
+  TRY(leave(h));
+  if (diverged) return fail(h, RICMRCC_DIVERGED, "non-finite energy or amplitude change");
+  if (!converged) return fail(h, RICMRCC_NOT_CONVERGED, "max_iter reached");
+  return RICMRCC_OK;
+}
+
+int ricmrcc_get_amplitudes(ricmrcc_t* h, double* T1, double* T2) {
+  if (!h || !T1 || !T2) return fail(h, RICMRCC_EINVAL, "null pointer");
+  TRY(enter(h));
+  launch_gather(h->rflat1, h->T + h->n2g, h->pack1, nullptr, h->t1_size, h->s);
+  launch_gather(h->rflat2, h->T, h->pack2, nullptr, h->t2_size, h->s);
+  CK(cudaMemcpyAsync(T1, h->rflat1, sizeof(double) * h->t1_size, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaMemcpyAsync(T2, h->rflat2, sizeof(double) * h->t2_size, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  return leave(h);
+}
+
+int ricmrcc_set_amplitudes(ricmrcc_t* h, const double* T1, const double* T2) {
+  if (!h || !T1 || !T2) return fail(h, RICMRCC_EINVAL, "null pointer");
+  if (!finite_host(T1, h->t1_size) || !finite_host(T2, h->t2_size))
+    return fail(h, RICMRCC_EINVAL, "non-finite amplitudes");
+  TRY(enter(h));
+  CK(cudaMemcpyAsync(h->flat1, T1, sizeof(double) * h->t1_size, cudaMemcpyHostToDevice, h->s));
+  CK(cudaMemcpyAsync(h->flat2, T2, sizeof(double) * h->t2_size, cudaMemcpyHostToDevice, h->s));
+  scatter_amplitudes(h, h->flat1, h->flat2);
+  CK(cudaStreamSynchronize(h->s));
+  return leave(h);
+}
+
+int ricmrcc_semicanonicalize(ricmrcc_t* h, double* U_out) {
+  if (!h) return RICMRCC_EINVAL;
+  return fail(h, RICMRCC_ENOTSUP, "semicanonicalize: not built yet");
+}
+
+}  // extern "C"

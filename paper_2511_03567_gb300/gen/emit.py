@@ -1,0 +1,107 @@
+"""Write the spin-free term tables as a C include (build-time tool).
+
+Run `python -m paper_2511_03567_gb300.gen.emit` to regenerate
+`paper_2511_03567_gb300/csrc/ric_terms.inc`.  The tables depend only on the
+method (not on problem sizes); the runtime planner turns them into binary
+contractions for the actual dimensions.
+"""
+from __future__ import annotations
+
+import os
+import sys
+import time
+
+from . import algebra as al
+from . import spinfree as sf
+
+TENSOR_ID = {"F": 0, "V": 1, "T1": 2, "T2": 3, "G": 4, "E": 5, "D2": 6, "D3": 7}
+OUT_ID = {"R1": 0, "X2": 1, "E": 2, "L3": 3}
+
+
+# index domain of every tensor axis and of every output (space masks)
+DOMAIN = {
+    "F": (al.GEN, al.GEN), "V": (al.GEN,) * 4, "T1": (al.PART, al.HOLE),
+    "T2": (al.PART, al.PART, al.HOLE, al.HOLE), "G": (al.ACT,) * 2, "E": (al.ACT,) * 2,
+    "D2": (al.ACT,) * 4, "D3": (al.ACT,) * 6,
+    "R1": (al.PART, al.HOLE), "X2": (al.PART, al.PART, al.HOLE, al.HOLE), "E": (),
+    "L3": (al.ACT,) * 6,
+}
+
+
+def restrict(terms):
+    """Intersect every index mask with the domains of the axes it sits on;
+    drop terms left with an empty index or with an amplitude block that is
+    not an amplitude (all-active singles / doubles)."""
+    out = []
+    for t in terms:
+        sp = dict(t.space)
+        for x, dom in zip(t.out_idx, DOMAIN[t.out]):
+            sp[x] &= dom
+        for nm, ix in t.factors:
+            for x, dom in zip(ix, DOMAIN[nm]):
+                sp[x] &= dom
+        if any(m == 0 for m in sp.values()):
+            continue
+        bad = False
+        for nm, ix in t.factors:
+            if nm in ("T1", "T2") and all(sp[x] == al.ACT for x in ix):
+                bad = True
+        if bad:
+            continue
+        out.append(sf.SFTerm(t.coef, t.factors, t.out, t.out_idx, tuple(sorted(sp.items()))))
+    return out
+
+
+def _term_c(t):
+    sp = dict(t.space)
+    labels = {}
+    for x in list(t.out_idx) + [x for _, ix in t.factors for x in ix]:
+        if x not in labels:
+            labels[x] = len(labels)
+    masks = [0] * len(labels)
+    for x, i in labels.items():
+        masks[i] = sp[x]
+    facs = []
+    for nm, ix in t.factors:
+        idx = [labels[x] for x in ix] + [0] * (6 - len(ix))
+        facs.append("{%d,%d,{%s}}" % (TENSOR_ID[nm], len(ix), ",".join(map(str, idx))))
+    while len(facs) < 7:
+        facs.append("{0,0,{0,0,0,0,0,0}}")
+    outl = [labels[x] for x in t.out_idx] + [0] * (6 - len(t.out_idx))
+    masks += [0] * (16 - len(masks))
+    return "{%.17g,%d,%d,{%s},%d,%d,{%s},{%s}}" % (
+        float(t.coef), OUT_ID[t.out], len(t.out_idx), ",".join(map(str, outl)),
+        len(t.factors), len(labels), ",".join(map(str, masks)), ",".join(facs))
+
+
+def write(path):
+    t0 = time.time()
+    res, en = sf.derive()
+    res = restrict(res)
+    en = restrict(en)
+    cum = restrict(sf.cumulant3_terms())
+    for t in res + en + cum:
+        nl = len({x for _, ix in t.factors for x in ix} | set(t.out_idx))
+        assert nl <= 16 and len(t.factors) <= 7
+    lines = [
+        "// Generated by paper_2511_03567_gb300/gen/emit.py -- do not edit.",
+        "// Spin-free RIC-MRCCSD terms (Sec. 2.2-2.3): coef * prod(factors) -> out[out_idx].",
+        "// tensor ids: F=0 V=1 T1=2 T2=3 G=4 E=5 D2=6 D3=7; outputs: R1=0 X2=1 E=2 L3=3",
+        "// space masks: core=1 active=2 virtual=4 (hole=3 particle=6 general=7)",
+        "static const RicTermDesc kResidualTerms[] = {",
+    ]
+    lines += ["  " + _term_c(t) + "," for t in res]
+    lines += ["};", "static const RicTermDesc kEnergyTerms[] = {"]
+    lines += ["  " + _term_c(t) + "," for t in en]
+    lines += ["};", "static const RicTermDesc kCumulant3Terms[] = {"]
+    lines += ["  " + _term_c(t) + "," for t in cum]
+    lines += ["};", ""]
+    with open(path, "w") as f:
+        f.write("\n".join(lines))
+    print(f"wrote {path}: {len(res)} residual, {len(en)} energy, {len(cum)} cumulant terms "
+          f"in {time.time() - t0:.1f}s", file=sys.stderr)
+
+
+if __name__ == "__main__":
+    here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    write(os.path.join(here, "csrc", "ric_terms.inc"))
