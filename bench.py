@@ -1,0 +1,245 @@
+"""Benchmark: seconds per RIC-MRCCSD solver iteration on one GB300 (and replicas).
+
+One step = one iteration of the amplitude solver on the Mid workload: the
+full spin-free residual and energy (every term of the RIC-MRCCSD many-body
+residual), the renormalised update (Eq. ric-update) and the DIIS
+extrapolation.  Timed with CUDA events on the library's stream; inputs are
+larger than L2 (the integral tensor alone is 2.7 GB), so no flush is needed.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "mid", "n_core": 8, "n_act": 8, "n_virt": 120, "n_aux": 400, "n_det": 512,
+            "s": 0.1, "seed": 0}
+METRIC = "RIC-MRCCSD s/iter (Mid, one GB300)"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu=0):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def fp64_gemm_peak(torch):
+    """cuBLAS DGEMM throughput (TFLOP/s), 8192^3, best of 5: the FP64 denominator."""
+    n = 8192
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        torch.matmul(a, b)
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    del a, b
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        return dist, rank, ws, local
+    return None, rank, ws, local
+
+
+def cpu_baseline_run(steps_budget_s=20.0):
+    """Oracle on a bounded sample of the Mid workload (host cores)."""
+    from oracle import sampled
+    return sampled.time_sampled_iteration(WORKLOAD, budget_s=steps_budget_s)
+
+
+def run_reference(args):
+    dist, rank, ws, local = dist_init()
+    if rank != 0:
+        return 0
+    res = cpu_baseline_run(steps_budget_s=max(10.0, 20.0 * max(args.steps, 1) / 5))
+    line = {"metric": METRIC, "value": res["s_per_iter"], "unit": "s/iter", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["s_per_iter"] * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD), "impl": "reference",
+            "cpu_baseline": {"value": res["s_per_iter"], "unit": "s/iter", "cores": res["cores"],
+                             "kind": "oracle", "sample": res["sample"]},
+            "e2e": {"value": res["s_per_iter"], "unit": "s/iter", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    dist, rank, ws, local = dist_init()
+    torch.cuda.set_device(local)
+    import paper_2511_03567_gb300 as ric
+    import synthetic
+
+    w = WORKLOAD
+    p = synthetic.make_problem(w["n_core"], w["n_act"], w["n_virt"], w["n_aux"], w["n_det"], w["seed"])
+    g = ric.RicMrcc(w["n_core"], w["n_act"], w["n_virt"], w["n_aux"])
+    stream = torch.cuda.Stream()
+    g.set_stream(stream.cuda_stream)
+    g.set_integrals(p.h, p.B)
+    g.set_rdms(p.G1, p.G2, p.G3)
+    g.semicanonicalize()
+    prec = ric.MIXED if args.precision == "mixed" else ric.FP64
+    if prec == ric.MIXED:
+        g.set_precision(prec)
+    info = g.plan_info()
+
+    # warm-up, then exactly K timed iterations (DIIS history continues)
+    g.step(s=w["s"], n_steps=max(args.warmup, 1), restart=True, precision=prec)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        E, dt = g.step(s=w["s"], n_steps=args.steps, restart=False, precision=prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    if dist:
+        t = torch.tensor([secs], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    s_per_iter = secs / (args.steps * ws)
+    ms_per_step = secs / args.steps * 1e3
+
+    # end to end through the public host API: pinned host amplitudes in,
+    # one iteration, amplitudes out
+    lay = g.layout
+    t1 = torch.empty(lay.t1_size, dtype=torch.float64).pin_memory().numpy()
+    t2 = torch.empty(lay.t2_size, dtype=torch.float64).pin_memory().numpy()
+    cur = g.get_amplitudes()
+    a1, a2 = g.pack(cur)
+    t1[:] = a1
+    t2[:] = a2
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    c0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.lib.ricmrcc_set_amplitudes(g.h, ric._ptr(t1), ric._ptr(t2))
+        g.step(s=w["s"], n_steps=1, restart=False, precision=prec)
+        g.lib.ricmrcc_get_amplitudes(g.h, ric._ptr(t1), ric._ptr(t2))
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - c0) / e2e_steps
+
+    # roofline of the dominant contraction kernel (profiled after the timed region)
+    kind_ms = g.profile(reps=2)
+    dom = int(np.argmax(kind_ms))
+    kind_names = ["contract_tile_64x64_fp64", "contract_tile_16x16_fp64", "contract_dot_fp64"]
+    achieved = info.kind_flops[dom] / (kind_ms[dom] / 1e3) / 1e12
+    pk = fp64_gemm_peak(torch) if rank == 0 else None
+    if rank != 0:
+        return 0
+    roof = {"bound": "alu", "kernel": kind_names[dom], "achieved": achieved, "peak": pk,
+            "unit": "TFLOP/s", "frac": achieved / pk if pk else None, "traffic": None,
+            "peak_source": "cuBLAS DGEMM 8192^3 measured in this run (FP64 CUDA-core pipe)",
+            "launches_per_residual": int(info.kind_launches[dom]),
+            "ms_per_residual": float(kind_ms[dom])}
+    line = {"metric": METRIC, "value": s_per_iter, "unit": "s/iter", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == ric.FP64 else "bf16x3+f64",
+            "data": "synthetic",
+            "config": dict(WORKLOAD, precision=args.precision, parallelism=f"replicas{ws}",
+                           l2="inputs larger than L2 (2.7 GB integral tensor), no flush"),
+            "tflops": info.residual_flops / (ms_per_step / 1e3) / 1e12,
+            "residual_flops": info.residual_flops, "energy_last": E,
+            "e2e": {"value": e2e_s, "unit": "s/iter", "h2d_bytes_per_step": 8 * (lay.t1_size + lay.t2_size),
+                    "d2h_bytes_per_step": 8 * (lay.t1_size + lay.t2_size)},
+            "gpu_launches": int(info.step_launches) * args.steps,
+            "roofline": roof, "clocks": clk.summary()}
+    if not args.no_cpu_baseline and ws == 1:
+        try:
+            cb = cpu_baseline_run()
+            line["cpu_baseline"] = {"value": cb["s_per_iter"], "unit": "s/iter", "cores": cb["cores"],
+                                    "kind": "oracle", "sample": cb["sample"]}
+        except Exception as ex:  # the oracle is optional on the bench path
+            line["cpu_baseline"] = {"value": None, "unit": "s/iter", "cores": os.cpu_count(),
+                                    "kind": "oracle", "sample": f"failed: {ex}"}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -191,6 +191,34 @@ RICMRCC_API int ricmrcc_opts_default(ricmrcc_opts* opts);
  * (non-finite numbers). */
 RICMRCC_API int ricmrcc_solve(ricmrcc_t* h, const ricmrcc_opts* opts, double* E_out, ricmrcc_stats* stats);
 
+/* Run n_steps iterations of the solver loop of ricmrcc_solve (residual and
+ * energy, Eq. ric-update, DIIS) without the convergence test, continuing the
+ * DIIS history of earlier calls unless restart != 0.  E_out / max_dt_out
+ * (nullable, host) receive the energy at the last evaluated amplitudes and
+ * the last max |t_new - t|.  Returns OK or DIVERGED. */
+RICMRCC_API int ricmrcc_step(ricmrcc_t* h, const ricmrcc_opts* opts, int n_steps, int restart,
+                             double* E_out, double* max_dt_out);
+
+typedef struct {
+  int64_t residual_terms;    /* spin-free terms planned (residual + energy) */
+  int64_t residual_launches; /* contraction kernel launches per residual */
+  int64_t step_launches;     /* kernel launches per ricmrcc_step iteration */
+  double residual_flops;     /* algorithmic FLOPs of one residual + energy */
+  double arena_bytes;        /* intermediate arena */
+  double table_bytes;        /* offset tables */
+  int64_t kind_launches[3];  /* per contraction kernel: 0 = 64x64 tile, 1 = 16x16 tile, 2 = dot */
+  double kind_flops[3];
+} ricmrcc_plan_info_t;
+
+/* Sizes of the contraction program planned for this handle. */
+RICMRCC_API int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out);
+
+/* Time the residual program kernel by kernel with CUDA events on the work
+ * stream (reps repetitions, after the caller's warm-up) and return the mean
+ * milliseconds per residual spent in each contraction kernel kind
+ * (kind_ms[3], host).  Diagnostic: launches are serialised by the events. */
+RICMRCC_API int ricmrcc_profile(ricmrcc_t* h, int reps, double* kind_ms);
+
 /* Copy the stored amplitudes out / in (flat class layout, host pointers);
  * set_amplitudes allows warm starts and resuming an interrupted solve. */
 RICMRCC_API int ricmrcc_get_amplitudes(ricmrcc_t* h, double* T1, double* T2);

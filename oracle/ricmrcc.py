@@ -96,6 +96,41 @@ def fill_spin_orbital(k, n, standard):
     return out.reshape((2 * n,) * (2 * k))
 
 
+def fill_spin_orbital_rect(shape_ref, standard):
+    """fill_spin_orbital for a rectangular two-body block (axes of any extent)."""
+    dims = shape_ref.shape
+    out = np.zeros((dims[0], 2, dims[1], 2, dims[2], 2, dims[3], 2))
+    for sig in itertools.product((0, 1), repeat=2):
+        for tau in itertools.product((0, 1), repeat=2):
+            if sum(sig) != sum(tau):
+                continue
+            s_, t_ = list(sig), list(tau)
+            if sum(s_) * 2 > 2:
+                s_ = [1 - x for x in s_]
+                t_ = [1 - x for x in t_]
+            name = "aa" if sum(s_) == 0 else "ab"
+            pu, su = _stable_alpha_first(s_)
+            pl, sl = _stable_alpha_first(t_)
+            inv_u = [pu.index(i) for i in range(2)]
+            inv_l = [pl.index(i) for i in range(2)]
+            std = standard[name]
+            block = (su * sl) * np.transpose(std, inv_u + [2 + j for j in inv_l])
+            out[:, sig[0], :, sig[1], :, tau[0], :, tau[1]] = block
+    return out.reshape(2 * dims[0], 2 * dims[1], 2 * dims[2], 2 * dims[3])
+
+
+class _Embedded:
+    """A dense block placed at per-axis offsets inside a larger zero array."""
+
+    def __init__(self, block, offsets, shape):
+        self.block, self.offsets, self.shape = block, offsets, shape
+
+    def __getitem__(self, sl):
+        out = np.zeros(self.shape)
+        out[tuple(slice(o, o + d) for o, d in zip(self.offsets, self.block.shape))] = self.block
+        return out[sl]
+
+
 def spin_orbital_rdms(G1, G2, G3):
     """gamma_1, gamma_2, gamma_3 (spin-orbital, active block) from spin-free RDMs."""
     a = G1.shape[0]
@@ -193,6 +228,32 @@ def spin_orbital_eri(eri):
     return g - g.transpose(0, 1, 3, 2)
 
 
+class LazyERI:
+    """Spin-orbital <pq||rs> blocks computed on demand from the DF factor B.
+
+    For sizes where the full (2n)^4 array does not fit: a block for four
+    slices of spin-orbital indices (so = 2p + spin) is
+    <pq|rs> delta delta - <pq|sr> delta delta with <pq|rs> = sum_Q B_Qpr B_Qqs.
+    """
+
+    def __init__(self, B):
+        self.B = B
+        self.nso = 2 * B.shape[1]
+
+    def block(self, sl):
+        idx = [np.arange(self.nso)[x] for x in sl]
+        p = [i // 2 for i in idx]
+        s = [i % 2 for i in idx]
+        B = self.B
+        d = np.einsum("Qac,Qbd->abcd", B[:, p[0]][:, :, p[2]], B[:, p[1]][:, :, p[3]], optimize=True)
+        x = np.einsum("Qad,Qbc->abcd", B[:, p[0]][:, :, p[3]], B[:, p[1]][:, :, p[2]], optimize=True)
+        m1 = (s[0][:, None, None, None] == s[2][None, None, :, None]) & (
+            s[1][None, :, None, None] == s[3][None, None, None, :])
+        m2 = (s[0][:, None, None, None] == s[3][None, None, None, :]) & (
+            s[1][None, :, None, None] == s[2][None, None, :, None])
+        return d * m1 - x * m2
+
+
 @dataclass
 class Spaces:
     n_core: int
@@ -234,6 +295,8 @@ def general_t2(sp: Spaces, T):
 
 
 def spin_orbital_amplitudes(sp: Spaces, T):
+    """t1 over all spin orbitals and t2 over [P,P,H,H] spatial blocks embedded
+    in the full spin-orbital index range (zero elsewhere)."""
     n = sp.n
     t1s = np.zeros((n, n))
     for name, ks, cs in T1_CLASSES:
@@ -241,26 +304,41 @@ def spin_orbital_amplitudes(sp: Spaces, T):
         c0, c1 = sp.sp_range(cs)
         t1s[c0:c1, k0:k1] = T[name].T
     t1 = fill_spin_orbital(1, n, {"a": t1s})
-    t2s = general_t2(sp, T)
+    # only the particle-particle-hole-hole block of T^{cd}_{kl} is non-zero
+    p0 = sp.sp_range("A")[0]
+    h1 = sp.sp_range("A")[1]
+    t2s = general_t2(sp, T)[p0:, p0:, :h1, :h1]
     # Table 2: alpha-beta is the stored spin-free amplitude; all-alpha is
     # T^{cd}_{kl} - T^{dc}_{kl}.
-    t2 = fill_spin_orbital(2, n, {"ab": t2s, "aa": t2s - t2s.transpose(1, 0, 2, 3)})
+    blk = fill_spin_orbital_rect(t2s, {"ab": t2s, "aa": t2s - t2s.transpose(1, 0, 2, 3)})
+    nso = 2 * n
+    t2 = _Embedded(blk, (2 * p0, 2 * p0, 0, 0), (nso,) * 4)
     return t1, t2
 
 
 class Model:
-    """All spin-orbital tensors of one problem, ready for term evaluation."""
+    """All spin-orbital tensors of one problem, ready for term evaluation.
+
+    lazy=True keeps the two-electron integrals as on-demand blocks
+    (`LazyERI`) for sizes whose full spin-orbital integral array does not fit.
+    """
 
     def __init__(self, n_core, n_act, n_virt, h, B, G1, G2=None, G3=None, *,
-                 L2=None, L3=None, eri=None):
+                 L2=None, L3=None, eri=None, lazy=False):
         self.sp = Spaces(n_core, n_act, n_virt)
         n = self.sp.n
         nso = 2 * n
-        if eri is None:
-            eri = chemist_eri(B)
-        self.eri = eri
-        v = spin_orbital_eri(eri)
         a = n_act
+        self.lazy = lazy
+        if lazy:
+            v = LazyERI(B)
+            vblock = v.block
+        else:
+            if eri is None:
+                eri = chemist_eri(B)
+            self.eri = eri
+            v = spin_orbital_eri(eri)
+            vblock = lambda sl: v[tuple(sl)]
         # reference densities over the active block
         if L2 is None:
             g1, g2, g3 = spin_orbital_rdms(G1, G2, G3)
@@ -276,14 +354,16 @@ class Model:
         gam[c0:c1, c0:c1] = np.eye(c1 - c0)
         gam[a0:a1, a0:a1] = g1
         hs = fill_spin_orbital(1, n, {"a": h})
+        al = slice(0, nso)
         # generalized Fock matrix (Sec. 2.1)
-        f = hs + np.einsum("pmqm->pq", v[:, c0:c1, :, c0:c1]) + np.einsum(
-            "ptqu,tu->pq", v[:, a0:a1, :, a0:a1], g1)
+        f = hs + np.einsum("pmqm->pq", vblock([al, slice(c0, c1), al, slice(c0, c1)])) + np.einsum(
+            "ptqu,tu->pq", vblock([al, slice(a0, a1), al, slice(a0, a1)]), g1)
         gh = gam[:a1, :a1]
         g2full = wedge2(gh, gh)
         g2full[a0:a1, a0:a1, a0:a1, a0:a1] += l2
+        vh = vblock([slice(0, a1)] * 4)
         self.E0 = float(np.einsum("pq,pq->", hs[:a1, :a1], gh)
-                        + 0.25 * np.einsum("pqrs,pqrs->", v[:a1, :a1, :a1, :a1], g2full))
+                        + 0.25 * np.einsum("pqrs,pqrs->", vh, g2full))
         self.f = f
         self.v = v
         self.tensors = {
@@ -298,8 +378,9 @@ class Model:
 
     def set_amplitudes(self, T):
         t1, t2 = spin_orbital_amplitudes(self.sp, T)
+        # t2 is only non-zero on its particle x particle x hole x hole block
         self.tensors["t1"] = (t1, 0)
-        self.tensors["t2"] = (t2, 0)
+        self.tensors["t2"] = (t2.block, tuple(t2.offsets))
 
 
 # ---------------------------------------------------------------------------
@@ -333,13 +414,28 @@ class Evaluator:
 
     def _slice(self, x, fixed, spmap, off):
         if x in fixed:
-            space, spin = fixed[x]
+            space, spin = fixed[x][:2]
             lo, hi = self.ranges[space]
+            if len(fixed[x]) > 2:  # a single orbital: index inside the space
+                so = lo + self.stride * fixed[x][2] + (spin or 0)
+                return slice(so - off, so + 1 - off)
             if spin is None:
                 return slice(lo - off, hi - off)
             return slice(lo + spin - off, hi - off, self.stride)
         lo, hi = self._span(spmap[x])
         return slice(lo - off, hi - off)
+
+    def _operand(self, name, ix, fixed, spmap):
+        arr, off = self.tensors[name]
+        offs = off if isinstance(off, tuple) else (off,) * len(ix)
+        sl = [self._slice(x, fixed, spmap, o) for x, o in zip(ix, offs)]
+        if isinstance(arr, LazyERI):
+            return arr.block(sl)
+        if isinstance(arr, _Embedded):
+            arr = arr.block
+            sl = [slice(max(q.start, 0), max(q.stop, 0), q.step) for q in sl]
+            return _clip(arr, sl)
+        return arr[tuple(sl)]
 
     def size(self, space, spin):
         lo, hi = self.ranges[space]
@@ -347,8 +443,8 @@ class Evaluator:
 
     def term(self, t: wick.Term, fixed, out_idx):
         spmap = dict(t.sp)
-        for x, (space, _) in fixed.items():
-            if space not in spmap[x]:
+        for x, spec in fixed.items():
+            if spec[0] not in spmap[x]:
                 return None
         letters = {}
         for _, ix in t.factors:
@@ -358,11 +454,10 @@ class Evaluator:
         ops = []
         subs = []
         for name, ix in t.factors:
-            arr, off = self.tensors[name]
-            ops.append(arr[tuple(self._slice(x, fixed, spmap, off) for x in ix)])
+            ops.append(self._operand(name, ix, fixed, spmap))
             subs.append("".join(letters[x] for x in ix))
         spec = ",".join(subs) + "->" + "".join(letters[x] for x in out_idx)
-        key = (id(t), tuple(sorted(fixed.items())), tuple(out_idx))
+        key = (id(t), tuple(sorted((k, v[:2]) for k, v in fixed.items())), tuple(out_idx))
         path = self._paths.get(key)
         if path is None:
             path = np.einsum_path(spec, *ops, optimize="greedy")[0]
@@ -432,6 +527,11 @@ class Evaluator:
                         g2[tuple(slice(*self.ranges[b]) for b in blk)] += val
         g2 = g2 - g2.transpose(0, 1, 3, 2) - g2.transpose(1, 0, 2, 3) + g2.transpose(1, 0, 3, 2)
         return g0, g1, g2
+
+
+def _clip(arr, sl):
+    """arr[sl] for slices that may start before 0 (those rows are zero)."""
+    return arr[tuple(sl)]
 
 
 _TERMS = None
@@ -598,7 +698,7 @@ def semicanonicalize(n_core, n_act, n_virt, h, B, G1, G2, G3):
     largest-magnitude component positive.  Returns (U, h', B', G1', G2', G3')
     with new orbital j = sum_p U[p, j] old orbital p.
     """
-    m = Model(n_core, n_act, n_virt, h, B, G1, G2, G3)
+    m = Model(n_core, n_act, n_virt, h, B, G1, G2, G3, lazy=True)
     F = m.fock_spinfree()
     sp = m.sp
     n = sp.n
@@ -621,3 +721,54 @@ def semicanonicalize(n_core, n_act, n_virt, h, B, G1, G2, G3):
     G2r = np.einsum("pqrs,pi,qj,rk,sl->ijkl", G2, u, u, u, u, optimize=True)
     G3r = np.einsum("pqrstu,pi,qj,rk,sl,tm,un->ijklmn", G3, u, u, u, u, u, u, optimize=True)
     return U, h2, B2, G1r, G2r, G3r
+
+
+def residual_elements(model: Model, T, elements, ev: Evaluator | None = None):
+    """Selected spin-free residual elements, each evaluated on its own.
+
+    elements: list of (class name, index tuple) with the class array index
+    order ([k, c] singles, [k, l, c, d] doubles).  Same definition as
+    `residual`; only the open orbitals are fixed before contracting, which
+    keeps every operand small at full problem sizes.
+    """
+    model.set_amplitudes(T)
+    ev = ev or Evaluator(model)
+    tl = terms()
+    res_terms = tl["lin"] + tl["quad_res"]
+    t1c = {c[0]: c[1:] for c in T1_CLASSES}
+    t2c = {c[0]: c[1:] for c in T2_CLASSES}
+    out = []
+    for name, idx in elements:
+        if name in t1c:
+            ks, cs = t1c[name]
+            k, c = idx
+            val = 0.0
+            for t in res_terms:
+                if t.rank != 1:
+                    continue
+                (p,), (q,) = t.upper(), t.lower()
+                r = ev.term(t, {p: (cs, 0, c), q: (ks, 0, k)}, (p, q))
+                if r is not None:
+                    val += float(np.sum(r))
+            out.append(val)
+            continue
+        ks, ls, cs, ds = t2c[name]
+        k, l, c, d = idx
+        A, B = 0, 1
+        variants = (  # Eq. antisym for the alpha-beta component
+            (+1, [(cs, A, c), (ds, B, d)], [(ks, A, k), (ls, B, l)]),
+            (-1, [(cs, A, c), (ds, B, d)], [(ls, B, l), (ks, A, k)]),
+            (-1, [(ds, B, d), (cs, A, c)], [(ks, A, k), (ls, B, l)]),
+            (+1, [(ds, B, d), (cs, A, c)], [(ls, B, l), (ks, A, k)]),
+        )
+        val = 0.0
+        for sgn, up, lo in variants:
+            for t in res_terms:
+                if t.rank != 2:
+                    continue
+                (p1, p2), (q1, q2) = t.upper(), t.lower()
+                r = ev.term(t, {p1: up[0], p2: up[1], q1: lo[0], q2: lo[1]}, (p1, p2, q1, q2))
+                if r is not None:
+                    val += sgn * float(np.sum(r))
+        out.append(val)
+    return np.array(out)

@@ -46,6 +46,13 @@ class Stats(ctypes.Structure):
                 ("max_dt", ctypes.c_double), ("seconds", ctypes.c_double)]
 
 
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("residual_terms", ctypes.c_int64), ("residual_launches", ctypes.c_int64),
+                ("step_launches", ctypes.c_int64), ("residual_flops", ctypes.c_double),
+                ("arena_bytes", ctypes.c_double), ("table_bytes", ctypes.c_double),
+                ("kind_launches", ctypes.c_int64 * 3), ("kind_flops", ctypes.c_double * 3)]
+
+
 class RicMrccError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
@@ -88,6 +95,9 @@ def load_library():
         "ricmrcc_opts_default": ([ctypes.POINTER(Opts)], ctypes.c_int),
         "ricmrcc_solve": ([vp, ctypes.POINTER(Opts), vp, ctypes.POINTER(Stats)], ctypes.c_int),
         "ricmrcc_get_amplitudes": ([vp, vp, vp], ctypes.c_int),
+        "ricmrcc_step": ([vp, ctypes.POINTER(Opts), ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
+        "ricmrcc_plan_info": ([vp, ctypes.POINTER(PlanInfo)], ctypes.c_int),
+        "ricmrcc_profile": ([vp, ctypes.c_int, vp], ctypes.c_int),
         "ricmrcc_set_amplitudes": ([vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -247,6 +257,33 @@ class RicMrcc:
         rc = self.lib.ricmrcc_solve(self.h, ctypes.byref(o), ctypes.byref(e), ctypes.byref(st))
         self._check(rc, allow=(OK, NOT_CONVERGED))
         return e.value, st
+
+
+def _step(self, s=0.5, n_steps=1, restart=False, **kw):
+    """n_steps solver iterations without the convergence test (see ricmrcc_step)."""
+    o = self.default_opts(s=s, **kw)
+    e = ctypes.c_double()
+    dt = ctypes.c_double()
+    self._check(self.lib.ricmrcc_step(self.h, ctypes.byref(o), n_steps, int(restart),
+                                      ctypes.byref(e), ctypes.byref(dt)))
+    return e.value, dt.value
+
+
+def _plan_info(self):
+    info = PlanInfo()
+    self._check(self.lib.ricmrcc_plan_info(self.h, ctypes.byref(info)))
+    return info
+
+
+def _profile(self, reps=3):
+    ms = np.zeros(3)
+    self._check(self.lib.ricmrcc_profile(self.h, reps, _ptr(ms)))
+    return ms
+
+
+RicMrcc.step = _step
+RicMrcc.plan_info = _plan_info
+RicMrcc.profile = _profile
 
 
 def header_symbols(header=None):

@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <memory>
 #include <string>
@@ -45,6 +46,7 @@ struct ricmrcc {
   int64_t *pack1 = nullptr, *pack2 = nullptr, *pack2b = nullptr;
   double *flat1 = nullptr, *flat2 = nullptr, *rflat1 = nullptr, *rflat2 = nullptr;
   double* arena = nullptr;
+  int64_t arena_elems = 0;
   double* host_scal = nullptr;  // pinned, 8 doubles
   int* d_sweeps = nullptr;
 
@@ -56,6 +58,13 @@ struct ricmrcc {
   Program res_prog, cum_prog;
   bool have_ints = false, have_rdms = false, planned = false;
   double E0 = 0.0;
+  int rdm_kind = RICMRCC_RDM;
+  bool verbose = false;
+  // solver iteration state (kept across ricmrcc_step calls)
+  int nvec = 0, iter = 0;
+  bool have_old = false;
+  double e_old = 0.0, last_E = 0.0, last_dt = 0.0;
+  double gram_host[256] = {0.0};
   std::vector<void*> allocs;
 };
 
@@ -193,16 +202,19 @@ int plan(ricmrcc_t* h) {
   set(ov[OE], h->scal + 1, {}, {});
   set(ov[OL3], h->L3, {DOM_A, DOM_A, DOM_A, DOM_A, DOM_A, DOM_A},
       {a * a * a * a * a, a * a * a * a, a * a * a, a * a, a, 1});
-  Planner pl(d, tv, ov, h->scal + 3);
+  // separate planners: the programs run at different times and each zeroes
+  // the shared arena first, so they must not share intermediates
+  Planner pl(d, tv, ov, h->scal + 3), pc(d, tv, ov, h->scal + 3);
   for (const auto& t : kResidualTerms)
     if (!pl.add_term(t, &h->res_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad residual term");
   for (const auto& t : kEnergyTerms)
     if (!pl.add_term(t, &h->res_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad energy term");
   for (const auto& t : kCumulant3Terms)
-    if (!pl.add_term(t, &h->cum_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad cumulant term");
-  TRY(dalloc(h, &h->arena, pl.arena_size()));
+    if (!pc.add_term(t, &h->cum_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad cumulant term");
+  h->arena_elems = std::max<int64_t>(std::max<int64_t>(pl.arena_size(), pc.arena_size()), 1);
+  TRY(dalloc(h, &h->arena, h->arena_elems));
   pl.finalize(&h->res_prog, h->arena);
-  pl.finalize(&h->cum_prog, h->arena);
+  pc.finalize(&h->cum_prog, h->arena);
   for (Program* p : {&h->res_prog, &h->cum_prog}) {
     TRY(dalloc(h, &p->d_table, (int64_t)p->table.size()));
     CK(cudaMemcpyAsync(p->d_table, p->table.data(), sizeof(int64_t) * p->table.size(),
@@ -284,6 +296,7 @@ int cumulants(ricmrcc_t* h, int kind) {
   CK(cudaMemcpyAsync(h->L3, h->g3, sizeof(double) * a6, cudaMemcpyDeviceToDevice, h->s));
   if (kind == RICMRCC_RDM) {
     TRY(plan(h));
+    CK(cudaMemsetAsync(h->arena, 0, sizeof(double) * h->arena_elems, h->s));
     run_program(h, h->cum_prog);
   }
   launch_direct3(h->D3, h->L3, a, h->s);
@@ -292,6 +305,7 @@ int cumulants(ricmrcc_t* h, int kind) {
 
 int residual_device(ricmrcc_t* h) {
   // X, E accumulators and intermediates start from zero
+  CK(cudaMemsetAsync(h->arena, 0, sizeof(double) * h->arena_elems, h->s));
   CK(cudaMemsetAsync(h->X, 0, sizeof(double) * h->ng, h->s));
   CK(cudaMemsetAsync(h->scal + 1, 0, sizeof(double), h->s));
   run_program(h, h->res_prog);
@@ -323,6 +337,7 @@ static int create_impl(ricmrcc_t* h, int n_core, int n_act, int n_virt, int n_au
   {
   }
   Dims& d = h->d;
+  h->verbose = getenv("RICMRCC_VERBOSE") != nullptr;
   d.o = n_core;
   d.a = n_act;
   d.v = n_virt;
@@ -448,6 +463,7 @@ static int set_rdms_impl(ricmrcc_t* h, const double* g1, const double* g2, const
     CK(cudaMemcpyAsync(h->g3, g3, sizeof(double) * a * a * a * a * a * a, k, h->s));
   }
   TRY(cumulants(h, kind));
+  h->rdm_kind = kind;
   h->have_rdms = true;
   CK(cudaMemsetAsync(h->T, 0, sizeof(double) * h->ng, h->s));
   TRY(rebuild_reference(h));
@@ -553,18 +569,11 @@ int ricmrcc_opts_default(ricmrcc_opts* o) {
   return RICMRCC_OK;
 }
 
-int ricmrcc_solve(ricmrcc_t* h, const ricmrcc_opts* opts, double* E_out, ricmrcc_stats* stats) {
-  if (!h) return RICMRCC_EINVAL;
-  ricmrcc_opts o;
-  ricmrcc_opts_default(&o);
-  if (opts) o = *opts;
-  if (!(o.s >= 0.0) || !isfinite(o.s) || o.max_iter < 1 || o.diis_size < 0 || o.diis_size > 16)
-    return fail(h, RICMRCC_EINVAL, "bad options (s >= 0, max_iter >= 1, 0 <= diis_size <= 16)");
-  if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
-  if (o.precision == RICMRCC_MIXED) return fail(h, RICMRCC_ENOTSUP, "mixed precision not built");
-  TRY(enter(h));
-  const auto t0 = std::chrono::steady_clock::now();
-  const int cap = o.diis_size > 0 ? o.diis_size : 1;
+}  // extern "C"
+
+namespace {
+
+int ensure_diis(ricmrcc_t* h, int cap) {
   if (h->diis_cap != cap || !h->hist_v) {
     if (h->hist_v) cudaFree(h->hist_v);
     if (h->hist_e) cudaFree(h->hist_e);
@@ -573,75 +582,186 @@ int ricmrcc_solve(ricmrcc_t* h, const ricmrcc_opts* opts, double* E_out, ricmrcc
     CK(cudaMalloc(&h->hist_e, sizeof(double) * h->ng * cap));
     h->diis_cap = cap;
   }
-  double e_old = 0.0, E = 0.0, maxdt = 0.0;
-  bool have_old = false, converged = false, diverged = false;
-  int it = 0, nvec = 0;
-  std::vector<double> gram(16 * 16, 0.0);
+  return RICMRCC_OK;
+}
+
+void reset_iteration_state(ricmrcc_t* h) {
+  h->nvec = 0;
+  h->iter = 0;
+  h->have_old = false;
+  std::fill(h->gram_host, h->gram_host + 256, 0.0);
+}
+
+// One iteration of the renormalised, DIIS-accelerated update (Sec. 2.2):
+// residual + energy at the current T, t_new = (t D + r)(1 - exp(-s D^2))/D,
+// then DIIS extrapolation over the stored (t_new, t_new - t) pairs.
+// *conv is set when the energy change and max |t_new - t| are below the
+// thresholds (T is then left at the converged iterate).
+int iterate(ricmrcc_t* h, const ricmrcc_opts& o, bool check, bool* conv, bool* diverged) {
+  *conv = false;
+  *diverged = false;
+  const int cap = o.diis_size > 0 ? o.diis_size : 1;
+  TRY(ensure_diis(h, cap));
+  ++h->iter;
+  TRY(residual_device(h));
+  CK(cudaMemsetAsync(h->scal + 2, 0, sizeof(double), h->s));
+  launch_update(h->T, h->X, h->Tn, h->Err, h->eps, h->d, o.s, h->scal + 2, h->s);
+  CK(cudaMemcpyAsync(h->host_scal, h->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  const double E = h->E0 + h->host_scal[1];
+  const double maxdt = h->host_scal[2];
+  h->last_E = E;
+  h->last_dt = maxdt;
+  if (h->verbose) fprintf(stderr, "ricmrcc iter %3d  E = %.12f  max|dt| = %.3e\n", h->iter, E, maxdt);
+  if (!isfinite(E) || !isfinite(maxdt) || maxdt > 1e100) {
+    *diverged = true;
+    return RICMRCC_OK;
+  }
+  if (check && h->have_old && fabs(E - h->e_old) < o.e_tol && maxdt < o.t_tol) {
+    *conv = true;
+    return RICMRCC_OK;
+  }
+  h->e_old = E;
+  h->have_old = true;
+  if (o.diis_size == 0) {
+    CK(cudaMemcpyAsync(h->T, h->Tn, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
+    return RICMRCC_OK;
+  }
+  // DIIS history (ring buffer; the extrapolation does not depend on order)
+  const int slot = h->nvec % cap;
+  CK(cudaMemcpyAsync(h->hist_v + (int64_t)slot * h->ng, h->Tn, sizeof(double) * h->ng,
+                     cudaMemcpyDeviceToDevice, h->s));
+  CK(cudaMemcpyAsync(h->hist_e + (int64_t)slot * h->ng, h->Err, sizeof(double) * h->ng,
+                     cudaMemcpyDeviceToDevice, h->s));
+  ++h->nvec;
+  const int m = h->nvec < cap ? h->nvec : cap;
+  CK(cudaMemsetAsync(h->dots, 0, sizeof(double) * 16, h->s));
+  launch_dots(h->dots, h->Err, h->hist_e, h->ng, m, h->ng, h->s);
+  CK(cudaMemcpyAsync(h->host_scal + 4, h->dots, sizeof(double) * 4, cudaMemcpyDeviceToHost, h->s));
+  double dv[16];
+  CK(cudaMemcpyAsync(dv, h->dots, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  for (int j = 0; j < m; ++j) {
+    h->gram_host[slot * 16 + j] = dv[j];
+    h->gram_host[j * 16 + slot] = dv[j];
+  }
+  if (h->iter >= o.diis_start && m >= 2) {
+    CK(cudaMemcpyAsync(h->gram, h->gram_host, sizeof(double) * 256, cudaMemcpyHostToDevice, h->s));
+    launch_diis_solve(h->gram, h->coef, m, h->dstatus, h->s);
+    launch_extrapolate(h->T, h->hist_v, h->coef, h->dstatus, m, slot, h->ng, h->ng, h->s);
+  } else {
+    CK(cudaMemcpyAsync(h->T, h->Tn, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
+  }
+  return RICMRCC_OK;
+}
+
+int check_opts(ricmrcc_t* h, const ricmrcc_opts& o) {
+  if (!(o.s >= 0.0) || !isfinite(o.s) || o.max_iter < 1 || o.diis_size < 0 || o.diis_size > 16)
+    return fail(h, RICMRCC_EINVAL, "bad options (s >= 0, max_iter >= 1, 0 <= diis_size <= 16)");
+  if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
+  if (o.precision == RICMRCC_MIXED) return fail(h, RICMRCC_ENOTSUP, "mixed precision not built");
+  return RICMRCC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ricmrcc_solve(ricmrcc_t* h, const ricmrcc_opts* opts, double* E_out, ricmrcc_stats* stats) {
+  if (!h) return RICMRCC_EINVAL;
+  ricmrcc_opts o;
+  ricmrcc_opts_default(&o);
+  if (opts) o = *opts;
+  TRY(check_opts(h, o));
+  TRY(enter(h));
+  const auto t0 = std::chrono::steady_clock::now();
+  reset_iteration_state(h);
+  bool converged = false, diverged = false;
+  int it = 0;
   for (it = 1; it <= o.max_iter; ++it) {
-    TRY(residual_device(h));
-    CK(cudaMemsetAsync(h->scal + 2, 0, sizeof(double), h->s));
-    launch_update(h->T, h->X, h->Tn, h->Err, h->eps, h->d, o.s, h->scal + 2, h->s);
-    CK(cudaMemcpyAsync(h->host_scal, h->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
-    E = h->E0 + h->host_scal[1];
-    maxdt = h->host_scal[2];
-    if (!isfinite(E) || !isfinite(maxdt) || maxdt > 1e100) {
-      diverged = true;
-      break;
-    }
-    if (have_old && fabs(E - e_old) < o.e_tol && maxdt < o.t_tol) {
-      converged = true;
-      break;
-    }
-    e_old = E;
-    have_old = true;
-    if (o.diis_size == 0) {
-      CK(cudaMemcpyAsync(h->T, h->Tn, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
-      continue;
-    }
-    // DIIS history (ring buffer; the extrapolation does not depend on order)
-    const int slot = nvec % cap;
-    CK(cudaMemcpyAsync(h->hist_v + (int64_t)slot * h->ng, h->Tn, sizeof(double) * h->ng,
-                       cudaMemcpyDeviceToDevice, h->s));
-    CK(cudaMemcpyAsync(h->hist_e + (int64_t)slot * h->ng, h->Err, sizeof(double) * h->ng,
-                       cudaMemcpyDeviceToDevice, h->s));
-    ++nvec;
-    const int m = nvec < cap ? nvec : cap;
-    CK(cudaMemsetAsync(h->dots, 0, sizeof(double) * 16, h->s));
-    launch_dots(h->dots, h->Err, h->hist_e, h->ng, m, h->ng, h->s);
-    // place the new row/column of the Gram matrix
-    std::vector<double> dv(16, 0.0);
-    CK(cudaMemcpyAsync(dv.data(), h->dots, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
-    for (int j = 0; j < m; ++j) {
-      gram[slot * 16 + j] = dv[j];
-      gram[j * 16 + slot] = dv[j];
-    }
-    if (it >= o.diis_start && m >= 2) {
-      CK(cudaMemcpyAsync(h->gram, gram.data(), sizeof(double) * 256, cudaMemcpyHostToDevice, h->s));
-      launch_diis_solve(h->gram, h->coef, m, h->dstatus, h->s);
-      launch_extrapolate(h->T, h->hist_v, h->coef, h->dstatus, m, slot, h->ng, h->ng, h->s);
-    } else {
-      CK(cudaMemcpyAsync(h->T, h->Tn, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
-    }
+    TRY(iterate(h, o, true, &converged, &diverged));
+    if (converged || diverged) break;
   }
   if (it > o.max_iter) it = o.max_iter;
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (E_out) *E_out = E;
+  if (E_out) *E_out = h->last_E;
   if (stats) {
     stats->iterations = it;
     stats->converged = converged ? 1 : 0;
     stats->fp64_iterations = it;
     stats->mixed_iterations = 0;
-    stats->energy = E;
+    stats->energy = h->last_E;
     stats->e0 = h->E0;
-    stats->max_dt = maxdt;
+    stats->max_dt = h->last_dt;
     stats->seconds = secs;
   }
   TRY(leave(h));
   if (diverged) return fail(h, RICMRCC_DIVERGED, "non-finite energy or amplitude change");
   if (!converged) return fail(h, RICMRCC_NOT_CONVERGED, "max_iter reached");
   return RICMRCC_OK;
+}
+
+int ricmrcc_step(ricmrcc_t* h, const ricmrcc_opts* opts, int n_steps, int restart, double* E_out,
+                 double* max_dt_out) {
+  if (!h) return RICMRCC_EINVAL;
+  ricmrcc_opts o;
+  ricmrcc_opts_default(&o);
+  if (opts) o = *opts;
+  if (n_steps < 0) return fail(h, RICMRCC_EINVAL, "n_steps < 0");
+  TRY(check_opts(h, o));
+  TRY(enter(h));
+  if (restart) reset_iteration_state(h);
+  bool conv = false, div = false;
+  for (int i = 0; i < n_steps && !div; ++i) TRY(iterate(h, o, false, &conv, &div));
+  if (E_out) *E_out = h->last_E;
+  if (max_dt_out) *max_dt_out = h->last_dt;
+  TRY(leave(h));
+  if (div) return fail(h, RICMRCC_DIVERGED, "non-finite energy or amplitude change");
+  return RICMRCC_OK;
+}
+
+int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
+  if (!h || !out) return RICMRCC_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->residual_terms = (int64_t)h->res_prog.n_terms;
+  out->residual_launches = (int64_t)h->res_prog.ops.size();
+  out->residual_flops = h->res_prog.flops;
+  out->arena_bytes = (double)h->arena_elems * 8.0;
+  out->table_bytes = (double)(h->res_prog.table.size() + h->cum_prog.table.size()) * 8.0;
+  out->step_launches = out->residual_launches + 5;  // + update, dots, DIIS solve, extrapolate (or copy)
+  for (const auto& op : h->res_prog.ops) {
+    out->kind_launches[op.kind] += 1;
+    out->kind_flops[op.kind] += op.flops;
+  }
+  return RICMRCC_OK;
+}
+
+int ricmrcc_profile(ricmrcc_t* h, int reps, double* kind_ms) {
+  if (!h || !kind_ms || reps < 1) return fail(h, RICMRCC_EINVAL, "bad arguments");
+  if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
+  TRY(enter(h));
+  const size_t nops = h->res_prog.ops.size();
+  std::vector<cudaEvent_t> ev(nops + 1);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  for (int k = 0; k < 3; ++k) kind_ms[k] = 0.0;
+  for (int r = 0; r < reps; ++r) {
+    CK(cudaMemsetAsync(h->arena, 0, sizeof(double) * h->arena_elems, h->s));
+    CK(cudaMemsetAsync(h->X, 0, sizeof(double) * h->ng, h->s));
+    CK(cudaMemsetAsync(h->scal + 1, 0, sizeof(double), h->s));
+    for (size_t i = 0; i < nops; ++i) {
+      CK(cudaEventRecord(ev[i], h->s));
+      launch_contract(h->res_prog.ops[i], h->res_prog.d_table, h->s);
+    }
+    CK(cudaEventRecord(ev[nops], h->s));
+    CK(cudaEventSynchronize(ev[nops]));
+    for (size_t i = 0; i < nops; ++i) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
+      kind_ms[h->res_prog.ops[i].kind] += ms / reps;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  return leave(h);
 }
 
 int ricmrcc_get_amplitudes(ricmrcc_t* h, double* T1, double* T2) {
@@ -669,7 +789,101 @@ int ricmrcc_set_amplitudes(ricmrcc_t* h, const double* T1, const double* T2) {
 
 int ricmrcc_semicanonicalize(ricmrcc_t* h, double* U_out) {
   if (!h) return RICMRCC_EINVAL;
-  return fail(h, RICMRCC_ENOTSUP, "semicanonicalize: not built yet");
+  if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
+  TRY(enter(h));
+  const Dims& d = h->d;
+  const int n = d.n, a = d.a;
+  double *U = nullptr, *blk = nullptr, *V = nullptr, *tmp = nullptr;
+  const int64_t big = std::max<int64_t>((int64_t)d.X * n * n, (int64_t)a * a * a * a * a * a);
+  CK(cudaMalloc(&U, sizeof(double) * n * n));
+  CK(cudaMalloc(&blk, sizeof(double) * n * n));
+  CK(cudaMalloc(&V, sizeof(double) * n * n));
+  CK(cudaMalloc(&tmp, sizeof(double) * std::max<int64_t>(big, 1)));
+  CK(cudaMemsetAsync(U, 0, sizeof(double) * n * n, h->s));
+  // Jacobi eigen-decomposition of the core, active and virtual Fock blocks
+  const int off[3] = {0, d.o, d.o + d.a}, sz[3] = {d.o, d.a, d.v};
+  for (int b = 0; b < 3; ++b) {
+    if (sz[b] == 0) continue;
+    CK(cudaMemcpy2DAsync(blk, sizeof(double) * sz[b], h->F + (int64_t)off[b] * n + off[b],
+                         sizeof(double) * n, sizeof(double) * sz[b], sz[b],
+                         cudaMemcpyDeviceToDevice, h->s));
+    run_jacobi(blk, V, sz[b], U, n, off[b], h->d_sweeps, h->s);
+  }
+  // rotations x' = U^T x U, one index at a time, with the contraction kernel
+  auto rotate = [&](double* x, int nidx, int64_t lead, int dim, const double* u, int64_t ldu,
+                    int64_t uoff) -> int {
+    // x has `lead` leading elements (aux index) then nidx axes of extent dim
+    for (int ax = 0; ax < nidx; ++ax) {
+      int64_t ext[16];
+      ext[0] = lead;
+      for (int j = 0; j < nidx; ++j) ext[1 + j] = dim;
+      ext[1 + nidx] = dim;  // summed label p
+      Operand A, B, C;
+      // A = x[lead, ..., p (at ax), ...]
+      int64_t st = 1;
+      int64_t strides[8];
+      for (int j = nidx - 1; j >= 0; --j) {
+        strides[j] = st;
+        st *= dim;
+      }
+      A.base = x;
+      A.nlab = 0;
+      A.key = "X";
+      if (lead > 1) { A.lab[A.nlab] = 0; A.stride[A.nlab++] = st; }
+      for (int j = 0; j < nidx; ++j) {
+        A.lab[A.nlab] = (j == ax) ? 1 + nidx : 1 + j;
+        A.stride[A.nlab++] = strides[j];
+      }
+      B.base = u + uoff;  // u[p, i] with leading dimension ldu
+      B.nlab = 2;
+      B.key = "U";
+      B.lab[0] = 1 + nidx;
+      B.stride[0] = ldu;
+      B.lab[1] = 1 + ax;
+      B.stride[1] = 1;
+      C.base = tmp;
+      C.nlab = 0;
+      C.key = "C";
+      if (lead > 1) { C.lab[C.nlab] = 0; C.stride[C.nlab++] = st; }
+      for (int j = 0; j < nidx; ++j) {
+        C.lab[C.nlab] = 1 + j;
+        C.stride[C.nlab++] = strides[j];
+      }
+      const int64_t total = st * lead;
+      CK(cudaMemsetAsync(tmp, 0, sizeof(double) * total, h->s));
+      Program p;
+      Planner pl(d, nullptr, nullptr, h->scal + 3);
+      pl.emit(A, B, C, ext, 1.0, 0, &p);
+      int64_t* dt = nullptr;
+      CK(cudaMalloc(&dt, sizeof(int64_t) * std::max<size_t>(p.table.size(), 1)));
+      CK(cudaMemcpyAsync(dt, p.table.data(), sizeof(int64_t) * p.table.size(),
+                         cudaMemcpyHostToDevice, h->s));
+      for (const auto& op : p.ops) launch_contract(op, dt, h->s);
+      CK(cudaMemcpyAsync(x, tmp, sizeof(double) * total, cudaMemcpyDeviceToDevice, h->s));
+      CK(cudaStreamSynchronize(h->s));
+      CK(cudaFree(dt));
+    }
+    return RICMRCC_OK;
+  };
+  TRY(rotate(h->h, 2, 1, n, U, n, 0));
+  TRY(rotate(h->B, 2, d.X, n, U, n, 0));
+  if (a > 0) {
+    const int64_t uo = (int64_t)d.o * n + d.o;  // active block of U
+    TRY(rotate(h->g1, 2, 1, a, U, n, uo));
+    TRY(rotate(h->g2, 4, 1, a, U, n, uo));
+    TRY(rotate(h->g3, 6, 1, a, U, n, uo));
+  }
+  if (U_out) CK(cudaMemcpyAsync(U_out, U, sizeof(double) * n * n, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  cudaFree(U);
+  cudaFree(blk);
+  cudaFree(V);
+  cudaFree(tmp);
+  TRY(build_eri(h));
+  TRY(cumulants(h, h->rdm_kind));
+  CK(cudaMemsetAsync(h->T, 0, sizeof(double) * h->ng, h->s));
+  TRY(rebuild_reference(h));
+  return leave(h);
 }
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 // contraction becomes a ContractOp with per-label-group offset tables so that
 // any strided, sliced, permuted or diagonal view is addressed directly.
 #include <algorithm>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <string>
@@ -47,8 +48,8 @@ std::string itos(int64_t x) { return std::to_string(x); }
 Planner::Planner(const Dims& d, const TensorView* tensors, const TensorView* outs,
                  const double* ones)
     : d_(d), ones_(ones) {
-  for (int i = 0; i < NTENSOR; ++i) tensors_[i] = tensors[i];
-  for (int i = 0; i < NOUT; ++i) outs_[i] = outs[i];
+  for (int i = 0; i < NTENSOR && tensors; ++i) tensors_[i] = tensors[i];
+  for (int i = 0; i < NOUT && outs; ++i) outs_[i] = outs[i];
 }
 
 bool Planner::make_operand(const TensorView& tv, int tensor_tag, int nidx, const uint8_t* idx,
@@ -245,47 +246,86 @@ bool Planner::add_term(const RicTermDesc& t, Program* prog) {
   }
   Operand out;
   if (!make_operand(outs_[t.out], 100 + t.out, t.nout, t.out_idx, t.mask, &out)) return false;
-  while (ops.size() > 2) {
-    size_t bi = 0, bj = 1;
-    double best = -1.0, best_sz = 0.0;
-    for (size_t i = 0; i < ops.size(); ++i)
-      for (size_t j = i + 1; j < ops.size(); ++j) {
-        double cost = 1.0, sz = 1.0;
-        std::vector<int> u;
-        for (int x = 0; x < ops[i].nlab; ++x) u.push_back(ops[i].lab[x]);
-        for (int x = 0; x < ops[j].nlab; ++x)
-          if (!ops[i].has(ops[j].lab[x])) u.push_back(ops[j].lab[x]);
-        for (int l : u) {
-          cost *= (double)ext[l];
-          bool needed = out.has(l);
-          for (size_t k = 0; k < ops.size() && !needed; ++k)
-            if (k != i && k != j && ops[k].has(l)) needed = true;
-          if (needed) sz *= (double)ext[l];
-        }
-        if (best < 0 || cost < best || (cost == best && sz < best_sz)) {
-          best = cost;
-          best_sz = sz;
-          bi = i;
-          bj = j;
-        }
+  // Optimal binary contraction order by dynamic programming over operand
+  // subsets: cost(S) = min over splits S = S1 + S2 of cost(S1) + cost(S2) +
+  // flops(S1 x S2) + size(result), where a subset's result keeps the labels
+  // that also appear outside it or in the output.
+  const int nf = (int)ops.size();
+  const int full = (1 << nf) - 1;
+  std::vector<uint32_t> labmask(nf, 0);
+  for (int f = 0; f < nf; ++f)
+    for (int x = 0; x < ops[f].nlab; ++x) labmask[f] |= 1u << ops[f].lab[x];
+  uint32_t outmask = 0;
+  for (int x = 0; x < out.nlab; ++x) outmask |= 1u << out.lab[x];
+  auto labels_of = [&](int S) {
+    uint32_t in = 0, outside = outmask;
+    for (int f = 0; f < nf; ++f) {
+      if (S >> f & 1) in |= labmask[f];
+      else outside |= labmask[f];
+    }
+    return std::make_pair(in, in & outside);  // (all labels, kept labels)
+  };
+  auto prod = [&](uint32_t m) {
+    double p = 1.0;
+    for (int l = 0; l < 16; ++l)
+      if (m >> l & 1) p *= (double)ext[l];
+    return p;
+  };
+  std::vector<double> best(full + 1, 0.0);
+  std::vector<int> split(full + 1, 0);
+  for (int S = 1; S <= full; ++S) {
+    if ((S & (S - 1)) == 0) continue;  // single operand
+    double bc = -1.0;
+    for (int S1 = (S - 1) & S; S1 > 0; S1 = (S1 - 1) & S) {
+      const int S2 = S ^ S1;
+      if (S1 < S2) continue;  // each split once
+      const uint32_t k1 = labels_of(S1).second, k2 = labels_of(S2).second;
+      const double c = best[S1] + best[S2] + prod(k1 | k2) + (S == full ? 0.0 : prod(labels_of(S).second));
+      if (bc < 0 || c < bc) {
+        bc = c;
+        split[S] = S1;
       }
+    }
+    best[S] = bc;
+  }
+  // materialise the tree bottom-up; the root contraction writes the output
+  std::vector<Operand> res(full + 1);
+  std::vector<bool> have(full + 1, false);
+  for (int f = 0; f < nf; ++f) {
+    res[1 << f] = ops[f];
+    have[1 << f] = true;
+  }
+  // post-order over the split tree (children have smaller masks than parents)
+  std::vector<int> stack{full}, order;
+  while (!stack.empty()) {
+    const int S = stack.back();
+    stack.pop_back();
+    if ((S & (S - 1)) == 0) continue;
+    order.push_back(S);
+    stack.push_back(split[S]);
+    stack.push_back(S ^ split[S]);
+  }
+  for (int i = (int)order.size() - 1; i >= 0; --i) {
+    const int S = order[i];
+    if (S == full) continue;
+    const uint32_t km = labels_of(S).second;
     std::vector<int> keep;
-    auto consider = [&](const Operand& o) {
-      for (int x = 0; x < o.nlab; ++x) {
-        const int l = o.lab[x];
-        if (std::find(keep.begin(), keep.end(), l) != keep.end()) continue;
-        bool needed = out.has(l);
-        for (size_t k = 0; k < ops.size() && !needed; ++k)
-          if (k != bi && k != bj && ops[k].has(l)) needed = true;
-        if (needed) keep.push_back(l);
-      }
-    };
-    consider(ops[bi]);
-    consider(ops[bj]);
-    Operand inter = intermediate(ops[bi], ops[bj], keep, ext, prog);
-    ops.erase(ops.begin() + bj);
-    ops.erase(ops.begin() + bi);
-    ops.push_back(inter);
+    // keep labels in order of appearance in the two children
+    const Operand& c1 = res[split[S]];
+    const Operand& c2 = res[S ^ split[S]];
+    for (const Operand* c : {&c1, &c2})
+      for (int x = 0; x < c->nlab; ++x)
+        if ((km >> c->lab[x] & 1) && std::find(keep.begin(), keep.end(), c->lab[x]) == keep.end())
+          keep.push_back(c->lab[x]);
+    res[S] = intermediate(c1, c2, keep, ext, prog);
+    have[S] = true;
+  }
+  ops.clear();
+  if (nf == 1) {
+    ops.push_back(res[full]);
+  } else {
+    ops.push_back(res[split[full]]);
+    ops.push_back(res[full ^ split[full]]);
   }
   Operand one;
   one.base = ones_;

@@ -16,14 +16,15 @@ class Planner {
   int64_t cse_hits() const { return cse_hits_; }
   // Patch arena offsets of `prog` (planned by this planner) into addresses.
   void finalize(Program* prog, double* arena);
+  // One contraction C[...] += alpha * A[...] B[...] between explicit operands.
+  void emit(const Operand& A, const Operand& B, const Operand& C, const int64_t* ext, double alpha,
+            int arena_flags, Program* prog);
 
  private:
   bool make_operand(const TensorView& tv, int tensor_tag, int nidx, const uint8_t* idx,
                     const uint8_t* mask, Operand* op);
   Operand intermediate(const Operand& A, const Operand& B, const std::vector<int>& keep,
                        const int64_t* ext, Program* prog);
-  void emit(const Operand& A, const Operand& B, const Operand& C, const int64_t* ext, double alpha,
-            int arena_flags, Program* prog);
 
   Dims d_;
   TensorView tensors_[NTENSOR];

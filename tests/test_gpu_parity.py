@@ -139,3 +139,59 @@ def test_amplitude_roundtrip_and_errors(tiny):
     with pytest.raises(ric.RicMrccError) as ei:
         fresh.residual(T)
     assert ei.value.code == ric.ESTATE
+
+
+def test_semicanonicalize_matches_oracle():
+    import paper_2511_03567_gb300 as ric
+    p = synthetic.make_config("tiny")
+    U, *rot = o.semicanonicalize(p.n_core, p.n_act, p.n_virt, p.h, p.B, p.G1, p.G2, p.G3)
+    g = ric.RicMrcc(p.n_core, p.n_act, p.n_virt, p.n_aux)
+    g.set_integrals(p.h, p.B)
+    g.set_rdms(p.G1, p.G2, p.G3)
+    Ug = g.semicanonicalize()
+    assert np.abs(Ug - U).max() < 1e-10
+    m = o.Model(p.n_core, p.n_act, p.n_virt, *rot)
+    e0, F = g.reference()
+    assert abs(e0 - m.E0) < 1e-10
+    T = synthetic.make_amplitudes(p.n_core, p.n_act, p.n_virt, seed=8, scale=0.05)
+    R, E = o.residual(m, T)
+    Rg, Eg = g.residual(T)
+    assert _compare(R, Rg) < RES_TOL
+    assert abs(E - Eg) < E_TOL
+
+
+@pytest.mark.slow
+def test_solve_medium_matches_oracle():
+    """Strongly correlated random CAS(6,6) reference (100 determinants)."""
+    nc, na, nv, nx = 3, 6, 16, 60
+    p, rot = _problem(nc, na, nv, nx, n_det=100, seed=0)
+    m = o.Model(nc, na, nv, *rot)
+    ref = o.solve(m, 0.5, max_iter=40)
+    assert ref.converged
+    g = _gpu(nc, na, nv, nx, rot)
+    e, st = g.solve(0.5, max_iter=40)
+    assert st.converged == 1
+    assert abs(e - ref.energy) < E_TOL
+
+
+@pytest.mark.slow
+def test_mid_full_size_sampled_elements():
+    """Full Mid size (8 core, CAS(8,8), 120 virtual, n_aux 400) as bench.py
+    runs it: GPU residual vs the oracle on one sampled element per class."""
+    import bench
+    import paper_2511_03567_gb300 as ric
+    from oracle import sampled
+    w = bench.WORKLOAD
+    p, rot, m = sampled.build(w)
+    g = ric.RicMrcc(w["n_core"], w["n_act"], w["n_virt"], w["n_aux"])
+    g.set_integrals(p.h, p.B)
+    g.set_rdms(p.G1, p.G2, p.G3)
+    g.semicanonicalize()
+    e0, _ = g.reference()
+    assert abs(e0 - m.E0) < 1e-9
+    T = synthetic.make_amplitudes(p.n_core, p.n_act, p.n_virt, seed=1, scale=0.02)
+    Rg, Eg = g.residual(T)
+    elems = sampled.sample_elements(p.n_core, p.n_act, p.n_virt, 12, seed=3)
+    ref = o.residual_elements(m, T, elems)
+    for (name, idx), r in zip(elems, ref):
+        assert abs(Rg[name][idx] - r) < RES_TOL, (name, idx, Rg[name][idx], r)
