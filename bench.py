@@ -23,8 +23,15 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = {"workload": "mid", "n_core": 8, "n_act": 8, "n_virt": 120, "n_aux": 400, "n_det": 512,
-            "s": 0.1, "seed": 0}
+WORKLOADS = {
+    # the BASELINE Mid configuration (first flow value)
+    "mid": {"workload": "mid", "n_core": 8, "n_act": 8, "n_virt": 120, "n_aux": 400, "n_det": 512,
+            "s": 0.1, "seed": 0},
+    # small case for profiler captures (integral tensor 215 MB > L2)
+    "prof": {"workload": "prof", "n_core": 4, "n_act": 4, "n_virt": 64, "n_aux": 200, "n_det": None,
+             "s": 0.1, "seed": 0},
+}
+WORKLOAD = WORKLOADS["mid"]
 METRIC = "RIC-MRCCSD s/iter (Mid, one GB300)"
 
 
@@ -142,7 +149,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
+    ap.add_argument("--ncu-largest", type=int, default=0,
+                    help="profiler mode: one residual, then only the N largest contractions")
     args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args)
 
@@ -164,6 +176,15 @@ def main():
     if prec == ric.MIXED:
         g.set_precision(prec)
     info = g.plan_info()
+    if args.ncu_largest:
+        T = synthetic.make_amplitudes(w["n_core"], w["n_act"], w["n_virt"], seed=1, scale=0.02)
+        g.residual(T)
+        torch.cuda.synchronize()
+        g.lib.ricmrcc_run_largest_ops(g.h, args.ncu_largest)
+        torch.cuda.synchronize()
+        print(json.dumps({"ncu_largest": args.ncu_largest, "workload": w["workload"],
+                          "residual_flops": info.residual_flops}))
+        return 0
 
     # warm-up, then exactly K timed iterations (DIIS history continues)
     g.step(s=w["s"], n_steps=max(args.warmup, 1), restart=True, precision=prec)
@@ -229,7 +250,7 @@ def main():
                     "d2h_bytes_per_step": 8 * (lay.t1_size + lay.t2_size)},
             "gpu_launches": int(info.step_launches) * args.steps,
             "roofline": roof, "clocks": clk.summary()}
-    if not args.no_cpu_baseline and ws == 1:
+    if not args.no_cpu_baseline and ws == 1 and args.workload == "mid":
         try:
             cb = cpu_baseline_run()
             line["cpu_baseline"] = {"value": cb["s_per_iter"], "unit": "s/iter", "cores": cb["cores"],

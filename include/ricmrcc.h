@@ -219,6 +219,11 @@ RICMRCC_API int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out);
  * (kind_ms[3], host).  Diagnostic: launches are serialised by the events. */
 RICMRCC_API int ricmrcc_profile(ricmrcc_t* h, int reps, double* kind_ms);
 
+/* Launch only the `count` largest-FLOP contractions of the residual program
+ * (largest first), reading the operands left by the last residual.  For
+ * profilers that capture one representative launch; blocks until done. */
+RICMRCC_API int ricmrcc_run_largest_ops(ricmrcc_t* h, int count);
+
 /* Copy the stored amplitudes out / in (flat class layout, host pointers);
  * set_amplitudes allows warm starts and resuming an interrupted solve. */
 RICMRCC_API int ricmrcc_get_amplitudes(ricmrcc_t* h, double* T1, double* T2);

@@ -99,6 +99,7 @@ def load_library():
         "ricmrcc_plan_info": ([vp, ctypes.POINTER(PlanInfo)], ctypes.c_int),
         "ricmrcc_profile": ([vp, ctypes.c_int, vp], ctypes.c_int),
         "ricmrcc_set_amplitudes": ([vp, vp, vp], ctypes.c_int),
+        "ricmrcc_run_largest_ops": ([vp, ctypes.c_int], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)

@@ -736,6 +736,22 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
   return RICMRCC_OK;
 }
 
+int ricmrcc_run_largest_ops(ricmrcc_t* h, int count) {
+  if (!h || count < 0) return fail(h, RICMRCC_EINVAL, "bad arguments");
+  if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
+  TRY(enter(h));
+  std::vector<size_t> idx(h->res_prog.ops.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](size_t x, size_t y) {
+    return h->res_prog.ops[x].flops > h->res_prog.ops[y].flops;
+  });
+  // intermediates they read keep their values from the last full residual
+  for (int i = 0; i < count && i < (int)idx.size(); ++i)
+    launch_contract(h->res_prog.ops[idx[i]], h->res_prog.d_table, h->s);
+  CK(cudaStreamSynchronize(h->s));
+  return leave(h);
+}
+
 int ricmrcc_profile(ricmrcc_t* h, int reps, double* kind_ms) {
   if (!h || !kind_ms || reps < 1) return fail(h, RICMRCC_EINVAL, "bad arguments");
   if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
