@@ -180,8 +180,10 @@ def main():
         T = synthetic.make_amplitudes(w["n_core"], w["n_act"], w["n_virt"], seed=1, scale=0.02)
         g.residual(T)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("largest")
         g.lib.ricmrcc_run_largest_ops(g.h, args.ncu_largest)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         print(json.dumps({"ncu_largest": args.ncu_largest, "workload": w["workload"],
                           "residual_flops": info.residual_flops}))
         return 0
