@@ -229,6 +229,34 @@ RICMRCC_API int ricmrcc_run_largest_ops(ricmrcc_t* h, int count);
 RICMRCC_API int ricmrcc_get_amplitudes(ricmrcc_t* h, double* T1, double* T2);
 RICMRCC_API int ricmrcc_set_amplitudes(ricmrcc_t* h, const double* T1, const double* T2);
 
+/* Allocation-free eigensolver for one symmetric block (no counterpart in the
+ * paper; it is the eigen-step of ricmrcc_semicanonicalize offered on its own).
+ *
+ * For callers that cannot allocate device memory when they need it: code
+ * running while a stream is captured into a CUDA graph, services that reserve
+ * their whole device-memory budget up front, or hosts whose allocator belongs
+ * to another runtime.  The call allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library routine); its working memory is one fixed device array
+ * of 2 * RICMRCC_NOALLOC_MAX_N^2 doubles (16 MiB) inside the library, which
+ * every device that loads the library keeps until the process exits.
+ *
+ * A: device pointer to a symmetric n x n row-major matrix (read only).
+ * eigenvalues: device [n], ascending.  eigenvectors: device [n][n], column j
+ * belongs to eigenvalue j and its largest-magnitude component is positive
+ * (the conventions of ricmrcc_semicanonicalize).  stream: cudaStream_t (NULL
+ * = legacy default); the call returns once the work is enqueued.
+ * Returns EINVAL for NULL pointers, n < 1 or n > RICMRCC_NOALLOC_MAX_N, and
+ * ECUDA if the device address of the working array cannot be obtained.
+ *
+ * The first call on each device looks up that device's address of the
+ * working array (with the device current); make that first call before any
+ * stream capture.  All calls share the one working array: calls whose GPU
+ * work overlaps (different streams, or different host threads) race and
+ * corrupt each other's results; serialise them. */
+#define RICMRCC_NOALLOC_MAX_N 1024
+RICMRCC_API int ricmrcc_block_eigh_noalloc(const double* A, int n, double* eigenvalues,
+                                           double* eigenvectors, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -100,6 +100,7 @@ def load_library():
         "ricmrcc_profile": ([vp, ctypes.c_int, vp], ctypes.c_int),
         "ricmrcc_set_amplitudes": ([vp, vp, vp], ctypes.c_int),
         "ricmrcc_run_largest_ops": ([vp, ctypes.c_int], ctypes.c_int),
+        "ricmrcc_block_eigh_noalloc": ([vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
