@@ -227,19 +227,45 @@ def main():
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - c0) / e2e_steps
 
-    # roofline of the dominant contraction kernel (profiled after the timed region)
-    kind_ms = g.profile(reps=2)
+    # roofline of the dominant kernel (per-kernel CUDA-event profile after the
+    # timed region, on the library's stream)
+    mixed = prec == ric.MIXED
+    kind_ms = g.profile(reps=2, mixed=mixed)
     dom = int(np.argmax(kind_ms))
-    kind_names = ["contract_tile_64x64_fp64", "contract_tile_16x16_fp64", "contract_dot_fp64"]
-    achieved = info.kind_flops[dom] / (kind_ms[dom] / 1e3) / 1e12
-    pk = fp64_gemm_peak(torch) if rank == 0 else None
+    pk = peaks()
+    fp64_peak = fp64_gemm_peak(torch) if rank == 0 else None
     if rank != 0:
         return 0
-    roof = {"bound": "alu", "kernel": kind_names[dom], "achieved": achieved, "peak": pk,
-            "unit": "TFLOP/s", "frac": achieved / pk if pk else None, "traffic": None,
-            "peak_source": "cuBLAS DGEMM 8192^3 measured in this run (FP64 CUDA-core pipe)",
-            "launches_per_residual": int(info.kind_launches[dom]),
-            "ms_per_residual": float(kind_ms[dom])}
+    names = ["contract_tile_64x64_fp64", "contract_tile_16x16_fp64", "contract_dot_fp64",
+             "tc_pack_split_bf16", "tc_gemm_tcgen05_bf16x3"]
+    launches = [int(info.kind_launches[0]), int(info.kind_launches[1]), int(info.kind_launches[2]),
+                2 * int(info.tc_contractions), int(info.tc_contractions)]
+    if dom <= 2:
+        fl = None if mixed else info.kind_flops[dom]
+        roof = {"bound": "alu", "kernel": names[dom],
+                "achieved": None if fl is None else fl / (kind_ms[dom] / 1e3) / 1e12,
+                "peak": fp64_peak, "unit": "TFLOP/s",
+                "peak_source": "cuBLAS DGEMM 8192^3 measured in this run (FP64 CUDA-core pipe), of measured"}
+    elif dom == 3:
+        roof = {"bound": "hbm", "kernel": names[dom], "achieved": info.tc_pack_bytes / (kind_ms[3] / 1e3) / 1e9,
+                "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), of measured"}
+    else:
+        roof = {"bound": "tensor", "kernel": names[dom],
+                "achieved": 3.0 * info.tc_flops / (kind_ms[4] / 1e3) / 1e12,
+                "peak": pk.get("bf16_tflops_sustained", 1700.0), "unit": "TFLOP/s",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, sustained), of measured"}
+    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof["achieved"] and roof["peak"] else None
+    roof["traffic"] = None
+    roof["launches_per_residual"] = launches[dom]
+    roof["ms_per_residual"] = float(kind_ms[dom])
+    roof["profile_ms_per_residual"] = {n: float(x) for n, x in zip(names, kind_ms)}
+    tc = None
+    if mixed:
+        tc = {"contractions": int(info.tc_contractions), "fp64_equiv_flops": info.tc_flops,
+              "bf16_flops": 3.0 * info.tc_flops,
+              "gemm_tflops": 3.0 * info.tc_flops / (kind_ms[4] / 1e3) / 1e12 if kind_ms[4] else None,
+              "pack_gbs": info.tc_pack_bytes / (kind_ms[3] / 1e3) / 1e9 if kind_ms[3] else None}
     line = {"metric": METRIC, "value": s_per_iter, "unit": "s/iter", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == ric.FP64 else "bf16x3+f64",
@@ -251,7 +277,7 @@ def main():
             "e2e": {"value": e2e_s, "unit": "s/iter", "h2d_bytes_per_step": 8 * (lay.t1_size + lay.t2_size),
                     "d2h_bytes_per_step": 8 * (lay.t1_size + lay.t2_size)},
             "gpu_launches": int(info.step_launches) * args.steps,
-            "roofline": roof, "clocks": clk.summary()}
+            "roofline": roof, "clocks": clk.summary(), "tensor_core": tc}
     if not args.no_cpu_baseline and ws == 1 and args.workload == "mid":
         try:
             cb = cpu_baseline_run()

@@ -208,6 +208,9 @@ typedef struct {
   double table_bytes;        /* offset tables */
   int64_t kind_launches[3];  /* per contraction kernel: 0 = 64x64 tile, 1 = 16x16 tile, 2 = dot */
   double kind_flops[3];
+  int64_t tc_contractions;   /* contractions the RICMRCC_MIXED path runs on tensor cores */
+  double tc_flops;           /* their FP64-equivalent FLOPs (the BF16 GEMM does 3x) */
+  double tc_pack_bytes;      /* algorithmic bytes of their operand packing */
 } ricmrcc_plan_info_t;
 
 /* Sizes of the contraction program planned for this handle. */
@@ -215,9 +218,22 @@ RICMRCC_API int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out);
 
 /* Time the residual program kernel by kernel with CUDA events on the work
  * stream (reps repetitions, after the caller's warm-up) and return the mean
- * milliseconds per residual spent in each contraction kernel kind
- * (kind_ms[3], host).  Diagnostic: launches are serialised by the events. */
-RICMRCC_API int ricmrcc_profile(ricmrcc_t* h, int reps, double* kind_ms);
+ * milliseconds per residual in kind_ms[5] (host): FP64 64x64 tile, FP64
+ * 16x16 tile, FP64 dot reduction, and with mixed != 0 the tensor-core path's
+ * operand packing and tcgen05 GEMMs.  Diagnostic: events serialise launches. */
+RICMRCC_API int ricmrcc_profile(ricmrcc_t* h, int reps, int mixed, double* kind_ms);
+
+/* Split-precision BF16 tensor-core GEMM (the contraction engine of the
+ * RICMRCC_MIXED path, offered on its own):
+ *   C[m][n] += alpha * sum_k A[m][k] * B[n][k]
+ * A [M][lda], B [N][ldb], C [M][ldc]: row-major FP64 device arrays.  Each
+ * operand is split into BF16 hi + lo parts; the product keeps hi*hi, hi*lo and
+ * lo*hi (about 16 significant bits) with FP32 accumulation on tcgen05 tensor
+ * cores.  Allocates its own temporary device memory; synchronises `stream`.
+ * Returns EINVAL (bad sizes), ENOMEM, ENOTSUP (no tensor-map support), ECUDA. */
+RICMRCC_API int ricmrcc_gemm_bf16x3(const double* A, int64_t lda, const double* B, int64_t ldb,
+                                    double* C, int64_t ldc, int64_t M, int64_t N, int64_t K,
+                                    double alpha, void* stream);
 
 /* Launch only the `count` largest-FLOP contractions of the residual program
  * (largest first), reading the operands left by the last residual.  For

@@ -50,7 +50,9 @@ class PlanInfo(ctypes.Structure):
     _fields_ = [("residual_terms", ctypes.c_int64), ("residual_launches", ctypes.c_int64),
                 ("step_launches", ctypes.c_int64), ("residual_flops", ctypes.c_double),
                 ("arena_bytes", ctypes.c_double), ("table_bytes", ctypes.c_double),
-                ("kind_launches", ctypes.c_int64 * 3), ("kind_flops", ctypes.c_double * 3)]
+                ("kind_launches", ctypes.c_int64 * 3), ("kind_flops", ctypes.c_double * 3),
+                ("tc_contractions", ctypes.c_int64), ("tc_flops", ctypes.c_double),
+                ("tc_pack_bytes", ctypes.c_double)]
 
 
 class RicMrccError(RuntimeError):
@@ -97,9 +99,12 @@ def load_library():
         "ricmrcc_get_amplitudes": ([vp, vp, vp], ctypes.c_int),
         "ricmrcc_step": ([vp, ctypes.POINTER(Opts), ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
         "ricmrcc_plan_info": ([vp, ctypes.POINTER(PlanInfo)], ctypes.c_int),
-        "ricmrcc_profile": ([vp, ctypes.c_int, vp], ctypes.c_int),
+        "ricmrcc_profile": ([vp, ctypes.c_int, ctypes.c_int, vp], ctypes.c_int),
         "ricmrcc_set_amplitudes": ([vp, vp, vp], ctypes.c_int),
         "ricmrcc_run_largest_ops": ([vp, ctypes.c_int], ctypes.c_int),
+        "ricmrcc_gemm_bf16x3": ([vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                                 ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, vp],
+                                ctypes.c_int),
         "ricmrcc_block_eigh_noalloc": ([vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -277,9 +282,10 @@ def _plan_info(self):
     return info
 
 
-def _profile(self, reps=3):
-    ms = np.zeros(3)
-    self._check(self.lib.ricmrcc_profile(self.h, reps, _ptr(ms)))
+def _profile(self, reps=3, mixed=False):
+    """Mean ms per residual: [tile64, tile16, dot, tc_pack, tc_gemm]."""
+    ms = np.zeros(5)
+    self._check(self.lib.ricmrcc_profile(self.h, reps, int(mixed), _ptr(ms)))
     return ms
 
 

@@ -15,6 +15,7 @@
 #include "internal.h"
 #include "kernels.h"
 #include "planner.h"
+#include "tcgemm.h"
 
 #include "ric_terms.inc"
 
@@ -46,6 +47,15 @@ struct ricmrcc {
   int64_t *pack1 = nullptr, *pack2 = nullptr, *pack2b = nullptr;
   double *flat1 = nullptr, *flat2 = nullptr, *rflat1 = nullptr, *rflat2 = nullptr;
   double* arena = nullptr;
+  void* tc_scratch = nullptr;  // kLanes slices of tc_scratch_bytes
+  size_t tc_scratch_bytes = 0;
+  // concurrent lanes of the captured residual graph
+  cudaStream_t lane[8] = {nullptr};
+  cudaEvent_t lane_ev[9] = {nullptr};
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [fp64, mixed]
+  int* d_err = nullptr;
+  int64_t tc_ops = 0;
+  double tc_flops = 0.0;
   int64_t arena_elems = 0;
   double* host_scal = nullptr;  // pinned, 8 doubles
   int* d_sweeps = nullptr;
@@ -231,8 +241,76 @@ int plan(ricmrcc_t* h) {
   return RICMRCC_OK;
 }
 
-void run_program(ricmrcc_t* h, const Program& p) {
-  for (const auto& op : p.ops) launch_contract(op, p.d_table, h->s);
+// Contractions routed to the tensor cores in mixed precision: large, unbatched
+// GEMM-shaped ops (95% of the residual FLOPs at the Mid size).
+constexpr int kLanes = 8;
+
+bool tc_eligible(const ContractOp& op) {
+  return op.kind != 2 && op.L == 1 && op.M >= 128 && op.K >= 64 && op.flops >= 1e8;
+}
+
+int ensure_tc(ricmrcc_t* h) {
+  if (h->tc_scratch) return RICMRCC_OK;
+  if (!tc_available()) return fail(h, RICMRCC_ENOTSUP, "cuTensorMapEncodeTiled unavailable");
+  if (!tc_prepare()) return fail(h, RICMRCC_ECUDA, "tensor-core kernel attributes");
+  size_t need = 0;
+  h->tc_ops = 0;
+  h->tc_flops = 0.0;
+  for (const auto& op : h->res_prog.ops)
+    if (tc_eligible(op)) {
+      need = std::max(need, tc_scratch_bytes(op.M, op.N, op.K));
+      ++h->tc_ops;
+      h->tc_flops += op.flops;
+    }
+  if (need == 0) need = 256;
+  need = (need + 255) / 256 * 256;
+  cudaError_t e = cudaMalloc(&h->tc_scratch, need * kLanes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, RICMRCC_ENOMEM, "tensor-core scratch");
+  }
+  h->allocs.push_back(h->tc_scratch);
+  h->tc_scratch_bytes = need;  // per lane
+  return RICMRCC_OK;
+}
+
+TcArgs tc_args(ricmrcc_t* h, const Program& p, const ContractOp& op, int lane = 0) {
+  const int64_t* t = p.d_table + op.tab;
+  const int64_t* th = p.table.data() + op.tab;
+  TcArgs a;
+  a.A = op.A;
+  a.B = op.B;
+  a.C = op.C;
+  a.aL = th[0];
+  a.bL = th[1];
+  a.cL = th[2];
+  a.tAM = t + 3;
+  a.tCM = a.tAM + op.M;
+  a.tBN = a.tCM + op.M;
+  a.tCN = a.tBN + op.N;
+  a.tAK = a.tCN + op.N;
+  a.tBK = a.tAK + op.K;
+  a.M = op.M;
+  a.N = op.N;
+  a.K = op.K;
+  a.alpha = op.alpha;
+  a.scratch = static_cast<char*>(h->tc_scratch) + (size_t)lane * h->tc_scratch_bytes;
+  a.scratch_bytes = h->tc_scratch_bytes;
+  a.err = h->d_err;
+  return a;
+}
+
+int run_program(ricmrcc_t* h, const Program& p, bool mixed = false) {
+  for (const auto& op : p.ops) {
+    if (mixed && tc_eligible(op)) {
+      TcArgs a = tc_args(h, p, op);
+      const int rc = tc_contract(a, h->s);
+      if (rc != 0) return fail(h, RICMRCC_ECUDA, "tensor-core contraction launch failed (" + std::to_string(rc) + ")");
+    } else {
+      launch_contract(op, p.d_table, h->s);
+    }
+  }
+  return RICMRCC_OK;
 }
 
 int rebuild_reference(ricmrcc_t* h) {
@@ -297,18 +375,82 @@ int cumulants(ricmrcc_t* h, int kind) {
   if (kind == RICMRCC_RDM) {
     TRY(plan(h));
     CK(cudaMemsetAsync(h->arena, 0, sizeof(double) * h->arena_elems, h->s));
-    run_program(h, h->cum_prog);
+    TRY(run_program(h, h->cum_prog));
   }
   launch_direct3(h->D3, h->L3, a, h->s);
   return RICMRCC_OK;
 }
 
-int residual_device(ricmrcc_t* h) {
-  // X, E accumulators and intermediates start from zero
-  CK(cudaMemsetAsync(h->arena, 0, sizeof(double) * h->arena_elems, h->s));
-  CK(cudaMemsetAsync(h->X, 0, sizeof(double) * h->ng, h->s));
-  CK(cudaMemsetAsync(h->scal + 1, 0, sizeof(double), h->s));
-  run_program(h, h->res_prog);
+// Capture the residual program as a CUDA graph: zero the accumulators and the
+// intermediate arena, then run the contractions level by level, each level's
+// independent ops spread over kLanes streams (outputs accumulate atomically, so
+// ops of one level need no ordering; intermediates flow only to later levels).
+int capture_residual(ricmrcc_t* h, bool mixed) {
+  const Program& p = h->res_prog;
+  cudaStream_t s0 = h->lane[0];
+  CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
+  auto fail_capture = [&](int rc) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(s0, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return rc;
+  };
+  if (cudaMemsetAsync(h->arena, 0, sizeof(double) * h->arena_elems, s0) != cudaSuccess ||
+      cudaMemsetAsync(h->X, 0, sizeof(double) * h->ng, s0) != cudaSuccess ||
+      cudaMemsetAsync(h->scal + 1, 0, sizeof(double), s0) != cudaSuccess)
+    return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: memset"));
+  if (mixed && cudaMemsetAsync(h->d_err, 0, sizeof(int), s0) != cudaSuccess)
+    return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: memset"));
+  for (int lvl = 0; lvl <= p.max_level; ++lvl) {
+    // fork
+    cudaEventRecord(h->lane_ev[8], s0);
+    for (int l = 1; l < kLanes; ++l) cudaStreamWaitEvent(h->lane[l], h->lane_ev[8], 0);
+    int k = 0;
+    for (const auto& op : p.ops) {
+      if (op.level != lvl) continue;
+      const int l = k++ % kLanes;
+      if (mixed && tc_eligible(op)) {
+        TcArgs a = tc_args(h, p, op, l);
+        if (tc_contract(a, h->lane[l]) != 0)
+          return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: tensor-core launch"));
+      } else {
+        launch_contract(op, p.d_table, h->lane[l]);
+      }
+    }
+    // join
+    for (int l = 1; l < kLanes; ++l) {
+      cudaEventRecord(h->lane_ev[l], h->lane[l]);
+      cudaStreamWaitEvent(s0, h->lane_ev[l], 0);
+    }
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamEndCapture(s0, &g));
+  cudaGraphExec_t ex = nullptr;
+  const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, RICMRCC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  h->graph[mixed ? 1 : 0] = ex;
+  return RICMRCC_OK;
+}
+
+int residual_device(ricmrcc_t* h, bool mixed) {
+  if (mixed) TRY(ensure_tc(h));
+  cudaGraphExec_t& ex = h->graph[mixed ? 1 : 0];
+  if (!ex) TRY(capture_residual(h, mixed));
+  CK(cudaGraphLaunch(ex, h->s));
+  return RICMRCC_OK;
+}
+
+// After a mixed-precision residual: report a timed-out tensor-core pipeline.
+int check_tc_error(ricmrcc_t* h) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (e) return fail(h, RICMRCC_ECUDA, "tensor-core pipeline wait timed out");
   return RICMRCC_OK;
 }
 
@@ -347,6 +489,8 @@ static int create_impl(ricmrcc_t* h, int n_core, int n_act, int n_virt, int n_au
   d.nh = n_core + n_act;
   CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
+  for (int l = 0; l < 8; ++l) CK(cudaStreamCreateWithFlags(&h->lane[l], cudaStreamNonBlocking));
+  for (int l = 0; l < 9; ++l) CK(cudaEventCreateWithFlags(&h->lane_ev[l], cudaEventDisableTiming));
   const int64_t n = d.n, a = d.a;
   h->n2g = (int64_t)d.np * d.np * d.nh * d.nh;
   h->n1g = (int64_t)d.np * d.nh;
@@ -375,6 +519,7 @@ static int create_impl(ricmrcc_t* h, int n_core, int n_act, int n_virt, int n_au
   TRY(dalloc(h, &h->dots, 16));
   TRY(dalloc(h, &h->dstatus, 4));
   TRY(dalloc(h, &h->d_sweeps, 4));
+  TRY(dalloc(h, &h->d_err, 4));
   CK(cudaMallocHost(&h->host_scal, 8 * sizeof(double)));
   std::vector<int64_t> p1, p2, p2b;
   build_layout(h, p1, p2, p2b);
@@ -401,6 +546,12 @@ void ricmrcc_destroy(ricmrcc_t* h) {
   if (h->host_scal) cudaFreeHost(h->host_scal);
   if (h->hist_v) cudaFree(h->hist_v);
   if (h->hist_e) cudaFree(h->hist_e);
+  for (auto& g : h->graph)
+    if (g) cudaGraphExecDestroy(g);
+  for (auto& e : h->lane_ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& l : h->lane)
+    if (l) cudaStreamDestroy(l);
   if (h->ev) cudaEventDestroy(h->ev);
   if (h->s) cudaStreamDestroy(h->s);
   delete h;
@@ -418,7 +569,6 @@ int ricmrcc_set_precision(ricmrcc_t* h, int precision) {
   if (!h) return RICMRCC_EINVAL;
   if (precision != RICMRCC_FP64 && precision != RICMRCC_MIXED)
     return fail(h, RICMRCC_EINVAL, "precision must be RICMRCC_FP64 or RICMRCC_MIXED");
-  if (precision == RICMRCC_MIXED) return fail(h, RICMRCC_ENOTSUP, "mixed precision not built");
   h->precision = precision;
   return RICMRCC_OK;
 }
@@ -529,7 +679,9 @@ static int residual_impl(ricmrcc_t* h, const double* T1, const double* T2, doubl
     f2 = h->flat2;
   }
   scatter_amplitudes(h, f1, f2);
-  TRY(residual_device(h));
+  const bool mixed = h->precision == RICMRCC_MIXED;
+  TRY(residual_device(h, mixed));
+  if (mixed) TRY(check_tc_error(h));
   double* r1 = dev ? R1 : h->rflat1;
   double* r2 = dev ? R2 : h->rflat2;
   launch_gather(r1, h->X + h->n2g, h->pack1, nullptr, h->t1_size, h->s);
@@ -597,13 +749,14 @@ void reset_iteration_state(ricmrcc_t* h) {
 // then DIIS extrapolation over the stored (t_new, t_new - t) pairs.
 // *conv is set when the energy change and max |t_new - t| are below the
 // thresholds (T is then left at the converged iterate).
-int iterate(ricmrcc_t* h, const ricmrcc_opts& o, bool check, bool* conv, bool* diverged) {
+int iterate(ricmrcc_t* h, const ricmrcc_opts& o, bool check, bool mixed, bool* conv, bool* diverged) {
   *conv = false;
   *diverged = false;
   const int cap = o.diis_size > 0 ? o.diis_size : 1;
   TRY(ensure_diis(h, cap));
   ++h->iter;
-  TRY(residual_device(h));
+  TRY(residual_device(h, mixed));
+  if (mixed) TRY(check_tc_error(h));
   CK(cudaMemsetAsync(h->scal + 2, 0, sizeof(double), h->s));
   launch_update(h->T, h->X, h->Tn, h->Err, h->eps, h->d, o.s, h->scal + 2, h->s);
   CK(cudaMemcpyAsync(h->host_scal, h->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
@@ -659,7 +812,8 @@ int check_opts(ricmrcc_t* h, const ricmrcc_opts& o) {
   if (!(o.s >= 0.0) || !isfinite(o.s) || o.max_iter < 1 || o.diis_size < 0 || o.diis_size > 16)
     return fail(h, RICMRCC_EINVAL, "bad options (s >= 0, max_iter >= 1, 0 <= diis_size <= 16)");
   if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
-  if (o.precision == RICMRCC_MIXED) return fail(h, RICMRCC_ENOTSUP, "mixed precision not built");
+  if (o.precision != RICMRCC_FP64 && o.precision != RICMRCC_MIXED)
+    return fail(h, RICMRCC_EINVAL, "precision must be RICMRCC_FP64 or RICMRCC_MIXED");
   return RICMRCC_OK;
 }
 
@@ -677,9 +831,16 @@ int ricmrcc_solve(ricmrcc_t* h, const ricmrcc_opts* opts, double* E_out, ricmrcc
   const auto t0 = std::chrono::steady_clock::now();
   reset_iteration_state(h);
   bool converged = false, diverged = false;
-  int it = 0;
+  int it = 0, n_mixed = 0;
+  // mixed precision: tensor-core iterations until max|dt| < refine_tol, then
+  // FP64 refinement iterations until the FP64 convergence test passes
+  bool mixed = o.precision == RICMRCC_MIXED;
   for (it = 1; it <= o.max_iter; ++it) {
-    TRY(iterate(h, o, true, &converged, &diverged));
+    TRY(iterate(h, o, !mixed, mixed, &converged, &diverged));
+    if (mixed) {
+      ++n_mixed;
+      if (!diverged && h->last_dt < o.refine_tol) mixed = false;
+    }
     if (converged || diverged) break;
   }
   if (it > o.max_iter) it = o.max_iter;
@@ -688,8 +849,8 @@ int ricmrcc_solve(ricmrcc_t* h, const ricmrcc_opts* opts, double* E_out, ricmrcc
   if (stats) {
     stats->iterations = it;
     stats->converged = converged ? 1 : 0;
-    stats->fp64_iterations = it;
-    stats->mixed_iterations = 0;
+    stats->fp64_iterations = it - n_mixed;
+    stats->mixed_iterations = n_mixed;
     stats->energy = h->last_E;
     stats->e0 = h->E0;
     stats->max_dt = h->last_dt;
@@ -712,7 +873,8 @@ int ricmrcc_step(ricmrcc_t* h, const ricmrcc_opts* opts, int n_steps, int restar
   TRY(enter(h));
   if (restart) reset_iteration_state(h);
   bool conv = false, div = false;
-  for (int i = 0; i < n_steps && !div; ++i) TRY(iterate(h, o, false, &conv, &div));
+  const bool mixed = o.precision == RICMRCC_MIXED || h->precision == RICMRCC_MIXED;
+  for (int i = 0; i < n_steps && !div; ++i) TRY(iterate(h, o, false, mixed, &conv, &div));
   if (E_out) *E_out = h->last_E;
   if (max_dt_out) *max_dt_out = h->last_dt;
   TRY(leave(h));
@@ -732,8 +894,71 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
   for (const auto& op : h->res_prog.ops) {
     out->kind_launches[op.kind] += 1;
     out->kind_flops[op.kind] += op.flops;
+    if (tc_eligible(op)) {
+      out->tc_contractions += 1;
+      out->tc_flops += op.flops;
+      out->tc_pack_bytes += tc_pack_bytes(op.M, op.N, op.K);
+    }
   }
   return RICMRCC_OK;
+}
+
+int ricmrcc_gemm_bf16x3(const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
+                        int64_t ldc, int64_t M, int64_t N, int64_t K, double alpha, void* stream) {
+  if (!A || !B || !C || M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldc < N) return RICMRCC_EINVAL;
+  if (M == 0 || N == 0 || K == 0) return RICMRCC_OK;
+  if (!tc_available()) return RICMRCC_ENOTSUP;
+  if (!tc_prepare()) return RICMRCC_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // offset tables of the plain row-major layouts
+  std::vector<int64_t> t;
+  t.reserve(2 * M + 2 * N + 2 * K);
+  for (int64_t m = 0; m < M; ++m) t.push_back(m * lda);
+  for (int64_t m = 0; m < M; ++m) t.push_back(m * ldc);
+  for (int64_t n = 0; n < N; ++n) t.push_back(n * ldb);
+  for (int64_t n = 0; n < N; ++n) t.push_back(n);
+  for (int64_t k = 0; k < K; ++k) t.push_back(k);
+  for (int64_t k = 0; k < K; ++k) t.push_back(k);
+  int64_t* dt = nullptr;
+  int* derr = nullptr;
+  void* scratch = nullptr;
+  const size_t sb = tc_scratch_bytes(M, N, K);
+  int rc = RICMRCC_OK;
+  if (cudaMalloc(&dt, sizeof(int64_t) * t.size()) != cudaSuccess || cudaMalloc(&derr, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&scratch, sb) != cudaSuccess) {
+    cudaGetLastError();
+    rc = RICMRCC_ENOMEM;
+  }
+  if (rc == RICMRCC_OK) {
+    cudaMemcpyAsync(dt, t.data(), sizeof(int64_t) * t.size(), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(derr, 0, sizeof(int), s);
+    TcArgs a;
+    a.A = A;
+    a.B = B;
+    a.C = C;
+    a.aL = a.bL = a.cL = 0;
+    a.tAM = dt;
+    a.tCM = dt + M;
+    a.tBN = dt + 2 * M;
+    a.tCN = dt + 2 * M + N;
+    a.tAK = dt + 2 * M + 2 * N;
+    a.tBK = a.tAK + K;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.alpha = alpha;
+    a.scratch = scratch;
+    a.scratch_bytes = sb;
+    a.err = derr;
+    if (tc_contract(a, s) != 0) rc = RICMRCC_ECUDA;
+    int e = 0;
+    cudaMemcpyAsync(&e, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess || e) rc = RICMRCC_ECUDA;
+  }
+  cudaFree(dt);
+  cudaFree(derr);
+  cudaFree(scratch);
+  return rc;
 }
 
 int ricmrcc_run_largest_ops(ricmrcc_t* h, int count) {
@@ -752,33 +977,51 @@ int ricmrcc_run_largest_ops(ricmrcc_t* h, int count) {
   return leave(h);
 }
 
-int ricmrcc_profile(ricmrcc_t* h, int reps, double* kind_ms) {
+int ricmrcc_profile(ricmrcc_t* h, int reps, int mixed, double* kind_ms) {
   if (!h || !kind_ms || reps < 1) return fail(h, RICMRCC_EINVAL, "bad arguments");
   if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
   TRY(enter(h));
-  const size_t nops = h->res_prog.ops.size();
-  std::vector<cudaEvent_t> ev(nops + 1);
+  if (mixed) TRY(ensure_tc(h));
+  const Program& p = h->res_prog;
+  const size_t nops = p.ops.size();
+  std::vector<cudaEvent_t> ev(2 * nops + 1);
   for (auto& e : ev) CK(cudaEventCreate(&e));
-  for (int k = 0; k < 3; ++k) kind_ms[k] = 0.0;
+  for (int k = 0; k < 5; ++k) kind_ms[k] = 0.0;
   for (int r = 0; r < reps; ++r) {
     CK(cudaMemsetAsync(h->arena, 0, sizeof(double) * h->arena_elems, h->s));
     CK(cudaMemsetAsync(h->X, 0, sizeof(double) * h->ng, h->s));
     CK(cudaMemsetAsync(h->scal + 1, 0, sizeof(double), h->s));
+    if (mixed) CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
     for (size_t i = 0; i < nops; ++i) {
-      CK(cudaEventRecord(ev[i], h->s));
-      launch_contract(h->res_prog.ops[i], h->res_prog.d_table, h->s);
+      CK(cudaEventRecord(ev[2 * i], h->s));
+      const ContractOp& op = p.ops[i];
+      if (mixed && tc_eligible(op)) {
+        TcArgs a = tc_args(h, p, op);
+        if (tc_contract_timed(a, h->s, &ev[2 * i + 1]) != 0) return fail(h, RICMRCC_ECUDA, "tc launch");
+      } else {
+        launch_contract(op, p.d_table, h->s);
+        CK(cudaEventRecord(ev[2 * i + 1], h->s));
+      }
     }
-    CK(cudaEventRecord(ev[nops], h->s));
-    CK(cudaEventSynchronize(ev[nops]));
+    CK(cudaEventRecord(ev[2 * nops], h->s));
+    CK(cudaEventSynchronize(ev[2 * nops]));
     for (size_t i = 0; i < nops; ++i) {
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, ev[i], ev[i + 1]));
-      kind_ms[h->res_prog.ops[i].kind] += ms / reps;
+      float a = 0.f, b = 0.f;
+      CK(cudaEventElapsedTime(&a, ev[2 * i], ev[2 * i + 1]));
+      CK(cudaEventElapsedTime(&b, ev[2 * i + 1], ev[2 * i + 2]));
+      if (mixed && tc_eligible(p.ops[i])) {
+        kind_ms[3] += a / reps;  // packing
+        kind_ms[4] += b / reps;  // tensor-core GEMM
+      } else {
+        kind_ms[p.ops[i].kind] += (a + b) / reps;
+      }
     }
   }
   for (auto& e : ev) cudaEventDestroy(e);
+  if (mixed) TRY(check_tc_error(h));
   return leave(h);
 }
+
 
 int ricmrcc_get_amplitudes(ricmrcc_t* h, double* T1, double* T2) {
   if (!h || !T1 || !T2) return fail(h, RICMRCC_EINVAL, "null pointer");

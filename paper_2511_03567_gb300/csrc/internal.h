@@ -86,6 +86,7 @@ struct ContractOp {
   int64_t kchunk;
   double flops;
   int arena = 0;  // bit 0/1/2: A/B/C hold arena offsets until Planner::finalize
+  int level = 0;  // 1 + the highest level of the ops producing its arena inputs
 };
 
 struct Program {
@@ -94,6 +95,7 @@ struct Program {
   int64_t* d_table = nullptr;
   double flops = 0.0;
   size_t n_terms = 0;
+  int max_level = 0;
 };
 
 // kernels.cu

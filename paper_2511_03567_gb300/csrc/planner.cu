@@ -174,6 +174,19 @@ void Planner::emit(const Operand& A, const Operand& B, const Operand& C, const i
   op.kchunk = (K + op.ksplit - 1) / op.ksplit;
   op.flops = 2.0 * (double)L * (double)M * (double)N * (double)K;
   op.arena = arena_flags;
+  // dependency level: operands in the arena were produced by earlier ops
+  int lvl = 0;
+  if (arena_flags & 1) {
+    auto it = producer_level_.find(reinterpret_cast<int64_t>(op.A));
+    if (it != producer_level_.end()) lvl = std::max(lvl, it->second + 1);
+  }
+  if (arena_flags & 2) {
+    auto it = producer_level_.find(reinterpret_cast<int64_t>(op.B));
+    if (it != producer_level_.end()) lvl = std::max(lvl, it->second + 1);
+  }
+  op.level = lvl;
+  if (arena_flags & 4) producer_level_[reinterpret_cast<int64_t>(op.C)] = lvl;
+  prog->max_level = std::max(prog->max_level, lvl);
   prog->ops.push_back(op);
   prog->flops += op.flops;
 }

@@ -33,4 +33,5 @@ class Planner {
   std::map<std::string, int64_t> cse_;
   int64_t arena_size_ = 0;
   int64_t cse_hits_ = 0;
+  std::map<int64_t, int> producer_level_;  // arena offset -> level of its producing op
 };

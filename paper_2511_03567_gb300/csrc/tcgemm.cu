@@ -1,0 +1,372 @@
+// Split-precision BF16 tensor-core contractions (tcgen05 + TMA, sm_103a).
+//
+// C[l?, m, n] += alpha * sum_k A[m, k] B[n, k] for one planned contraction:
+//  1. pack: A and B are gathered through the contraction's offset tables into
+//     K-major BF16 matrices.  Each FP64 value x is split x = hi + lo (hi =
+//     bf16(x), lo = bf16(x - hi)); the K axis holds three segments, A as
+//     [hi | hi | lo] and B as [hi | lo | hi], so one GEMM of depth 3K gives
+//     hi*hi + hi*lo + lo*hi (the split-precision product; lo*lo is dropped).
+//  2. GEMM: TMA loads 128 x 64 (A) and BN x 64 (B) BF16 tiles with the 128-byte
+//     swizzle into a 4-stage shared-memory ring; one thread issues
+//     tcgen05.mma (M = 128, N = BN, K = 16) into an FP32 accumulator in TMEM;
+//     tcgen05.commit releases stages back to the TMA producer.
+//  3. epilogue: four warps read the accumulator with tcgen05.ld (one TMEM lane
+//     per output row) and add alpha * C to the FP64 destination through the
+//     output offset tables (atomic, so split-K CTAs and terms accumulate).
+// Every mbarrier wait is bounded by the global timer; on timeout the kernel
+// records an error, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "tcgemm.h"
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;  // 64 BF16 = 128 bytes: one swizzle atom row
+constexpr int STAGES = 4;
+constexpr uint64_t kWaitNs = 4000000000ull;  // 4 s bound on every wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+               : "memory");
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
+  const uint32_t a = smem_u32(b);
+  const uint64_t t0 = gtime();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (*(volatile int*)err) return false;
+    if (gtime() - t0 > kWaitNs) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row swizzle atoms 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);      // start address
+  d |= (uint64_t)1 << 16;                      // leading byte offset (unused with swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: BF16 x BF16 -> FP32, both
+// operands K-major, shape BM x BN.
+template <int BN>
+__device__ __forceinline__ uint32_t instr_desc() {
+  return (1u << 4)                  // D = F32
+         | (1u << 7)                // A = BF16
+         | (1u << 10)               // B = BF16
+         | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              int kt_per_split, int kt_total, int64_t M, int64_t N, int mtiles, int ntiles,
+              double* __restrict__ C, const int64_t* __restrict__ tCM, const int64_t* __restrict__ tCN,
+              int64_t cL, double alpha, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * BM * BK * 2;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * BN * BK * 2);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int t = blockIdx.x;
+  const int mi = t % mtiles;
+  t /= mtiles;
+  const int ni = t % ntiles;
+  const int ks = t / ntiles;
+  const int kt0 = ks * kt_per_split;
+  const int kt1 = min(kt_total, kt0 + kt_per_split);
+  const int nkt = kt1 - kt0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (nkt > 0) {
+    if (warp == 0 && lane == 0) {
+      // TMA producer
+      for (int i = 0; i < nkt; ++i) {
+        const int s = i % STAGES;
+        if (i >= STAGES && !mbar_wait(empty + s, ((i / STAGES) - 1) & 1, err)) break;
+        mbar_expect_tx(full + s, (BM + BN) * BK * 2);
+        const int kx = (kt0 + i) * BK;
+        tma_load_2d(sA + s * BM * BK * 2, &tmA, kx, mi * BM, full + s);
+        tma_load_2d(sB + s * BN * BK * 2, &tmB, kx, ni * BN, full + s);
+      }
+    } else if (warp == 1 && lane == 0) {
+      // MMA issuer
+      const uint32_t idesc = instr_desc<BN>();
+      bool ok = true;
+      for (int i = 0; i < nkt; ++i) {
+        const int s = i % STAGES;
+        if (!mbar_wait(full + s, (i / STAGES) & 1, err)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(sA + s * BM * BK * 2);
+        const uint32_t b0 = smem_u32(sB + s * BN * BK * 2);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint64_t ad = smem_desc(a0 + k * 32);
+          const uint64_t bd = smem_desc(b0 + k * 32);
+          const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(empty + s))
+                     : "memory");
+      }
+      // always signal completion of the MMAs issued so far (also after a
+      // timeout), so the epilogue never frees TMEM under a running MMA
+      (void)ok;
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(done))
+                   : "memory");
+    }
+    __syncwarp();
+    // epilogue: warp w owns TMEM lanes 32w .. 32w+31 (output rows)
+    const bool ready = mbar_wait(done, 0, err);
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ready && !*(volatile int*)err) {
+      const int64_t m = (int64_t)mi * BM + warp * 32 + lane;
+      const int64_t cm = m < M ? tCM[m] : 0;
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+              "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+              "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+              "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (m < M) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t n = (int64_t)ni * BN + c + j;
+            const float v = __uint_as_float(r[j]);
+            if (n < N && v != 0.0f) atomicAdd(C + cL + cm + tCN[n], alpha * (double)v);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+}
+
+// Gather one operand through offset tables and split it into BF16 hi/lo:
+// out[r][seg * Kp + k], r < rows_pad, three segments with pattern `pat`
+// (bit s set: segment s holds lo, else hi).  Pad rows/columns are zero.
+__global__ void k_pack_split(const double* __restrict__ X, int64_t xL, const int64_t* __restrict__ tR,
+                             const int64_t* __restrict__ tK, int64_t rows, int64_t K, int64_t rows_pad,
+                             int64_t Kp, int pat, __nv_bfloat16* __restrict__ out) {
+  for (int64_t r = blockIdx.x; r < rows_pad; r += gridDim.x) {
+    const bool live = r < rows;
+    const int64_t base = live ? xL + tR[r] : 0;
+    __nv_bfloat16* row = out + r * 3 * Kp;
+    for (int64_t k = threadIdx.x; k < Kp; k += blockDim.x) {
+      const double x = (live && k < K) ? X[base + tK[k]] : 0.0;
+      const __nv_bfloat16 hi = __double2bfloat16(x);
+      const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+      row[k] = (pat & 1) ? lo : hi;
+      row[Kp + k] = (pat & 2) ? lo : hi;
+      row[2 * Kp + k] = (pat & 4) ? lo : hi;
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool get_encode() {
+  if (g_encode) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess || !fn ||
+      q != cudaDriverEntryPointSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return true;
+}
+
+bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, int box_rows) {
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(inner * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+size_t smem_bytes() {
+  return 1024 + (size_t)STAGES * (BM + BN) * BK * 2 + (2 * STAGES + 1) * 8 + 16;
+}
+
+template <int BN>
+int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int64_t M, int64_t N, int64_t Mp, int64_t Np,
+              int kt_total, double* C, const int64_t* tCM, const int64_t* tCN, int64_t cL, double alpha,
+              int* err, cudaStream_t s) {
+  const int mt = (int)(Mp / BM), nt = (int)(Np / BN);
+  const int tiles = mt * nt;
+  int ksplit = 1;
+  if (tiles < 2 * 152) ksplit = (2 * 152 + tiles - 1) / tiles;
+  if (ksplit > kt_total) ksplit = kt_total;
+  if (ksplit < 1) ksplit = 1;
+  const int kps = (kt_total + ksplit - 1) / ksplit;
+  ksplit = (kt_total + kps - 1) / kps;
+  k_tc_gemm<BN><<<tiles * ksplit, 128, smem_bytes<BN>(), s>>>(ma, mb, kps, kt_total, M, N, mt, nt, C, tCM, tCN,
+                                                               cL, alpha, err);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace
+
+int tc_pick_bn(int64_t N) {
+  if (N <= 32) return 32;
+  if (N <= 64) return 64;
+  if (N <= 128) return 128;
+  return 256;
+}
+
+int64_t tc_pad(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+bool tc_available() { return get_encode(); }
+
+// Opt the GEMM kernels into their dynamic shared memory (outside any graph
+// capture, before the first launch on the current device).
+bool tc_prepare() {
+  if (!get_encode()) return false;
+  bool ok = cudaFuncSetAttribute(k_tc_gemm<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes<32>()) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_tc_gemm<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<64>()) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<128>()) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem_bytes<256>()) == cudaSuccess;
+  if (!ok) cudaGetLastError();
+  return ok;
+}
+
+int tc_contract(const TcArgs& a, cudaStream_t s) { return tc_contract_timed(a, s, nullptr); }
+
+int tc_contract_timed(const TcArgs& a, cudaStream_t s, cudaEvent_t* mid) {
+  if (!get_encode()) return -2;
+  static bool prepared = false;  // callers inside a capture prepared beforehand
+  if (!prepared) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &st);
+    if (st == cudaStreamCaptureStatusNone) {
+      if (!tc_prepare()) return -1;
+      prepared = true;
+    }
+  }
+  const int bn = tc_pick_bn(a.N);
+  const int64_t Mp = tc_pad(a.M, BM), Np = tc_pad(a.N, bn), Kp = tc_pad(a.K, BK);
+  const int64_t inner = 3 * Kp;
+  if ((size_t)(Mp + Np) * inner * 2 > a.scratch_bytes) return -3;
+  __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(a.scratch);
+  __nv_bfloat16* pb = pa + Mp * inner;
+  const int threads = 256;
+  auto rgrid = [](int64_t rows) { return (int)std::min<int64_t>(rows, 152 * 16); };
+  k_pack_split<<<rgrid(Mp), threads, 0, s>>>(a.A, a.aL, a.tAM, a.tAK, a.M, a.K, Mp, Kp, 0b100, pa);
+  k_pack_split<<<rgrid(Np), threads, 0, s>>>(a.B, a.bL, a.tBN, a.tBK, a.N, a.K, Np, Kp, 0b010, pb);
+  if (mid) cudaEventRecord(*mid, s);
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, pa, inner, Mp, BM) || !make_map(&mb, pb, inner, Np, bn)) return -4;
+  const int kt_total = (int)(inner / BK);
+  switch (bn) {
+    case 32: return launch_tc<32>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.err, s);
+    case 64: return launch_tc<64>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.err, s);
+    case 128: return launch_tc<128>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.err, s);
+    default: return launch_tc<256>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.err, s);
+  }
+}
+
+size_t tc_scratch_bytes(int64_t M, int64_t N, int64_t K) {
+  const int bn = tc_pick_bn(N);
+  return (size_t)(tc_pad(M, BM) + tc_pad(N, bn)) * 3 * tc_pad(K, BK) * 2;
+}
+
+double tc_pack_bytes(int64_t M, int64_t N, int64_t K) {
+  // algorithmic bytes of the packing step: read both FP64 operands once,
+  // write the padded three-segment BF16 copies
+  const int bn = tc_pick_bn(N);
+  return 8.0 * (double)(M + N) * (double)K +
+         2.0 * 3.0 * (double)(tc_pad(M, BM) + tc_pad(N, bn)) * (double)tc_pad(K, BK);
+}

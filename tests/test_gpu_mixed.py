@@ -1,0 +1,57 @@
+"""Split-precision tensor-core path (tcgen05) against FP64."""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import ricmrcc as o
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (300, 40, 100), (1000, 257, 999), (77, 33, 130),
+                                   (4624, 16, 4096)])
+def test_gemm_bf16x3_matches_fp64(M, N, K):
+    import torch
+
+    import paper_2511_03567_gb300 as ric
+    lib = ric.load_library()
+    rng = np.random.default_rng(M + N + K)
+    A = rng.normal(size=(M, K))
+    B = rng.normal(size=(N, K))
+    C0 = rng.normal(size=(M, N))
+    dA, dB, dC = (torch.tensor(x, device="cuda") for x in (A, B, C0))
+    rc = lib.ricmrcc_gemm_bf16x3(dA.data_ptr(), K, dB.data_ptr(), K, dC.data_ptr(), N, M, N, K, 0.5,
+                                 torch.cuda.current_stream().cuda_stream)
+    assert rc == ric.OK
+    ref = C0 + 0.5 * A @ B.T
+    err = np.abs(dC.cpu().numpy() - ref).max()
+    # three BF16 products keep ~16 significant bits per product; FP32 accumulation
+    assert err < 2e-4 * np.sqrt(K), err
+    assert err > 0.0  # really the reduced-precision path
+
+
+def _prof_problem():
+    nc, na, nv, nx = 4, 4, 64, 200
+    p = synthetic.make_problem(nc, na, nv, nx, None, 0)
+    return p
+
+
+def test_mixed_residual_close_to_fp64():
+    import paper_2511_03567_gb300 as ric
+    p = _prof_problem()
+    g = ric.RicMrcc(p.n_core, p.n_act, p.n_virt, p.n_aux)
+    g.set_integrals(p.h, p.B)
+    g.set_rdms(p.G1, p.G2, p.G3)
+    g.semicanonicalize()
+    info = g.plan_info()
+    assert info.tc_contractions > 0 and info.tc_flops > 0.2 * info.residual_flops
+    T = synthetic.make_amplitudes(p.n_core, p.n_act, p.n_virt, seed=1, scale=0.02)
+    R64, E64 = g.residual(T)
+    g.set_precision(ric.MIXED)
+    Rm, Em = g.residual(T)
+    g.set_precision(ric.FP64)
+    scale = max(np.abs(R64[k]).max() for k in R64 if R64[k].size)
+    worst = max(np.abs(R64[k] - Rm[k]).max() for k in R64 if R64[k].size)
+    assert worst < 1e-4 * scale, (worst, scale)
+    assert worst > 0.0
+    assert abs(E64 - Em) < 1e-6
