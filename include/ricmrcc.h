@@ -240,6 +240,19 @@ RICMRCC_API int ricmrcc_gemm_bf16x3(const double* A, int64_t lda, const double* 
  * profilers that capture one representative launch; blocks until done. */
 RICMRCC_API int ricmrcc_run_largest_ops(ricmrcc_t* h, int count);
 
+/* Hand-written adjoint of the converged solve (Sec. 2.2 fixed point of Eq.
+ * ric-update): with G(T) = (T Delta + R(T)) phi - T, phi = (1 - exp(-s Delta^2))
+ * / Delta, the multipliers solve Lam = (dU/dT)^T Lam + dE/dT (U = G + T, the
+ * transposed fixed-point iteration, DIIS-accelerated), and
+ *   dE/dtheta = dE/dtheta|_T + Lam . dG/dtheta
+ * through the generalized Fock matrix, E0, the integrals and Delta (eps = diag f,
+ * the basis is held fixed: no re-canonicalisation).  Outputs (host, nullable):
+ * dE_dh [n][n] and dE_dB [n_aux][n][n] with every entry treated as independent
+ * (for the symmetric parameters add the transposed entry), dE_ds scalar.
+ * Requires the last ricmrcc_solve to have converged (else ESTATE); uses its
+ * flow s and options.  Returns NOT_CONVERGED / DIVERGED for the multipliers. */
+RICMRCC_API int ricmrcc_energy_backward(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds);
+
 /* Copy the stored amplitudes out / in (flat class layout, host pointers);
  * set_amplitudes allows warm starts and resuming an interrupted solve. */
 RICMRCC_API int ricmrcc_get_amplitudes(ricmrcc_t* h, double* T1, double* T2);

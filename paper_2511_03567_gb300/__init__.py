@@ -102,6 +102,7 @@ def load_library():
         "ricmrcc_profile": ([vp, ctypes.c_int, ctypes.c_int, vp], ctypes.c_int),
         "ricmrcc_set_amplitudes": ([vp, vp, vp], ctypes.c_int),
         "ricmrcc_run_largest_ops": ([vp, ctypes.c_int], ctypes.c_int),
+        "ricmrcc_energy_backward": ([vp, vp, vp, vp], ctypes.c_int),
         "ricmrcc_gemm_bf16x3": ([vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, vp],
                                 ctypes.c_int),
@@ -289,6 +290,17 @@ def _profile(self, reps=3, mixed=False):
     return ms
 
 
+def _energy_backward(self):
+    """(dE/dh [n,n], dE/dB [n_aux,n,n], dE/ds) of the last converged solve."""
+    n = sum(self.dims[:3])
+    dh = np.zeros((n, n))
+    dB = np.zeros((self.dims[3], n, n))
+    ds = ctypes.c_double()
+    self._check(self.lib.ricmrcc_energy_backward(self.h, _ptr(dh), _ptr(dB), ctypes.byref(ds)))
+    return dh, dB, ds.value
+
+
+RicMrcc.energy_backward = _energy_backward
 RicMrcc.step = _step
 RicMrcc.plan_info = _plan_info
 RicMrcc.profile = _profile

@@ -66,6 +66,14 @@ struct ricmrcc {
   int diis_cap = 8;
 
   Program res_prog, cum_prog;
+  // adjoint (energy_backward)
+  Program gradt_prog, gradh_prog;
+  bool adj_planned = false, solved = false;
+  double solved_s = 0.0;
+  ricmrcc_opts solved_opts{};
+  double *Lam = nullptr, *Yraw = nullptr, *Ytil = nullptr, *GT = nullptr, *gF = nullptr, *gFt = nullptr,
+         *gh = nullptr, *geps = nullptr, *geri = nullptr, *gB = nullptr, *adj_arena = nullptr;
+  int64_t adj_arena_elems = 0;
   bool have_ints = false, have_rdms = false, planned = false;
   double E0 = 0.0;
   int rdm_kind = RICMRCC_RDM;
@@ -585,6 +593,7 @@ static int set_integrals_impl(ricmrcc_t* h, const double* hm, const double* B, b
   CK(cudaMemcpyAsync(h->B, B, sizeof(double) * n2 * d.X, k, h->s));
   TRY(build_eri(h));
   h->have_ints = true;
+  h->solved = false;
   TRY(rebuild_reference(h));
   return leave(h);
 }
@@ -615,6 +624,7 @@ static int set_rdms_impl(ricmrcc_t* h, const double* g1, const double* g2, const
   TRY(cumulants(h, kind));
   h->rdm_kind = kind;
   h->have_rdms = true;
+  h->solved = false;
   CK(cudaMemsetAsync(h->T, 0, sizeof(double) * h->ng, h->s));
   TRY(rebuild_reference(h));
   return leave(h);
@@ -857,6 +867,9 @@ int ricmrcc_solve(ricmrcc_t* h, const ricmrcc_opts* opts, double* E_out, ricmrcc
     stats->seconds = secs;
   }
   TRY(leave(h));
+  h->solved = converged;
+  h->solved_s = o.s;
+  h->solved_opts = o;
   if (diverged) return fail(h, RICMRCC_DIVERGED, "non-finite energy or amplitude change");
   if (!converged) return fail(h, RICMRCC_NOT_CONVERGED, "max_iter reached");
   return RICMRCC_OK;
@@ -1036,6 +1049,7 @@ int ricmrcc_get_amplitudes(ricmrcc_t* h, double* T1, double* T2) {
 
 int ricmrcc_set_amplitudes(ricmrcc_t* h, const double* T1, const double* T2) {
   if (!h || !T1 || !T2) return fail(h, RICMRCC_EINVAL, "null pointer");
+  h->solved = false;
   if (!finite_host(T1, h->t1_size) || !finite_host(T2, h->t2_size))
     return fail(h, RICMRCC_EINVAL, "non-finite amplitudes");
   TRY(enter(h));
@@ -1142,6 +1156,194 @@ int ricmrcc_semicanonicalize(ricmrcc_t* h, double* U_out) {
   TRY(cumulants(h, h->rdm_kind));
   CK(cudaMemsetAsync(h->T, 0, sizeof(double) * h->ng, h->s));
   TRY(rebuild_reference(h));
+  return leave(h);
+}
+
+
+}  // extern "C"
+
+namespace {
+
+int plan_adjoint(ricmrcc_t* h) {
+  if (h->adj_planned) return RICMRCC_OK;
+  const Dims& d = h->d;
+  const int64_t n = d.n, np = d.np, nh = d.nh, a = d.a, n4 = n * n * n * n;
+  TRY(dalloc(h, &h->Lam, h->ng));
+  TRY(dalloc(h, &h->Yraw, h->ng));
+  TRY(dalloc(h, &h->Ytil, h->ng));
+  TRY(dalloc(h, &h->GT, h->ng));
+  TRY(dalloc(h, &h->gF, n * n));
+  TRY(dalloc(h, &h->gFt, n * n));
+  TRY(dalloc(h, &h->gh, n * n));
+  TRY(dalloc(h, &h->geps, n));
+  TRY(dalloc(h, &h->geri, n4));
+  TRY(dalloc(h, &h->gB, (int64_t)d.X * n * n));
+  TensorView tv[NTENSOR], ov[NOUT];
+  auto set = [](TensorView& t, double* base, std::initializer_list<int> dom, std::initializer_list<int64_t> st) {
+    t.base = base;
+    t.nax = (int)dom.size();
+    int i = 0;
+    for (int x : dom) t.dom[i++] = x;
+    i = 0;
+    for (int64_t x : st) t.stride[i++] = x;
+  };
+  set(tv[TF], h->F, {DOM_G, DOM_G}, {n, 1});
+  set(tv[TV], h->eri, {DOM_G, DOM_G, DOM_G, DOM_G}, {n * n * n, n, n * n, 1});
+  set(tv[TT1], h->T + h->n2g, {DOM_P, DOM_H}, {nh, 1});
+  set(tv[TT2], h->T, {DOM_P, DOM_P, DOM_H, DOM_H}, {np * nh * nh, nh * nh, nh, 1});
+  set(tv[TG], h->G, {DOM_A, DOM_A}, {a, 1});
+  set(tv[TE], h->E, {DOM_A, DOM_A}, {a, 1});
+  set(tv[TD2], h->D2, {DOM_A, DOM_A, DOM_A, DOM_A}, {a * a * a, a * a, a, 1});
+  set(tv[TD3], h->D3, {DOM_A, DOM_A, DOM_A, DOM_A, DOM_A, DOM_A},
+      {a * a * a * a * a, a * a * a * a, a * a * a, a * a, a, 1});
+  set(tv[TY1], h->Ytil + h->n2g, {DOM_P, DOM_H}, {nh, 1});
+  set(tv[TY2], h->Ytil, {DOM_P, DOM_P, DOM_H, DOM_H}, {np * nh * nh, nh * nh, nh, 1});
+  set(ov[OGT1], h->GT + h->n2g, {DOM_P, DOM_H}, {nh, 1});
+  set(ov[OGT2], h->GT, {DOM_P, DOM_P, DOM_H, DOM_H}, {np * nh * nh, nh * nh, nh, 1});
+  set(ov[OGF], h->gF, {DOM_G, DOM_G}, {n, 1});
+  // d/dV[p,q,r,s] lands on d/d(pr|qs): the same permuted view as the input V
+  set(ov[OGV], h->geri, {DOM_G, DOM_G, DOM_G, DOM_G}, {n * n * n, n, n * n, 1});
+  Planner pt(d, tv, ov, h->scal + 3), ph(d, tv, ov, h->scal + 3);
+  for (const auto& t : kGradTTerms)
+    if (!pt.add_term(t, &h->gradt_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad dT term");
+  for (const auto& t : kGradHTerms)
+    if (!ph.add_term(t, &h->gradh_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad d(F,V) term");
+  h->adj_arena_elems = std::max<int64_t>(std::max<int64_t>(pt.arena_size(), ph.arena_size()), 1);
+  TRY(dalloc(h, &h->adj_arena, h->adj_arena_elems));
+  pt.finalize(&h->gradt_prog, h->adj_arena);
+  ph.finalize(&h->gradh_prog, h->adj_arena);
+  for (Program* p : {&h->gradt_prog, &h->gradh_prog}) {
+    TRY(dalloc(h, &p->d_table, (int64_t)p->table.size()));
+    CK(cudaMemcpyAsync(p->d_table, p->table.data(), sizeof(int64_t) * p->table.size(), cudaMemcpyHostToDevice,
+                       h->s));
+  }
+  h->adj_planned = true;
+  return RICMRCC_OK;
+}
+
+// Pulay step on (vec, err) pairs kept in the DIIS ring of the handle;
+// writes the extrapolated (or plain) next iterate into `target`.
+int diis_step(ricmrcc_t* h, const double* vec, const double* err, double* target, int cap, int it,
+              int diis_start) {
+  const int slot = h->nvec % cap;
+  CK(cudaMemcpyAsync(h->hist_v + (int64_t)slot * h->ng, vec, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice,
+                     h->s));
+  CK(cudaMemcpyAsync(h->hist_e + (int64_t)slot * h->ng, err, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice,
+                     h->s));
+  ++h->nvec;
+  const int m = h->nvec < cap ? h->nvec : cap;
+  CK(cudaMemsetAsync(h->dots, 0, sizeof(double) * 16, h->s));
+  launch_dots(h->dots, err, h->hist_e, h->ng, m, h->ng, h->s);
+  double dv[16];
+  CK(cudaMemcpyAsync(dv, h->dots, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  for (int j = 0; j < m; ++j) {
+    h->gram_host[slot * 16 + j] = dv[j];
+    h->gram_host[j * 16 + slot] = dv[j];
+  }
+  if (it >= diis_start && m >= 2) {
+    CK(cudaMemcpyAsync(h->gram, h->gram_host, sizeof(double) * 256, cudaMemcpyHostToDevice, h->s));
+    launch_diis_solve(h->gram, h->coef, m, h->dstatus, h->s);
+    launch_extrapolate(target, h->hist_v, h->coef, h->dstatus, m, slot, h->ng, h->ng, h->s);
+  } else {
+    CK(cudaMemcpyAsync(target, vec, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
+  }
+  return RICMRCC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ricmrcc_energy_backward(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds) {
+  if (!h) return RICMRCC_EINVAL;
+  if (!h->solved) return fail(h, RICMRCC_ESTATE, "energy_backward needs a converged ricmrcc_solve");
+  TRY(enter(h));
+  TRY(plan_adjoint(h));
+  const Dims& d = h->d;
+  const int64_t n = d.n, n2 = n * n;
+  const ricmrcc_opts& o = h->solved_opts;
+  const double s = h->solved_s;
+  const int cap = o.diis_size > 0 ? o.diis_size : 1;
+  TRY(ensure_diis(h, cap));
+  // residual at the converged amplitudes (for the epsilon and flow terms)
+  TRY(residual_device(h, false));
+  // multipliers: Lam = Delta (phi Lam) + d/dT [E + Ytil . X],  Y = phi Lam
+  CK(cudaMemsetAsync(h->Lam, 0, sizeof(double) * h->ng, h->s));
+  reset_iteration_state(h);
+  const double tol = std::max(o.t_tol, 1e-11);
+  bool conv = false;
+  for (int it = 1; it <= 4 * o.max_iter; ++it) {
+    launch_adj_y(h->Lam, h->Yraw, h->Ytil, h->eps, d, s, h->s);
+    CK(cudaMemsetAsync(h->GT, 0, sizeof(double) * h->ng, h->s));
+    CK(cudaMemsetAsync(h->adj_arena, 0, sizeof(double) * h->adj_arena_elems, h->s));
+    TRY(run_program(h, h->gradt_prog));
+    CK(cudaMemsetAsync(h->scal + 2, 0, sizeof(double), h->s));
+    launch_adj_update(h->Lam, h->Yraw, h->GT, h->Tn, h->Err, h->eps, d, h->scal + 2, h->s);
+    CK(cudaMemcpyAsync(h->host_scal + 2, h->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    const double md = h->host_scal[2];
+    if (h->verbose) fprintf(stderr, "ricmrcc adjoint iter %3d  max|dLam| = %.3e\n", it, md);
+    if (!isfinite(md) || md > 1e100) return fail(h, RICMRCC_DIVERGED, "adjoint iteration diverged");
+    if (md < tol) {
+      CK(cudaMemcpyAsync(h->Lam, h->Tn, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
+      conv = true;
+      break;
+    }
+    if (o.diis_size == 0) {
+      CK(cudaMemcpyAsync(h->Lam, h->Tn, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
+    } else {
+      TRY(diis_step(h, h->Tn, h->Err, h->Lam, cap, it, o.diis_start));
+    }
+  }
+  if (!conv) return fail(h, RICMRCC_NOT_CONVERGED, "adjoint (multiplier) equations did not converge");
+  // parameter gradient: dL/dF, dL/dV through the terms, then epsilon, E0, Fock, B
+  launch_adj_y(h->Lam, h->Yraw, h->Ytil, h->eps, d, s, h->s);
+  CK(cudaMemsetAsync(h->gF, 0, sizeof(double) * n2, h->s));
+  CK(cudaMemsetAsync(h->geri, 0, sizeof(double) * n2 * n2, h->s));
+  CK(cudaMemsetAsync(h->adj_arena, 0, sizeof(double) * h->adj_arena_elems, h->s));
+  TRY(run_program(h, h->gradh_prog));
+  CK(cudaMemsetAsync(h->geps, 0, sizeof(double) * n, h->s));
+  CK(cudaMemsetAsync(h->scal + 5, 0, sizeof(double), h->s));
+  launch_adj_eps(h->Lam, h->T, h->X, h->eps, d, s, h->geps, h->scal + 5, h->s);
+  launch_adj_chain(h->geri, h->gF, h->geps, h->g1, h->L2, d, h->gFt, h->gh, h->s);
+  // dE/dB[Q][pq] = sum_rs (geri[pq,rs] + geri[rs,pq]) B[Q][rs]  (geri symmetrised above)
+  CK(cudaMemsetAsync(h->gB, 0, sizeof(double) * d.X * n2, h->s));
+  {
+    ContractOp op{};
+    op.A = h->geri;  // [pq][rs]
+    op.B = h->B;     // [Q][rs]
+    op.C = h->gB;    // [Q][pq]
+    op.L = 1;
+    op.M = n2;
+    op.N = d.X;
+    op.K = n2;
+    op.alpha = 1.0;
+    std::vector<int64_t> t;
+    t.push_back(0);
+    t.push_back(0);
+    t.push_back(0);
+    for (int64_t i = 0; i < n2; ++i) t.push_back(i * n2);  // AM
+    for (int64_t i = 0; i < n2; ++i) t.push_back(i);       // CM
+    for (int64_t q = 0; q < d.X; ++q) t.push_back(q * n2); // BN
+    for (int64_t q = 0; q < d.X; ++q) t.push_back(q * n2); // CN
+    for (int64_t i = 0; i < n2; ++i) t.push_back(i);       // AK
+    for (int64_t i = 0; i < n2; ++i) t.push_back(i);       // BK
+    op.kind = (n2 >= 64 && d.X >= 32) ? 0 : 1;
+    op.ksplit = 1;
+    op.kchunk = n2;
+    int64_t* dt = nullptr;
+    CK(cudaMalloc(&dt, sizeof(int64_t) * t.size()));
+    CK(cudaMemcpyAsync(dt, t.data(), sizeof(int64_t) * t.size(), cudaMemcpyHostToDevice, h->s));
+    launch_contract(op, dt, h->s);
+    CK(cudaStreamSynchronize(h->s));
+    CK(cudaFree(dt));
+  }
+  if (dE_dh) CK(cudaMemcpyAsync(dE_dh, h->gh, sizeof(double) * n2, cudaMemcpyDeviceToHost, h->s));
+  if (dE_dB) CK(cudaMemcpyAsync(dE_dB, h->gB, sizeof(double) * d.X * n2, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaMemcpyAsync(h->host_scal + 5, h->scal + 5, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (dE_ds) *dE_ds = h->host_scal[5];
   return leave(h);
 }
 

@@ -29,8 +29,8 @@ struct RicTermDesc {
   RicFactorDesc fac[7];
 };
 
-enum TensorId { TF = 0, TV = 1, TT1 = 2, TT2 = 3, TG = 4, TE = 5, TD2 = 6, TD3 = 7, NTENSOR = 8 };
-enum OutId { OR1 = 0, OX2 = 1, OE = 2, OL3 = 3, NOUT = 4 };
+enum TensorId { TF = 0, TV = 1, TT1 = 2, TT2 = 3, TG = 4, TE = 5, TD2 = 6, TD3 = 7, TY1 = 8, TY2 = 9, NTENSOR = 10 };
+enum OutId { OR1 = 0, OX2 = 1, OE = 2, OL3 = 3, OGT1 = 4, OGT2 = 5, OGF = 6, OGV = 7, NOUT = 8 };
 enum Domain { DOM_G = 0, DOM_P = 1, DOM_H = 2, DOM_A = 3 };
 
 struct Dims {

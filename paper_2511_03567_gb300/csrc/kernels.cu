@@ -565,3 +565,198 @@ __global__ void k_energy_out(double* out, const double* acc, double e0) { *out =
 void launch_energy_out(double* out, const double* acc, double e0, cudaStream_t s) {
   k_energy_out<<<1, 1, 0, s>>>(out, acc, e0);
 }
+
+// ---------------------------------------------------------------------------
+// Adjoint of the renormalised fixed point (Lagrangian of G(T) = U(T) - T)
+// ---------------------------------------------------------------------------
+namespace {
+__device__ __forceinline__ bool zero_block(int64_t i, const Dims& d, int64_t* c, int64_t* dd, int64_t* k,
+                                           int64_t* l, bool* doubles) {
+  const int64_t np = d.np, nh = d.nh, n2 = np * np * nh * nh;
+  if (i < n2) {
+    *doubles = true;
+    *c = i / (np * nh * nh);
+    *dd = (i / (nh * nh)) % np;
+    *k = (i / nh) % nh;
+    *l = i % nh;
+    return *c < d.a && *dd < d.a && *k >= d.o && *l >= d.o;
+  }
+  *doubles = false;
+  const int64_t j = i - n2;
+  *c = j / nh;
+  *k = j % nh;
+  *dd = 0;
+  *l = 0;
+  return *c < d.a && *k >= d.o;
+}
+__device__ __forceinline__ double delta_of(const double* eps, const Dims& d, bool dbl, int64_t c, int64_t dd,
+                                           int64_t k, int64_t l) {
+  return dbl ? eps[k] + eps[l] - eps[d.o + c] - eps[d.o + dd] : eps[k] - eps[d.o + c];
+}
+__device__ __forceinline__ double phi_of(double D, double s) {
+  return D == 0.0 ? 0.0 : -expm1(-s * D * D) / D;
+}
+// d phi / d Delta
+__device__ __forceinline__ double dphi_of(double D, double s) {
+  const double x = s * D * D;
+  if (x < 1e-8) return s - 1.5 * s * s * D * D;
+  return (2.0 * x * exp(-x) + expm1(-x)) / (D * D);
+}
+
+// Yraw = phi * Lam (zero outside the amplitude blocks); Ytil = Yraw with the
+// doubles part pair-symmetrised, the weight of the raw doubles output X.
+__global__ void k_adj_y(const double* __restrict__ Lam, double* __restrict__ Yraw, double* __restrict__ Ytil,
+                        const double* __restrict__ eps, Dims d, double s) {
+  const int64_t np = d.np, nh = d.nh, n2 = np * np * nh * nh, n = n2 + np * nh;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c, dd, k, l;
+    bool dbl;
+    const bool z = zero_block(i, d, &c, &dd, &k, &l, &dbl);
+    Yraw[i] = z ? 0.0 : phi_of(delta_of(eps, d, dbl, c, dd, k, l), s) * Lam[i];
+  }
+}
+__global__ void k_adj_sym(const double* __restrict__ Yraw, double* __restrict__ Ytil, Dims d) {
+  const int64_t np = d.np, nh = d.nh, n2 = np * np * nh * nh, n = n2 + np * nh;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < n2) {
+      const int64_t c = i / (np * nh * nh), dd = (i / (nh * nh)) % np, k = (i / nh) % nh, l = i % nh;
+      Ytil[i] = Yraw[i] + Yraw[((dd * np + c) * nh + l) * nh + k];
+    } else {
+      Ytil[i] = Yraw[i];
+    }
+  }
+}
+// Lam_new = S [Delta * Yraw + GT];  err = Lam_new - Lam;  max |err|.
+// S averages each doubles element with its pair-swapped partner: the
+// amplitudes live on the pair-symmetric subspace (Eq. spinfree-perm-sym), so
+// the multipliers of the constrained fixed point are the projected ones.
+__global__ void k_adj_update(const double* __restrict__ Lam, const double* __restrict__ Yraw,
+                             const double* __restrict__ GT, double* __restrict__ Ln, double* __restrict__ Err,
+                             const double* __restrict__ eps, Dims d, double* maxd) {
+  const int64_t np = d.np, nh = d.nh, n2 = np * np * nh * nh, n = n2 + np * nh;
+  double mx = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c, dd, k, l;
+    bool dbl;
+    const bool z = zero_block(i, d, &c, &dd, &k, &l, &dbl);
+    double v = 0.0;
+    if (!z) {
+      const double D = delta_of(eps, d, dbl, c, dd, k, l);  // pair-swap invariant
+      v = D * Yraw[i] + GT[i];
+      if (dbl) {
+        const int64_t j = ((dd * np + c) * nh + l) * nh + k;
+        v = 0.5 * (v + D * Yraw[j] + GT[j]);
+      }
+    }
+    Ln[i] = v;
+    const double e = v - Lam[i];
+    Err[i] = e;
+    const double ae = fabs(e);
+    mx = (ae > mx || ae != ae) ? ae : mx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double y = __shfl_down_sync(0xffffffffu, mx, o);
+    mx = (y > mx || y != y) ? y : mx;
+  }
+  if ((threadIdx.x & 31) == 0)
+    atomicMax(reinterpret_cast<unsigned long long*>(maxd),
+              (unsigned long long)__double_as_longlong(mx != mx ? 1.0e300 : mx));
+}
+// geps[p] += sum_nu Lam_nu dG_nu/dDelta_nu * dDelta_nu/deps_p and
+// dEds += sum_nu Lam_nu (T Delta + R) dphi/ds, R = X + X^{pair}.
+__global__ void k_adj_eps(const double* __restrict__ Lam, const double* __restrict__ T,
+                          const double* __restrict__ X, const double* __restrict__ eps, Dims d, double s,
+                          double* __restrict__ geps, double* __restrict__ dEds) {
+  const int64_t np = d.np, nh = d.nh, n2 = np * np * nh * nh, n = n2 + np * nh;
+  double acc_s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t c, dd, k, l;
+    bool dbl;
+    if (zero_block(i, d, &c, &dd, &k, &l, &dbl)) continue;
+    const double lam = Lam[i];
+    if (lam == 0.0) continue;
+    const double D = delta_of(eps, d, dbl, c, dd, k, l);
+    const double r = dbl ? X[i] + X[((dd * np + c) * nh + l) * nh + k] : X[i];
+    const double t = T[i];
+    const double g = lam * (t * phi_of(D, s) + (t * D + r) * dphi_of(D, s));
+    atomicAdd(geps + k, g);
+    atomicAdd(geps + d.o + c, -g);
+    if (dbl) {
+      atomicAdd(geps + l, g);
+      atomicAdd(geps + d.o + dd, -g);
+    }
+    acc_s += lam * (t * D + r) * D * exp(-s * D * D);
+  }
+  acc_s = block_sum(acc_s);
+  if (threadIdx.x == 0) atomicAdd(dEds, acc_s);
+}
+// Chain through E0 = 1/2 sum D (h + f) + 1/2 sum (tu|vw) L2[t,v,u,w] and the
+// Fock build f_pq = h_pq + sum_rs D_rs [(pq|rs) - 1/2 (ps|rq)]:
+//   gFt = gF + diag(geps) + D/2 ;  gh = gFt + D/2
+//   geri[p,q,r,s] += gFt[p,q] D[r,s] - 1/2 gFt[p,s] D[r,q] + 1/2 L2[p,r,q,s] (active)
+// with D = 2 delta on the core, Gamma1 on the active block.
+__device__ __forceinline__ double dens(const double* g1, const Dims& d, int64_t p, int64_t q) {
+  if (p < d.o && q < d.o) return p == q ? 2.0 : 0.0;
+  if (p >= d.o && q >= d.o && p < d.o + d.a && q < d.o + d.a) return g1[(p - d.o) * d.a + (q - d.o)];
+  return 0.0;
+}
+__global__ void k_adj_fock(const double* __restrict__ gF, const double* __restrict__ geps,
+                           const double* __restrict__ g1, Dims d, double* __restrict__ gFt, double* __restrict__ gh) {
+  const int64_t n = d.n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i / n, q = i % n;
+    const double D = dens(g1, d, p, q);
+    const double v = gF[i] + (p == q ? geps[p] : 0.0) + 0.5 * D;
+    gFt[i] = v;
+    gh[i] = v + 0.5 * D;
+  }
+}
+__global__ void k_adj_eri(double* __restrict__ geri, const double* __restrict__ gFt, const double* __restrict__ g1,
+                          const double* __restrict__ l2, Dims d) {
+  const int64_t n = d.n, nh = d.o + d.a, n2 = n * n, n3 = n2 * n, tot = n2 * n2;
+  const int64_t a = d.a, a2 = a * a, a3 = a2 * a;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < tot; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = i / n3, q = (i / n2) % n, r = (i / n) % n, s = i % n;
+    double v = 0.0;
+    if (r < nh && s < nh) v += gFt[p * n + q] * dens(g1, d, r, s);
+    if (r < nh && q < nh) v -= 0.5 * gFt[p * n + s] * dens(g1, d, r, q);
+    if (a > 0 && p >= d.o && q >= d.o && r >= d.o && s >= d.o && p < nh && q < nh && r < nh && s < nh)
+      v += 0.5 * l2[(p - d.o) * a3 + (r - d.o) * a2 + (q - d.o) * a + (s - d.o)];
+    if (v != 0.0) geri[i] += v;
+  }
+}
+// geri <- geri + geri^T over the (pq) <-> (rs) pair exchange (in place, upper triangle)
+__global__ void k_sym_pairs(double* __restrict__ g, int64_t n2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2 * n2; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = i / n2, y = i % n2;
+    if (y < x) continue;
+    const double a = g[x * n2 + y], b = g[y * n2 + x];
+    g[x * n2 + y] = a + b;
+    g[y * n2 + x] = a + b;
+  }
+}
+}  // namespace
+
+void launch_adj_y(const double* Lam, double* Yraw, double* Ytil, const double* eps, const Dims& d, double s,
+                  cudaStream_t st) {
+  const int64_t n = (int64_t)d.np * d.np * d.nh * d.nh + (int64_t)d.np * d.nh;
+  k_adj_y<<<grid_for(n), kThreads, 0, st>>>(Lam, Yraw, Ytil, eps, d, s);
+  k_adj_sym<<<grid_for(n), kThreads, 0, st>>>(Yraw, Ytil, d);
+}
+void launch_adj_update(const double* Lam, const double* Yraw, const double* GT, double* Ln, double* Err,
+                       const double* eps, const Dims& d, double* maxd, cudaStream_t st) {
+  const int64_t n = (int64_t)d.np * d.np * d.nh * d.nh + (int64_t)d.np * d.nh;
+  k_adj_update<<<grid_for(n), kThreads, 0, st>>>(Lam, Yraw, GT, Ln, Err, eps, d, maxd);
+}
+void launch_adj_eps(const double* Lam, const double* T, const double* X, const double* eps, const Dims& d,
+                    double s, double* geps, double* dEds, cudaStream_t st) {
+  const int64_t n = (int64_t)d.np * d.np * d.nh * d.nh + (int64_t)d.np * d.nh;
+  k_adj_eps<<<grid_for(n), kThreads, 0, st>>>(Lam, T, X, eps, d, s, geps, dEds);
+}
+void launch_adj_chain(double* geri, const double* gF, const double* geps, const double* g1, const double* l2,
+                      const Dims& d, double* gFt, double* gh, cudaStream_t st) {
+  const int64_t n = d.n;
+  k_adj_fock<<<grid_for(n * n), kThreads, 0, st>>>(gF, geps, g1, d, gFt, gh);
+  k_adj_eri<<<grid_for(n * n * n * n), kThreads, 0, st>>>(geri, gFt, g1, l2, d);
+  k_sym_pairs<<<grid_for(n * n * n * n), kThreads, 0, st>>>(geri, n * n);
+}

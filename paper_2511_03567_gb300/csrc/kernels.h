@@ -26,3 +26,12 @@ void launch_extrapolate(double* T, const double* vecs, const double* coef, const
 int run_jacobi(double* Ablk, double* V, int n, double* U, int n_full, int off, int* d_sweeps,
                cudaStream_t s);
 void launch_energy_out(double* out, const double* acc, double e0, cudaStream_t s);
+void launch_adj_y(const double* Lam, double* Yraw, double* Ytil, const double* eps, const Dims& d, double s,
+                  cudaStream_t st);
+void launch_adj_update(const double* Lam, const double* Yraw, const double* GT, double* Ln, double* Err,
+                       const double* eps, const Dims& d, double* maxd, cudaStream_t st);
+void launch_adj_eps(const double* Lam, const double* T, const double* X, const double* eps, const Dims& d,
+                    double s, double* geps, double* dEds, cudaStream_t st);
+// gFt, gh [n][n]; geri gets the Fock/E0 chain and is then pair-symmetrised
+void launch_adj_chain(double* geri, const double* gF, const double* geps, const double* g1, const double* l2,
+                      const Dims& d, double* gFt, double* gh, cudaStream_t st);

@@ -14,8 +14,8 @@ import time
 from . import algebra as al
 from . import spinfree as sf
 
-TENSOR_ID = {"F": 0, "V": 1, "T1": 2, "T2": 3, "G": 4, "E": 5, "D2": 6, "D3": 7}
-OUT_ID = {"R1": 0, "X2": 1, "E": 2, "L3": 3}
+TENSOR_ID = {"F": 0, "V": 1, "T1": 2, "T2": 3, "G": 4, "E": 5, "D2": 6, "D3": 7, "Y1": 8, "Y2": 9}
+OUT_ID = {"R1": 0, "X2": 1, "E": 2, "L3": 3, "GT1": 4, "GT2": 5, "GF": 6, "GV": 7}
 
 
 # index domain of every tensor axis and of every output (space masks)
@@ -25,7 +25,34 @@ DOMAIN = {
     "D2": (al.ACT,) * 4, "D3": (al.ACT,) * 6,
     "R1": (al.PART, al.HOLE), "X2": (al.PART, al.PART, al.HOLE, al.HOLE), "E": (),
     "L3": (al.ACT,) * 6,
+    "Y1": (al.PART, al.HOLE), "Y2": (al.PART, al.PART, al.HOLE, al.HOLE),
+    "GT1": (al.PART, al.HOLE), "GT2": (al.PART, al.PART, al.HOLE, al.HOLE),
+    "GF": (al.GEN, al.GEN), "GV": (al.GEN,) * 4,
 }
+
+
+def gradient_terms(terms, wrt):
+    """Derivative terms of the scalar  E + sum Y1 R1 + sum Y2 X2  with respect to
+    every occurrence of a tensor in `wrt` (product rule).
+
+    Residual terms get the adjoint weight of their output (Y1 for R1, Y2 for the
+    raw doubles part X2: with R2 = X2 + X2^{pair}, sum Y R2 = sum (Y + Y^{pair}) X2,
+    so Y2 here is the pair-symmetrised weight).  The derivative with respect to
+    a factor is written to the gradient output named after that factor, with
+    the factor's labels as output labels."""
+    out_of = {"T1": "GT1", "T2": "GT2", "F": "GF", "V": "GV"}
+    res = []
+    for t in terms:
+        for i, (nm, ix) in enumerate(t.factors):
+            if nm not in wrt:
+                continue
+            facs = [f for j, f in enumerate(t.factors) if j != i]
+            if t.out == "R1":
+                facs.append(("Y1", t.out_idx))
+            elif t.out == "X2":
+                facs.append(("Y2", t.out_idx))
+            res.append(sf.SFTerm(t.coef, tuple(facs), out_of[nm], tuple(ix), t.space))
+    return res
 
 
 def restrict(terms):
@@ -80,13 +107,16 @@ def write(path):
     res = restrict(res)
     en = restrict(en)
     cum = restrict(sf.cumulant3_terms())
-    for t in res + en + cum:
+    gradt = gradient_terms(res + en, ("T1", "T2"))
+    gradh = gradient_terms(res + en, ("F", "V"))
+    for t in res + en + cum + gradt + gradh:
         nl = len({x for _, ix in t.factors for x in ix} | set(t.out_idx))
         assert nl <= 16 and len(t.factors) <= 7
     lines = [
         "// Generated by paper_2511_03567_gb300/gen/emit.py -- do not edit.",
         "// Spin-free RIC-MRCCSD terms (Sec. 2.2-2.3): coef * prod(factors) -> out[out_idx].",
-        "// tensor ids: F=0 V=1 T1=2 T2=3 G=4 E=5 D2=6 D3=7; outputs: R1=0 X2=1 E=2 L3=3",
+        "// tensor ids: F=0 V=1 T1=2 T2=3 G=4 E=5 D2=6 D3=7 Y1=8 Y2=9;",
+        "// outputs: R1=0 X2=1 E=2 L3=3 GT1=4 GT2=5 GF=6 GV=7",
         "// space masks: core=1 active=2 virtual=4 (hole=3 particle=6 general=7)",
         "static const RicTermDesc kResidualTerms[] = {",
     ]
@@ -95,11 +125,16 @@ def write(path):
     lines += ["  " + _term_c(t) + "," for t in en]
     lines += ["};", "static const RicTermDesc kCumulant3Terms[] = {"]
     lines += ["  " + _term_c(t) + "," for t in cum]
+    lines += ["};", "// adjoint: d/dT and d/d(F, V) of E + Y1.R1 + Y2.X2",
+              "static const RicTermDesc kGradTTerms[] = {"]
+    lines += ["  " + _term_c(t) + "," for t in gradt]
+    lines += ["};", "static const RicTermDesc kGradHTerms[] = {"]
+    lines += ["  " + _term_c(t) + "," for t in gradh]
     lines += ["};", ""]
     with open(path, "w") as f:
         f.write("\n".join(lines))
-    print(f"wrote {path}: {len(res)} residual, {len(en)} energy, {len(cum)} cumulant terms "
-          f"in {time.time() - t0:.1f}s", file=sys.stderr)
+    print(f"wrote {path}: {len(res)} residual, {len(en)} energy, {len(cum)} cumulant, "
+          f"{len(gradt)} dT, {len(gradh)} d(F,V) terms in {time.time() - t0:.1f}s", file=sys.stderr)
 
 
 if __name__ == "__main__":

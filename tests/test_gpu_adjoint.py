@@ -1,0 +1,116 @@
+"""Hand-written adjoint (dE/dh, dE/dB, dE/ds) against finite differences."""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import ricmrcc as o
+
+pytestmark = pytest.mark.gpu
+
+TIGHT = dict(e_tol=1e-13, t_tol=1e-12, max_iter=200)
+STEP = 1e-5
+
+
+def _setup(nc, na, nv, nx, seed=0):
+    import paper_2511_03567_gb300 as ric
+    p = synthetic.make_problem(nc, na, nv, nx, None, seed)
+    _, *rot = o.semicanonicalize(nc, na, nv, p.h, p.B, p.G1, p.G2, p.G3)
+    h, B, G1, G2, G3 = rot
+    g = ric.RicMrcc(nc, na, nv, nx)
+    g.set_integrals(h, B)
+    g.set_rdms(G1, G2, G3)
+    return g, h, B, rot
+
+
+def _energy(g, h, B, s):
+    g.set_integrals(h, B)
+    e, st = g.solve(s, **TIGHT)
+    assert st.converged == 1
+    return e
+
+
+def _check(nc, na, nv, nx, s, n_entries, seed):
+    g, h, B, rot = _setup(nc, na, nv, nx, seed)
+    e0 = _energy(g, h, B, s)
+    dh, dB, ds = g.energy_backward()
+    rng = np.random.default_rng(seed + 100)
+    n = nc + na + nv
+    fd_s = (_energy(g, h, B, s + STEP) - _energy(g, h, B, s - STEP)) / (2 * STEP)
+    assert abs(fd_s - ds) < 1e-6 * max(1.0, abs(fd_s)), (fd_s, ds)
+    for _ in range(n_entries):
+        p, q = rng.integers(0, n, size=2)
+        hp, hm = h.copy(), h.copy()
+        hp[p, q] += STEP
+        hm[p, q] -= STEP
+        fd = (_energy(g, hp, B, s) - _energy(g, hm, B, s)) / (2 * STEP)
+        assert abs(fd - dh[p, q]) < 1e-6 * max(1.0, abs(fd)), ("h", p, q, fd, dh[p, q])
+        Q = rng.integers(0, nx)
+        p, q = rng.integers(0, n, size=2)
+        Bp, Bm = B.copy(), B.copy()
+        Bp[Q, p, q] += STEP
+        Bm[Q, p, q] -= STEP
+        fd = (_energy(g, h, Bp, s) - _energy(g, h, Bm, s)) / (2 * STEP)
+        assert abs(fd - dB[Q, p, q]) < 1e-6 * max(1.0, abs(fd)), ("B", Q, p, q, fd, dB[Q, p, q])
+    return e0, dh, dB, ds
+
+
+def test_adjoint_tiny_against_finite_differences():
+    _check(2, 4, 10, 48, 0.5, 10, seed=0)
+
+
+def test_adjoint_small_copy_against_finite_differences():
+    """The 4-core / CAS(4,4) / 20-virtual copy of the adjoint workload."""
+    _check(4, 4, 20, 112, 0.5, 5, seed=1)
+
+
+@pytest.mark.slow
+def test_adjoint_against_oracle_gradient():
+    """dE/ds, one dE/dh and one dE/dB entry from central differences of the
+    FP64 oracle's own converged energies (fixed basis)."""
+    nc, na, nv, nx = 2, 4, 10, 48
+    g, h, B, rot = _setup(nc, na, nv, nx, 0)
+    s = 0.5
+    _energy(g, h, B, s)
+    dh, dB, ds = g.energy_backward()
+    G1, G2, G3 = rot[2:]
+
+    def oracle_e(hh, BB, ss):
+        m = o.Model(nc, na, nv, hh, BB, G1, G2, G3)
+        r = o.solve(m, ss, max_iter=200, e_tol=1e-13, t_tol=1e-12)
+        assert r.converged
+        return r.energy
+    fd = (oracle_e(h, B, s + STEP) - oracle_e(h, B, s - STEP)) / (2 * STEP)
+    assert abs(fd - ds) < 1e-6 * max(1.0, abs(fd))
+    hp, hm = h.copy(), h.copy()
+    hp[1, 9] += STEP
+    hm[1, 9] -= STEP
+    fd = (oracle_e(hp, B, s) - oracle_e(hm, B, s)) / (2 * STEP)
+    assert abs(fd - dh[1, 9]) < 1e-6 * max(1.0, abs(fd))
+    Bp, Bm = B.copy(), B.copy()
+    Bp[5, 3, 12] += STEP
+    Bm[5, 3, 12] -= STEP
+    fd = (oracle_e(h, Bp, s) - oracle_e(h, Bm, s)) / (2 * STEP)
+    assert abs(fd - dB[5, 3, 12]) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_autograd_function():
+    import torch
+
+    from paper_2511_03567_gb300.autograd import RicMrccEnergy
+    g, h, B, rot = _setup(2, 4, 10, 48, 0)
+    th = torch.tensor(h, requires_grad=True)
+    tB = torch.tensor(B, requires_grad=True)
+    ts = torch.tensor(0.5, dtype=torch.float64, requires_grad=True)
+    E = RicMrccEnergy.apply(th, tB, ts, g, TIGHT)
+    E.backward()
+    dh, dB, ds = g.energy_backward()
+    assert np.allclose(th.grad.numpy(), dh) and np.allclose(tB.grad.numpy(), dB)
+    assert abs(float(ts.grad) - ds) < 1e-12
+
+
+def test_backward_requires_converged_solve():
+    import paper_2511_03567_gb300 as ric
+    g, h, B, rot = _setup(2, 4, 10, 48, 0)
+    with pytest.raises(ric.RicMrccError) as ei:
+        g.energy_backward()
+    assert ei.value.code == ric.ESTATE
