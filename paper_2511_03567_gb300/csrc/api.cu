@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <memory>
 #include <string>
@@ -16,6 +17,7 @@
 #include "kernels.h"
 #include "planner.h"
 #include "tcgemm.h"
+#include "grouped.h"
 
 #include "ric_terms.inc"
 
@@ -53,6 +55,8 @@ struct ricmrcc {
   cudaStream_t lane[8] = {nullptr};
   cudaEvent_t lane_ev[9] = {nullptr};
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [fp64, mixed]
+  int sms = 152;
+  std::vector<void*> group_allocs;  // grouped-launch descriptor arrays
   int* d_err = nullptr;
   int64_t tc_ops = 0;
   double tc_flops = 0.0;
@@ -393,8 +397,71 @@ int cumulants(ricmrcc_t* h, int kind) {
 // intermediate arena, then run the contractions level by level, each level's
 // independent ops spread over kLanes streams (outputs accumulate atomically, so
 // ops of one level need no ordering; intermediates flow only to later levels).
+// Descriptor arrays of one grouped launch (device), kept for the graph's life.
+struct Group {
+  const GroupOp* ops = nullptr;
+  const int64_t* begin = nullptr;
+  int nops = 0;
+  int64_t total = 0;
+};
+
+int make_group(ricmrcc_t* h, const std::vector<GroupOp>& ops, int kind, Group* g) {
+  g->nops = (int)ops.size();
+  if (ops.empty()) return RICMRCC_OK;
+  std::vector<int64_t> begin(ops.size());
+  int64_t t = 0;
+  for (size_t i = 0; i < ops.size(); ++i) {
+    begin[i] = t;
+    t += group_units(ops[i], kind);
+  }
+  g->total = t;
+  void *dops = nullptr, *dbeg = nullptr;
+  CK(cudaMalloc(&dops, sizeof(GroupOp) * ops.size()));
+  CK(cudaMalloc(&dbeg, sizeof(int64_t) * begin.size()));
+  h->group_allocs.push_back(dops);
+  h->group_allocs.push_back(dbeg);
+  CK(cudaMemcpy(dops, ops.data(), sizeof(GroupOp) * ops.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dbeg, begin.data(), sizeof(int64_t) * begin.size(), cudaMemcpyHostToDevice));
+  g->ops = static_cast<const GroupOp*>(dops);
+  g->begin = static_cast<const int64_t*>(dbeg);
+  return RICMRCC_OK;
+}
+
+GroupOp group_op(const Program& p, const ContractOp& op) {
+  GroupOp g{};
+  g.A = op.A;
+  g.B = op.B;
+  g.C = op.C;
+  g.tab = p.d_table + op.tab;
+  g.L = op.L;
+  g.M = op.M;
+  g.N = op.N;
+  g.K = op.K;
+  g.kchunk = op.kchunk;
+  g.alpha = op.alpha;
+  g.ksplit = op.ksplit;
+  return g;
+}
+
+// Capture the residual program as a CUDA graph: zero the accumulators and the
+// intermediate arena, then run the contractions level by level.  Per level the
+// FP64 contractions of each tile kind are one persistent grouped launch (lanes
+// 0-2); in mixed precision the tensor-core contractions run on lanes 3-7.
+// Outputs accumulate atomically, so ops of one level need no ordering;
+// intermediates flow only to later levels.
 int capture_residual(ricmrcc_t* h, bool mixed) {
   const Program& p = h->res_prog;
+  // descriptor arrays first (allocation is not allowed inside the capture)
+  std::vector<std::array<Group, 3>> groups(p.max_level + 1);
+  for (int lvl = 0; lvl <= p.max_level; ++lvl) {
+    std::vector<GroupOp> by_kind[3];
+    for (const auto& op : p.ops) {
+      if (op.level != lvl || (mixed && tc_eligible(op))) continue;
+      if (op.L == 0 || op.M == 0 || op.N == 0 || op.K == 0) continue;
+      by_kind[op.kind].push_back(group_op(p, op));
+    }
+    for (int k = 0; k < 3; ++k) TRY(make_group(h, by_kind[k], k, &groups[lvl][k]));
+  }
   cudaStream_t s0 = h->lane[0];
   CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
   auto fail_capture = [&](int rc) {
@@ -411,23 +478,23 @@ int capture_residual(ricmrcc_t* h, bool mixed) {
   if (mixed && cudaMemsetAsync(h->d_err, 0, sizeof(int), s0) != cudaSuccess)
     return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: memset"));
   for (int lvl = 0; lvl <= p.max_level; ++lvl) {
-    // fork
-    cudaEventRecord(h->lane_ev[8], s0);
+    cudaEventRecord(h->lane_ev[8], s0);  // fork
     for (int l = 1; l < kLanes; ++l) cudaStreamWaitEvent(h->lane[l], h->lane_ev[8], 0);
-    int k = 0;
-    for (const auto& op : p.ops) {
-      if (op.level != lvl) continue;
-      const int l = k++ % kLanes;
-      if (mixed && tc_eligible(op)) {
+    for (int k = 0; k < 3; ++k) {
+      const Group& g = groups[lvl][k];
+      launch_grouped(k, g.ops, g.begin, g.nops, g.total, h->sms, h->lane[k]);
+    }
+    if (mixed) {
+      int j = 0;
+      for (const auto& op : p.ops) {
+        if (op.level != lvl || !tc_eligible(op)) continue;
+        const int l = 3 + (j++ % (kLanes - 3));
         TcArgs a = tc_args(h, p, op, l);
         if (tc_contract(a, h->lane[l]) != 0)
           return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: tensor-core launch"));
-      } else {
-        launch_contract(op, p.d_table, h->lane[l]);
       }
     }
-    // join
-    for (int l = 1; l < kLanes; ++l) {
+    for (int l = 1; l < kLanes; ++l) {  // join
       cudaEventRecord(h->lane_ev[l], h->lane[l]);
       cudaStreamWaitEvent(s0, h->lane_ev[l], 0);
     }
@@ -498,6 +565,11 @@ static int create_impl(ricmrcc_t* h, int n_core, int n_act, int n_virt, int n_au
   CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
   for (int l = 0; l < 8; ++l) CK(cudaStreamCreateWithFlags(&h->lane[l], cudaStreamNonBlocking));
+  {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
+  }
   for (int l = 0; l < 9; ++l) CK(cudaEventCreateWithFlags(&h->lane_ev[l], cudaEventDisableTiming));
   const int64_t n = d.n, a = d.a;
   h->n2g = (int64_t)d.np * d.np * d.nh * d.nh;
@@ -556,6 +628,7 @@ void ricmrcc_destroy(ricmrcc_t* h) {
   if (h->hist_e) cudaFree(h->hist_e);
   for (auto& g : h->graph)
     if (g) cudaGraphExecDestroy(g);
+  for (void* p : h->group_allocs) cudaFree(p);
   for (auto& e : h->lane_ev)
     if (e) cudaEventDestroy(e);
   for (auto& l : h->lane)

@@ -1,0 +1,198 @@
+// Persistent grouped FP64 contraction kernels.
+//
+// One launch executes every contraction of one dependency level (and one tile
+// kind), from one or many problem instances: the ops' tiles are numbered
+// consecutively (prefix sums in `tile_begin`), persistent CTAs stride over the
+// global tile index, find their op by binary search and run that tile exactly
+// like the single-op kernels (offset-table gathers, atomic accumulation).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "grouped.h"
+
+namespace {
+
+__device__ __forceinline__ int find_op(const int64_t* __restrict__ begin, int nops, int64_t t) {
+  int lo = 0, hi = nops - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (begin[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int BM, int BN, int TM, int TN, int BK>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+    k_grouped_tile(const GroupOp* __restrict__ ops, const int64_t* __restrict__ begin, int nops, int64_t total) {
+  constexpr int NT = (BM / TM) * (BN / TN);
+  __shared__ double As[BK][BM + 1];
+  __shared__ double Bs[BK][BN + 1];
+  __shared__ int64_t sAM[BM], sCM[BM], sBN[BN], sCN[BN];
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN);
+  const int ty = tid / (BN / TN);
+  for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    const int oi = find_op(begin, nops, tile);
+    const GroupOp& op = ops[oi];
+    const int64_t L = op.L, M = op.M, N = op.N, K = op.K;
+    const int64_t* tab = op.tab;
+    const int64_t* tAL = tab;
+    const int64_t* tBL = tAL + L;
+    const int64_t* tCL = tBL + L;
+    const int64_t* tAM = tCL + L;
+    const int64_t* tCM = tAM + M;
+    const int64_t* tBN = tCM + M;
+    const int64_t* tCN = tBN + N;
+    const int64_t* tAK = tCN + N;
+    const int64_t* tBK = tAK + K;
+    const int64_t mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+    int64_t r = tile - begin[oi];
+    const int64_t ni = r % nt;
+    r /= nt;
+    const int64_t mi = r % mt;
+    r /= mt;
+    const int ks = (int)(r % op.ksplit);
+    const int64_t l = r / op.ksplit;
+    const int64_t m0 = mi * BM, n0 = ni * BN;
+    for (int i = tid; i < BM; i += NT) {
+      const int64_t m = m0 + i;
+      sAM[i] = m < M ? tAM[m] : 0;
+      sCM[i] = m < M ? tCM[m] : 0;
+    }
+    for (int i = tid; i < BN; i += NT) {
+      const int64_t n = n0 + i;
+      sBN[i] = n < N ? tBN[n] : 0;
+      sCN[i] = n < N ? tCN[n] : 0;
+    }
+    const int64_t aL = tAL[l], bL = tBL[l], cL = tCL[l];
+    const int64_t kb = (int64_t)ks * op.kchunk;
+    const int64_t ke = kb + op.kchunk < K ? kb + op.kchunk : K;
+    const double* __restrict__ A = op.A;
+    const double* __restrict__ B = op.B;
+    double acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+    __syncthreads();
+    for (int64_t k0 = kb; k0 < ke; k0 += BK) {
+      for (int i = tid; i < BK * BM; i += NT) {
+        const int kk = i / BM, mm = i % BM;
+        const int64_t k = k0 + kk, m = m0 + mm;
+        As[kk][mm] = (k < ke && m < M) ? A[aL + sAM[mm] + tAK[k]] : 0.0;
+      }
+      for (int i = tid; i < BK * BN; i += NT) {
+        const int kk = i / BN, nn = i % BN;
+        const int64_t k = k0 + kk, n = n0 + nn;
+        Bs[kk][nn] = (k < ke && n < N) ? B[bL + sBN[nn] + tBK[k]] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < BK; ++kk) {
+        double a[TM], b[TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+    double* C = op.C;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int mm = ty * TM + i;
+      if (m0 + mm >= M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int nn = tx * TN + j;
+        if (n0 + nn >= N) continue;
+        if (acc[i][j] != 0.0) atomicAdd(C + cL + sCM[mm] + sCN[nn], op.alpha * acc[i][j]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ double gsum(double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  __syncthreads();
+  return s;
+}
+
+// Dot-product contractions (tiny outputs, long K): one work item per
+// (op, output element, K chunk).
+__global__ void __launch_bounds__(256)
+    k_grouped_dot(const GroupOp* __restrict__ ops, const int64_t* __restrict__ begin, int nops, int64_t total) {
+  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    const int oi = find_op(begin, nops, w);
+    const GroupOp& op = ops[oi];
+    const int64_t L = op.L, M = op.M, N = op.N, K = op.K;
+    const int64_t* tAL = op.tab;
+    const int64_t* tBL = tAL + L;
+    const int64_t* tCL = tBL + L;
+    const int64_t* tAM = tCL + L;
+    const int64_t* tCM = tAM + M;
+    const int64_t* tBN = tCM + M;
+    const int64_t* tCN = tBN + N;
+    const int64_t* tAK = tCN + N;
+    const int64_t* tBK = tAK + K;
+    const int64_t r = w - begin[oi];
+    const int ks = (int)(r % op.ksplit);
+    const int64_t o = r / op.ksplit;
+    const int64_t l = o / (M * N), mn = o % (M * N), m = mn / N, n = mn % N;
+    const int64_t ao = tAL[l] + tAM[m], bo = tBL[l] + tBN[n];
+    const int64_t kb = (int64_t)ks * op.kchunk;
+    const int64_t ke = kb + op.kchunk < K ? kb + op.kchunk : K;
+    double s = 0.0;
+    for (int64_t k = kb + threadIdx.x; k < ke; k += blockDim.x) s = fma(op.A[ao + tAK[k]], op.B[bo + tBK[k]], s);
+    s = gsum(s);
+    if (threadIdx.x == 0 && s != 0.0) atomicAdd(op.C + tCL[l] + tCM[m] + tCN[n], op.alpha * s);
+  }
+}
+
+}  // namespace
+
+int64_t group_units(const GroupOp& op, int kind) {
+  if (kind == 2) return op.L * op.M * op.N * op.ksplit;
+  const int64_t bm = kind == 0 ? 64 : 16;
+  return op.L * op.ksplit * ((op.M + bm - 1) / bm) * ((op.N + bm - 1) / bm);
+}
+
+void launch_grouped(int kind, const GroupOp* ops, const int64_t* begin, int nops, int64_t total, int sms,
+                    cudaStream_t s) {
+  if (nops <= 0 || total <= 0) return;
+  // persistent grid: every resident CTA slot of every SM (occupancy API)
+  static int per_sm[3] = {0, 0, 0};
+  if (!per_sm[kind]) {
+    int b = 1;
+    if (kind == 0)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_grouped_tile<64, 64, 4, 4, 16>, 256, 0);
+    else if (kind == 1)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_grouped_tile<16, 16, 1, 1, 16>, 256, 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_grouped_dot, 256, 0);
+    per_sm[kind] = b > 0 ? b : 1;
+  }
+  const int64_t slots = (int64_t)sms * per_sm[kind];
+  const int g = (int)(total < slots ? total : slots);
+  if (kind == 0)
+    k_grouped_tile<64, 64, 4, 4, 16><<<g, 256, 0, s>>>(ops, begin, nops, total);
+  else if (kind == 1)
+    k_grouped_tile<16, 16, 1, 1, 16><<<g, 256, 0, s>>>(ops, begin, nops, total);
+  else
+    k_grouped_dot<<<g, 256, 0, s>>>(ops, begin, nops, total);
+}
