@@ -1,12 +1,20 @@
 """Benchmark: seconds per RIC-MRCCSD solver iteration on one GB300 (and replicas).
 
-One step = one iteration of the amplitude solver on the Mid workload: the
-full spin-free residual and energy (every term of the RIC-MRCCSD many-body
-residual), the renormalised update (Eq. ric-update) and the DIIS
-extrapolation.  Timed with CUDA events on the library's stream; inputs are
-larger than L2 (the integral tensor alone is 2.7 GB), so no flush is needed.
+One step = one iteration of the amplitude solver on the Mid workload (8 core,
+CAS(8,8), 120 virtual, n_aux 400): the full spin-free residual and energy
+(every term of the RIC-MRCCSD many-body residual), the renormalised update
+(Eq. ric-update) and the DIIS extrapolation.  The headline runs the mixed
+path (split-precision BF16 tensor-core contractions, FP64 elsewhere; the
+solver refines in FP64); the FP64 path is timed beside it.  Timed with CUDA
+events on the library's stream; inputs are larger than L2 (the integral
+tensor alone is 2.7 GB), so no flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--precision mixed|fp64] [--workload mid|prof|batched]
+
+`--workload batched` times one iteration of 48 independent instances of
+uneven sizes (core 2-10, CAS(4,4)-CAS(8,8), virtual 40-120, n_aux 4n) run
+as one batch: one graph of grouped launches per iteration.
 """
 from __future__ import annotations
 
@@ -31,8 +39,11 @@ WORKLOADS = {
     "prof": {"workload": "prof", "n_core": 4, "n_act": 4, "n_virt": 64, "n_aux": 200, "n_det": None,
              "s": 0.1, "seed": 0},
 }
+WORKLOADS["batched"] = {"workload": "batched", "instances": 48, "s": 0.5, "seed": 0,
+                        "sizes": "core U{2..10}, CAS(4,4)/(6,6)/(8,8), virtual U{40..120}, n_aux 4n"}
 WORKLOAD = WORKLOADS["mid"]
 METRIC = "RIC-MRCCSD s/iter (Mid, one GB300)"
+METRIC_BATCHED = "RIC-MRCCSD s/iter (Batched, 48 instances per iteration, one GB300)"
 
 
 def peaks():
@@ -107,6 +118,55 @@ def fp64_gemm_peak(torch):
     return 2.0 * n ** 3 / best / 1e12
 
 
+KERNEL_NAMES = ("grouped_tile_64x64", "grouped_tile_16x16", "grouped_dot", "tc_pack_split_bf16",
+                "tc_gemm_tcgen05_bf16x3", "grouped_tile_128x16", "grouped_tile_64x32")
+
+
+def fp32_peak_tflops(torch):
+    """Nominal FP32 CUDA-core rate: SMs x 128 lanes x 2 FLOP (FMA) x max SM clock."""
+    props = torch.cuda.get_device_properties(0)
+    mhz = 2070.0
+    try:
+        out = subprocess.run(["nvidia-smi", "-i", "0", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        mhz = float(out.splitlines()[0])
+    except Exception:
+        pass
+    return props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def roofline(kind_ms, info, mixed, pk, fp64_peak, torch):
+    """Dominant kernel of the serialised per-kernel profile against its roof."""
+    c = int(np.argmax(kind_ms))
+    t = kind_ms[c] / 1e3  # s per residual in this kernel
+    work = info.kernel_work[c]
+    name = KERNEL_NAMES[c] + ("" if c in (3, 4) else ("_fp32" if mixed else "_fp64"))
+    if c == 3:
+        roof = {"bound": "hbm", "achieved": work / t / 1e9, "unit": "GB/s", "peak": pk.get("hbm_gbs", 6800.0),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), of measured",
+                "work": "bytes: FP64 source read + three BF16 segments written, per packed buffer"}
+    elif c == 4:
+        roof = {"bound": "tensor", "achieved": 3.0 * work / t / 1e12, "unit": "TFLOP/s",
+                "peak": pk.get("bf16_tflops_sustained", 1700.0),
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16), of measured",
+                "work": "BF16 FLOPs: 3 x the contraction FLOPs (hi*hi + hi*lo + lo*hi)"}
+    elif mixed:
+        roof = {"bound": "alu", "achieved": work / t / 1e12, "unit": "TFLOP/s", "peak": fp32_peak_tflops(torch),
+                "peak_source": "nominal FP32 FMA rate: SMs x 128 x 2 x max SM clock (derived)",
+                "work": "contraction FLOPs (FP32 compute)"}
+    else:
+        roof = {"bound": "alu", "achieved": work / t / 1e12, "unit": "TFLOP/s", "peak": fp64_peak,
+                "peak_source": "cuBLAS DGEMM 8192^3 measured in this run (FP64 pipe), of measured",
+                "work": "contraction FLOPs (FP64)"}
+    roof["kernel"] = name
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
+    roof["traffic"] = None
+    roof["contractions_per_residual"] = int(info.kernel_ops[c])
+    roof["ms_per_residual"] = float(kind_ms[c])
+    roof["profile_ms_per_residual"] = {n: float(x) for n, x in zip(KERNEL_NAMES, kind_ms)}
+    return roof
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -147,7 +207,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip timing the FP64 path beside the mixed one")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default tile rule")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
     ap.add_argument("--ncu-largest", type=int, default=0,
@@ -157,6 +220,8 @@ def main():
     WORKLOAD = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
 
     import torch
     dist, rank, ws, local = dist_init()
@@ -173,6 +238,12 @@ def main():
     g.set_rdms(p.G1, p.G2, p.G3)
     g.semicanonicalize()
     prec = ric.MIXED if args.precision == "mixed" else ric.FP64
+    tuning = None
+    if not args.no_tune and not args.ncu_largest:
+        # tile rule for this workload, timed at representative (non-zero)
+        # amplitudes after a few solver steps (part of setup)
+        g.step(s=w["s"], n_steps=3, restart=True, precision=prec)
+        tuning = g.tune(prec, reps=2)
     if prec == ric.MIXED:
         g.set_precision(prec)
     info = g.plan_info()
@@ -207,6 +278,25 @@ def main():
         secs = float(t.item())
     s_per_iter = secs / (args.steps * ws)
     ms_per_step = secs / args.steps * 1e3
+    info = g.plan_info()  # graph launch counts are known once captured
+
+    fp64_line = None
+    if prec == ric.MIXED and not args.no_fp64_compare:
+        # the FP64 path on the same handle, same amplitudes' history
+        g.set_precision(ric.FP64)
+        g.step(s=w["s"], n_steps=max(args.warmup, 1), restart=True, precision=ric.FP64)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        g.step(s=w["s"], n_steps=args.steps, restart=False, precision=ric.FP64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        f_secs = f0.elapsed_time(f1) / 1e3 / args.steps
+        fp64_line = {"s_per_iter": f_secs, "tflops": info.residual_flops / f_secs / 1e12,
+                     "speedup_mixed": f_secs / (ms_per_step / 1e3)}
+        g.set_precision(ric.MIXED)
+        g.step(s=w["s"], n_steps=1, restart=True, precision=ric.MIXED)
 
     # end to end through the public host API: pinned host amplitudes in,
     # one iteration, amplitudes out
@@ -231,44 +321,24 @@ def main():
     # timed region, on the library's stream)
     mixed = prec == ric.MIXED
     kind_ms = g.profile(reps=2, mixed=mixed)
-    dom = int(np.argmax(kind_ms))
+    info = g.plan_info()
     pk = peaks()
     fp64_peak = fp64_gemm_peak(torch) if rank == 0 else None
     if rank != 0:
         return 0
-    names = ["contract_tile_64x64_fp64", "contract_tile_16x16_fp64", "contract_dot_fp64",
-             "tc_pack_split_bf16", "tc_gemm_tcgen05_bf16x3"]
-    launches = [int(info.kind_launches[0]), int(info.kind_launches[1]), int(info.kind_launches[2]),
-                2 * int(info.tc_contractions), int(info.tc_contractions)]
-    if dom <= 2:
-        fl = None if mixed else info.kind_flops[dom]
-        roof = {"bound": "alu", "kernel": names[dom],
-                "achieved": None if fl is None else fl / (kind_ms[dom] / 1e3) / 1e12,
-                "peak": fp64_peak, "unit": "TFLOP/s",
-                "peak_source": "cuBLAS DGEMM 8192^3 measured in this run (FP64 CUDA-core pipe), of measured"}
-    elif dom == 3:
-        roof = {"bound": "hbm", "kernel": names[dom], "achieved": info.tc_pack_bytes / (kind_ms[3] / 1e3) / 1e9,
-                "peak": pk.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), of measured"}
-    else:
-        roof = {"bound": "tensor", "kernel": names[dom],
-                "achieved": 3.0 * info.tc_flops / (kind_ms[4] / 1e3) / 1e12,
-                "peak": pk.get("bf16_tflops_sustained", 1700.0), "unit": "TFLOP/s",
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, sustained), of measured"}
-    roof["frac"] = (roof["achieved"] / roof["peak"]) if roof["achieved"] and roof["peak"] else None
-    roof["traffic"] = None
-    roof["launches_per_residual"] = launches[dom]
-    roof["ms_per_residual"] = float(kind_ms[dom])
-    roof["profile_ms_per_residual"] = {n: float(x) for n, x in zip(names, kind_ms)}
+    roof = roofline(kind_ms, info, mixed, pk, fp64_peak, torch)
     tc = None
     if mixed:
         tc = {"contractions": int(info.tc_contractions), "fp64_equiv_flops": info.tc_flops,
+              "pack_bytes_per_residual": info.tc_pack_bytes,
               "bf16_flops": 3.0 * info.tc_flops,
               "gemm_tflops": 3.0 * info.tc_flops / (kind_ms[4] / 1e3) / 1e12 if kind_ms[4] else None,
-              "pack_gbs": info.tc_pack_bytes / (kind_ms[3] / 1e3) / 1e9 if kind_ms[3] else None}
+              "pack_gbs": info.tc_pack_bytes / (kind_ms[3] / 1e3) / 1e9 if kind_ms[3] else None,
+              "flop_fraction": info.tc_flops / info.residual_flops}
     line = {"metric": METRIC, "value": s_per_iter, "unit": "s/iter", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == ric.FP64 else "bf16x3+f64",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == ric.FP64 else "bf16x3(f32 acc)+f64",
             "data": "synthetic",
             "config": dict(WORKLOAD, precision=args.precision, parallelism=f"replicas{ws}",
                            l2="inputs larger than L2 (2.7 GB integral tensor), no flush"),
@@ -277,7 +347,8 @@ def main():
             "e2e": {"value": e2e_s, "unit": "s/iter", "h2d_bytes_per_step": 8 * (lay.t1_size + lay.t2_size),
                     "d2h_bytes_per_step": 8 * (lay.t1_size + lay.t2_size)},
             "gpu_launches": int(info.step_launches) * args.steps,
-            "roofline": roof, "clocks": clk.summary(), "tensor_core": tc}
+            "roofline": roof, "clocks": clk.summary(), "tensor_core": tc, "fp64_path": fp64_line,
+            "tile_rule": g.get_tile_rule(), "tuning": tuning}
     if not args.no_cpu_baseline and ws == 1 and args.workload == "mid":
         try:
             cb = cpu_baseline_run()
@@ -286,6 +357,80 @@ def main():
         except Exception as ex:  # the oracle is optional on the bench path
             line["cpu_baseline"] = {"value": None, "unit": "s/iter", "cores": os.cpu_count(),
                                     "kind": "oracle", "sample": f"failed: {ex}"}
+    print(json.dumps(line))
+    return 0
+
+
+def run_batched(args):
+    """48 uneven instances solved as one batch: s per batch iteration."""
+    import torch
+    dist, rank, ws, local = dist_init()
+    torch.cuda.set_device(local)
+    import paper_2511_03567_gb300 as ric
+    import synthetic
+    w = WORKLOADS["batched"]
+    count = w["instances"]
+    dims = synthetic.batched_dims(count, w["seed"])
+    b = ric.RicMrccBatch(dims)
+    for i, g in enumerate(b.instances):
+        p = synthetic.make_batched_problem(i, count, w["seed"])
+        g.set_integrals(p.h, p.B)
+        g.set_rdms(p.G1, p.G2, p.G3)
+        g.semicanonicalize()
+    prec = ric.MIXED if args.precision == "mixed" else ric.FP64
+    tuning = None
+    if not args.no_tune:
+        b.step(s=w["s"], n_steps=2, restart=True, precision=prec)
+        tuning = b.tune(prec, reps=2)
+    b.step(s=w["s"], n_steps=max(args.warmup, 1), restart=True, precision=prec)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        c0 = time.perf_counter()
+        E, dt = b.step(s=w["s"], n_steps=args.steps, restart=False, precision=prec)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - c0
+    if dist:
+        t = torch.tensor([secs], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    info = b.info()
+    s_per_iter = secs / (args.steps * ws)
+    # per-kernel profile summed over the instances (serialised launches)
+    mixed = prec == ric.MIXED
+    kind_ms = np.zeros(len(KERNEL_NAMES))
+    for g in b.instances:
+        kind_ms += g.profile(reps=1, mixed=mixed)
+
+    class _Sum:  # plan_info summed over the instances
+        pass
+    tot = _Sum()
+    tot.kernel_work = np.zeros(len(KERNEL_NAMES))
+    tot.kernel_ops = np.zeros(len(KERNEL_NAMES), dtype=np.int64)
+    for g in b.instances:
+        g.set_precision(prec)
+        inf = g.plan_info()
+        tot.kernel_work += np.array(inf.kernel_work[:])
+        tot.kernel_ops += np.array(inf.kernel_ops[:])
+    if rank != 0:
+        return 0
+    pk = peaks()
+    fp64_peak = None if mixed else fp64_gemm_peak(torch)
+    roof = roofline(kind_ms, tot, mixed, pk, fp64_peak, torch)
+    roof["scope"] = "dominant kernel, profile summed over the 48 instances"
+    line = {"metric": METRIC_BATCHED, "value": s_per_iter, "unit": "s/iter", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == ric.FP64 else "bf16x3(f32 acc)+f64", "data": "synthetic",
+            "config": dict(w, precision=args.precision, parallelism=f"replicas{ws}",
+                           l2="inputs larger than L2 (34 GB of integral tensors), no flush"),
+            "instance_iterations_per_s": count / s_per_iter,
+            "tflops": info["flops"] / s_per_iter / 1e12, "batch_info": info,
+            "tensor_flop_fraction": info["tc_flops"] / info["flops"] if info["flops"] else 0.0,
+            "gpu_launches": int(info["kernel_launches"] + 4 * count) * args.steps,
+            "roofline": roof, "clocks": clk.summary(), "tile_rule": b.instances[0].get_tile_rule(),
+            "tuning": tuning, "energy_mean": float(np.mean(E)), "max_dt_max": float(np.max(dt))}
     print(json.dumps(line))
     return 0
 

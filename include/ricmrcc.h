@@ -211,16 +211,28 @@ typedef struct {
   int64_t tc_contractions;   /* contractions the RICMRCC_MIXED path runs on tensor cores */
   double tc_flops;           /* their FP64-equivalent FLOPs (the BF16 GEMM does 3x) */
   double tc_pack_bytes;      /* algorithmic bytes of their operand packing */
+  int64_t graph_launches[2]; /* kernel launches of the captured residual graph [FP64, MIXED]
+                                (0 until that graph has been captured) */
+  /* per kernel of ricmrcc_profile (same order), for the handle's precision and
+   * tile rule: contractions and their FLOPs (tensor-core FLOPs FP64-equivalent;
+   * [3], the packing, counts the packed operand buffers and their bytes) */
+  int64_t kernel_ops[7];
+  double kernel_work[7];
 } ricmrcc_plan_info_t;
 
 /* Sizes of the contraction program planned for this handle. */
 RICMRCC_API int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out);
 
 /* Time the residual program kernel by kernel with CUDA events on the work
- * stream (reps repetitions, after the caller's warm-up) and return the mean
- * milliseconds per residual in kind_ms[5] (host): FP64 64x64 tile, FP64
- * 16x16 tile, FP64 dot reduction, and with mixed != 0 the tensor-core path's
- * operand packing and tcgen05 GEMMs.  Diagnostic: events serialise launches. */
+ * stream (reps repetitions, after the caller's warm-up): every contraction
+ * runs alone through the kernel the captured residual uses for it.  Returns
+ * the mean milliseconds per residual in kind_ms[RICMRCC_PROFILE_KINDS]
+ * (host), per kernel: [0] 64x64 tile, [1] 16x16 tile, [2] dot reduction,
+ * [3] tensor-core operand packing, [4] tcgen05 GEMM, [5] 128x16 tile,
+ * [6] 64x32 tile.  The tiles compute in FP64, or in FP32 with mixed != 0,
+ * which also routes the large contractions to the tensor cores ([3], [4]).
+ * Diagnostic: the events serialise the launches. */
+#define RICMRCC_PROFILE_KINDS 7
 RICMRCC_API int ricmrcc_profile(ricmrcc_t* h, int reps, int mixed, double* kind_ms);
 
 /* Split-precision BF16 tensor-core GEMM (the contraction engine of the
@@ -257,6 +269,102 @@ RICMRCC_API int ricmrcc_energy_backward(ricmrcc_t* h, double* dE_dh, double* dE_
  * set_amplitudes allows warm starts and resuming an interrupted solve. */
 RICMRCC_API int ricmrcc_get_amplitudes(ricmrcc_t* h, double* T1, double* T2);
 RICMRCC_API int ricmrcc_set_amplitudes(ricmrcc_t* h, const double* T1, const double* T2);
+
+/* Residual of the last evaluation (ricmrcc_residual, ricmrcc_step,
+ * ricmrcc_solve or ricmrcc_batch_residual / _step / _solve on a batch that
+ * owns this handle), in the flat class layout (host pointers T1-sized and
+ * T2-sized), at the amplitudes it was evaluated for.  R2 is the
+ * pair-symmetrised residual of Eq. antisym, as ricmrcc_residual returns it. */
+RICMRCC_API int ricmrcc_get_residual(ricmrcc_t* h, double* R1, double* R2);
+
+/* ---- Kernel choice (tiles) and its autotuner -------------------------------
+ *
+ * The FP64 contractions of a captured residual run as persistent grouped
+ * launches of one of five kernels (64x64, 16x16, 128x16 and 64x32 FP64 output
+ * tiles, and a dot reduction); in RICMRCC_MIXED the large GEMM-shaped ones run
+ * on the tcgen05 tensor cores instead.  A tile rule fixes both choices:
+ *   tc_min_flops  smallest contraction (FLOPs) sent to the tensor cores
+ *   skinny        nonzero: tall-skinny contractions (N < 32 <= 64 <= M) use the
+ *                 128x16 / 64x32 tiles, else the 16x16 tile.
+ * The result does not depend on the rule beyond rounding. */
+typedef struct {
+  double tc_min_flops;
+  int skinny;
+} ricmrcc_tile_rule;
+
+#define RICMRCC_TUNE_MAX 8
+typedef struct {
+  int n_candidates;                         /* rules timed */
+  ricmrcc_tile_rule rule[RICMRCC_TUNE_MAX]; /* the candidates */
+  double ms[RICMRCC_TUNE_MAX];              /* mean residual time of each (CUDA events) */
+  int chosen;                               /* index of the fastest; now in effect */
+} ricmrcc_tuning;
+
+RICMRCC_API int ricmrcc_set_tile_rule(ricmrcc_t* h, const ricmrcc_tile_rule* rule);
+RICMRCC_API int ricmrcc_get_tile_rule(const ricmrcc_t* h, ricmrcc_tile_rule* rule);
+/* Time the captured residual under each candidate rule for `precision`
+ * (reps timed launches after one warm-up each; changes no amplitudes) and
+ * keep the fastest.  The residual is timed at the current amplitudes: tune
+ * after a few solver steps, since zero amplitudes skip most accumulations.
+ * Needs integrals and RDMs.  out: host, nullable. */
+RICMRCC_API int ricmrcc_tune(ricmrcc_t* h, int precision, int reps, ricmrcc_tuning* out);
+
+/* ---- Batched instances -----------------------------------------------------
+ *
+ * Many independent problems of uneven sizes solved together on one GPU.  Each
+ * iteration evaluates every instance's residual in one CUDA graph whose
+ * dependency levels ("waves") are each one persistent grouped launch per FP64
+ * tile kind over the contractions of all instances (plus the instances'
+ * tensor-core contractions in RICMRCC_MIXED); the renormalised update and DIIS
+ * then run per instance, with one host synchronisation per phase for the
+ * whole batch.  Results equal those of solving each instance on its own
+ * (ricmrcc_solve) up to the accumulation order of the atomic reductions. */
+typedef struct ricmrcc_batch ricmrcc_batch_t;
+
+/* dims[i] = {n_core, n_act, n_virt, n_aux} of instance i (count >= 1).
+ * Instances are planned in parallel host threads. */
+RICMRCC_API int ricmrcc_batch_create(int count, const int (*dims)[4], ricmrcc_batch_t** out);
+RICMRCC_API void ricmrcc_batch_destroy(ricmrcc_batch_t* b);
+RICMRCC_API const char* ricmrcc_batch_last_error(const ricmrcc_batch_t* b);
+/* Borrowed handle of instance i (owned by the batch: never destroy it).  All
+ * single-instance calls apply to it: set_integrals, set_rdms,
+ * semicanonicalize, amplitude_layout, get/set_amplitudes, get_residual, ... */
+RICMRCC_API int ricmrcc_batch_instance(ricmrcc_batch_t* b, int i, ricmrcc_t** out);
+/* Shorthands for ricmrcc_set_integrals / ricmrcc_set_rdms on instance i. */
+RICMRCC_API int ricmrcc_batch_set_integrals(ricmrcc_batch_t* b, int i, const double* h, const double* B);
+RICMRCC_API int ricmrcc_batch_set_rdms(ricmrcc_batch_t* b, int i, const double* g1, const double* g2,
+                                       const double* g3, int kind);
+/* Residuals and energies of all instances at their current amplitudes, in
+ * `precision` (RICMRCC_FP64 / RICMRCC_MIXED).  E_out: host [count], nullable;
+ * read the residuals with ricmrcc_get_residual on the instances. */
+RICMRCC_API int ricmrcc_batch_residual(ricmrcc_batch_t* b, int precision, double* E_out);
+/* Solve all instances with one set of options (precision, flow s, ...).  In
+ * RICMRCC_MIXED every instance iterates on the tensor-core path until all
+ * unconverged instances reach max|dt| < refine_tol, then the batch refines in
+ * FP64.  Converged instances stop updating; the graph drops them once half of
+ * its instances have finished.  E_out: host [count]; stats: host [count],
+ * nullable.  Returns OK when all converged, else NOT_CONVERGED or DIVERGED
+ * (the per-instance outcome is in stats). */
+RICMRCC_API int ricmrcc_batch_solve(ricmrcc_batch_t* b, const ricmrcc_opts* opts, double* E_out,
+                                    ricmrcc_stats* stats);
+/* n_steps batch iterations without convergence tests (restart != 0 resets the
+ * DIIS histories).  E_out, max_dt_out: host [count], nullable. */
+RICMRCC_API int ricmrcc_batch_step(ricmrcc_batch_t* b, const ricmrcc_opts* opts, int n_steps, int restart,
+                                   double* E_out, double* max_dt_out);
+/* ricmrcc_tune for the batch graph: one rule for all instances. */
+RICMRCC_API int ricmrcc_batch_tune(ricmrcc_batch_t* b, int precision, int reps, ricmrcc_tuning* out);
+/* Sizes of the last captured batch graph: waves (dependency levels), grouped
+ * FP64 launches, tensor-core contractions and FP64-equivalent FLOPs per
+ * iteration over all instances. */
+typedef struct {
+  int waves;
+  int64_t grouped_launches;
+  int64_t tc_contractions;
+  double flops;
+  double tc_flops;
+  int64_t kernel_launches; /* kernel launches of one batch residual graph */
+} ricmrcc_batch_info_t;
+RICMRCC_API int ricmrcc_batch_info(const ricmrcc_batch_t* b, ricmrcc_batch_info_t* out);
 
 /* Allocation-free eigensolver for one symmetric block (no counterpart in the
  * paper; it is the eigen-step of ricmrcc_semicanonicalize offered on its own).

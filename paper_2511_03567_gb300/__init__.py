@@ -52,7 +52,26 @@ class PlanInfo(ctypes.Structure):
                 ("arena_bytes", ctypes.c_double), ("table_bytes", ctypes.c_double),
                 ("kind_launches", ctypes.c_int64 * 3), ("kind_flops", ctypes.c_double * 3),
                 ("tc_contractions", ctypes.c_int64), ("tc_flops", ctypes.c_double),
-                ("tc_pack_bytes", ctypes.c_double)]
+                ("tc_pack_bytes", ctypes.c_double), ("graph_launches", ctypes.c_int64 * 2),
+                ("kernel_ops", ctypes.c_int64 * 7), ("kernel_work", ctypes.c_double * 7)]
+
+
+class TileRule(ctypes.Structure):
+    _fields_ = [("tc_min_flops", ctypes.c_double), ("skinny", ctypes.c_int)]
+
+
+TUNE_MAX = 8
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int), ("rule", TileRule * TUNE_MAX),
+                ("ms", ctypes.c_double * TUNE_MAX), ("chosen", ctypes.c_int)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("waves", ctypes.c_int), ("grouped_launches", ctypes.c_int64),
+                ("tc_contractions", ctypes.c_int64), ("flops", ctypes.c_double),
+                ("tc_flops", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
 
 
 class RicMrccError(RuntimeError):
@@ -107,6 +126,22 @@ def load_library():
                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, vp],
                                 ctypes.c_int),
         "ricmrcc_block_eigh_noalloc": ([vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "ricmrcc_get_residual": ([vp, vp, vp], ctypes.c_int),
+        "ricmrcc_set_tile_rule": ([vp, ctypes.POINTER(TileRule)], ctypes.c_int),
+        "ricmrcc_get_tile_rule": ([vp, ctypes.POINTER(TileRule)], ctypes.c_int),
+        "ricmrcc_tune": ([vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Tuning)], ctypes.c_int),
+        "ricmrcc_batch_create": ([ctypes.c_int, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "ricmrcc_batch_destroy": ([vp], None),
+        "ricmrcc_batch_last_error": ([vp], ctypes.c_char_p),
+        "ricmrcc_batch_instance": ([vp, ctypes.c_int, ctypes.POINTER(vp)], ctypes.c_int),
+        "ricmrcc_batch_set_integrals": ([vp, ctypes.c_int, vp, vp], ctypes.c_int),
+        "ricmrcc_batch_set_rdms": ([vp, ctypes.c_int, vp, vp, vp, ctypes.c_int], ctypes.c_int),
+        "ricmrcc_batch_residual": ([vp, ctypes.c_int, vp], ctypes.c_int),
+        "ricmrcc_batch_solve": ([vp, ctypes.POINTER(Opts), vp, vp], ctypes.c_int),
+        "ricmrcc_batch_step": ([vp, ctypes.POINTER(Opts), ctypes.c_int, ctypes.c_int, vp, vp],
+                               ctypes.c_int),
+        "ricmrcc_batch_tune": ([vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Tuning)], ctypes.c_int),
+        "ricmrcc_batch_info": ([vp, ctypes.POINTER(BatchInfo)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -136,13 +171,18 @@ def _host(x):
 class RicMrcc:
     """One problem (sizes fixed at creation) on the current CUDA device."""
 
-    def __init__(self, n_core, n_act, n_virt, n_aux):
+    def __init__(self, n_core, n_act, n_virt, n_aux, _borrowed=None):
         self.lib = load_library()
         self.dims = (n_core, n_act, n_virt, n_aux)
-        h = ctypes.c_void_p()
-        rc = self.lib.ricmrcc_create(n_core, n_act, n_virt, n_aux, ctypes.byref(h))
-        if rc != OK:
-            raise RicMrccError(rc, "ricmrcc_create failed")
+        self._owner = None
+        if _borrowed is not None:
+            # handle owned by a RicMrccBatch (kept alive through _owner)
+            h, self._owner = _borrowed
+        else:
+            h = ctypes.c_void_p()
+            rc = self.lib.ricmrcc_create(n_core, n_act, n_virt, n_aux, ctypes.byref(h))
+            if rc != OK:
+                raise RicMrccError(rc, "ricmrcc_create failed")
         self.h = h
         lay = Layout()
         self._check(self.lib.ricmrcc_amplitude_layout(self.h, ctypes.byref(lay)))
@@ -156,8 +196,10 @@ class RicMrcc:
 
     def close(self):
         if getattr(self, "h", None):
-            self.lib.ricmrcc_destroy(self.h)
+            if getattr(self, "_owner", None) is None:
+                self.lib.ricmrcc_destroy(self.h)
             self.h = None
+            self._owner = None
 
     def __del__(self):
         try:
@@ -283,9 +325,12 @@ def _plan_info(self):
     return info
 
 
+PROFILE_KINDS = ("tile_64x64", "tile_16x16", "dot", "tc_pack", "tc_gemm", "tile_128x16", "tile_64x32")
+
+
 def _profile(self, reps=3, mixed=False):
-    """Mean ms per residual: [tile64, tile16, dot, tc_pack, tc_gemm]."""
-    ms = np.zeros(5)
+    """Mean ms per residual per kernel (names in PROFILE_KINDS), launches serialised."""
+    ms = np.zeros(len(PROFILE_KINDS))
     self._check(self.lib.ricmrcc_profile(self.h, reps, int(mixed), _ptr(ms)))
     return ms
 
@@ -300,10 +345,125 @@ def _energy_backward(self):
     return dh, dB, ds.value
 
 
+def _get_residual(self):
+    """(R1, R2) flat class layout of the last residual evaluation."""
+    r1 = np.zeros(self.layout.t1_size)
+    r2 = np.zeros(self.layout.t2_size)
+    self._check(self.lib.ricmrcc_get_residual(self.h, _ptr(r1), _ptr(r2)))
+    return r1, r2
+
+
+def _set_tile_rule(self, tc_min_flops=1e8, skinny=True):
+    r = TileRule(float(tc_min_flops), int(bool(skinny)))
+    self._check(self.lib.ricmrcc_set_tile_rule(self.h, ctypes.byref(r)))
+
+
+def _get_tile_rule(self):
+    r = TileRule()
+    self._check(self.lib.ricmrcc_get_tile_rule(self.h, ctypes.byref(r)))
+    return {"tc_min_flops": r.tc_min_flops, "skinny": bool(r.skinny)}
+
+
+def _tuning_dict(t):
+    cands = [{"tc_min_flops": t.rule[i].tc_min_flops, "skinny": bool(t.rule[i].skinny),
+              "ms": t.ms[i]} for i in range(t.n_candidates)]
+    return {"candidates": cands, "chosen": t.chosen}
+
+
+def _tune(self, precision=MIXED, reps=3):
+    """Time the captured residual under each candidate tile rule; keep the fastest."""
+    t = Tuning()
+    self._check(self.lib.ricmrcc_tune(self.h, precision, reps, ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+RicMrcc.get_residual = _get_residual
+RicMrcc.set_tile_rule = _set_tile_rule
+RicMrcc.get_tile_rule = _get_tile_rule
+RicMrcc.tune = _tune
 RicMrcc.energy_backward = _energy_backward
 RicMrcc.step = _step
 RicMrcc.plan_info = _plan_info
 RicMrcc.profile = _profile
+
+
+class RicMrccBatch:
+    """Independent problems of uneven sizes solved together (ricmrcc_batch_*)."""
+
+    def __init__(self, dims):
+        self.lib = load_library()
+        self.dims = [tuple(int(x) for x in d) for d in dims]
+        arr = np.ascontiguousarray(np.array(self.dims, dtype=np.int32).reshape(-1, 4))
+        b = ctypes.c_void_p()
+        rc = self.lib.ricmrcc_batch_create(len(self.dims), arr.ctypes.data, ctypes.byref(b))
+        if rc != OK:
+            raise RicMrccError(rc, "ricmrcc_batch_create failed")
+        self.b = b
+        self.instances = []
+        for i, d in enumerate(self.dims):
+            h = ctypes.c_void_p()
+            self._check(self.lib.ricmrcc_batch_instance(self.b, i, ctypes.byref(h)))
+            self.instances.append(RicMrcc(*d, _borrowed=(h, self)))
+
+    @property
+    def count(self):
+        return len(self.dims)
+
+    def _check(self, rc, allow=(OK,)):
+        if rc not in allow:
+            raise RicMrccError(rc, self.lib.ricmrcc_batch_last_error(self.b).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "b", None):
+            for inst in self.instances:
+                inst.h = None
+                inst._owner = None
+            self.lib.ricmrcc_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __getitem__(self, i):
+        return self.instances[i]
+
+    def residual(self, precision=FP64):
+        """Energies of all instances at their current amplitudes (residuals: get_residual)."""
+        e = np.zeros(self.count)
+        self._check(self.lib.ricmrcc_batch_residual(self.b, precision, _ptr(e)))
+        return e
+
+    def solve(self, s=0.5, **kw):
+        o = RicMrcc.default_opts(s=s, **kw)
+        e = np.zeros(self.count)
+        st = (Stats * self.count)()
+        rc = self.lib.ricmrcc_batch_solve(self.b, ctypes.byref(o), _ptr(e), ctypes.cast(st, ctypes.c_void_p))
+        self._check(rc, allow=(OK, NOT_CONVERGED, DIVERGED))
+        return e, list(st), rc
+
+    def step(self, s=0.5, n_steps=1, restart=False, **kw):
+        o = RicMrcc.default_opts(s=s, **kw)
+        e = np.zeros(self.count)
+        dt = np.zeros(self.count)
+        self._check(self.lib.ricmrcc_batch_step(self.b, ctypes.byref(o), n_steps, int(restart),
+                                                _ptr(e), _ptr(dt)))
+        return e, dt
+
+    def tune(self, precision=MIXED, reps=3):
+        t = Tuning()
+        self._check(self.lib.ricmrcc_batch_tune(self.b, precision, reps, ctypes.byref(t)))
+        return _tuning_dict(t)
+
+    def info(self):
+        i = BatchInfo()
+        self._check(self.lib.ricmrcc_batch_info(self.b, ctypes.byref(i)))
+        return {"waves": i.waves, "grouped_launches": i.grouped_launches,
+                "tc_contractions": i.tc_contractions, "flops": i.flops, "tc_flops": i.tc_flops,
+                "kernel_launches": i.kernel_launches}
 
 
 def header_symbols(header=None):

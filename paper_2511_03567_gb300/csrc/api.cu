@@ -10,6 +10,7 @@
 #include <chrono>
 #include <memory>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/ricmrcc.h"
@@ -17,92 +18,19 @@
 #include "kernels.h"
 #include "planner.h"
 #include "tcgemm.h"
+#include "handle.h"
 #include "grouped.h"
 
 #include "ric_terms.inc"
 
-namespace {
 
-struct DevBuf {
-  double* p = nullptr;
-  int64_t n = 0;
-};
-
-}  // namespace
-
-struct ricmrcc {
-  Dims d{};
-  std::string err;
-  cudaStream_t user_stream = nullptr;
-  cudaStream_t s = nullptr;  // internal work stream
-  cudaEvent_t ev = nullptr;
-  int precision = RICMRCC_FP64;
-
-  // device data
-  double *h = nullptr, *B = nullptr, *eri = nullptr, *F = nullptr, *eps = nullptr;
-  double *g1 = nullptr, *g2 = nullptr, *g3 = nullptr, *L2 = nullptr, *D2 = nullptr, *G = nullptr,
-         *E = nullptr, *L3 = nullptr, *D3 = nullptr;
-  double *T = nullptr, *X = nullptr, *Tn = nullptr, *Err = nullptr;
-  double *scal = nullptr;  // [0] E0, [1] Eacc, [2] maxdt, [3] one, [4] energy out
-  double *hist_v = nullptr, *hist_e = nullptr, *gram = nullptr, *coef = nullptr, *dots = nullptr;
-  int* dstatus = nullptr;
-  int64_t *pack1 = nullptr, *pack2 = nullptr, *pack2b = nullptr;
-  double *flat1 = nullptr, *flat2 = nullptr, *rflat1 = nullptr, *rflat2 = nullptr;
-  double* arena = nullptr;
-  void* tc_scratch = nullptr;  // kLanes slices of tc_scratch_bytes
-  size_t tc_scratch_bytes = 0;
-  // concurrent lanes of the captured residual graph
-  cudaStream_t lane[8] = {nullptr};
-  cudaEvent_t lane_ev[9] = {nullptr};
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [fp64, mixed]
-  int sms = 152;
-  std::vector<void*> group_allocs;  // grouped-launch descriptor arrays
-  int* d_err = nullptr;
-  int64_t tc_ops = 0;
-  double tc_flops = 0.0;
-  int64_t arena_elems = 0;
-  double* host_scal = nullptr;  // pinned, 8 doubles
-  int* d_sweeps = nullptr;
-
-  int64_t n2g = 0, n1g = 0, ng = 0, t1_size = 0, t2_size = 0;
-  int64_t t1_off[3], t2_off[9];
-  int t1_shape[3][2], t2_shape[9][4];
-  int diis_cap = 8;
-
-  Program res_prog, cum_prog;
-  // adjoint (energy_backward)
-  Program gradt_prog, gradh_prog;
-  bool adj_planned = false, solved = false;
-  double solved_s = 0.0;
-  ricmrcc_opts solved_opts{};
-  double *Lam = nullptr, *Yraw = nullptr, *Ytil = nullptr, *GT = nullptr, *gF = nullptr, *gFt = nullptr,
-         *gh = nullptr, *geps = nullptr, *geri = nullptr, *gB = nullptr, *adj_arena = nullptr;
-  int64_t adj_arena_elems = 0;
-  bool have_ints = false, have_rdms = false, planned = false;
-  double E0 = 0.0;
-  int rdm_kind = RICMRCC_RDM;
-  bool verbose = false;
-  // solver iteration state (kept across ricmrcc_step calls)
-  int nvec = 0, iter = 0;
-  bool have_old = false;
-  double e_old = 0.0, last_E = 0.0, last_dt = 0.0;
-  double gram_host[256] = {0.0};
-  std::vector<void*> allocs;
-};
-
-namespace {
+namespace ric {
 
 int fail(ricmrcc_t* h, int code, const std::string& msg) {
   if (h) h->err = msg;
   return code;
 }
 
-#define CK(call)                                                                         \
-  do {                                                                                   \
-    cudaError_t e_ = (call);                                                             \
-    if (e_ != cudaSuccess)                                                               \
-      return fail(h, RICMRCC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-  } while (0)
 
 template <typename T>
 int dalloc(ricmrcc_t* h, T** p, int64_t n) {
@@ -118,11 +46,6 @@ int dalloc(ricmrcc_t* h, T** p, int64_t n) {
   return RICMRCC_OK;
 }
 
-#define TRY(x)                     \
-  do {                             \
-    int rc_ = (x);                 \
-    if (rc_ != RICMRCC_OK) return rc_; \
-  } while (0)
 
 bool finite_host(const double* x, int64_t n) {
   for (int64_t i = 0; i < n; ++i)
@@ -253,40 +176,239 @@ int plan(ricmrcc_t* h) {
   return RICMRCC_OK;
 }
 
-// Contractions routed to the tensor cores in mixed precision: large, unbatched
-// GEMM-shaped ops (95% of the residual FLOPs at the Mid size).
-constexpr int kLanes = 8;
+// Contractions routed to the tensor cores in mixed precision: unbatched
+// GEMM-shaped ops above the rule's size (98% of the residual FLOPs at the
+// 8/8/120 size).  M and K are padded to the 128 x 64 tile, so ops with M >= 64
+// and K >= 32 waste at most half of each.
+bool tc_eligible(const ContractOp& op, const TileRule& r) {
+  return op.kind != 2 && op.L == 1 && op.M >= 64 && op.K >= 32 && op.flops >= r.tc_min_flops;
+}
 
-bool tc_eligible(const ContractOp& op) {
-  return op.kind != 2 && op.L == 1 && op.M >= 128 && op.K >= 64 && op.flops >= 1e8;
+// FP64 kernel of an op: the planner's choice (64x64 tile, 16x16 tile or dot
+// reduction), with tall-skinny ops moved to the 128x16 / 64x32 tiles, whose
+// threads own one output column each and so write C rows contiguously.
+int op_kind(const ContractOp& op, const TileRule& r) {
+  if (op.kind == 2) return 2;
+  if (r.skinny && op.M >= 64 && op.N < 32) return op.N <= 16 ? 3 : 4;
+  return op.kind;
+}
+
+namespace {
+
+// Operand tensors that stay fixed during a solve (the integrals and the RDM
+// tensors); their packed BF16 copies are cached across residual evaluations.
+bool constant_operand(const ricmrcc_t* h, const double* x) {
+  const Dims& d = h->d;
+  const int64_t n = d.n, a = d.a;
+  auto in = [x](const double* base, int64_t len) { return base && x >= base && x < base + len; };
+  return in(h->eri, n * n * n * n) || in(h->F, n * n) || in(h->G, a * a) || in(h->E, a * a) ||
+         in(h->D2, a * a * a * a) || in(h->D3, a * a * a * a * a * a);
+}
+
+uint64_t fnv(uint64_t hsh, const void* p, size_t bytes) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < bytes; ++i) hsh = (hsh ^ c[i]) * 1099511628211ull;
+  return hsh;
+}
+
+}  // namespace
+
+// Which index of a gathered operand runs through memory with unit stride
+// more often: rows (pack with lanes along rows) or K (lanes along K).
+int rows_fast(const int64_t* hR, int64_t rows, const int64_t* hK, int64_t K) {
+  int64_t ur = 0, uk = 0;
+  for (int64_t i = 1; i < rows; ++i) ur += hR[i] - hR[i - 1] == 1;
+  for (int64_t i = 1; i < K; ++i) uk += hK[i] - hK[i - 1] == 1;
+  const double fr = rows > 1 ? (double)ur / (rows - 1) : 0.0, fk = K > 1 ? (double)uk / (K - 1) : 0.0;
+  return fr > fk ? 1 : 0;
+}
+
+// Plan the tensor-core path of the residual program: every operand side of
+// every tensor-core contraction gets a packed split-BF16 buffer, shared by all
+// contractions that gather the same elements (same tensor, offsets and tables).
+// Constant operands (integrals, RDM tensors) are packed once per integral / RDM
+// change (refresh_tc_cache); amplitude-dependent ones (T and intermediates) are
+// packed inside every residual evaluation, at the dependency level of their
+// first consumer, once for all their consumers.
+int ensure_tc_plan(ricmrcc_t* h) {
+  if (h->tc_planned) return RICMRCC_OK;
+  if (!tc_available()) return fail(h, RICMRCC_ENOTSUP, "cuTensorMapEncodeTiled unavailable");
+  if (!tc_prepare()) return fail(h, RICMRCC_ECUDA, "tensor-core kernel attributes");
+  const Program& p = h->res_prog;
+  h->tc_ops = 0;
+  h->tc_flops = 0.0;
+  h->tc_cacheA.assign(p.ops.size(), -1);
+  h->tc_cacheB.assign(p.ops.size(), -1);
+  h->tc_cache.clear();
+  struct Key {
+    int entry;
+    const int64_t* hR;
+    const int64_t* hK;
+  };
+  std::unordered_map<uint64_t, std::vector<Key>> keys;
+  std::vector<const int64_t*> hRs, hKs;
+  for (size_t i = 0; i < p.ops.size(); ++i) {
+    const ContractOp& op = p.ops[i];
+    if (!tc_eligible(op, h->rule)) continue;
+    ++h->tc_ops;
+    h->tc_flops += op.flops;
+    const int64_t* th = p.table.data() + op.tab;
+    const int64_t* tAM = th + 3;
+    const int64_t* tBN = tAM + 2 * op.M;
+    const int64_t* tAK = tBN + 2 * op.N;
+    const int64_t* tBK = tAK + op.K;
+    for (int side = 0; side < 2; ++side) {
+      PackedOperand e;
+      e.X = side ? op.B : op.A;
+      e.xL = th[side];
+      e.rows = side ? op.N : op.M;
+      e.K = op.K;
+      e.rows_pad = side ? tc_pad(op.N, tc_pick_bn(op.N)) : tc_pad(op.M, 128);
+      e.Kp = tc_pad(op.K, 64);
+      e.pat = side ? 0b010 : 0b100;
+      e.level = constant_operand(h, e.X) ? -1 : op.level;
+      const int64_t* hR = side ? tBN : tAM;
+      const int64_t* hK = side ? tBK : tAK;
+      const int64_t* dt = p.d_table + op.tab;
+      e.tR = dt + (hR - th);
+      e.tK = dt + (hK - th);
+      uint64_t k = 1469598103934665603ull;
+      k = fnv(k, &e.X, sizeof(e.X));
+      k = fnv(k, &e.xL, sizeof(e.xL));
+      k = fnv(k, &e.rows, sizeof(e.rows));
+      k = fnv(k, &e.K, sizeof(e.K));
+      k = fnv(k, &e.rows_pad, sizeof(e.rows_pad));
+      k = fnv(k, &e.pat, sizeof(e.pat));
+      k = fnv(k, hR, sizeof(int64_t) * e.rows);
+      k = fnv(k, hK, sizeof(int64_t) * e.K);
+      int found = -1;
+      for (const Key& q : keys[k]) {
+        const PackedOperand& o = h->tc_cache[q.entry];
+        if (o.X == e.X && o.xL == e.xL && o.rows == e.rows && o.K == e.K && o.rows_pad == e.rows_pad &&
+            o.pat == e.pat && !memcmp(q.hR, hR, sizeof(int64_t) * e.rows) &&
+            !memcmp(q.hK, hK, sizeof(int64_t) * e.K)) {
+          found = q.entry;
+          break;
+        }
+      }
+      if (found < 0) {
+        e.rows_fast = rows_fast(hR, e.rows, hK, e.K);
+        const size_t bytes = (size_t)e.rows_pad * 3 * e.Kp * 2;
+        cudaError_t err = cudaMalloc(&e.data, bytes);
+        if (err != cudaSuccess) {
+          cudaGetLastError();
+          return fail(h, RICMRCC_ENOMEM, "tensor-core operand buffers");
+        }
+        h->allocs.push_back(e.data);
+        found = (int)h->tc_cache.size();
+        h->tc_cache.push_back(e);
+        keys[k].push_back({found, hR, hK});
+      } else if (h->tc_cache[found].level >= 0) {
+        // packed once, before the earliest consumer
+        h->tc_cache[found].level = std::min(h->tc_cache[found].level, op.level);
+      }
+      (side ? h->tc_cacheB : h->tc_cacheA)[i] = found;
+    }
+  }
+  h->tc_need = 256;  // every operand side has its own packed buffer
+  h->tc_cache_valid = false;
+  h->tc_planned = true;
+  return RICMRCC_OK;
+}
+
+int pack_entry(const PackedOperand& e, cudaStream_t s) {
+  return tc_pack(e.X, e.xL, e.tR, e.tK, e.rows, e.K, e.rows_pad, e.Kp, e.pat, e.rows_fast, e.data, s);
 }
 
 int ensure_tc(ricmrcc_t* h) {
+  TRY(ensure_tc_plan(h));
   if (h->tc_scratch) return RICMRCC_OK;
-  if (!tc_available()) return fail(h, RICMRCC_ENOTSUP, "cuTensorMapEncodeTiled unavailable");
-  if (!tc_prepare()) return fail(h, RICMRCC_ECUDA, "tensor-core kernel attributes");
-  size_t need = 0;
-  h->tc_ops = 0;
-  h->tc_flops = 0.0;
-  for (const auto& op : h->res_prog.ops)
-    if (tc_eligible(op)) {
-      need = std::max(need, tc_scratch_bytes(op.M, op.N, op.K));
-      ++h->tc_ops;
-      h->tc_flops += op.flops;
-    }
-  if (need == 0) need = 256;
-  need = (need + 255) / 256 * 256;
-  cudaError_t e = cudaMalloc(&h->tc_scratch, need * kLanes);
+  // one slice per stream that runs tensor-core contractions
+  cudaError_t e = cudaMalloc(&h->tc_scratch, h->tc_need * kTcLanes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return fail(h, RICMRCC_ENOMEM, "tensor-core scratch");
   }
   h->allocs.push_back(h->tc_scratch);
-  h->tc_scratch_bytes = need;  // per lane
+  h->tc_scratch_bytes = h->tc_need;  // per lane
   return RICMRCC_OK;
 }
 
-TcArgs tc_args(ricmrcc_t* h, const Program& p, const ContractOp& op, int lane = 0) {
+void release_graphs(ricmrcc_t* h) {
+  if (h->s) cudaStreamSynchronize(h->s);  // no launch of the graphs in flight
+  for (auto& g : h->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  h->graph_launches[0] = h->graph_launches[1] = 0;
+  for (void* p : h->group_allocs) cudaFree(p);
+  h->group_allocs.clear();
+}
+
+void release_tc(ricmrcc_t* h) {
+  release_graphs(h);
+  auto drop = [h](void* p) {
+    if (!p) return;
+    cudaFree(p);
+    h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), p), h->allocs.end());
+  };
+  for (auto& e : h->tc_cache) drop(e.data);
+  h->tc_cache.clear();
+  h->tc_cacheA.clear();
+  h->tc_cacheB.clear();
+  drop(h->tc_scratch);
+  h->tc_scratch = nullptr;
+  h->tc_scratch_bytes = 0;
+  h->tc_planned = false;
+  h->tc_cache_valid = false;
+}
+
+std::vector<TileRule> tune_candidates(const TileRule& cur, bool mixed) {
+  std::vector<TileRule> c;
+  if (!mixed) {
+    for (int sk = 0; sk < 2; ++sk) {
+      TileRule r = cur;
+      r.skinny = sk;
+      c.push_back(r);
+    }
+    return c;
+  }
+  // tensor-core threshold sweep with the tall-skinny tiles, plus one point
+  // without them
+  const double tc[7] = {3e6, 1e7, 3e7, 1e8, 3e8, 1e9, 3e9};
+  for (double f : tc) {
+    TileRule r;
+    r.tc_min_flops = f;
+    r.skinny = 1;
+    c.push_back(r);
+  }
+  TileRule r;
+  r.tc_min_flops = 1e8;
+  r.skinny = 0;
+  c.push_back(r);
+  return c;
+}
+
+int set_rule(ricmrcc_t* h, const TileRule& r) {
+  if (r.tc_min_flops == h->rule.tc_min_flops && r.skinny == h->rule.skinny) return RICMRCC_OK;
+  CK(cudaStreamSynchronize(h->s));
+  release_tc(h);
+  h->rule = r;
+  return RICMRCC_OK;
+}
+
+int refresh_tc_cache(ricmrcc_t* h, cudaStream_t s) {
+  if (h->tc_cache_valid) return RICMRCC_OK;
+  for (const PackedOperand& e : h->tc_cache)
+    if (e.level < 0 && pack_entry(e, s) != 0) return fail(h, RICMRCC_ECUDA, "tensor-core operand packing");
+  CK(cudaGetLastError());
+  h->tc_cache_valid = true;
+  return RICMRCC_OK;
+}
+
+TcArgs tc_args(ricmrcc_t* h, const Program& p, int op_index, int lane) {
+  const ContractOp& op = p.ops[op_index];
   const int64_t* t = p.d_table + op.tab;
   const int64_t* th = p.table.data() + op.tab;
   TcArgs a;
@@ -306,16 +428,40 @@ TcArgs tc_args(ricmrcc_t* h, const Program& p, const ContractOp& op, int lane = 
   a.N = op.N;
   a.K = op.K;
   a.alpha = op.alpha;
-  a.scratch = static_cast<char*>(h->tc_scratch) + (size_t)lane * h->tc_scratch_bytes;
+  const int slice = lane >= kTcLane0 ? lane - kTcLane0 : 0;
+  a.scratch = static_cast<char*>(h->tc_scratch) + (size_t)slice * h->tc_scratch_bytes;
   a.scratch_bytes = h->tc_scratch_bytes;
   a.err = h->d_err;
+  if (&p == &h->res_prog && (size_t)op_index < h->tc_cacheA.size()) {
+    const int ca = h->tc_cacheA[op_index], cb = h->tc_cacheB[op_index];
+    if (ca >= 0) a.packA = h->tc_cache[ca].data;
+    if (cb >= 0) a.packB = h->tc_cache[cb].data;
+  }
   return a;
 }
 
+// Serial execution: pack the amplitude-dependent operand sides of one
+// tensor-core contraction just before it (their producers precede it).
+// `done` marks the buffers already packed in this evaluation.
+int pack_variable_sides(ricmrcc_t* h, const Program& p, int i, std::vector<char>& done, cudaStream_t s) {
+  if (&p != &h->res_prog || (size_t)i >= h->tc_cacheA.size()) return RICMRCC_OK;
+  done.resize(h->tc_cache.size(), 0);
+  for (int e : {h->tc_cacheA[i], h->tc_cacheB[i]}) {
+    if (e < 0 || h->tc_cache[e].level < 0 || done[e]) continue;
+    if (pack_entry(h->tc_cache[e], s) != 0) return fail(h, RICMRCC_ECUDA, "tensor-core operand packing");
+    done[e] = 1;
+  }
+  return RICMRCC_OK;
+}
+
 int run_program(ricmrcc_t* h, const Program& p, bool mixed = false) {
-  for (const auto& op : p.ops) {
-    if (mixed && tc_eligible(op)) {
-      TcArgs a = tc_args(h, p, op);
+  std::vector<char> packed;
+  if (mixed && &p == &h->res_prog) TRY(refresh_tc_cache(h, h->s));
+  for (size_t i = 0; i < p.ops.size(); ++i) {
+    const ContractOp& op = p.ops[i];
+    if (mixed && tc_eligible(op, h->rule)) {
+      TRY(pack_variable_sides(h, p, (int)i, packed, h->s));
+      TcArgs a = tc_args(h, p, (int)i, 0);
       const int rc = tc_contract(a, h->s);
       if (rc != 0) return fail(h, RICMRCC_ECUDA, "tensor-core contraction launch failed (" + std::to_string(rc) + ")");
     } else {
@@ -326,6 +472,7 @@ int run_program(ricmrcc_t* h, const Program& p, bool mixed = false) {
 }
 
 int rebuild_reference(ricmrcc_t* h) {
+  h->tc_cache_valid = false;  // integrals or RDM tensors changed
   if (!(h->have_ints && h->have_rdms)) return RICMRCC_OK;
   const Dims& d = h->d;
   launch_fock(h->F, h->h, h->eri, h->g1, d, h->s);
@@ -393,19 +540,15 @@ int cumulants(ricmrcc_t* h, int kind) {
   return RICMRCC_OK;
 }
 
-// Capture the residual program as a CUDA graph: zero the accumulators and the
-// intermediate arena, then run the contractions level by level, each level's
-// independent ops spread over kLanes streams (outputs accumulate atomically, so
-// ops of one level need no ordering; intermediates flow only to later levels).
-// Descriptor arrays of one grouped launch (device), kept for the graph's life.
-struct Group {
-  const GroupOp* ops = nullptr;
-  const int64_t* begin = nullptr;
-  int nops = 0;
-  int64_t total = 0;
-};
+void tc_lanes_meet(cudaStream_t* lanes, cudaEvent_t* ev) {
+  for (int l = 0; l < kTcLanes; ++l) cudaEventRecord(ev[l], lanes[l]);
+  for (int l = 0; l < kTcLanes; ++l)
+    for (int m = 0; m < kTcLanes; ++m)
+      if (m != l) cudaStreamWaitEvent(lanes[l], ev[m], 0);
+}
 
-int make_group(ricmrcc_t* h, const std::vector<GroupOp>& ops, int kind, Group* g) {
+int make_group(ricmrcc_t* h, std::vector<void*>& allocs, const std::vector<GroupOp>& ops, int kind,
+               Group* g) {
   g->nops = (int)ops.size();
   if (ops.empty()) return RICMRCC_OK;
   std::vector<int64_t> begin(ops.size());
@@ -417,9 +560,9 @@ int make_group(ricmrcc_t* h, const std::vector<GroupOp>& ops, int kind, Group* g
   g->total = t;
   void *dops = nullptr, *dbeg = nullptr;
   CK(cudaMalloc(&dops, sizeof(GroupOp) * ops.size()));
+  allocs.push_back(dops);
   CK(cudaMalloc(&dbeg, sizeof(int64_t) * begin.size()));
-  h->group_allocs.push_back(dops);
-  h->group_allocs.push_back(dbeg);
+  allocs.push_back(dbeg);
   CK(cudaMemcpy(dops, ops.data(), sizeof(GroupOp) * ops.size(), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(dbeg, begin.data(), sizeof(int64_t) * begin.size(), cudaMemcpyHostToDevice));
   g->ops = static_cast<const GroupOp*>(dops);
@@ -443,25 +586,19 @@ GroupOp group_op(const Program& p, const ContractOp& op) {
   return g;
 }
 
+namespace {
+
 // Capture the residual program as a CUDA graph: zero the accumulators and the
-// intermediate arena, then run the contractions level by level.  Per level the
-// FP64 contractions of each tile kind are one persistent grouped launch (lanes
-// 0-2); in mixed precision the tensor-core contractions run on lanes 3-7.
-// Outputs accumulate atomically, so ops of one level need no ordering;
-// intermediates flow only to later levels.
+// intermediate arena, then the launch schedule of schedule.cu (grouped FP64-path
+// launches per level, tensor-core packing and GEMMs in mixed precision) on the
+// handle's lanes.  Outputs accumulate atomically, so ops of one level need no
+// ordering; intermediates flow only to later levels.
 int capture_residual(ricmrcc_t* h, bool mixed) {
-  const Program& p = h->res_prog;
+  const std::vector<ricmrcc_t*> inst{h};
+  const std::vector<char> live{1};
+  Schedule sc;
   // descriptor arrays first (allocation is not allowed inside the capture)
-  std::vector<std::array<Group, 3>> groups(p.max_level + 1);
-  for (int lvl = 0; lvl <= p.max_level; ++lvl) {
-    std::vector<GroupOp> by_kind[3];
-    for (const auto& op : p.ops) {
-      if (op.level != lvl || (mixed && tc_eligible(op))) continue;
-      if (op.L == 0 || op.M == 0 || op.N == 0 || op.K == 0) continue;
-      by_kind[op.kind].push_back(group_op(p, op));
-    }
-    for (int k = 0; k < 3; ++k) TRY(make_group(h, by_kind[k], k, &groups[lvl][k]));
-  }
+  TRY(build_schedule(h, inst, live, h->rule, mixed, h->group_allocs, &sc));
   cudaStream_t s0 = h->lane[0];
   CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
   auto fail_capture = [&](int rc) {
@@ -477,28 +614,11 @@ int capture_residual(ricmrcc_t* h, bool mixed) {
     return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: memset"));
   if (mixed && cudaMemsetAsync(h->d_err, 0, sizeof(int), s0) != cudaSuccess)
     return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: memset"));
-  for (int lvl = 0; lvl <= p.max_level; ++lvl) {
-    cudaEventRecord(h->lane_ev[8], s0);  // fork
-    for (int l = 1; l < kLanes; ++l) cudaStreamWaitEvent(h->lane[l], h->lane_ev[8], 0);
-    for (int k = 0; k < 3; ++k) {
-      const Group& g = groups[lvl][k];
-      launch_grouped(k, g.ops, g.begin, g.nops, g.total, h->sms, h->lane[k]);
-    }
-    if (mixed) {
-      int j = 0;
-      for (const auto& op : p.ops) {
-        if (op.level != lvl || !tc_eligible(op)) continue;
-        const int l = 3 + (j++ % (kLanes - 3));
-        TcArgs a = tc_args(h, p, op, l);
-        if (tc_contract(a, h->lane[l]) != 0)
-          return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: tensor-core launch"));
-      }
-    }
-    for (int l = 1; l < kLanes; ++l) {  // join
-      cudaEventRecord(h->lane_ev[l], h->lane[l]);
-      cudaStreamWaitEvent(s0, h->lane_ev[l], 0);
-    }
-  }
+  StreamTarget tgt(h->lane, h->lane_ev, h->tc_ev);
+  int64_t launches = 0;
+  const int rc = run_schedule(h, sc, inst, live, h->rule, mixed, tgt, h->tc_scratch, h->tc_scratch_bytes,
+                              h->d_err, &launches);
+  if (rc != RICMRCC_OK) return fail_capture(rc);
   cudaGraph_t g = nullptr;
   CK(cudaStreamEndCapture(s0, &g));
   cudaGraphExec_t ex = nullptr;
@@ -509,11 +629,17 @@ int capture_residual(ricmrcc_t* h, bool mixed) {
     return fail(h, RICMRCC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
   h->graph[mixed ? 1 : 0] = ex;
+  h->graph_launches[mixed ? 1 : 0] = launches;
   return RICMRCC_OK;
 }
 
+}  // namespace
+
 int residual_device(ricmrcc_t* h, bool mixed) {
-  if (mixed) TRY(ensure_tc(h));
+  if (mixed) {
+    TRY(ensure_tc(h));
+    TRY(refresh_tc_cache(h, h->s));
+  }
   cudaGraphExec_t& ex = h->graph[mixed ? 1 : 0];
   if (!ex) TRY(capture_residual(h, mixed));
   CK(cudaGraphLaunch(ex, h->s));
@@ -529,7 +655,9 @@ int check_tc_error(ricmrcc_t* h) {
   return RICMRCC_OK;
 }
 
-}  // namespace
+}  // namespace ric
+
+using namespace ric;
 
 extern "C" {
 
@@ -564,13 +692,14 @@ static int create_impl(ricmrcc_t* h, int n_core, int n_act, int n_virt, int n_au
   d.nh = n_core + n_act;
   CK(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&h->ev, cudaEventDisableTiming));
-  for (int l = 0; l < 8; ++l) CK(cudaStreamCreateWithFlags(&h->lane[l], cudaStreamNonBlocking));
+  for (int l = 0; l < kLanes; ++l) CK(cudaStreamCreateWithFlags(&h->lane[l], cudaStreamNonBlocking));
   {
     int dev = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  for (int l = 0; l < 9; ++l) CK(cudaEventCreateWithFlags(&h->lane_ev[l], cudaEventDisableTiming));
+  for (int l = 0; l <= kLanes; ++l) CK(cudaEventCreateWithFlags(&h->lane_ev[l], cudaEventDisableTiming));
+  for (int l = 0; l < kTcLanes; ++l) CK(cudaEventCreateWithFlags(&h->tc_ev[l], cudaEventDisableTiming));
   const int64_t n = d.n, a = d.a;
   h->n2g = (int64_t)d.np * d.np * d.nh * d.nh;
   h->n1g = (int64_t)d.np * d.nh;
@@ -600,7 +729,7 @@ static int create_impl(ricmrcc_t* h, int n_core, int n_act, int n_virt, int n_au
   TRY(dalloc(h, &h->dstatus, 4));
   TRY(dalloc(h, &h->d_sweeps, 4));
   TRY(dalloc(h, &h->d_err, 4));
-  CK(cudaMallocHost(&h->host_scal, 8 * sizeof(double)));
+  CK(cudaMallocHost(&h->host_scal, 32 * sizeof(double)));
   std::vector<int64_t> p1, p2, p2b;
   build_layout(h, p1, p2, p2b);
   TRY(dalloc(h, &h->pack1, (int64_t)p1.size()));
@@ -630,6 +759,8 @@ void ricmrcc_destroy(ricmrcc_t* h) {
     if (g) cudaGraphExecDestroy(g);
   for (void* p : h->group_allocs) cudaFree(p);
   for (auto& e : h->lane_ev)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : h->tc_ev)
     if (e) cudaEventDestroy(e);
   for (auto& l : h->lane)
     if (l) cudaStreamDestroy(l);
@@ -806,7 +937,7 @@ int ricmrcc_opts_default(ricmrcc_opts* o) {
 
 }  // extern "C"
 
-namespace {
+namespace ric {
 
 int ensure_diis(ricmrcc_t* h, int cap) {
   if (h->diis_cap != cap || !h->hist_v) {
@@ -832,18 +963,19 @@ void reset_iteration_state(ricmrcc_t* h) {
 // then DIIS extrapolation over the stored (t_new, t_new - t) pairs.
 // *conv is set when the energy change and max |t_new - t| are below the
 // thresholds (T is then left at the converged iterate).
-int iterate(ricmrcc_t* h, const ricmrcc_opts& o, bool check, bool mixed, bool* conv, bool* diverged) {
-  *conv = false;
-  *diverged = false;
-  const int cap = o.diis_size > 0 ? o.diis_size : 1;
-  TRY(ensure_diis(h, cap));
+int iter_update(ricmrcc_t* h, const ricmrcc_opts& o) {
+  TRY(ensure_diis(h, o.diis_size > 0 ? o.diis_size : 1));
   ++h->iter;
-  TRY(residual_device(h, mixed));
-  if (mixed) TRY(check_tc_error(h));
   CK(cudaMemsetAsync(h->scal + 2, 0, sizeof(double), h->s));
   launch_update(h->T, h->X, h->Tn, h->Err, h->eps, h->d, o.s, h->scal + 2, h->s);
   CK(cudaMemcpyAsync(h->host_scal, h->scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->s));
-  CK(cudaStreamSynchronize(h->s));
+  return RICMRCC_OK;
+}
+
+int iter_check(ricmrcc_t* h, const ricmrcc_opts& o, bool check, bool* conv, bool* diverged, bool* diis) {
+  *conv = false;
+  *diverged = false;
+  *diis = false;
   const double E = h->E0 + h->host_scal[1];
   const double maxdt = h->host_scal[2];
   h->last_E = E;
@@ -864,6 +996,7 @@ int iterate(ricmrcc_t* h, const ricmrcc_opts& o, bool check, bool mixed, bool* c
     return RICMRCC_OK;
   }
   // DIIS history (ring buffer; the extrapolation does not depend on order)
+  const int cap = h->diis_cap;
   const int slot = h->nvec % cap;
   CK(cudaMemcpyAsync(h->hist_v + (int64_t)slot * h->ng, h->Tn, sizeof(double) * h->ng,
                      cudaMemcpyDeviceToDevice, h->s));
@@ -873,13 +1006,18 @@ int iterate(ricmrcc_t* h, const ricmrcc_opts& o, bool check, bool mixed, bool* c
   const int m = h->nvec < cap ? h->nvec : cap;
   CK(cudaMemsetAsync(h->dots, 0, sizeof(double) * 16, h->s));
   launch_dots(h->dots, h->Err, h->hist_e, h->ng, m, h->ng, h->s);
-  CK(cudaMemcpyAsync(h->host_scal + 4, h->dots, sizeof(double) * 4, cudaMemcpyDeviceToHost, h->s));
-  double dv[16];
-  CK(cudaMemcpyAsync(dv, h->dots, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s));
-  CK(cudaStreamSynchronize(h->s));
+  CK(cudaMemcpyAsync(h->host_scal + 8, h->dots, sizeof(double) * m, cudaMemcpyDeviceToHost, h->s));
+  *diis = true;
+  return RICMRCC_OK;
+}
+
+int iter_finish(ricmrcc_t* h, const ricmrcc_opts& o) {
+  const int cap = h->diis_cap;
+  const int slot = (h->nvec - 1) % cap;
+  const int m = h->nvec < cap ? h->nvec : cap;
   for (int j = 0; j < m; ++j) {
-    h->gram_host[slot * 16 + j] = dv[j];
-    h->gram_host[j * 16 + slot] = dv[j];
+    h->gram_host[slot * 16 + j] = h->host_scal[8 + j];
+    h->gram_host[j * 16 + slot] = h->host_scal[8 + j];
   }
   if (h->iter >= o.diis_start && m >= 2) {
     CK(cudaMemcpyAsync(h->gram, h->gram_host, sizeof(double) * 256, cudaMemcpyHostToDevice, h->s));
@@ -891,6 +1029,22 @@ int iterate(ricmrcc_t* h, const ricmrcc_opts& o, bool check, bool mixed, bool* c
   return RICMRCC_OK;
 }
 
+namespace {
+
+int iterate(ricmrcc_t* h, const ricmrcc_opts& o, bool check, bool mixed, bool* conv, bool* diverged) {
+  TRY(residual_device(h, mixed));
+  if (mixed) TRY(check_tc_error(h));
+  TRY(iter_update(h, o));
+  CK(cudaStreamSynchronize(h->s));
+  bool diis = false;
+  TRY(iter_check(h, o, check, conv, diverged, &diis));
+  if (!diis) return RICMRCC_OK;
+  CK(cudaStreamSynchronize(h->s));
+  return iter_finish(h, o);
+}
+
+}  // namespace
+
 int check_opts(ricmrcc_t* h, const ricmrcc_opts& o) {
   if (!(o.s >= 0.0) || !isfinite(o.s) || o.max_iter < 1 || o.diis_size < 0 || o.diis_size > 16)
     return fail(h, RICMRCC_EINVAL, "bad options (s >= 0, max_iter >= 1, 0 <= diis_size <= 16)");
@@ -900,7 +1054,7 @@ int check_opts(ricmrcc_t* h, const ricmrcc_opts& o) {
   return RICMRCC_OK;
 }
 
-}  // namespace
+}  // namespace ric
 
 extern "C" {
 
@@ -976,14 +1130,37 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
   out->residual_flops = h->res_prog.flops;
   out->arena_bytes = (double)h->arena_elems * 8.0;
   out->table_bytes = (double)(h->res_prog.table.size() + h->cum_prog.table.size()) * 8.0;
-  out->step_launches = out->residual_launches + 5;  // + update, dots, DIIS solve, extrapolate (or copy)
-  for (const auto& op : h->res_prog.ops) {
+  out->graph_launches[0] = h->graph_launches[0];
+  out->graph_launches[1] = h->graph_launches[1];
+  // launches of one solver iteration: the residual graph (once captured, else
+  // one per contraction) + update, dots, DIIS solve, extrapolate
+  const int64_t gl = h->graph_launches[h->precision == RICMRCC_MIXED ? 1 : 0];
+  out->step_launches = (gl ? gl : out->residual_launches) + 4;
+  const bool mixed = h->precision == RICMRCC_MIXED;
+  static const int slot[kGroupKinds] = {0, 1, 2, 5, 6};
+  for (size_t i = 0; i < h->res_prog.ops.size(); ++i) {
+    const ContractOp& op = h->res_prog.ops[i];
     out->kind_launches[op.kind] += 1;
     out->kind_flops[op.kind] += op.flops;
-    if (tc_eligible(op)) {
+    if (tc_eligible(op, h->rule)) {
       out->tc_contractions += 1;
       out->tc_flops += op.flops;
-      out->tc_pack_bytes += tc_pack_bytes(op.M, op.N, op.K);
+    }
+    const int k = mixed && tc_eligible(op, h->rule) ? 4 : slot[op_kind(op, h->rule)];
+    out->kernel_ops[k] += 1;
+    out->kernel_work[k] += op.flops;
+  }
+  // operand packing per evaluation: each amplitude-dependent buffer once
+  // (read FP64 source, write three BF16 segments); constant ones are packed
+  // only when the integrals or RDMs change.  Known once the tensor-core path
+  // is planned.
+  for (const PackedOperand& e : h->tc_cache) {
+    if (e.level < 0) continue;
+    const double bytes = 8.0 * e.rows * e.K + 6.0 * e.rows_pad * e.Kp;
+    out->tc_pack_bytes += bytes;
+    if (mixed) {
+      out->kernel_ops[3] += 1;
+      out->kernel_work[3] += bytes;
     }
   }
   return RICMRCC_OK;
@@ -1067,43 +1244,35 @@ int ricmrcc_profile(ricmrcc_t* h, int reps, int mixed, double* kind_ms) {
   if (!h || !kind_ms || reps < 1) return fail(h, RICMRCC_EINVAL, "bad arguments");
   if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
   TRY(enter(h));
-  if (mixed) TRY(ensure_tc(h));
-  const Program& p = h->res_prog;
-  const size_t nops = p.ops.size();
-  std::vector<cudaEvent_t> ev(2 * nops + 1);
-  for (auto& e : ev) CK(cudaEventCreate(&e));
-  for (int k = 0; k < 5; ++k) kind_ms[k] = 0.0;
+  // the residual's launch schedule (as captured into the graph) replayed on
+  // the work stream, one launch at a time, with events between launches
+  if (mixed) {
+    TRY(ensure_tc(h));
+    TRY(refresh_tc_cache(h, h->s));
+  }
+  const std::vector<ricmrcc_t*> inst{h};
+  const std::vector<char> live{1};
+  std::vector<void*> allocs;
+  struct Cleanup {
+    std::vector<void*>& a;
+    ~Cleanup() {
+      for (void* q : a) cudaFree(q);
+    }
+  } cleanup{allocs};
+  Schedule sc;
+  TRY(build_schedule(h, inst, live, h->rule, mixed != 0, allocs, &sc));
+  for (int k = 0; k < RICMRCC_PROFILE_KINDS; ++k) kind_ms[k] = 0.0;
   for (int r = 0; r < reps; ++r) {
     CK(cudaMemsetAsync(h->arena, 0, sizeof(double) * h->arena_elems, h->s));
     CK(cudaMemsetAsync(h->X, 0, sizeof(double) * h->ng, h->s));
     CK(cudaMemsetAsync(h->scal + 1, 0, sizeof(double), h->s));
     if (mixed) CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
-    for (size_t i = 0; i < nops; ++i) {
-      CK(cudaEventRecord(ev[2 * i], h->s));
-      const ContractOp& op = p.ops[i];
-      if (mixed && tc_eligible(op)) {
-        TcArgs a = tc_args(h, p, op);
-        if (tc_contract_timed(a, h->s, &ev[2 * i + 1]) != 0) return fail(h, RICMRCC_ECUDA, "tc launch");
-      } else {
-        launch_contract(op, p.d_table, h->s);
-        CK(cudaEventRecord(ev[2 * i + 1], h->s));
-      }
-    }
-    CK(cudaEventRecord(ev[2 * nops], h->s));
-    CK(cudaEventSynchronize(ev[2 * nops]));
-    for (size_t i = 0; i < nops; ++i) {
-      float a = 0.f, b = 0.f;
-      CK(cudaEventElapsedTime(&a, ev[2 * i], ev[2 * i + 1]));
-      CK(cudaEventElapsedTime(&b, ev[2 * i + 1], ev[2 * i + 2]));
-      if (mixed && tc_eligible(p.ops[i])) {
-        kind_ms[3] += a / reps;  // packing
-        kind_ms[4] += b / reps;  // tensor-core GEMM
-      } else {
-        kind_ms[p.ops[i].kind] += (a + b) / reps;
-      }
-    }
+    ProfileTarget tgt(h->s);
+    TRY(run_schedule(h, sc, inst, live, h->rule, mixed != 0, tgt, h->tc_scratch, h->tc_scratch_bytes, h->d_err,
+                     nullptr));
+    if (!tgt.accumulate(kind_ms, 1.0 / reps)) return fail(h, RICMRCC_ECUDA, "profile events");
   }
-  for (auto& e : ev) cudaEventDestroy(e);
+  CK(cudaStreamSynchronize(h->s));
   if (mixed) TRY(check_tc_error(h));
   return leave(h);
 }
@@ -1117,6 +1286,75 @@ int ricmrcc_get_amplitudes(ricmrcc_t* h, double* T1, double* T2) {
   CK(cudaMemcpyAsync(T1, h->rflat1, sizeof(double) * h->t1_size, cudaMemcpyDeviceToHost, h->s));
   CK(cudaMemcpyAsync(T2, h->rflat2, sizeof(double) * h->t2_size, cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
+  return leave(h);
+}
+
+int ricmrcc_get_residual(ricmrcc_t* h, double* R1, double* R2) {
+  if (!h || !R1 || !R2) return fail(h, RICMRCC_EINVAL, "null pointer");
+  TRY(enter(h));
+  launch_gather(h->rflat1, h->X + h->n2g, h->pack1, nullptr, h->t1_size, h->s);
+  launch_gather(h->rflat2, h->X, h->pack2, h->pack2b, h->t2_size, h->s);  // X + X^{pair swap}
+  CK(cudaMemcpyAsync(R1, h->rflat1, sizeof(double) * h->t1_size, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaMemcpyAsync(R2, h->rflat2, sizeof(double) * h->t2_size, cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  return leave(h);
+}
+
+int ricmrcc_set_tile_rule(ricmrcc_t* h, const ricmrcc_tile_rule* rule) {
+  if (!h || !rule) return fail(h, RICMRCC_EINVAL, "null pointer");
+  if (!(rule->tc_min_flops >= 0.0)) return fail(h, RICMRCC_EINVAL, "tc_min_flops must be >= 0");
+  TileRule r;
+  r.tc_min_flops = rule->tc_min_flops;
+  r.skinny = rule->skinny ? 1 : 0;
+  return set_rule(h, r);
+}
+
+int ricmrcc_get_tile_rule(const ricmrcc_t* h, ricmrcc_tile_rule* rule) {
+  if (!h || !rule) return RICMRCC_EINVAL;
+  rule->tc_min_flops = h->rule.tc_min_flops;
+  rule->skinny = h->rule.skinny;
+  return RICMRCC_OK;
+}
+
+int ricmrcc_tune(ricmrcc_t* h, int precision, int reps, ricmrcc_tuning* out) {
+  if (!h || reps < 1) return fail(h, RICMRCC_EINVAL, "bad arguments");
+  if (precision != RICMRCC_FP64 && precision != RICMRCC_MIXED)
+    return fail(h, RICMRCC_EINVAL, "precision must be RICMRCC_FP64 or RICMRCC_MIXED");
+  if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
+  TRY(enter(h));
+  const bool mixed = precision == RICMRCC_MIXED;
+  const std::vector<TileRule> cand = tune_candidates(h->rule, mixed);
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  ricmrcc_tuning res{};
+  double best = 1e300;
+  int bi = 0;
+  for (size_t c = 0; c < cand.size(); ++c) {
+    TRY(set_rule(h, cand[c]));
+    TRY(residual_device(h, mixed));  // capture, cache packing, warm-up
+    if (mixed) TRY(check_tc_error(h));
+    CK(cudaEventRecord(e0, h->s));
+    for (int r = 0; r < reps; ++r) TRY(residual_device(h, mixed));
+    CK(cudaEventRecord(e1, h->s));
+    CK(cudaEventSynchronize(e1));
+    if (mixed) TRY(check_tc_error(h));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    res.rule[c].tc_min_flops = cand[c].tc_min_flops;
+    res.rule[c].skinny = cand[c].skinny;
+    res.ms[c] = ms / reps;
+    if (res.ms[c] < best) {
+      best = res.ms[c];
+      bi = (int)c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  res.n_candidates = (int)cand.size();
+  res.chosen = bi;
+  TRY(set_rule(h, cand[bi]));
+  if (out) *out = res;
   return leave(h);
 }
 

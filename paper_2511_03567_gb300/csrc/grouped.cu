@@ -1,10 +1,18 @@
-// Persistent grouped FP64 contraction kernels.
+// Persistent grouped contraction kernels.
 //
 // One launch executes every contraction of one dependency level (and one tile
 // kind), from one or many problem instances: the ops' tiles are numbered
-// consecutively (prefix sums in `tile_begin`), persistent CTAs stride over the
+// consecutively (prefix sums in `begin`), persistent CTAs stride over the
 // global tile index, find their op by binary search and run that tile exactly
-// like the single-op kernels (offset-table gathers, atomic accumulation).
+// like the single-op kernels (offset-table gathers, atomic accumulation into
+// the FP64 outputs).
+//
+// The compute type CT is double for the FP64 path and float for the FP64
+// remainder of the mixed-precision path.  GB300's FP64 pipe is narrow (about
+// 1.2 TFLOP/s for the whole GPU, which the FP64 tiles saturate), so in mixed
+// precision the operands are rounded to FP32 as they are staged in shared
+// memory and products accumulate in FP32; only the final alpha * sum is
+// widened to FP64 for the atomic update.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,12 +30,12 @@ __device__ __forceinline__ int find_op(const int64_t* __restrict__ begin, int no
   return lo;
 }
 
-template <int BM, int BN, int TM, int TN, int BK>
+template <typename CT, int BM, int BN, int TM, int TN, int BK>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     k_grouped_tile(const GroupOp* __restrict__ ops, const int64_t* __restrict__ begin, int nops, int64_t total) {
   constexpr int NT = (BM / TM) * (BN / TN);
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  __shared__ CT As[BK][BM + 1];
+  __shared__ CT Bs[BK][BN + 1];
   __shared__ int64_t sAM[BM], sCM[BM], sBN[BN], sCN[BN];
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN);
@@ -70,27 +78,28 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     const int64_t ke = kb + op.kchunk < K ? kb + op.kchunk : K;
     const double* __restrict__ A = op.A;
     const double* __restrict__ B = op.B;
-    double acc[TM][TN];
+    const CT alpha = (CT)op.alpha;
+    CT acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
-      for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
+      for (int j = 0; j < TN; ++j) acc[i][j] = (CT)0;
     __syncthreads();
     for (int64_t k0 = kb; k0 < ke; k0 += BK) {
       for (int i = tid; i < BK * BM; i += NT) {
         const int kk = i / BM, mm = i % BM;
         const int64_t k = k0 + kk, m = m0 + mm;
-        As[kk][mm] = (k < ke && m < M) ? A[aL + sAM[mm] + tAK[k]] : 0.0;
+        As[kk][mm] = (k < ke && m < M) ? (CT)A[aL + sAM[mm] + tAK[k]] : (CT)0;
       }
       for (int i = tid; i < BK * BN; i += NT) {
         const int kk = i / BN, nn = i % BN;
         const int64_t k = k0 + kk, n = n0 + nn;
-        Bs[kk][nn] = (k < ke && n < N) ? B[bL + sBN[nn] + tBK[k]] : 0.0;
+        Bs[kk][nn] = (k < ke && n < N) ? (CT)B[bL + sBN[nn] + tBK[k]] : (CT)0;
       }
       __syncthreads();
 #pragma unroll 4
       for (int kk = 0; kk < BK; ++kk) {
-        double a[TM], b[TN];
+        CT a[TM], b[TN];
 #pragma unroll
         for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
 #pragma unroll
@@ -111,22 +120,24 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       for (int j = 0; j < TN; ++j) {
         const int nn = tx * TN + j;
         if (n0 + nn >= N) continue;
-        if (acc[i][j] != 0.0) atomicAdd(C + cL + sCM[mm] + sCN[nn], op.alpha * acc[i][j]);
+        const CT v = alpha * acc[i][j];
+        if (v != (CT)0) atomicAdd(C + cL + sCM[mm] + sCN[nn], (double)v);
       }
     }
     __syncthreads();
   }
 }
 
-__device__ double gsum(double v) {
-  __shared__ double red[32];
+template <typename CT>
+__device__ CT gsum(CT v) {
+  __shared__ CT red[32];
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) red[w] = v;
   __syncthreads();
-  double s = 0.0;
+  CT s = (CT)0;
   if (w == 0) {
-    s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    s = lane < (int)(blockDim.x >> 5) ? red[lane] : (CT)0;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   }
   __syncthreads();
@@ -135,6 +146,7 @@ __device__ double gsum(double v) {
 
 // Dot-product contractions (tiny outputs, long K): one work item per
 // (op, output element, K chunk).
+template <typename CT>
 __global__ void __launch_bounds__(256)
     k_grouped_dot(const GroupOp* __restrict__ ops, const int64_t* __restrict__ begin, int nops, int64_t total) {
   for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
@@ -157,42 +169,70 @@ __global__ void __launch_bounds__(256)
     const int64_t ao = tAL[l] + tAM[m], bo = tBL[l] + tBN[n];
     const int64_t kb = (int64_t)ks * op.kchunk;
     const int64_t ke = kb + op.kchunk < K ? kb + op.kchunk : K;
-    double s = 0.0;
-    for (int64_t k = kb + threadIdx.x; k < ke; k += blockDim.x) s = fma(op.A[ao + tAK[k]], op.B[bo + tBK[k]], s);
-    s = gsum(s);
-    if (threadIdx.x == 0 && s != 0.0) atomicAdd(op.C + tCL[l] + tCM[m] + tCN[n], op.alpha * s);
+    CT s = (CT)0;
+    for (int64_t k = kb + threadIdx.x; k < ke; k += blockDim.x) s = fma((CT)op.A[ao + tAK[k]], (CT)op.B[bo + tBK[k]], s);
+    s = gsum(s) * (CT)op.alpha;
+    if (threadIdx.x == 0 && s != (CT)0) atomicAdd(op.C + tCL[l] + tCM[m] + tCN[n], (double)s);
   }
 }
 
 }  // namespace
 
+// Output tile (rows x columns) of each tile kind.
+constexpr int kTileM[5] = {64, 16, 1, 128, 64};
+constexpr int kTileN[5] = {64, 16, 1, 16, 32};
+
 int64_t group_units(const GroupOp& op, int kind) {
   if (kind == 2) return op.L * op.M * op.N * op.ksplit;
-  const int64_t bm = kind == 0 ? 64 : 16;
-  return op.L * op.ksplit * ((op.M + bm - 1) / bm) * ((op.N + bm - 1) / bm);
+  const int64_t bm = kTileM[kind], bn = kTileN[kind];
+  return op.L * op.ksplit * ((op.M + bm - 1) / bm) * ((op.N + bn - 1) / bn);
 }
 
-void launch_grouped(int kind, const GroupOp* ops, const int64_t* begin, int nops, int64_t total, int sms,
-                    cudaStream_t s) {
-  if (nops <= 0 || total <= 0) return;
+namespace {
+
+template <typename F>
+int resident_per_sm(F kernel) {
+  int b = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, 256, 0) != cudaSuccess) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return b > 0 ? b : 1;
+}
+
+
+template <typename CT>
+void launch_typed(int kind, const GroupOp* ops, const int64_t* begin, int nops, int64_t total, int sms,
+                  cudaStream_t s) {
   // persistent grid: every resident CTA slot of every SM (occupancy API)
-  static int per_sm[3] = {0, 0, 0};
+  static int per_sm[kGroupKinds] = {0, 0, 0, 0, 0};
   if (!per_sm[kind]) {
-    int b = 1;
-    if (kind == 0)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_grouped_tile<64, 64, 4, 4, 16>, 256, 0);
-    else if (kind == 1)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_grouped_tile<16, 16, 1, 1, 16>, 256, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_grouped_dot, 256, 0);
-    per_sm[kind] = b > 0 ? b : 1;
+    switch (kind) {
+      case 0: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 64, 64, 4, 4, 16>); break;
+      case 1: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 16, 16, 1, 1, 16>); break;
+      case 2: per_sm[kind] = resident_per_sm(k_grouped_dot<CT>); break;
+      case 3: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 128, 16, 8, 1, 8>); break;
+      default: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 64, 32, 8, 1, 8>); break;
+    }
   }
   const int64_t slots = (int64_t)sms * per_sm[kind];
   const int g = (int)(total < slots ? total : slots);
-  if (kind == 0)
-    k_grouped_tile<64, 64, 4, 4, 16><<<g, 256, 0, s>>>(ops, begin, nops, total);
-  else if (kind == 1)
-    k_grouped_tile<16, 16, 1, 1, 16><<<g, 256, 0, s>>>(ops, begin, nops, total);
+  switch (kind) {
+    case 0: k_grouped_tile<CT, 64, 64, 4, 4, 16><<<g, 256, 0, s>>>(ops, begin, nops, total); break;
+    case 1: k_grouped_tile<CT, 16, 16, 1, 1, 16><<<g, 256, 0, s>>>(ops, begin, nops, total); break;
+    case 2: k_grouped_dot<CT><<<g, 256, 0, s>>>(ops, begin, nops, total); break;
+    case 3: k_grouped_tile<CT, 128, 16, 8, 1, 8><<<g, 256, 0, s>>>(ops, begin, nops, total); break;
+    default: k_grouped_tile<CT, 64, 32, 8, 1, 8><<<g, 256, 0, s>>>(ops, begin, nops, total); break;
+  }
+}
+
+}  // namespace
+
+void launch_grouped(int kind, bool fp32, const GroupOp* ops, const int64_t* begin, int nops, int64_t total,
+                    int sms, cudaStream_t s) {
+  if (nops <= 0 || total <= 0 || kind < 0 || kind >= kGroupKinds) return;
+  if (fp32)
+    launch_typed<float>(kind, ops, begin, nops, total, sms, s);
   else
-    k_grouped_dot<<<g, 256, 0, s>>>(ops, begin, nops, total);
+    launch_typed<double>(kind, ops, begin, nops, total, sms, s);
 }

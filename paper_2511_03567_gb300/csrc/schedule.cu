@@ -1,0 +1,153 @@
+// Launch schedule of a residual evaluation over one or many instances.
+//
+// The contractions of every instance carry a dependency level (an op only
+// reads intermediates written at lower levels).  Per level ("wave"):
+//   - the FP64-path contractions of each tile kind, from all instances, are
+//     one persistent grouped launch (grouped.cu), on lanes 0 .. kGroupKinds-1;
+//   - in mixed precision, the amplitude-dependent tensor-core operands first
+//     consumed at this level are packed once (tensor-core lanes), the
+//     tensor-core lanes meet, and the tensor-core GEMMs follow, spread over
+//     those lanes;
+//   - the level ends when every lane has finished (join).
+// The same schedule is captured into a CUDA graph (lanes = streams) and, for
+// the per-kernel profile, replayed on one stream with events between launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <vector>
+
+#include "handle.h"
+
+namespace ric {
+
+int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std::vector<char>& live,
+                   const TileRule& rule, bool mixed, std::vector<void*>& allocs, Schedule* out) {
+  out->max_level = 0;
+  for (size_t i = 0; i < inst.size(); ++i)
+    if (live[i]) out->max_level = std::max(out->max_level, inst[i]->res_prog.max_level);
+  out->groups.assign(out->max_level + 1, {});
+  out->flops = out->tc_flops = 0.0;
+  out->tc_contractions = 0;
+  for (int lvl = 0; lvl <= out->max_level; ++lvl) {
+    std::vector<GroupOp> by_kind[kGroupKinds];
+    for (size_t i = 0; i < inst.size(); ++i) {
+      if (!live[i]) continue;
+      const Program& p = inst[i]->res_prog;
+      for (const auto& op : p.ops) {
+        if (op.level != lvl || op.L == 0 || op.M == 0 || op.N == 0 || op.K == 0) continue;
+        out->flops += op.flops;
+        if (mixed && tc_eligible(op, rule)) {
+          out->tc_contractions += 1;
+          out->tc_flops += op.flops;
+          continue;
+        }
+        by_kind[op_kind(op, rule)].push_back(group_op(p, op));
+      }
+    }
+    for (int k = 0; k < kGroupKinds; ++k) TRY(make_group(eh, allocs, by_kind[k], k, &out->groups[lvl][k]));
+  }
+  return RICMRCC_OK;
+}
+
+int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*>& inst,
+                 const std::vector<char>& live, const TileRule& rule, bool mixed, ScheduleTarget& tgt,
+                 void* scratch, size_t slice, int* err, int64_t* launches) {
+  static const int slot[kGroupKinds] = {0, 1, 2, 5, 6};  // profile kernel index per tile kind
+  int64_t n = 0;
+  for (int lvl = 0; lvl <= sc.max_level; ++lvl) {
+    tgt.fork();
+    for (int k = 0; k < kGroupKinds; ++k) {
+      const Group& g = sc.groups[lvl][k];
+      if (!g.nops) continue;
+      tgt.mark(slot[k]);
+      launch_grouped(k, mixed, g.ops, g.begin, g.nops, g.total, eh->sms, tgt.lane(k));
+      ++n;
+    }
+    if (mixed) {
+      int j = 0;
+      for (size_t i = 0; i < inst.size(); ++i) {
+        if (!live[i]) continue;
+        for (const PackedOperand& e : inst[i]->tc_cache) {
+          if (e.level != lvl) continue;
+          tgt.mark(3);
+          if (pack_entry(e, tgt.lane(kTcLane0 + (j++ % kTcLanes))) != 0)
+            return fail(eh, RICMRCC_ECUDA, "operand packing launch");
+          ++n;
+        }
+      }
+      if (j) tgt.tc_meet();
+      j = 0;
+      for (size_t i = 0; i < inst.size(); ++i) {
+        if (!live[i]) continue;
+        ricmrcc_t* h = inst[i];
+        const Program& p = h->res_prog;
+        for (size_t q = 0; q < p.ops.size(); ++q) {
+          const ContractOp& op = p.ops[q];
+          if (op.level != lvl || !tc_eligible(op, rule)) continue;
+          if (op.L == 0 || op.M == 0 || op.N == 0 || op.K == 0) continue;
+          const int s = j++ % kTcLanes;
+          TcArgs a = tc_args(h, p, (int)q, 0);
+          a.scratch = static_cast<char*>(scratch) + (size_t)s * slice;
+          a.scratch_bytes = slice;
+          a.err = err;
+          tgt.mark(4);
+          if (tc_contract(a, tgt.lane(kTcLane0 + s)) != 0)
+            return fail(eh, RICMRCC_ECUDA, "tensor-core launch");
+          n += 1 + (a.packA ? 0 : 1) + (a.packB ? 0 : 1);
+        }
+      }
+    }
+    tgt.join();
+  }
+  tgt.mark(-1);
+  if (launches) *launches = n;
+  return RICMRCC_OK;
+}
+
+// Lanes are the streams of a graph capture: fork from lane 0 at the start of
+// a level, join back into lane 0 at its end.
+StreamTarget::StreamTarget(cudaStream_t* lanes, cudaEvent_t* lane_ev, cudaEvent_t* tc_ev)
+    : lanes_(lanes), lane_ev_(lane_ev), tc_ev_(tc_ev) {}
+cudaStream_t StreamTarget::lane(int l) { return lanes_[l]; }
+void StreamTarget::fork() {
+  cudaEventRecord(lane_ev_[kLanes], lanes_[0]);
+  for (int l = 1; l < kLanes; ++l) cudaStreamWaitEvent(lanes_[l], lane_ev_[kLanes], 0);
+}
+void StreamTarget::tc_meet() { tc_lanes_meet(lanes_ + kTcLane0, tc_ev_); }
+void StreamTarget::join() {
+  for (int l = 1; l < kLanes; ++l) {
+    cudaEventRecord(lane_ev_[l], lanes_[l]);
+    cudaStreamWaitEvent(lanes_[0], lane_ev_[l], 0);
+  }
+}
+
+// Every launch on one stream with an event before it (and one at the end);
+// the interval up to the next event is charged to the launch's kernel.
+ProfileTarget::ProfileTarget(cudaStream_t s) : s_(s) {}
+ProfileTarget::~ProfileTarget() {
+  for (auto& m : marks_) cudaEventDestroy(m.first);
+}
+cudaStream_t ProfileTarget::lane(int) { return s_; }
+void ProfileTarget::mark(int kernel) {
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    ok_ = false;
+    return;
+  }
+  cudaEventRecord(e, s_);
+  marks_.push_back({e, kernel});
+}
+bool ProfileTarget::accumulate(double* kernel_ms, double weight) {
+  if (!ok_ || marks_.empty()) return ok_;
+  if (cudaEventSynchronize(marks_.back().first) != cudaSuccess) return false;
+  for (size_t i = 0; i + 1 < marks_.size(); ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, marks_[i].first, marks_[i + 1].first) != cudaSuccess) return false;
+    if (marks_[i].second >= 0) kernel_ms[marks_[i].second] += weight * ms;
+  }
+  return true;
+}
+
+}  // namespace ric

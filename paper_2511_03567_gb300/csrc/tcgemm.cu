@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(128, 1)
     if (ready && !*(volatile int*)err) {
       const int64_t m = (int64_t)mi * BM + warp * 32 + lane;
       const int64_t cm = m < M ? tCM[m] : 0;
+      const float alpha_f = (float)alpha;
 #pragma unroll 1
       for (int c = 0; c < BN; c += 32) {
         uint32_t r[32];
@@ -213,7 +214,8 @@ __global__ void __launch_bounds__(128, 1)
           for (int j = 0; j < 32; ++j) {
             const int64_t n = (int64_t)ni * BN + c + j;
             const float v = __uint_as_float(r[j]);
-            if (n < N && v != 0.0f) atomicAdd(C + cL + cm + tCN[n], alpha * (double)v);
+            const float w = alpha_f * v;  // one widening per output on the FP64 pipe
+            if (n < N && w != 0.0f) atomicAdd(C + cL + cm + tCN[n], (double)w);
           }
         }
       }
@@ -226,25 +228,96 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
+// Split two values into BF16 hi parts and BF16 lo parts (the rounding error of
+// hi).  The operand is first rounded to FP32 (one conversion on the narrow FP64
+// pipe); hi and lo then come from FP32 arithmetic, and hi + lo keeps about 16
+// significant bits, well inside FP32's 24.
+__device__ __forceinline__ void split_bf16(float x0, float x1, __nv_bfloat162* hi, __nv_bfloat162* lo) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+  const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+  const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+  *hi = __halves2bfloat162(h0, h1);
+  *lo = __halves2bfloat162(l0, l1);
+}
+
 // Gather one operand through offset tables and split it into BF16 hi/lo:
 // out[r][seg * Kp + k], r < rows_pad, three segments with pattern `pat`
 // (bit s set: segment s holds lo, else hi).  Pad rows/columns are zero.
-__global__ void k_pack_split(const double* __restrict__ X, int64_t xL, const int64_t* __restrict__ tR,
-                             const int64_t* __restrict__ tK, int64_t rows, int64_t K, int64_t rows_pad,
-                             int64_t Kp, int pat, __nv_bfloat16* __restrict__ out) {
-  for (int64_t r = blockIdx.x; r < rows_pad; r += gridDim.x) {
+// Work items are (row, 64-wide K chunk) pairs, one per warp and step, two K
+// elements per lane (Kp is a multiple of 64), so short-and-wide operands
+// spread over the whole GPU as well as tall ones.
+__global__ void __launch_bounds__(256)
+    k_pack_split(const double* __restrict__ X, int64_t xL, const int64_t* __restrict__ tR,
+                 const int64_t* __restrict__ tK, int64_t rows, int64_t K, int64_t rows_pad, int64_t Kp, int pat,
+                 __nv_bfloat16* __restrict__ out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nkc = Kp >> 6, items = rows_pad * nkc, seg = Kp >> 1;
+  for (int64_t it = (int64_t)blockIdx.x * 8 + warp; it < items; it += (int64_t)gridDim.x * 8) {
+    const int64_t r = it / nkc, k = ((it - r * nkc) << 6) + 2 * lane;
     const bool live = r < rows;
     const int64_t base = live ? xL + tR[r] : 0;
-    __nv_bfloat16* row = out + r * 3 * Kp;
-    for (int64_t k = threadIdx.x; k < Kp; k += blockDim.x) {
-      const double x = (live && k < K) ? X[base + tK[k]] : 0.0;
-      const __nv_bfloat16 hi = __double2bfloat16(x);
-      const __nv_bfloat16 lo = __double2bfloat16(x - (double)__bfloat162float(hi));
-      row[k] = (pat & 1) ? lo : hi;
-      row[Kp + k] = (pat & 2) ? lo : hi;
-      row[2 * Kp + k] = (pat & 4) ? lo : hi;
-    }
+    const float x0 = (live && k < K) ? (float)X[base + tK[k]] : 0.f;
+    const float x1 = (live && k + 1 < K) ? (float)X[base + tK[k + 1]] : 0.f;
+    __nv_bfloat162 hi, lo;
+    split_bf16(x0, x1, &hi, &lo);
+    __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(out + r * 3 * Kp);
+    const int64_t c = k >> 1;
+    row[c] = (pat & 1) ? lo : hi;
+    row[seg + c] = (pat & 2) ? lo : hi;
+    row[2 * seg + c] = (pat & 4) ? lo : hi;
   }
+}
+
+// Same packing for operands whose rows, not K, are contiguous in memory:
+// 32-row x 64-K tiles are read with lanes along rows (coalesced), transposed
+// in shared memory and written with lanes along K.  rows_pad is a multiple of
+// 32 and Kp of 64.
+__global__ void __launch_bounds__(256)
+    k_pack_split_rows(const double* __restrict__ X, int64_t xL, const int64_t* __restrict__ tR,
+                      const int64_t* __restrict__ tK, int64_t rows, int64_t K, int64_t rows_pad, int64_t Kp,
+                      int pat, __nv_bfloat16* __restrict__ out) {
+  __shared__ float tile[64][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nkt = Kp / 64, ntiles = (rows_pad / 32) * nkt;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = (t / nkt) * 32, k0 = (t % nkt) * 64;
+    const int64_t r = r0 + lane;
+    const bool live = r < rows;
+    const int64_t base = live ? xL + tR[r] : 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int kk = warp + 8 * j;
+      const int64_t k = k0 + kk;
+      tile[kk][lane] = (live && k < K) ? (float)X[base + tK[k]] : 0.f;
+    }
+    __syncthreads();
+    const int64_t seg = Kp >> 1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int rr = warp + 8 * j;
+      __nv_bfloat162 hi, lo;
+      split_bf16(tile[2 * lane][rr], tile[2 * lane + 1][rr], &hi, &lo);
+      __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(out + (r0 + rr) * 3 * Kp);
+      const int64_t c = (k0 >> 1) + lane;
+      row[c] = (pat & 1) ? lo : hi;
+      row[seg + c] = (pat & 2) ? lo : hi;
+      row[2 * seg + c] = (pat & 4) ? lo : hi;
+    }
+    __syncthreads();
+  }
+}
+
+void pack_launch(const double* X, int64_t xL, const int64_t* tR, const int64_t* tK, int64_t rows, int64_t K,
+                 int64_t rows_pad, int64_t Kp, int pat, int rows_fast, __nv_bfloat16* out, cudaStream_t s) {
+  if (rows_fast && rows_pad % 32 == 0) {
+    const int64_t tiles = (rows_pad / 32) * (Kp / 64);
+    const int64_t blocks = std::min<int64_t>(tiles, 152 * 8);
+    k_pack_split_rows<<<(int)blocks, 256, 0, s>>>(X, xL, tR, tK, rows, K, rows_pad, Kp, pat, out);
+    return;
+  }
+  const int64_t items = rows_pad * (Kp / 64);
+  const int64_t blocks = std::min<int64_t>((items + 7) / 8, 152 * 16);
+  k_pack_split<<<(int)blocks, 256, 0, s>>>(X, xL, tR, tK, rows, K, rows_pad, Kp, pat, out);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -339,13 +412,23 @@ int tc_contract_timed(const TcArgs& a, cudaStream_t s, cudaEvent_t* mid) {
   const int bn = tc_pick_bn(a.N);
   const int64_t Mp = tc_pad(a.M, BM), Np = tc_pad(a.N, bn), Kp = tc_pad(a.K, BK);
   const int64_t inner = 3 * Kp;
-  if ((size_t)(Mp + Np) * inner * 2 > a.scratch_bytes) return -3;
-  __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(a.scratch);
-  __nv_bfloat16* pb = pa + Mp * inner;
-  const int threads = 256;
-  auto rgrid = [](int64_t rows) { return (int)std::min<int64_t>(rows, 152 * 16); };
-  k_pack_split<<<rgrid(Mp), threads, 0, s>>>(a.A, a.aL, a.tAM, a.tAK, a.M, a.K, Mp, Kp, 0b100, pa);
-  k_pack_split<<<rgrid(Np), threads, 0, s>>>(a.B, a.bL, a.tBN, a.tBK, a.N, a.K, Np, Kp, 0b010, pb);
+  // scratch for the sides packed here (none when both come packed)
+  if ((size_t)((a.packA ? 0 : Mp) + (a.packB ? 0 : Np)) * inner * 2 > a.scratch_bytes) return -3;
+  // operands packed by the caller are used as given; the others are packed
+  // into the scratch (A first, then B)
+  __nv_bfloat16* free_at = reinterpret_cast<__nv_bfloat16*>(a.scratch);
+  __nv_bfloat16* pa = free_at;
+  if (a.packA) {
+    pa = reinterpret_cast<__nv_bfloat16*>(const_cast<void*>(a.packA));
+  } else {
+    pack_launch(a.A, a.aL, a.tAM, a.tAK, a.M, a.K, Mp, Kp, 0b100, 0, pa, s);
+    free_at += Mp * inner;
+  }
+  __nv_bfloat16* pb = free_at;
+  if (a.packB)
+    pb = reinterpret_cast<__nv_bfloat16*>(const_cast<void*>(a.packB));
+  else
+    pack_launch(a.B, a.bL, a.tBN, a.tBK, a.N, a.K, Np, Kp, 0b010, 0, pb, s);
   if (mid) cudaEventRecord(*mid, s);
   CUtensorMap ma, mb;
   if (!make_map(&ma, pa, inner, Mp, BM) || !make_map(&mb, pb, inner, Np, bn)) return -4;
@@ -356,6 +439,13 @@ int tc_contract_timed(const TcArgs& a, cudaStream_t s, cudaEvent_t* mid) {
     case 128: return launch_tc<128>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.err, s);
     default: return launch_tc<256>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.err, s);
   }
+}
+
+int tc_pack(const double* X, int64_t xL, const int64_t* tR, const int64_t* tK, int64_t rows, int64_t K,
+            int64_t rows_pad, int64_t Kp, int pat, int rows_fast, void* out, cudaStream_t s) {
+  if (!X || !tR || !tK || !out || rows < 0 || rows > rows_pad || K < 0 || K > Kp || Kp % BK) return -1;
+  pack_launch(X, xL, tR, tK, rows, K, rows_pad, Kp, pat, rows_fast, static_cast<__nv_bfloat16*>(out), s);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 size_t tc_scratch_bytes(int64_t M, int64_t N, int64_t K) {

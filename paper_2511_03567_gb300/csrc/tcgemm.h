@@ -15,9 +15,22 @@ struct TcArgs {
   void* scratch;  // packed BF16 operands, tc_scratch_bytes(M, N, K) bytes
   size_t scratch_bytes;
   int* err;       // device flag, set to 1 if a pipeline wait timed out
+  // optional operands already in packed form (tc_pack layout, same padding);
+  // the corresponding side is then not gathered
+  const void* packA = nullptr;
+  const void* packB = nullptr;
 };
 
 bool tc_available();
+int tc_pick_bn(int64_t N);  // N tile of the GEMM for an N extent
+int64_t tc_pad(int64_t x, int64_t m);
+// Gather X[xL + tR[r] + tK[k]] (r < rows, k < K) into the packed split-BF16
+// layout of one operand: rows_pad rows of three Kp segments, segment s the lo
+// part where bit s of `pat` is set, else the hi part (A side 0b100, B side
+// 0b010).  rows_fast != 0 reads with lanes along rows (for operands whose
+// rows are contiguous in X), else along K.  0 on success.
+int tc_pack(const double* X, int64_t xL, const int64_t* tR, const int64_t* tK, int64_t rows, int64_t K,
+            int64_t rows_pad, int64_t Kp, int pat, int rows_fast, void* out, cudaStream_t s);
 // Set the GEMM kernels' shared-memory attribute; call outside graph capture.
 bool tc_prepare();
 size_t tc_scratch_bytes(int64_t M, int64_t N, int64_t K);

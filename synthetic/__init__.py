@@ -296,6 +296,18 @@ def make_config(name, seed=0):
     return make_problem(c["n_core"], c["n_act"], c["n_virt"], c["n_aux"], c["n_det"], seed)
 
 
+# determinants of the batched instances' CI vectors: every M_S = 0
+# determinant of CAS(4,4) and CAS(6,6), 512 random ones of CAS(8,8) (as the
+# 8/8/120 workload)
+BATCH_N_DET = {4: None, 6: None, 8: 512}
+
+
+def make_batched_problem(i, count=48, seed=0):
+    """Instance i of the batched workload (sizes from batched_dims, seed i)."""
+    o, a, v, x = batched_dims(count, seed)[i]
+    return make_problem(o, a, v, x, BATCH_N_DET.get(a, 512), seed + i)
+
+
 def batched_dims(count=48, seed=0):
     """Uneven instance sizes of the batched workload: (n_core, n_act, n_virt, n_aux)."""
     rng = np.random.default_rng([seed, 4])

@@ -31,7 +31,9 @@ def test_library_exports_every_header_symbol(lib_path):
 def test_binding_declares_every_symbol(lib_path):
     lib = ric.load_library()
     for name in ric.header_symbols():
-        assert getattr(lib, name).restype is not None or name == "ricmrcc_destroy"
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert fn.restype is not None or name.endswith("_destroy"), name
 
 
 def test_argument_errors_without_gpu(lib_path):
@@ -39,6 +41,15 @@ def test_argument_errors_without_gpu(lib_path):
     h = ctypes.c_void_p()
     assert lib.ricmrcc_create(-1, 2, 3, 4, ctypes.byref(h)) == ric.EINVAL
     assert lib.ricmrcc_create(1, 2, 3, 0, ctypes.byref(h)) == ric.EINVAL
+    # batch sizes are validated before any device work
+    dims = (ctypes.c_int * 8)(2, 4, 10, 48, 1, 2, 3, 0)
+    b = ctypes.c_void_p()
+    assert lib.ricmrcc_batch_create(0, dims, ctypes.byref(b)) == ric.EINVAL
+    assert lib.ricmrcc_batch_create(2, dims, ctypes.byref(b)) == ric.EINVAL  # n_aux = 0
+    assert lib.ricmrcc_batch_create(1, None, ctypes.byref(b)) == ric.EINVAL
+    assert lib.ricmrcc_batch_create(1, dims, None) == ric.EINVAL
+    assert lib.ricmrcc_tune(None, 0, 1, None) == ric.EINVAL
+    assert lib.ricmrcc_batch_residual(None, 0, None) == ric.EINVAL
     o = ric.Opts()
     assert lib.ricmrcc_opts_default(ctypes.byref(o)) == ric.OK
     assert o.s == 0.5 and o.max_iter == 100 and o.diis_size == 8
