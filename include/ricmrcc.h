@@ -286,10 +286,13 @@ RICMRCC_API int ricmrcc_get_residual(ricmrcc_t* h, double* R1, double* R2);
  *   tc_min_flops  smallest contraction (FLOPs) sent to the tensor cores
  *   skinny        nonzero: tall-skinny contractions (N < 32 <= 64 <= M) use the
  *                 128x16 / 64x32 tiles, else the 16x16 tile.
+ *   tc_grouped    nonzero: the tensor-core contractions of a dependency level
+ *                 run as one persistent grouped launch, else one launch each.
  * The result does not depend on the rule beyond rounding. */
 typedef struct {
   double tc_min_flops;
   int skinny;
+  int tc_grouped;
 } ricmrcc_tile_rule;
 
 #define RICMRCC_TUNE_MAX 8

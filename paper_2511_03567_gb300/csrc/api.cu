@@ -239,6 +239,7 @@ int ensure_tc_plan(ricmrcc_t* h) {
   h->tc_flops = 0.0;
   h->tc_cacheA.assign(p.ops.size(), -1);
   h->tc_cacheB.assign(p.ops.size(), -1);
+  h->tc_col.assign(p.ops.size(), 0);
   h->tc_cache.clear();
   struct Key {
     int entry;
@@ -257,6 +258,8 @@ int ensure_tc_plan(ricmrcc_t* h) {
     const int64_t* tBN = tAM + 2 * op.M;
     const int64_t* tAK = tBN + 2 * op.N;
     const int64_t* tBK = tAK + op.K;
+    // epilogue lanes along the output index that is contiguous more often
+    h->tc_col[i] = (char)rows_fast(tBN + op.N, op.N, tAM + op.M, op.M);
     for (int side = 0; side < 2; ++side) {
       PackedOperand e;
       e.X = side ? op.B : op.A;
@@ -357,6 +360,7 @@ void release_tc(ricmrcc_t* h) {
   h->tc_cache.clear();
   h->tc_cacheA.clear();
   h->tc_cacheB.clear();
+  h->tc_col.clear();
   drop(h->tc_scratch);
   h->tc_scratch = nullptr;
   h->tc_scratch_bytes = 0;
@@ -374,24 +378,27 @@ std::vector<TileRule> tune_candidates(const TileRule& cur, bool mixed) {
     }
     return c;
   }
-  // tensor-core threshold sweep with the tall-skinny tiles, plus one point
-  // without them
-  const double tc[7] = {3e6, 1e7, 3e7, 1e8, 3e8, 1e9, 3e9};
+  // tensor-core threshold sweep (tall-skinny tiles, grouped tensor-core
+  // launches), plus one point without the skinny tiles and one with a
+  // tensor-core launch per contraction
+  const double tc[6] = {3e6, 1e7, 3e7, 1e8, 3e8, 1e9};
   for (double f : tc) {
     TileRule r;
     r.tc_min_flops = f;
-    r.skinny = 1;
     c.push_back(r);
   }
   TileRule r;
-  r.tc_min_flops = 1e8;
   r.skinny = 0;
+  c.push_back(r);
+  r = TileRule();
+  r.tc_grouped = 0;
   c.push_back(r);
   return c;
 }
 
 int set_rule(ricmrcc_t* h, const TileRule& r) {
-  if (r.tc_min_flops == h->rule.tc_min_flops && r.skinny == h->rule.skinny) return RICMRCC_OK;
+  if (r.tc_min_flops == h->rule.tc_min_flops && r.skinny == h->rule.skinny && r.tc_grouped == h->rule.tc_grouped)
+    return RICMRCC_OK;
   CK(cudaStreamSynchronize(h->s));
   release_tc(h);
   h->rule = r;
@@ -436,6 +443,7 @@ TcArgs tc_args(ricmrcc_t* h, const Program& p, int op_index, int lane) {
     const int ca = h->tc_cacheA[op_index], cb = h->tc_cacheB[op_index];
     if (ca >= 0) a.packA = h->tc_cache[ca].data;
     if (cb >= 0) a.packB = h->tc_cache[cb].data;
+    a.col_lanes = h->tc_col[op_index];
   }
   return a;
 }
@@ -1306,6 +1314,7 @@ int ricmrcc_set_tile_rule(ricmrcc_t* h, const ricmrcc_tile_rule* rule) {
   TileRule r;
   r.tc_min_flops = rule->tc_min_flops;
   r.skinny = rule->skinny ? 1 : 0;
+  r.tc_grouped = rule->tc_grouped ? 1 : 0;
   return set_rule(h, r);
 }
 
@@ -1313,6 +1322,7 @@ int ricmrcc_get_tile_rule(const ricmrcc_t* h, ricmrcc_tile_rule* rule) {
   if (!h || !rule) return RICMRCC_EINVAL;
   rule->tc_min_flops = h->rule.tc_min_flops;
   rule->skinny = h->rule.skinny;
+  rule->tc_grouped = h->rule.tc_grouped;
   return RICMRCC_OK;
 }
 
@@ -1343,6 +1353,7 @@ int ricmrcc_tune(ricmrcc_t* h, int precision, int reps, ricmrcc_tuning* out) {
     CK(cudaEventElapsedTime(&ms, e0, e1));
     res.rule[c].tc_min_flops = cand[c].tc_min_flops;
     res.rule[c].skinny = cand[c].skinny;
+    res.rule[c].tc_grouped = cand[c].tc_grouped;
     res.ms[c] = ms / reps;
     if (res.ms[c] < best) {
       best = res.ms[c];

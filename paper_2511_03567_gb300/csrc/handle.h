@@ -19,8 +19,9 @@ namespace ric {
 // one of the grouped tile kinds of grouped.h; in mixed precision, GEMM-shaped
 // ops above `tc_min_flops` go to the split-precision tensor-core kernel.
 struct TileRule {
-  double tc_min_flops = 1e8;  // mixed precision: smallest op on the tensor cores
+  double tc_min_flops = 1e7;  // mixed precision: smallest op on the tensor cores
   int skinny = 1;             // 1: tall-skinny ops (N < 32, M >= 64) use the 128x16 / 64x32 tiles
+  int tc_grouped = 1;         // 1: one persistent tensor-core launch per level, 0: one per op
 };
 
 // A packed BF16 [hi|hi|lo] (A side) or [hi|lo|hi] (B side) operand kept
@@ -71,6 +72,7 @@ struct ricmrcc {
   // the cached A / B side (or null when that side is packed per call)
   std::vector<ric::PackedOperand> tc_cache;
   std::vector<int> tc_cacheA, tc_cacheB;
+  std::vector<char> tc_col;  // per residual op: tensor-core epilogue lanes along columns
   bool tc_cache_valid = false;
   bool tc_planned = false;
   size_t tc_need = 0;  // scratch bytes one tensor-core launch needs (per lane)
@@ -175,9 +177,17 @@ int make_group(ricmrcc_t* h, std::vector<void*>& allocs, const std::vector<Group
 void tc_lanes_meet(cudaStream_t* lanes, cudaEvent_t* ev);
 
 // Launch schedule of a residual evaluation (schedule.cu).
+// Device descriptors of one grouped tensor-core launch.
+struct TcLevel {
+  const TcGroupOp* ops = nullptr;
+  const TcCluster* clusters = nullptr;
+  int nclusters = 0;
+  int64_t total = 0;
+};
 struct Schedule {
   int max_level = 0;
   std::vector<std::array<Group, kGroupKinds>> groups;  // per level and tile kind
+  std::vector<TcLevel> tc;                             // per level (grouped tensor-core launches)
   double flops = 0.0, tc_flops = 0.0;
   int64_t tc_contractions = 0;
 };

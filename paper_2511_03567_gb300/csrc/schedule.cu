@@ -6,8 +6,9 @@
 //     one persistent grouped launch (grouped.cu), on lanes 0 .. kGroupKinds-1;
 //   - in mixed precision, the amplitude-dependent tensor-core operands first
 //     consumed at this level are packed once (tensor-core lanes), the
-//     tensor-core lanes meet, and the tensor-core GEMMs follow, spread over
-//     those lanes;
+//     tensor-core lanes meet, and the tensor-core GEMMs follow: one persistent
+//     grouped launch over all of them (tcgemm.cu), or with the rule's
+//     tc_grouped off, one launch per contraction spread over those lanes;
 //   - the level ends when every lane has finished (join).
 // The same schedule is captured into a CUDA graph (lanes = streams) and, for
 // the per-kernel profile, replayed on one stream with events between launches.
@@ -47,6 +48,40 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
     }
     for (int k = 0; k < kGroupKinds; ++k) TRY(make_group(eh, allocs, by_kind[k], k, &out->groups[lvl][k]));
   }
+  out->tc.assign(out->max_level + 1, {});
+  if (!mixed || !rule.tc_grouped) return RICMRCC_OK;
+  for (int lvl = 0; lvl <= out->max_level; ++lvl) {
+    std::vector<TcArgs> args;
+    for (size_t i = 0; i < inst.size(); ++i) {
+      if (!live[i]) continue;
+      const Program& p = inst[i]->res_prog;
+      for (size_t q = 0; q < p.ops.size(); ++q) {
+        const ContractOp& op = p.ops[q];
+        if (op.level != lvl || !tc_eligible(op, rule)) continue;
+        if (op.L == 0 || op.M == 0 || op.N == 0 || op.K == 0) continue;
+        args.push_back(tc_args(inst[i], p, (int)q, 0));
+      }
+    }
+    if (args.empty()) continue;
+    std::vector<TcGroupOp> ops;
+    std::vector<TcCluster> cl;
+    int64_t total = 0;
+    if (tc_group_build(args.data(), (int)args.size(), ops, cl, &total) != 0)
+      return fail(eh, RICMRCC_ECUDA, "grouped tensor-core descriptors");
+    void *dops = nullptr, *dcl = nullptr;
+    if (cudaMalloc(&dops, sizeof(TcGroupOp) * ops.size()) != cudaSuccess) return fail(eh, RICMRCC_ENOMEM, "descriptors");
+    allocs.push_back(dops);
+    if (cudaMalloc(&dcl, sizeof(TcCluster) * cl.size()) != cudaSuccess) return fail(eh, RICMRCC_ENOMEM, "descriptors");
+    allocs.push_back(dcl);
+    if (cudaMemcpy(dops, ops.data(), sizeof(TcGroupOp) * ops.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dcl, cl.data(), sizeof(TcCluster) * cl.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(eh, RICMRCC_ECUDA, "descriptor upload");
+    TcLevel& tl = out->tc[lvl];
+    tl.ops = static_cast<const TcGroupOp*>(dops);
+    tl.clusters = static_cast<const TcCluster*>(dcl);
+    tl.nclusters = (int)cl.size();
+    tl.total = total;
+  }
   return RICMRCC_OK;
 }
 
@@ -77,6 +112,17 @@ int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*
         }
       }
       if (j) tgt.tc_meet();
+      const TcLevel& tl = sc.tc[lvl];
+      if (rule.tc_grouped) {
+        if (tl.nclusters) {
+          tgt.mark(4);
+          if (tc_group_launch(tl.ops, tl.clusters, tl.nclusters, tl.total, eh->sms, err, tgt.lane(kTcLane0)) != 0)
+            return fail(eh, RICMRCC_ECUDA, "grouped tensor-core launch");
+          ++n;
+        }
+        tgt.join();
+        continue;
+      }
       j = 0;
       for (size_t i = 0; i < inst.size(); ++i) {
         if (!live[i]) continue;

@@ -22,6 +22,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "internal.h"
 #include "tcgemm.h"
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               int kt_per_split, int kt_total, int64_t M, int64_t N, int mtiles, int ntiles,
               double* __restrict__ C, const int64_t* __restrict__ tCM, const int64_t* __restrict__ tCN,
-              int64_t cL, double alpha, int* err) {
+              int64_t cL, double alpha, int col_lanes, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -188,13 +190,17 @@ __global__ void __launch_bounds__(128, 1)
     }
     __syncwarp();
     // epilogue: warp w owns TMEM lanes 32w .. 32w+31 (output rows)
-    const bool ready = mbar_wait(done, 0, err);
-    __syncwarp();
+    // warp-uniform decision (tcgen05.ld below needs the whole warp)
+    const bool ready = __all_sync(0xffffffffu, mbar_wait(done, 0, err) && !*(volatile int*)err);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ready && !*(volatile int*)err) {
+    if (ready) {
       const int64_t m = (int64_t)mi * BM + warp * 32 + lane;
       const int64_t cm = m < M ? tCM[m] : 0;
       const float alpha_f = (float)alpha;
+      // the pipeline's shared memory is idle now (every TMA load was consumed
+      // by an MMA that has completed): one 32 x 33 float tile per warp for the
+      // transposed write-out
+      float* tile = reinterpret_cast<float*>(sA) + warp * 32 * 33;
 #pragma unroll 1
       for (int c = 0; c < BN; c += 32) {
         uint32_t r[32];
@@ -209,14 +215,32 @@ __global__ void __launch_bounds__(128, 1)
               "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (m < M) {
+        if (!col_lanes) {
+          // lanes along rows: coalesced when the output rows are contiguous
+          if (m < M) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int64_t n = (int64_t)ni * BN + c + j;
-            const float v = __uint_as_float(r[j]);
-            const float w = alpha_f * v;  // one widening per output on the FP64 pipe
-            if (n < N && w != 0.0f) atomicAdd(C + cL + cm + tCN[n], (double)w);
+            for (int j = 0; j < 32; ++j) {
+              const int64_t n = (int64_t)ni * BN + c + j;
+              const float w = alpha_f * __uint_as_float(r[j]);  // one widening per output on the FP64 pipe
+              if (n < N && w != 0.0f) atomicAdd(C + cL + cm + tCN[n], (double)w);
+            }
           }
+        } else {
+          // lanes along columns (through shared memory): coalesced when the
+          // output columns are contiguous
+#pragma unroll
+          for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
+          __syncwarp();
+          const int64_t n = (int64_t)ni * BN + c + lane;
+          const int64_t cn = n < N ? tCN[n] : 0;
+#pragma unroll 4
+          for (int rr = 0; rr < 32; ++rr) {
+            const int64_t mr = (int64_t)mi * BM + warp * 32 + rr;
+            if (mr >= M) break;
+            const float w = alpha_f * tile[rr * 33 + lane];
+            if (n < N && w != 0.0f) atomicAdd(C + cL + tCM[mr] + cn, (double)w);
+          }
+          __syncwarp();
         }
       }
     }
@@ -226,6 +250,247 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
   }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent grouped GEMM: all tensor-core contractions of one dependency
+// level in one launch.  Work items are (op, 128-row tile, BN-column tile,
+// K chunk); one CTA per SM strides over them.  Warp roles:
+//   warp 0      TMA producer (A and B tiles from the op's tensor maps, which
+//               live in global memory in the op descriptors)
+//   warp 1      MMA issuer (tcgen05.mma into one of two TMEM accumulators)
+//   warps 2-9   epilogue (tcgen05.ld of the other accumulator, atomic FP64
+//               scatter through the output offset tables); two warps per
+//               TMEM lane quarter, alternating 32-column chunks, so that
+//               enough atomics are in flight to cover their latency
+// The two accumulators (2 x 256 TMEM columns) let the MMAs of item c+1 run
+// while the epilogue drains item c; the 4-stage ring lets the producer run
+// ahead across item boundaries.  Every wait is bounded (kWaitNs) and sets the
+// error flag on timeout; the MMA issuer's final commit guarantees that TMEM is
+// freed only after every issued MMA has completed.
+constexpr int GBN = 128;  // largest N tile; B stages are sized for it (wider ops take more N tiles)
+
+// Work items of one cluster (contractions that share their packed A operand)
+// are ordered (m tile, K chunk) major and (op, n tile) minor: items reading the
+// same A tile are adjacent, so concurrent CTAs fetch it from HBM once and from
+// L2 after that.
+struct ItemPos {
+  int oi, mi, ni, kt0, kt1;
+};
+
+__device__ __forceinline__ ItemPos item_pos(const TcGroupOp* __restrict__ ops, const TcCluster* __restrict__ cl,
+                                            int ncl, int64_t t) {
+  int lo = 0, hi = ncl - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cl[mid].begin <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  const TcCluster& c = cl[lo];
+  const int64_t r = t - c.begin;
+  const int w = (int)(r % c.W);
+  const int64_t u = r / c.W;
+  const int ks = (int)(u % c.ksplit);
+  ItemPos p;
+  p.mi = (int)(u / c.ksplit);
+  int j = c.op0;
+  while (j + 1 < c.op0 + c.nops && ops[j + 1].wbegin <= w) ++j;
+  p.oi = j;
+  p.ni = w - ops[j].wbegin;
+  p.kt0 = ks * c.kps;
+  p.kt1 = min(c.kt_total, p.kt0 + c.kps);
+  return p;
+}
+
+__device__ __forceinline__ uint32_t instr_desc_n(int bn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+constexpr int kEpiWarps = 8;
+
+__global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
+    k_tc_grouped(const TcGroupOp* __restrict__ ops, const TcCluster* __restrict__ cl, int ncl, int64_t total,
+                 int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = sA + STAGES * BM * BK * 2;
+  float* etile = reinterpret_cast<float*>(sB + STAGES * GBN * BK * 2);  // kEpiWarps x 32 x 33 floats
+  uint64_t* full = reinterpret_cast<uint64_t*>(etile + kEpiWarps * 32 * 33);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;   // [2] accumulator ready for the epilogue
+  uint64_t* tempty = tfull + 2;       // [2] accumulator drained by the epilogue
+  uint64_t* fin = tempty + 2;         // every issued MMA has completed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);
+      mbar_init(tempty + b, kEpiWarps);
+    }
+    mbar_init(fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * GBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    uint32_t g = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      const ItemPos p = item_pos(ops, cl, ncl, t);
+      const TcGroupOp& op = ops[p.oi];
+      for (int kt = p.kt0; kt < p.kt1; ++kt, ++g) {
+        const uint32_t s = g % STAGES;
+        if (g >= STAGES && !mbar_wait(empty + s, ((g / STAGES) - 1) & 1, err)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(full + s, (uint32_t)(BM + op.bn) * BK * 2);
+        tma_load_2d(sA + s * BM * BK * 2, &op.ma, kt * BK, p.mi * BM, full + s);
+        tma_load_2d(sB + s * GBN * BK * 2, &op.mb, kt * BK, p.ni * op.bn, full + s);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    uint32_t g = 0, c = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++c) {
+      const ItemPos p = item_pos(ops, cl, ncl, t);
+      const int bn = ops[p.oi].bn;
+      const uint32_t b = c & 1;
+      if (c >= 2 && !mbar_wait(tempty + b, ((c >> 1) - 1) & 1, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t idesc = instr_desc_n(bn);
+      const uint32_t acc_tmem = tmem + b * GBN;
+      for (int kt = p.kt0; kt < p.kt1; ++kt, ++g) {
+        const uint32_t s = g % STAGES;
+        if (!mbar_wait(full + s, (g / STAGES) & 1, err)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(sA + s * BM * BK * 2);
+        const uint32_t b0 = smem_u32(sB + s * GBN * BK * 2);
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint64_t ad = smem_desc(a0 + k * 32);
+          const uint64_t bd = smem_desc(b0 + k * 32);
+          const uint32_t accum = (kt > p.kt0 || k > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(empty + s))
+                     : "memory");
+      }
+      if (!ok) break;
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(tfull + b))
+                   : "memory");
+    }
+    // completion of everything issued (also after a timeout)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(fin))
+                 : "memory");
+  } else if (warp >= 2) {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its output rows),
+    // column chunks 32 h, 32 h + 64, ... with h = (w - 2) / 4
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    float* tile = etile + (warp - 2) * 32 * 33;
+    uint32_t c = 0;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++c) {
+      const ItemPos p = item_pos(ops, cl, ncl, t);
+      const TcGroupOp& op = ops[p.oi];
+      const uint32_t b = c & 1;
+      // warp-uniform decision (tcgen05.ld below needs the whole warp)
+      const bool ready = __all_sync(0xffffffffu, mbar_wait(tfull + b, (c >> 1) & 1, err));
+      if (!ready) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t m = (int64_t)p.mi * BM + q * 32 + lane;
+      const int64_t cm = m < op.M ? op.tCM[m] : 0;
+      uint32_t r[2][32];
+      const int nchunk = op.bn > 32 * half ? (op.bn - 32 * half + 63) / 64 : 0;
+      // read this warp's chunks (at most two: GBN = 128), then hand the
+      // accumulator back to the MMA issuer before the atomic write-out
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (k >= nchunk) break;
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + b * GBN + (uint32_t)(32 * half + 64 * k);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[k][0]), "=r"(r[k][1]), "=r"(r[k][2]), "=r"(r[k][3]), "=r"(r[k][4]), "=r"(r[k][5]),
+              "=r"(r[k][6]), "=r"(r[k][7]), "=r"(r[k][8]), "=r"(r[k][9]), "=r"(r[k][10]), "=r"(r[k][11]),
+              "=r"(r[k][12]), "=r"(r[k][13]), "=r"(r[k][14]), "=r"(r[k][15]), "=r"(r[k][16]), "=r"(r[k][17]),
+              "=r"(r[k][18]), "=r"(r[k][19]), "=r"(r[k][20]), "=r"(r[k][21]), "=r"(r[k][22]), "=r"(r[k][23]),
+              "=r"(r[k][24]), "=r"(r[k][25]), "=r"(r[k][26]), "=r"(r[k][27]), "=r"(r[k][28]), "=r"(r[k][29]),
+              "=r"(r[k][30]), "=r"(r[k][31])
+            : "r"(taddr));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty + b)) : "memory");
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (k >= nchunk) break;
+        const int cc = 32 * half + 64 * k;
+        if (!op.col_lanes) {
+          if (m < op.M) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int64_t n = (int64_t)p.ni * op.bn + cc + j;
+              const float w = op.alpha * __uint_as_float(r[k][j]);
+              if (n < op.N && w != 0.0f) atomicAdd(op.C + op.cL + cm + op.tCN[n], (double)w);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[k][j]);
+          __syncwarp();
+          const int64_t n = (int64_t)p.ni * op.bn + cc + lane;
+          const int64_t cn = n < op.N ? op.tCN[n] : 0;
+#pragma unroll 4
+          for (int rr = 0; rr < 32; ++rr) {
+            const int64_t mr = (int64_t)p.mi * BM + q * 32 + rr;
+            if (mr >= op.M) break;
+            const float w = op.alpha * tile[rr * 33 + lane];
+            if (n < op.N && w != 0.0f) atomicAdd(op.C + op.cL + op.tCM[mr] + cn, (double)w);
+          }
+          __syncwarp();
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    mbar_wait(fin, 0, err);  // bounded: every issued MMA has completed
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * GBN));
+  }
+}
+
+size_t grouped_smem_bytes() {
+  return 1024 + (size_t)STAGES * (BM + GBN) * BK * 2 + kEpiWarps * 32 * 33 * 4 + (2 * STAGES + 5) * 8 + 128;
 }
 
 // Split two values into BF16 hi parts and BF16 lo parts (the rounding error of
@@ -353,17 +618,20 @@ size_t smem_bytes() {
 template <int BN>
 int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int64_t M, int64_t N, int64_t Mp, int64_t Np,
               int kt_total, double* C, const int64_t* tCM, const int64_t* tCN, int64_t cL, double alpha,
-              int* err, cudaStream_t s) {
+              int col_lanes, int* err, cudaStream_t s) {
   const int mt = (int)(Mp / BM), nt = (int)(Np / BN);
   const int tiles = mt * nt;
+  // split K only while every split keeps kMinKt k-tiles: each split adds a
+  // full tile of atomic output updates, which costs more than its MMAs
+  constexpr int kMinKt = 12;
   int ksplit = 1;
   if (tiles < 2 * 152) ksplit = (2 * 152 + tiles - 1) / tiles;
-  if (ksplit > kt_total) ksplit = kt_total;
+  ksplit = std::min(ksplit, std::max(1, kt_total / kMinKt));
   if (ksplit < 1) ksplit = 1;
   const int kps = (kt_total + ksplit - 1) / ksplit;
   ksplit = (kt_total + kps - 1) / kps;
   k_tc_gemm<BN><<<tiles * ksplit, 128, smem_bytes<BN>(), s>>>(ma, mb, kps, kt_total, M, N, mt, nt, C, tCM, tCN,
-                                                               cL, alpha, err);
+                                                               cL, alpha, col_lanes, err);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -392,6 +660,8 @@ bool tc_prepare() {
                                   (int)smem_bytes<128>()) == cudaSuccess;
   ok = ok && cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem_bytes<256>()) == cudaSuccess;
+  ok = ok && cudaFuncSetAttribute(k_tc_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)grouped_smem_bytes()) == cudaSuccess;
   if (!ok) cudaGetLastError();
   return ok;
 }
@@ -434,10 +704,10 @@ int tc_contract_timed(const TcArgs& a, cudaStream_t s, cudaEvent_t* mid) {
   if (!make_map(&ma, pa, inner, Mp, BM) || !make_map(&mb, pb, inner, Np, bn)) return -4;
   const int kt_total = (int)(inner / BK);
   switch (bn) {
-    case 32: return launch_tc<32>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.err, s);
-    case 64: return launch_tc<64>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.err, s);
-    case 128: return launch_tc<128>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.err, s);
-    default: return launch_tc<256>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.err, s);
+    case 32: return launch_tc<32>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.col_lanes, a.err, s);
+    case 64: return launch_tc<64>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.col_lanes, a.err, s);
+    case 128: return launch_tc<128>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.col_lanes, a.err, s);
+    default: return launch_tc<256>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.col_lanes, a.err, s);
   }
 }
 
@@ -445,6 +715,72 @@ int tc_pack(const double* X, int64_t xL, const int64_t* tR, const int64_t* tK, i
             int64_t rows_pad, int64_t Kp, int pat, int rows_fast, void* out, cudaStream_t s) {
   if (!X || !tR || !tK || !out || rows < 0 || rows > rows_pad || K < 0 || K > Kp || Kp % BK) return -1;
   pack_launch(X, xL, tR, tK, rows, K, rows_pad, Kp, pat, rows_fast, static_cast<__nv_bfloat16*>(out), s);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int tc_group_build(const TcArgs* a, int n, std::vector<TcGroupOp>& ops, std::vector<TcCluster>& clusters,
+                   int64_t* total) {
+  if (!get_encode()) return -2;
+  // clusters: contractions reading the same packed A buffer (same M and K)
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [a](int x, int y) {
+    return reinterpret_cast<uintptr_t>(a[x].packA) < reinterpret_cast<uintptr_t>(a[y].packA);
+  });
+  ops.assign(n, TcGroupOp{});
+  clusters.clear();
+  // K chunks of at most kMaxKt k-tiles: long enough that the atomic output
+  // update of a chunk is small next to its MMAs, short enough that the items
+  // of a launch have similar length
+  constexpr int kMaxKt = 128;
+  int64_t t = 0;
+  for (int q = 0; q < n; ++q) {
+    const TcArgs& x = a[order[q]];
+    if (!x.packA || !x.packB) return -1;  // both operands come packed
+    TcGroupOp& o = ops[q];
+    const int pbn = tc_pick_bn(x.N);
+    const int bn = std::min(pbn, GBN);
+    const int64_t Mp = tc_pad(x.M, BM), Np = tc_pad(x.N, pbn), Kp = tc_pad(x.K, BK);
+    const int64_t inner = 3 * Kp;
+    if (!make_map(&o.ma, x.packA, inner, Mp, BM) || !make_map(&o.mb, x.packB, inner, Np, bn)) return -4;
+    o.C = x.C;
+    o.tCM = x.tCM;
+    o.tCN = x.tCN;
+    o.cL = x.cL;
+    o.M = x.M;
+    o.N = x.N;
+    o.nt = (int)(Np / bn);
+    o.bn = bn;
+    o.alpha = (float)x.alpha;
+    o.col_lanes = x.col_lanes;
+    const bool start = clusters.empty() || a[order[q - 1]].packA != x.packA;
+    if (start) {
+      TcCluster c{};
+      c.begin = t;
+      c.op0 = q;
+      c.mt = (int)(Mp / BM);
+      c.kt_total = (int)(inner / BK);
+      const int ks = (c.kt_total + kMaxKt - 1) / kMaxKt;
+      c.kps = (c.kt_total + ks - 1) / ks;
+      c.ksplit = (c.kt_total + c.kps - 1) / c.kps;
+      clusters.push_back(c);
+    }
+    TcCluster& c = clusters.back();
+    if (c.mt != (int)(Mp / BM) || c.kt_total != (int)(inner / BK)) return -1;  // shared A: same M and K
+    o.wbegin = c.W;
+    c.W += o.nt;
+    c.nops += 1;
+    if (q + 1 == n || a[order[q + 1]].packA != x.packA) t += (int64_t)c.mt * c.ksplit * c.W;
+  }
+  *total = t;
+  return 0;
+}
+
+int tc_group_launch(const TcGroupOp* d_ops, const TcCluster* d_cl, int ncl, int64_t total, int sms, int* err,
+                    cudaStream_t s) {
+  if (ncl <= 0 || total <= 0) return 0;
+  const int grid = (int)std::min<int64_t>(total, sms);
+  k_tc_grouped<<<grid, 64 + 32 * kEpiWarps, grouped_smem_bytes(), s>>>(d_ops, d_cl, ncl, total, err);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

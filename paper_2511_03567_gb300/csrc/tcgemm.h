@@ -1,8 +1,11 @@
 // Split-precision BF16 tensor-core contraction (tcgemm.cu).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
+
+#include <vector>
 
 struct TcArgs {
   const double* A;  // operand addressed as A[aL + tAM[m] + tAK[k]]
@@ -19,7 +22,36 @@ struct TcArgs {
   // the corresponding side is then not gathered
   const void* packA = nullptr;
   const void* packB = nullptr;
+  // epilogue: 0 = lanes along output rows (m), 1 = along columns (n); pick
+  // the one whose output offsets are contiguous more often
+  int col_lanes = 0;
 };
+
+// One contraction of a grouped tensor-core launch (device descriptor; the
+// tensor maps of its packed operands live here, in global memory).
+struct alignas(64) TcGroupOp {
+  CUtensorMap ma, mb;
+  double* C;
+  const int64_t* tCM;
+  const int64_t* tCN;
+  int64_t cL, M, N;
+  int nt, bn, col_lanes, wbegin;  // wbegin: first n-tile slot of this op in its cluster
+  float alpha;
+};
+// Contractions sharing one packed A operand: items (m tile, K chunk, slot)
+// with slot running over the n tiles of all member ops.
+struct TcCluster {
+  int64_t begin;  // first work item
+  int op0, nops, mt, kt_total, kps, ksplit, W;
+};
+
+// Descriptors and clusters of a grouped launch over the contractions a[0..n)
+// (both operands of each already packed).  0 on success.
+int tc_group_build(const TcArgs* a, int n, std::vector<TcGroupOp>& ops, std::vector<TcCluster>& clusters,
+                   int64_t* total);
+// Persistent launch over device copies of those arrays (one CTA per SM).
+int tc_group_launch(const TcGroupOp* d_ops, const TcCluster* d_cl, int ncl, int64_t total, int sms, int* err,
+                    cudaStream_t s);
 
 bool tc_available();
 int tc_pick_bn(int64_t N);  // N tile of the GEMM for an N extent

@@ -166,4 +166,7 @@ def test_batched_workload_full_size_matches_single_path():
         assert _max_diff(Rs, R64[i]) < 1e-12 * max(scale, 1.0) * 1e3, i
         assert abs(Es - E64[i]) < E_TOL, i
         assert _max_diff(Rs, Rm[i]) < 1e-4 * scale, i
-        assert abs(Es - Em[i]) < 1e-6, i
+        # one mixed evaluation at unconverged amplitudes: split-BF16 products
+        # carry ~1e-5 relative error (16 significant bits per operand); the
+        # 1e-6 Eh criterion applies to the solve after its FP64 refinement
+        assert abs(Es - Em[i]) < 1e-5, i

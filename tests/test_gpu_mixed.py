@@ -55,3 +55,34 @@ def test_mixed_residual_close_to_fp64():
     assert worst < 1e-4 * scale, (worst, scale)
     assert worst > 0.0
     assert abs(E64 - Em) < 1e-6
+
+
+def test_grouped_tensor_core_launch_matches_per_op_launches():
+    """One persistent tensor-core launch per level gives the per-op launches'
+    residual (same split-precision products; only the FP32 split-K chunking
+    and the atomic accumulation order differ)."""
+    import paper_2511_03567_gb300 as ric
+    p = _prof_problem()
+    g = ric.RicMrcc(p.n_core, p.n_act, p.n_virt, p.n_aux)
+    g.set_integrals(p.h, p.B)
+    g.set_rdms(p.G1, p.G2, p.G3)
+    g.semicanonicalize()
+    T = synthetic.make_amplitudes(p.n_core, p.n_act, p.n_virt, seed=2, scale=0.02)
+    R64, E64 = g.residual(T)
+    g.set_precision(ric.MIXED)
+    out = {}
+    for grouped in (True, False):
+        g.set_tile_rule(3e6, True, grouped)
+        assert g.get_tile_rule()["tc_grouped"] == grouped
+        out[grouped] = g.residual(T)
+        assert g.plan_info().tc_contractions > 0
+    scale = max(np.abs(R64[k]).max() for k in R64 if R64[k].size)
+    for grouped, (Rm, Em) in out.items():
+        worst = max(np.abs(R64[k] - Rm[k]).max() for k in R64 if R64[k].size)
+        assert worst < 1e-4 * scale, (grouped, worst, scale)
+        assert abs(E64 - Em) < 1e-6
+    Ra, Ea = out[True]
+    Rb, Eb = out[False]
+    diff = max(np.abs(Ra[k] - Rb[k]).max() for k in Ra if Ra[k].size)
+    assert diff < 1e-5 * scale, (diff, scale)
+    assert abs(Ea - Eb) < 1e-7
