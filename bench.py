@@ -146,10 +146,18 @@ def roofline(kind_ms, info, mixed, pk, fp64_peak, torch):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), of measured",
                 "work": "bytes: FP64 source read + three BF16 segments written, per packed buffer"}
     elif c == 4:
-        roof = {"bound": "tensor", "achieved": 3.0 * work / t / 1e12, "unit": "TFLOP/s",
-                "peak": pk.get("bf16_tflops_sustained", 1700.0),
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16), of measured",
-                "work": "BF16 FLOPs: 3 x the contraction FLOPs (hi*hi + hi*lo + lo*hi)"}
+        # the tensor-core GEMMs read every packed operand once and update every
+        # output in FP64: 3 x 2MNK BF16 FLOPs over these bytes is ~94 FLOP/B at
+        # the 8/8/120 size, below the machine balance (measured BF16 / HBM =
+        # 250 FLOP/B), so HBM is their roof
+        gb = getattr(info, "tc_gemm_bytes", 0.0)
+        roof = {"bound": "hbm", "achieved": gb / t / 1e9, "unit": "GB/s", "peak": pk.get("hbm_gbs", 6800.0),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), of measured",
+                "work": "bytes: packed operand buffers read once + 16 B (FP64 read+write) per output "
+                        "element per contraction",
+                "tensor_tflops": 3.0 * work / t / 1e12,
+                "tensor_frac": 3.0 * work / t / 1e12 / pk.get("bf16_tflops_sustained", 1700.0),
+                "tensor_peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"}
     elif mixed:
         roof = {"bound": "alu", "achieved": work / t / 1e12, "unit": "TFLOP/s", "peak": fp32_peak_tflops(torch),
                 "peak_source": "nominal FP32 FMA rate: SMs x 128 x 2 x max SM clock (derived)",
@@ -161,6 +169,8 @@ def roofline(kind_ms, info, mixed, pk, fp64_peak, torch):
     roof["kernel"] = name
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
     roof["traffic"] = None
+    roof["traffic_note"] = ("not captured at this size; on the 4/CAS(4,4)/64/200 case the tensor-core "
+                            "launches moved 0.71x their algorithmic bytes (profiles/tc_grouped_prof_full.md)")
     roof["contractions_per_residual"] = int(info.kernel_ops[c])
     roof["ms_per_residual"] = float(kind_ms[c])
     roof["profile_ms_per_residual"] = {n: float(x) for n, x in zip(KERNEL_NAMES, kind_ms)}
@@ -215,6 +225,11 @@ def main():
     ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
     ap.add_argument("--ncu-largest", type=int, default=0,
                     help="profiler mode: one residual, then only the N largest contractions")
+    ap.add_argument("--ncu-residual", type=int, default=0,
+                    help="profiler mode: N residual evaluations at fixed amplitudes under --tile-rule, then exit")
+    ap.add_argument("--tile-rule", type=float, default=None,
+                    help="tensor-core FLOP threshold of a fixed tile rule (skinny tiles and grouped "
+                         "tensor-core launches on); implies --no-tune")
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = WORKLOADS[args.workload]
@@ -239,7 +254,21 @@ def main():
     g.semicanonicalize()
     prec = ric.MIXED if args.precision == "mixed" else ric.FP64
     tuning = None
-    if not args.no_tune and not args.ncu_largest:
+    if args.tile_rule is not None:
+        g.set_tile_rule(args.tile_rule, True, True)
+    if args.ncu_residual:
+        # profiler mode: the residual graph alone, twice or more, same amplitudes
+        g.set_precision(prec)
+        T = synthetic.make_amplitudes(w["n_core"], w["n_act"], w["n_virt"], seed=1, scale=0.02)
+        for _ in range(args.ncu_residual):
+            R, E = g.residual(T)
+        torch.cuda.synchronize()
+        info = g.plan_info()
+        print(json.dumps({"ncu_residual": args.ncu_residual, "workload": w["workload"], "precision": args.precision,
+                          "tile_rule": g.get_tile_rule(), "energy": E,
+                          "graph_launches": int(info.graph_launches[1 if prec == ric.MIXED else 0])}))
+        return 0
+    if not args.no_tune and args.tile_rule is None and not args.ncu_largest:
         # tile rule for this workload, timed at representative (non-zero)
         # amplitudes after a few solver steps (part of setup)
         g.step(s=w["s"], n_steps=3, restart=True, precision=prec)
@@ -408,11 +437,13 @@ def run_batched(args):
     tot = _Sum()
     tot.kernel_work = np.zeros(len(KERNEL_NAMES))
     tot.kernel_ops = np.zeros(len(KERNEL_NAMES), dtype=np.int64)
+    tot.tc_gemm_bytes = 0.0
     for g in b.instances:
         g.set_precision(prec)
         inf = g.plan_info()
         tot.kernel_work += np.array(inf.kernel_work[:])
         tot.kernel_ops += np.array(inf.kernel_ops[:])
+        tot.tc_gemm_bytes += inf.tc_gemm_bytes
     if rank != 0:
         return 0
     pk = peaks()

@@ -218,6 +218,10 @@ typedef struct {
    * [3], the packing, counts the packed operand buffers and their bytes) */
   int64_t kernel_ops[7];
   double kernel_work[7];
+  /* algorithmic bytes of the tensor-core GEMMs per residual: every packed
+   * operand buffer read once, every output element read and written once in
+   * FP64 per contraction (known once the tensor-core path is planned) */
+  double tc_gemm_bytes;
 } ricmrcc_plan_info_t;
 
 /* Sizes of the contraction program planned for this handle. */

@@ -53,7 +53,8 @@ class PlanInfo(ctypes.Structure):
                 ("kind_launches", ctypes.c_int64 * 3), ("kind_flops", ctypes.c_double * 3),
                 ("tc_contractions", ctypes.c_int64), ("tc_flops", ctypes.c_double),
                 ("tc_pack_bytes", ctypes.c_double), ("graph_launches", ctypes.c_int64 * 2),
-                ("kernel_ops", ctypes.c_int64 * 7), ("kernel_work", ctypes.c_double * 7)]
+                ("kernel_ops", ctypes.c_int64 * 7), ("kernel_work", ctypes.c_double * 7),
+                ("tc_gemm_bytes", ctypes.c_double)]
 
 
 class TileRule(ctypes.Structure):

@@ -1157,12 +1157,14 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
     const int k = mixed && tc_eligible(op, h->rule) ? 4 : slot[op_kind(op, h->rule)];
     out->kernel_ops[k] += 1;
     out->kernel_work[k] += op.flops;
+    if (h->tc_planned && tc_eligible(op, h->rule)) out->tc_gemm_bytes += 16.0 * (double)op.M * (double)op.N;
   }
   // operand packing per evaluation: each amplitude-dependent buffer once
   // (read FP64 source, write three BF16 segments); constant ones are packed
   // only when the integrals or RDMs change.  Known once the tensor-core path
   // is planned.
   for (const PackedOperand& e : h->tc_cache) {
+    out->tc_gemm_bytes += 6.0 * e.rows_pad * e.Kp;
     if (e.level < 0) continue;
     const double bytes = 8.0 * e.rows * e.K + 6.0 * e.rows_pad * e.Kp;
     out->tc_pack_bytes += bytes;
