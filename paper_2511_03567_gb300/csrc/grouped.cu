@@ -20,6 +20,12 @@
 
 namespace {
 
+// Fire-and-forget FP64 reduction into global memory (PTX red: no value comes
+// back, so consecutive updates do not wait on each other's completion).
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v) : "memory");
+}
+
 __device__ __forceinline__ int find_op(const int64_t* __restrict__ begin, int nops, int64_t t) {
   int lo = 0, hi = nops - 1;
   while (lo < hi) {
@@ -121,7 +127,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         const int nn = tx * TN + j;
         if (n0 + nn >= N) continue;
         const CT v = alpha * acc[i][j];
-        if (v != (CT)0) atomicAdd(C + cL + sCM[mm] + sCN[nn], (double)v);
+        if (v != (CT)0) red_add(C + cL + sCM[mm] + sCN[nn], (double)v);
       }
     }
     __syncthreads();
@@ -172,7 +178,7 @@ __global__ void __launch_bounds__(256)
     CT s = (CT)0;
     for (int64_t k = kb + threadIdx.x; k < ke; k += blockDim.x) s = fma((CT)op.A[ao + tAK[k]], (CT)op.B[bo + tBK[k]], s);
     s = gsum(s) * (CT)op.alpha;
-    if (threadIdx.x == 0 && s != (CT)0) atomicAdd(op.C + tCL[l] + tCM[m] + tCN[n], (double)s);
+    if (threadIdx.x == 0 && s != (CT)0) red_add(op.C + tCL[l] + tCM[m] + tCN[n], (double)s);
   }
 }
 

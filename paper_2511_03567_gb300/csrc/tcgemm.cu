@@ -30,6 +30,12 @@
 
 namespace {
 
+// Fire-and-forget FP64 reduction into global memory (PTX red: no value comes
+// back, so consecutive updates do not wait on each other's completion).
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v) : "memory");
+}
+
 constexpr int BM = 128;
 constexpr int BK = 64;  // 64 BF16 = 128 bytes: one swizzle atom row
 constexpr int STAGES = 4;
@@ -222,7 +228,7 @@ __global__ void __launch_bounds__(128, 1)
             for (int j = 0; j < 32; ++j) {
               const int64_t n = (int64_t)ni * BN + c + j;
               const float w = alpha_f * __uint_as_float(r[j]);  // one widening per output on the FP64 pipe
-              if (n < N && w != 0.0f) atomicAdd(C + cL + cm + tCN[n], (double)w);
+              if (n < N && w != 0.0f) red_add(C + cL + cm + tCN[n], (double)w);
             }
           }
         } else {
@@ -238,7 +244,7 @@ __global__ void __launch_bounds__(128, 1)
             const int64_t mr = (int64_t)mi * BM + warp * 32 + rr;
             if (mr >= M) break;
             const float w = alpha_f * tile[rr * 33 + lane];
-            if (n < N && w != 0.0f) atomicAdd(C + cL + tCM[mr] + cn, (double)w);
+            if (n < N && w != 0.0f) red_add(C + cL + tCM[mr] + cn, (double)w);
           }
           __syncwarp();
         }
@@ -458,7 +464,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
             for (int j = 0; j < 32; ++j) {
               const int64_t n = (int64_t)p.ni * op.bn + cc + j;
               const float w = op.alpha * __uint_as_float(r[k][j]);
-              if (n < op.N && w != 0.0f) atomicAdd(op.C + op.cL + cm + op.tCN[n], (double)w);
+              if (n < op.N && w != 0.0f) red_add(op.C + op.cL + cm + op.tCN[n], (double)w);
             }
           }
         } else {
@@ -472,7 +478,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
             const int64_t mr = (int64_t)p.mi * BM + q * 32 + rr;
             if (mr >= op.M) break;
             const float w = op.alpha * tile[rr * 33 + lane];
-            if (n < op.N && w != 0.0f) atomicAdd(op.C + op.cL + op.tCM[mr] + cn, (double)w);
+            if (n < op.N && w != 0.0f) red_add(op.C + op.cL + op.tCM[mr] + cn, (double)w);
           }
           __syncwarp();
         }
