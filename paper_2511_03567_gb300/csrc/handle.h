@@ -183,6 +183,10 @@ struct TcLevel {
   const TcCluster* clusters = nullptr;
   int nclusters = 0;
   int64_t total = 0;
+  // amplitude-dependent operand buffers first consumed at this level
+  const PackDesc* packs = nullptr;
+  int npacks = 0;
+  int64_t pack_total = 0;
 };
 struct Schedule {
   int max_level = 0;

@@ -5,10 +5,10 @@
 //   - the FP64-path contractions of each tile kind, from all instances, are
 //     one persistent grouped launch (grouped.cu), on lanes 0 .. kGroupKinds-1;
 //   - in mixed precision, the amplitude-dependent tensor-core operands first
-//     consumed at this level are packed once (tensor-core lanes), the
-//     tensor-core lanes meet, and the tensor-core GEMMs follow: one persistent
-//     grouped launch over all of them (tcgemm.cu), or with the rule's
-//     tc_grouped off, one launch per contraction spread over those lanes;
+//     consumed at this level are packed once, all in one grouped launch, and
+//     the tensor-core GEMMs follow: one persistent grouped launch over all of
+//     them (tcgemm.cu), or with the rule's tc_grouped off, one launch per
+//     contraction spread over the tensor-core lanes (after they meet);
 //   - the level ends when every lane has finished (join).
 // The same schedule is captured into a CUDA graph (lanes = streams) and, for
 // the per-kernel profile, replayed on one stream with events between launches.
@@ -49,7 +49,44 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
     for (int k = 0; k < kGroupKinds; ++k) TRY(make_group(eh, allocs, by_kind[k], k, &out->groups[lvl][k]));
   }
   out->tc.assign(out->max_level + 1, {});
-  if (!mixed || !rule.tc_grouped) return RICMRCC_OK;
+  if (!mixed) return RICMRCC_OK;
+  // grouped packing launches (one per level)
+  for (int lvl = 0; lvl <= out->max_level; ++lvl) {
+    std::vector<PackDesc> in;
+    for (size_t i = 0; i < inst.size(); ++i) {
+      if (!live[i]) continue;
+      for (const PackedOperand& e : inst[i]->tc_cache) {
+        if (e.level != lvl) continue;
+        PackDesc pd{};
+        pd.X = e.X;
+        pd.xL = e.xL;
+        pd.tR = e.tR;
+        pd.tK = e.tK;
+        pd.rows = e.rows;
+        pd.K = e.K;
+        pd.rows_pad = e.rows_pad;
+        pd.Kp = e.Kp;
+        pd.pat = e.pat;
+        pd.rows_fast = e.rows_fast;
+        pd.out = static_cast<__nv_bfloat16*>(e.data);
+        in.push_back(pd);
+      }
+    }
+    if (in.empty()) continue;
+    std::vector<PackDesc> pk;
+    int64_t total = 0;
+    if (tc_pack_group_build(in.data(), (int)in.size(), pk, &total) != 0)
+      return fail(eh, RICMRCC_ECUDA, "packing descriptors");
+    void* dp = nullptr;
+    if (cudaMalloc(&dp, sizeof(PackDesc) * pk.size()) != cudaSuccess) return fail(eh, RICMRCC_ENOMEM, "descriptors");
+    allocs.push_back(dp);
+    if (cudaMemcpy(dp, pk.data(), sizeof(PackDesc) * pk.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      return fail(eh, RICMRCC_ECUDA, "descriptor upload");
+    out->tc[lvl].packs = static_cast<const PackDesc*>(dp);
+    out->tc[lvl].npacks = (int)pk.size();
+    out->tc[lvl].pack_total = total;
+  }
+  if (!rule.tc_grouped) return RICMRCC_OK;
   for (int lvl = 0; lvl <= out->max_level; ++lvl) {
     std::vector<TcArgs> args;
     for (size_t i = 0; i < inst.size(); ++i) {
@@ -100,19 +137,18 @@ int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*
       ++n;
     }
     if (mixed) {
-      int j = 0;
-      for (size_t i = 0; i < inst.size(); ++i) {
-        if (!live[i]) continue;
-        for (const PackedOperand& e : inst[i]->tc_cache) {
-          if (e.level != lvl) continue;
-          tgt.mark(3);
-          if (pack_entry(e, tgt.lane(kTcLane0 + (j++ % kTcLanes))) != 0)
-            return fail(eh, RICMRCC_ECUDA, "operand packing launch");
-          ++n;
-        }
-      }
-      if (j) tgt.tc_meet();
+      // one grouped packing launch on the first tensor-core lane, then the
+      // tensor-core launches behind it (same lane) or after the lanes meet
       const TcLevel& tl = sc.tc[lvl];
+      int j = 0;
+      if (tl.npacks) {
+        tgt.mark(3);
+        if (tc_pack_group_launch(tl.packs, tl.npacks, tl.pack_total, eh->sms, tgt.lane(kTcLane0)) != 0)
+          return fail(eh, RICMRCC_ECUDA, "operand packing launch");
+        ++n;
+        j = 1;
+      }
+      if (j && !rule.tc_grouped) tgt.tc_meet();
       if (rule.tc_grouped) {
         if (tl.nclusters) {
           tgt.mark(4);

@@ -578,6 +578,68 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Grouped packing: every operand buffer of one list in one persistent launch.
+// Work items are 32-row x 64-K tiles of each buffer (prefix sums in
+// PackDesc::begin); a tile is gathered with lanes along rows through shared
+// memory (rows_fast) or with lanes along K.
+__global__ void __launch_bounds__(256)
+    k_pack_grouped(const PackDesc* __restrict__ d, int nd, int64_t total) {
+  __shared__ float tile[64][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (d[mid].begin <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    const PackDesc& e = d[lo];
+    const int64_t nkt = e.Kp / 64, local = t - e.begin;
+    const int64_t r0 = (local / nkt) * 32, k0 = (local % nkt) * 64, seg = e.Kp >> 1;
+    if (e.rows_fast) {
+      const int64_t r = r0 + lane;
+      const bool live = r < e.rows;
+      const int64_t base = live ? e.xL + e.tR[r] : 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int kk = warp + 8 * j;
+        const int64_t k = k0 + kk;
+        tile[kk][lane] = (live && k < e.K) ? (float)e.X[base + e.tK[k]] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int rr = warp + 8 * j;
+        __nv_bfloat162 h2, l2;
+        split_bf16(tile[2 * lane][rr], tile[2 * lane + 1][rr], &h2, &l2);
+        __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(e.out + (r0 + rr) * 3 * e.Kp);
+        const int64_t c = (k0 >> 1) + lane;
+        row[c] = (e.pat & 1) ? l2 : h2;
+        row[seg + c] = (e.pat & 2) ? l2 : h2;
+        row[2 * seg + c] = (e.pat & 4) ? l2 : h2;
+      }
+      __syncthreads();
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t r = r0 + warp + 8 * j;
+        const bool live = r < e.rows;
+        const int64_t base = live ? e.xL + e.tR[r] : 0;
+        const int64_t k = k0 + 2 * lane;
+        const float x0 = (live && k < e.K) ? (float)e.X[base + e.tK[k]] : 0.f;
+        const float x1 = (live && k + 1 < e.K) ? (float)e.X[base + e.tK[k + 1]] : 0.f;
+        __nv_bfloat162 h2, l2;
+        split_bf16(x0, x1, &h2, &l2);
+        __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(e.out + r * 3 * e.Kp);
+        const int64_t c = k >> 1;
+        row[c] = (e.pat & 1) ? l2 : h2;
+        row[seg + c] = (e.pat & 2) ? l2 : h2;
+        row[2 * seg + c] = (e.pat & 4) ? l2 : h2;
+      }
+    }
+  }
+}
+
 void pack_launch(const double* X, int64_t xL, const int64_t* tR, const int64_t* tK, int64_t rows, int64_t K,
                  int64_t rows_pad, int64_t Kp, int pat, int rows_fast, __nv_bfloat16* out, cudaStream_t s) {
   if (rows_fast && rows_pad % 32 == 0) {
@@ -780,6 +842,27 @@ int tc_group_build(const TcArgs* a, int n, std::vector<TcGroupOp>& ops, std::vec
   }
   *total = t;
   return 0;
+}
+
+int tc_pack_group_build(const PackDesc* in, int n, std::vector<PackDesc>& out, int64_t* total) {
+  out.assign(in, in + n);
+  int64_t t = 0;
+  for (PackDesc& e : out) {
+    if (!e.X || !e.tR || !e.tK || !e.out || e.rows < 0 || e.rows > e.rows_pad || e.K > e.Kp || e.Kp % 64 ||
+        e.rows_pad % 32)
+      return -1;
+    e.begin = t;
+    t += (e.rows_pad / 32) * (e.Kp / 64);
+  }
+  *total = t;
+  return 0;
+}
+
+int tc_pack_group_launch(const PackDesc* d, int nd, int64_t total, int sms, cudaStream_t s) {
+  if (nd <= 0 || total <= 0) return 0;
+  const int grid = (int)std::min<int64_t>(total, (int64_t)sms * 8);
+  k_pack_grouped<<<grid, 256, 0, s>>>(d, nd, total);
+  return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 int tc_group_launch(const TcGroupOp* d_ops, const TcCluster* d_cl, int ncl, int64_t total, int sms, int* err,

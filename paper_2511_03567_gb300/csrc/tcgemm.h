@@ -1,6 +1,7 @@
 // Split-precision BF16 tensor-core contraction (tcgemm.cu).
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -52,6 +53,23 @@ int tc_group_build(const TcArgs* a, int n, std::vector<TcGroupOp>& ops, std::vec
 // Persistent launch over device copies of those arrays (one CTA per SM).
 int tc_group_launch(const TcGroupOp* d_ops, const TcCluster* d_cl, int ncl, int64_t total, int sms, int* err,
                     cudaStream_t s);
+
+// One operand buffer of a grouped packing launch (the tc_pack layout).
+struct PackDesc {
+  const double* X;
+  int64_t xL;
+  const int64_t* tR;
+  const int64_t* tK;
+  int64_t rows, K, rows_pad, Kp;
+  int pat, rows_fast;
+  __nv_bfloat16* out;
+  int64_t begin;  // first work item (filled by tc_pack_group_build)
+};
+// Work-item prefix sums of a grouped packing launch over in[0..n)
+// (rows_pad a multiple of 32, Kp of 64).  0 on success.
+int tc_pack_group_build(const PackDesc* in, int n, std::vector<PackDesc>& out, int64_t* total);
+// One persistent launch packing every buffer of a device copy of that list.
+int tc_pack_group_launch(const PackDesc* d, int nd, int64_t total, int sms, cudaStream_t s);
 
 bool tc_available();
 int tc_pick_bn(int64_t N);  // N tile of the GEMM for an N extent
