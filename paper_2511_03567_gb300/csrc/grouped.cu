@@ -23,7 +23,7 @@ namespace {
 // Fire-and-forget FP64 reduction into global memory (PTX red: no value comes
 // back, so consecutive updates do not wait on each other's completion).
 __device__ __forceinline__ void red_add(double* p, double v) {
-  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v) : "memory");
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v));
 }
 
 __device__ __forceinline__ int find_op(const int64_t* __restrict__ begin, int nops, int64_t t) {

@@ -33,7 +33,7 @@ namespace {
 // Fire-and-forget FP64 reduction into global memory (PTX red: no value comes
 // back, so consecutive updates do not wait on each other's completion).
 __device__ __forceinline__ void red_add(double* p, double v) {
-  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v) : "memory");
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v));
 }
 
 constexpr int BM = 128;
@@ -429,10 +429,17 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
       const bool ready = __all_sync(0xffffffffu, mbar_wait(tfull + b, (c >> 1) & 1, err));
       if (!ready) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // descriptor fields in registers, and the output offsets of this
+      // warp's rows (lane = row) fetched once; lanes exchange them by shuffle
+      double* const C = op.C + op.cL;
+      const int64_t M = op.M, N = op.N;
+      const int bn = op.bn, col_lanes = op.col_lanes;
+      const float alpha = op.alpha;
+      const int64_t* __restrict__ tCN = op.tCN;
       const int64_t m = (int64_t)p.mi * BM + q * 32 + lane;
-      const int64_t cm = m < op.M ? op.tCM[m] : 0;
+      const int64_t cm = m < M ? op.tCM[m] : -1;
       uint32_t r[2][32];
-      const int nchunk = op.bn > 32 * half ? (op.bn - 32 * half + 63) / 64 : 0;
+      const int nchunk = bn > 32 * half ? (bn - 32 * half + 63) / 64 : 0;
       // read this warp's chunks (at most two: GBN = 128), then hand the
       // accumulator back to the MMA issuer before the atomic write-out
 #pragma unroll
@@ -458,27 +465,28 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
       for (int k = 0; k < 2; ++k) {
         if (k >= nchunk) break;
         const int cc = 32 * half + 64 * k;
-        if (!op.col_lanes) {
-          if (m < op.M) {
+        // output offset of column cc + lane (-1 past N)
+        const int64_t nl = (int64_t)p.ni * bn + cc + lane;
+        const int64_t cnl = nl < N ? tCN[nl] : -1;
+        if (!col_lanes) {
+          // lanes along rows: lane = row, loop over the 32 columns
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int64_t n = (int64_t)p.ni * op.bn + cc + j;
-              const float w = op.alpha * __uint_as_float(r[k][j]);
-              if (n < op.N && w != 0.0f) red_add(op.C + op.cL + cm + op.tCN[n], (double)w);
-            }
+          for (int j = 0; j < 32; ++j) {
+            const int64_t cn = __shfl_sync(0xffffffffu, cnl, j);
+            const float w = alpha * __uint_as_float(r[k][j]);
+            if (cm >= 0 && cn >= 0 && w != 0.0f) red_add(C + cm + cn, (double)w);
           }
         } else {
+          // lanes along columns (through shared memory): lane = column,
+          // loop over the warp's 32 rows
 #pragma unroll
           for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[k][j]);
           __syncwarp();
-          const int64_t n = (int64_t)p.ni * op.bn + cc + lane;
-          const int64_t cn = n < op.N ? op.tCN[n] : 0;
-#pragma unroll 4
+#pragma unroll 8
           for (int rr = 0; rr < 32; ++rr) {
-            const int64_t mr = (int64_t)p.mi * BM + q * 32 + rr;
-            if (mr >= op.M) break;
-            const float w = op.alpha * tile[rr * 33 + lane];
-            if (n < op.N && w != 0.0f) red_add(op.C + op.cL + op.tCM[mr] + cn, (double)w);
+            const int64_t cmr = __shfl_sync(0xffffffffu, cm, rr);
+            const float w = alpha * tile[rr * 33 + lane];
+            if (cmr >= 0 && cnl >= 0 && w != 0.0f) red_add(C + cmr + cnl, (double)w);
           }
           __syncwarp();
         }
