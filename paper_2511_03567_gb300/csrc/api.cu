@@ -580,8 +580,6 @@ int make_group(ricmrcc_t* h, std::vector<void*>& allocs, const std::vector<Group
 
 GroupOp group_op(const Program& p, const ContractOp& op) {
   GroupOp g{};
-  g.A = op.A;
-  g.B = op.B;
   g.C = op.C;
   g.tab = p.d_table + op.tab;
   g.L = op.L;
@@ -589,8 +587,14 @@ GroupOp group_op(const Program& p, const ContractOp& op) {
   g.N = op.N;
   g.K = op.K;
   g.kchunk = op.kchunk;
-  g.alpha = op.alpha;
   g.ksplit = op.ksplit;
+  g.nseg = 1;
+  g.seg[0].A = op.A;
+  g.seg[0].B = op.B;
+  g.seg[0].tab = g.tab;
+  g.seg[0].K = op.K;
+  g.seg[0].koff = 0;
+  g.seg[0].alpha = op.alpha;
   return g;
 }
 

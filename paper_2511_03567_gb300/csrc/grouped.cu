@@ -50,16 +50,10 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     const int oi = find_op(begin, nops, tile);
     const GroupOp& op = ops[oi];
     const int64_t L = op.L, M = op.M, N = op.N, K = op.K;
-    const int64_t* tab = op.tab;
-    const int64_t* tAL = tab;
-    const int64_t* tBL = tAL + L;
-    const int64_t* tCL = tBL + L;
-    const int64_t* tAM = tCL + L;
-    const int64_t* tCM = tAM + M;
-    const int64_t* tBN = tCM + M;
-    const int64_t* tCN = tBN + N;
-    const int64_t* tAK = tCN + N;
-    const int64_t* tBK = tAK + K;
+    // output tables (AL BL CL | AM CM | BN CN | AK BK layout)
+    const int64_t* tCL = op.tab + 2 * L;
+    const int64_t* tCM = tCL + L + M;
+    const int64_t* tCN = tCM + M + N;
     const int64_t mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
     int64_t r = tile - begin[oi];
     const int64_t ni = r % nt;
@@ -71,51 +65,75 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     const int64_t m0 = mi * BM, n0 = ni * BN;
     for (int i = tid; i < BM; i += NT) {
       const int64_t m = m0 + i;
-      sAM[i] = m < M ? tAM[m] : 0;
       sCM[i] = m < M ? tCM[m] : 0;
     }
     for (int i = tid; i < BN; i += NT) {
       const int64_t n = n0 + i;
-      sBN[i] = n < N ? tBN[n] : 0;
       sCN[i] = n < N ? tCN[n] : 0;
     }
-    const int64_t aL = tAL[l], bL = tBL[l], cL = tCL[l];
+    const int64_t cL = tCL[l];
     const int64_t kb = (int64_t)ks * op.kchunk;
     const int64_t ke = kb + op.kchunk < K ? kb + op.kchunk : K;
-    const double* __restrict__ A = op.A;
-    const double* __restrict__ B = op.B;
-    const CT alpha = (CT)op.alpha;
     CT acc[TM][TN];
 #pragma unroll
     for (int i = 0; i < TM; ++i)
 #pragma unroll
       for (int j = 0; j < TN; ++j) acc[i][j] = (CT)0;
-    __syncthreads();
-    for (int64_t k0 = kb; k0 < ke; k0 += BK) {
-      for (int i = tid; i < BK * BM; i += NT) {
-        const int kk = i / BM, mm = i % BM;
-        const int64_t k = k0 + kk, m = m0 + mm;
-        As[kk][mm] = (k < ke && m < M) ? (CT)A[aL + sAM[mm] + tAK[k]] : (CT)0;
+    // segments: contractions into the same outputs, K ranges concatenated;
+    // each one's alpha is applied to its B values as they are staged
+    for (int sgi = 0; sgi < op.nseg; ++sgi) {
+      const GroupSeg& sg = op.seg[sgi];
+      const int64_t lo = kb > sg.koff ? kb : sg.koff;
+      const int64_t hi = ke < sg.koff + sg.K ? ke : sg.koff + sg.K;
+      if (lo >= hi) continue;
+      const int64_t Ks = sg.K;
+      const int64_t* tAL = sg.tab;
+      const int64_t* tBL = tAL + L;
+      const int64_t* tAM = tBL + 2 * L;
+      const int64_t* tBN = tAM + 2 * M;
+      const int64_t* tAK = tBN + 2 * N;
+      const int64_t* tBK = tAK + Ks;
+      __syncthreads();  // the previous segment is done with sAM / sBN
+      for (int i = tid; i < BM; i += NT) {
+        const int64_t m = m0 + i;
+        sAM[i] = m < M ? tAM[m] : 0;
       }
-      for (int i = tid; i < BK * BN; i += NT) {
-        const int kk = i / BN, nn = i % BN;
-        const int64_t k = k0 + kk, n = n0 + nn;
-        Bs[kk][nn] = (k < ke && n < N) ? (CT)B[bL + sBN[nn] + tBK[k]] : (CT)0;
+      for (int i = tid; i < BN; i += NT) {
+        const int64_t n = n0 + i;
+        sBN[i] = n < N ? tBN[n] : 0;
       }
+      const int64_t aL = tAL[l], bL = tBL[l];
+      const double* __restrict__ A = sg.A;
+      const double* __restrict__ B = sg.B;
+      const double alpha = sg.alpha;
+      const int64_t klo = lo - sg.koff, khi = hi - sg.koff;
       __syncthreads();
+      for (int64_t k0 = klo; k0 < khi; k0 += BK) {
+        for (int i = tid; i < BK * BM; i += NT) {
+          const int kk = i / BM, mm = i % BM;
+          const int64_t k = k0 + kk, m = m0 + mm;
+          As[kk][mm] = (k < khi && m < M) ? (CT)A[aL + sAM[mm] + tAK[k]] : (CT)0;
+        }
+        for (int i = tid; i < BK * BN; i += NT) {
+          const int kk = i / BN, nn = i % BN;
+          const int64_t k = k0 + kk, n = n0 + nn;
+          Bs[kk][nn] = (k < khi && n < N) ? (CT)(alpha * B[bL + sBN[nn] + tBK[k]]) : (CT)0;
+        }
+        __syncthreads();
 #pragma unroll 4
-      for (int kk = 0; kk < BK; ++kk) {
-        CT a[TM], b[TN];
+        for (int kk = 0; kk < BK; ++kk) {
+          CT a[TM], b[TN];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+          for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
 #pragma unroll
-        for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+          for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
 #pragma unroll
-        for (int i = 0; i < TM; ++i)
+          for (int i = 0; i < TM; ++i)
 #pragma unroll
-          for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
       }
-      __syncthreads();
     }
     double* C = op.C;
 #pragma unroll
@@ -126,7 +144,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       for (int j = 0; j < TN; ++j) {
         const int nn = tx * TN + j;
         if (n0 + nn >= N) continue;
-        const CT v = alpha * acc[i][j];
+        const CT v = acc[i][j];
         if (v != (CT)0) red_add(C + cL + sCM[mm] + sCN[nn], (double)v);
       }
     }
@@ -151,7 +169,7 @@ __device__ CT gsum(CT v) {
 }
 
 // Dot-product contractions (tiny outputs, long K): one work item per
-// (op, output element, K chunk).
+// (op, output element, K chunk), summed over the op's segments.
 template <typename CT>
 __global__ void __launch_bounds__(256)
     k_grouped_dot(const GroupOp* __restrict__ ops, const int64_t* __restrict__ begin, int nops, int64_t total) {
@@ -159,25 +177,34 @@ __global__ void __launch_bounds__(256)
     const int oi = find_op(begin, nops, w);
     const GroupOp& op = ops[oi];
     const int64_t L = op.L, M = op.M, N = op.N, K = op.K;
-    const int64_t* tAL = op.tab;
-    const int64_t* tBL = tAL + L;
-    const int64_t* tCL = tBL + L;
-    const int64_t* tAM = tCL + L;
-    const int64_t* tCM = tAM + M;
-    const int64_t* tBN = tCM + M;
-    const int64_t* tCN = tBN + N;
-    const int64_t* tAK = tCN + N;
-    const int64_t* tBK = tAK + K;
+    const int64_t* tCL = op.tab + 2 * L;
+    const int64_t* tCM = tCL + L + M;
+    const int64_t* tCN = tCM + M + N;
     const int64_t r = w - begin[oi];
     const int ks = (int)(r % op.ksplit);
     const int64_t o = r / op.ksplit;
     const int64_t l = o / (M * N), mn = o % (M * N), m = mn / N, n = mn % N;
-    const int64_t ao = tAL[l] + tAM[m], bo = tBL[l] + tBN[n];
     const int64_t kb = (int64_t)ks * op.kchunk;
     const int64_t ke = kb + op.kchunk < K ? kb + op.kchunk : K;
     CT s = (CT)0;
-    for (int64_t k = kb + threadIdx.x; k < ke; k += blockDim.x) s = fma((CT)op.A[ao + tAK[k]], (CT)op.B[bo + tBK[k]], s);
-    s = gsum(s) * (CT)op.alpha;
+    for (int sgi = 0; sgi < op.nseg; ++sgi) {
+      const GroupSeg& sg = op.seg[sgi];
+      const int64_t lo = kb > sg.koff ? kb : sg.koff;
+      const int64_t hi = ke < sg.koff + sg.K ? ke : sg.koff + sg.K;
+      if (lo >= hi) continue;
+      const int64_t* tAL = sg.tab;
+      const int64_t* tBL = tAL + L;
+      const int64_t* tAM = tBL + 2 * L;
+      const int64_t* tBN = tAM + 2 * M;
+      const int64_t* tAK = tBN + 2 * N;
+      const int64_t* tBK = tAK + sg.K;
+      const int64_t ao = tAL[l] + tAM[m], bo = tBL[l] + tBN[n];
+      CT part = (CT)0;
+      for (int64_t k = lo - sg.koff + threadIdx.x; k < hi - sg.koff; k += blockDim.x)
+        part = fma((CT)sg.A[ao + tAK[k]], (CT)sg.B[bo + tBK[k]], part);
+      s += (CT)sg.alpha * part;
+    }
+    s = gsum(s);
     if (threadIdx.x == 0 && s != (CT)0) red_add(op.C + tCL[l] + tCM[m] + tCN[n], (double)s);
   }
 }
@@ -187,6 +214,25 @@ __global__ void __launch_bounds__(256)
 // Output tile (rows x columns) of each tile kind.
 constexpr int kTileM[5] = {64, 16, 1, 128, 64};
 constexpr int kTileN[5] = {64, 16, 1, 16, 32};
+
+void group_split(GroupOp& op, int kind) {
+  const int64_t K = op.K;
+  int64_t ks = 1;
+  if (kind == 2) {
+    ks = K / 4096;
+    if (ks > 4096) ks = 4096;
+  } else {
+    const int64_t bm = kTileM[kind], bn = kTileN[kind];
+    const int64_t tiles = op.L * ((op.M + bm - 1) / bm) * ((op.N + bn - 1) / bn);
+    if (tiles < 2 * 152 && K >= 256) {
+      ks = (2 * 152 + tiles - 1) / tiles;
+      if (ks > K / 128) ks = K / 128;
+    }
+  }
+  if (ks < 1) ks = 1;
+  op.ksplit = (int)ks;
+  op.kchunk = (K + ks - 1) / ks;
+}
 
 int64_t group_units(const GroupOp& op, int kind) {
   if (kind == 2) return op.L * op.M * op.N * op.ksplit;

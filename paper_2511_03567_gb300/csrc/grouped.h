@@ -1,20 +1,35 @@
-// Persistent grouped FP64 contraction kernels (grouped.cu).
+// Persistent grouped FP64 / FP32 contraction kernels (grouped.cu).
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-// One contraction of a grouped launch: C[l,m,n] += alpha sum_k A[l,m,k] B[l,n,k]
-// with the offset tables of internal.h at `tab` (AL BL CL | AM CM | BN CN | AK BK).
-struct GroupOp {
+// One operand pair of a grouped op: alpha sum_k A[l,m,k] B[l,n,k] over its own
+// K range, with the offset tables of internal.h at `tab` (AL BL CL | AM CM |
+// BN CN | AK BK); koff places that range in the op's concatenated K.
+struct GroupSeg {
   const double* A;
   const double* B;
+  const int64_t* tab;
+  int64_t K, koff;
+  double alpha;
+};
+// Contractions that add into the same output elements (same C, L, M, N and
+// output tables) are one grouped op with up to kMaxSeg segments, so each
+// output element is updated once per op instead of once per contraction:
+// C[l,m,n] += sum_s alpha_s sum_k A_s[l,m,k] B_s[l,n,k]; the output tables
+// (CL CM CN) are those of `tab`.
+constexpr int kMaxSeg = 8;
+struct GroupOp {
   double* C;
   const int64_t* tab;
-  int64_t L, M, N, K, kchunk;
-  double alpha;
-  int ksplit;
-  int pad;
+  int64_t L, M, N, K, kchunk;  // K: sum of the segments' K
+  int ksplit, nseg;
+  GroupSeg seg[kMaxSeg];
 };
+
+// K split of a grouped op of `kind` (enough work items for the GPU while
+// every chunk keeps at least 128 K steps): sets op.ksplit and op.kchunk.
+void group_split(GroupOp& op, int kind);
 
 // Work units (tiles, or dot work items for kind 2) of one op.
 int64_t group_units(const GroupOp& op, int kind);

@@ -16,6 +16,8 @@
 
 #include <algorithm>
 #include <array>
+#include <map>
+#include <string>
 #include <vector>
 
 #include "handle.h"
@@ -35,6 +37,9 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
     for (size_t i = 0; i < inst.size(); ++i) {
       if (!live[i]) continue;
       const Program& p = inst[i]->res_prog;
+      // contractions of one kind that add into the same output elements
+      // (same C, extents and output offset tables) merge into one op
+      std::map<std::string, size_t> merge[kGroupKinds];
       for (const auto& op : p.ops) {
         if (op.level != lvl || op.L == 0 || op.M == 0 || op.N == 0 || op.K == 0) continue;
         out->flops += op.flops;
@@ -43,9 +48,34 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
           out->tc_flops += op.flops;
           continue;
         }
-        by_kind[op_kind(op, rule)].push_back(group_op(p, op));
+        const int kind = op_kind(op, rule);
+        const int64_t* th = p.table.data() + op.tab;
+        std::string key(reinterpret_cast<const char*>(&op.C), sizeof(op.C));
+        const int64_t ext[3] = {op.L, op.M, op.N};
+        key.append(reinterpret_cast<const char*>(ext), sizeof(ext));
+        key.append(reinterpret_cast<const char*>(th + 2 * op.L), sizeof(int64_t) * op.L);          // CL
+        key.append(reinterpret_cast<const char*>(th + 3 * op.L + op.M), sizeof(int64_t) * op.M);   // CM
+        key.append(reinterpret_cast<const char*>(th + 3 * op.L + 2 * op.M + op.N), sizeof(int64_t) * op.N);  // CN
+        auto it = merge[kind].find(key);
+        if (it != merge[kind].end() && by_kind[kind][it->second].nseg < kMaxSeg) {
+          GroupOp& g = by_kind[kind][it->second];
+          GroupSeg& sg = g.seg[g.nseg++];
+          sg.A = op.A;
+          sg.B = op.B;
+          sg.tab = p.d_table + op.tab;
+          sg.K = op.K;
+          sg.koff = g.K;
+          sg.alpha = op.alpha;
+          g.K += op.K;
+          continue;
+        }
+        merge[kind][key] = by_kind[kind].size();
+        by_kind[kind].push_back(group_op(p, op));
       }
     }
+    for (int k = 0; k < kGroupKinds; ++k)
+      for (GroupOp& g : by_kind[k])
+        if (g.nseg > 1) group_split(g, k);
     for (int k = 0; k < kGroupKinds; ++k) TRY(make_group(eh, allocs, by_kind[k], k, &out->groups[lvl][k]));
   }
   out->tc.assign(out->max_level + 1, {});
