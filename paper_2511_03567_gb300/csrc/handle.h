@@ -180,6 +180,7 @@ void tc_lanes_meet(cudaStream_t* lanes, cudaEvent_t* ev);
 // Device descriptors of one grouped tensor-core launch.
 struct TcLevel {
   const TcGroupOp* ops = nullptr;
+  const TcSeg* segs = nullptr;
   const TcCluster* clusters = nullptr;
   int nclusters = 0;
   int64_t total = 0;

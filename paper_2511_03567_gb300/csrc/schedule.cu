@@ -117,32 +117,63 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
     out->tc[lvl].pack_total = total;
   }
   if (!rule.tc_grouped) return RICMRCC_OK;
+  constexpr int kTcMaxSeg = 8;
   for (int lvl = 0; lvl <= out->max_level; ++lvl) {
-    std::vector<TcArgs> args;
+    // tensor-core contractions of one instance that add into the same output
+    // elements with the same alpha merge into one op (concatenated K)
+    std::vector<std::vector<TcArgs>> merged;
     for (size_t i = 0; i < inst.size(); ++i) {
       if (!live[i]) continue;
       const Program& p = inst[i]->res_prog;
+      std::map<std::string, size_t> merge;
       for (size_t q = 0; q < p.ops.size(); ++q) {
         const ContractOp& op = p.ops[q];
         if (op.level != lvl || !tc_eligible(op, rule)) continue;
         if (op.L == 0 || op.M == 0 || op.N == 0 || op.K == 0) continue;
-        args.push_back(tc_args(inst[i], p, (int)q, 0));
+        const int64_t* th = p.table.data() + op.tab;
+        std::string key(reinterpret_cast<const char*>(&op.C), sizeof(op.C));
+        key.append(reinterpret_cast<const char*>(&op.alpha), sizeof(op.alpha));
+        const int64_t ext[3] = {op.L, op.M, op.N};
+        key.append(reinterpret_cast<const char*>(ext), sizeof(ext));
+        key.append(reinterpret_cast<const char*>(th + 2 * op.L), sizeof(int64_t) * op.L);
+        key.append(reinterpret_cast<const char*>(th + 3 * op.L + op.M), sizeof(int64_t) * op.M);
+        key.append(reinterpret_cast<const char*>(th + 3 * op.L + 2 * op.M + op.N), sizeof(int64_t) * op.N);
+        auto it = merge.find(key);
+        if (it != merge.end() && merged[it->second].size() < (size_t)kTcMaxSeg) {
+          merged[it->second].push_back(tc_args(inst[i], p, (int)q, 0));
+          continue;
+        }
+        merge[key] = merged.size();
+        merged.push_back({tc_args(inst[i], p, (int)q, 0)});
       }
     }
-    if (args.empty()) continue;
+    if (merged.empty()) continue;
+    std::vector<TcArgs> args;
+    std::vector<int> nseg;
+    for (const auto& m : merged) {
+      args.insert(args.end(), m.begin(), m.end());
+      nseg.push_back((int)m.size());
+    }
     std::vector<TcGroupOp> ops;
+    std::vector<TcSeg> segs;
     std::vector<TcCluster> cl;
     int64_t total = 0;
-    if (tc_group_build(args.data(), (int)args.size(), ops, cl, &total) != 0)
+    if (tc_group_build(args.data(), nseg.data(), (int)nseg.size(), ops, segs, cl, &total) != 0)
       return fail(eh, RICMRCC_ECUDA, "grouped tensor-core descriptors");
-    void *dops = nullptr, *dcl = nullptr;
+    void *dops = nullptr, *dcl = nullptr, *dsg = nullptr;
     if (cudaMalloc(&dops, sizeof(TcGroupOp) * ops.size()) != cudaSuccess) return fail(eh, RICMRCC_ENOMEM, "descriptors");
     allocs.push_back(dops);
     if (cudaMalloc(&dcl, sizeof(TcCluster) * cl.size()) != cudaSuccess) return fail(eh, RICMRCC_ENOMEM, "descriptors");
     allocs.push_back(dcl);
+    if (cudaMalloc(&dsg, sizeof(TcSeg) * std::max<size_t>(segs.size(), 1)) != cudaSuccess)
+      return fail(eh, RICMRCC_ENOMEM, "descriptors");
+    allocs.push_back(dsg);
     if (cudaMemcpy(dops, ops.data(), sizeof(TcGroupOp) * ops.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(dcl, cl.data(), sizeof(TcCluster) * cl.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(dcl, cl.data(), sizeof(TcCluster) * cl.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!segs.empty() &&
+         cudaMemcpy(dsg, segs.data(), sizeof(TcSeg) * segs.size(), cudaMemcpyHostToDevice) != cudaSuccess))
       return fail(eh, RICMRCC_ECUDA, "descriptor upload");
+    out->tc[lvl].segs = static_cast<const TcSeg*>(dsg);
     TcLevel& tl = out->tc[lvl];
     tl.ops = static_cast<const TcGroupOp*>(dops);
     tl.clusters = static_cast<const TcCluster*>(dcl);
@@ -182,7 +213,7 @@ int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*
       if (rule.tc_grouped) {
         if (tl.nclusters) {
           tgt.mark(4);
-          if (tc_group_launch(tl.ops, tl.clusters, tl.nclusters, tl.total, eh->sms, err, tgt.lane(kTcLane0)) != 0)
+          if (tc_group_launch(tl.ops, tl.segs, tl.clusters, tl.nclusters, tl.total, eh->sms, err, tgt.lane(kTcLane0)) != 0)
             return fail(eh, RICMRCC_ECUDA, "grouped tensor-core launch");
           ++n;
         }

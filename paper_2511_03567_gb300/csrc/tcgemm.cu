@@ -315,8 +315,8 @@ __device__ __forceinline__ uint32_t instr_desc_n(int bn) {
 constexpr int kEpiWarps = 8;
 
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
-    k_tc_grouped(const TcGroupOp* __restrict__ ops, const TcCluster* __restrict__ cl, int ncl, int64_t total,
-                 int* err) {
+    k_tc_grouped(const TcGroupOp* __restrict__ ops, const TcSeg* __restrict__ segs, const TcCluster* __restrict__ cl,
+                 int ncl, int64_t total, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -359,15 +359,27 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
       const ItemPos p = item_pos(ops, cl, ncl, t);
       const TcGroupOp& op = ops[p.oi];
+      // K segments: the op's own operand pair, then op.nseg - 1 more from segs
+      const CUtensorMap* ma = &op.ma;
+      const CUtensorMap* mb = &op.mb;
+      int sidx = 0, off = 0, len = op.kt0;
       for (int kt = p.kt0; kt < p.kt1; ++kt, ++g) {
+        while (kt >= off + len && sidx + 1 < op.nseg) {
+          off += len;
+          const TcSeg& sg = segs[op.seg0 + sidx];
+          ++sidx;
+          ma = &sg.ma;
+          mb = &sg.mb;
+          len = sg.kt;
+        }
         const uint32_t s = g % STAGES;
         if (g >= STAGES && !mbar_wait(empty + s, ((g / STAGES) - 1) & 1, err)) {
           ok = false;
           break;
         }
         mbar_expect_tx(full + s, (uint32_t)(BM + op.bn) * BK * 2);
-        tma_load_2d(sA + s * BM * BK * 2, &op.ma, kt * BK, p.mi * BM, full + s);
-        tma_load_2d(sB + s * GBN * BK * 2, &op.mb, kt * BK, p.ni * op.bn, full + s);
+        tma_load_2d(sA + s * BM * BK * 2, ma, (kt - off) * BK, p.mi * BM, full + s);
+        tma_load_2d(sB + s * GBN * BK * 2, mb, (kt - off) * BK, p.ni * op.bn, full + s);
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -794,16 +806,19 @@ int tc_pack(const double* X, int64_t xL, const int64_t* tR, const int64_t* tK, i
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int tc_group_build(const TcArgs* a, int n, std::vector<TcGroupOp>& ops, std::vector<TcCluster>& clusters,
-                   int64_t* total) {
+int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupOp>& ops, std::vector<TcSeg>& segs,
+                   std::vector<TcCluster>& clusters, int64_t* total) {
   if (!get_encode()) return -2;
-  // clusters: contractions reading the same packed A buffer (same M and K)
+  std::vector<int> first(n + 1, 0);  // op j's operand pairs: a[first[j] .. first[j + 1])
+  for (int j = 0; j < n; ++j) first[j + 1] = first[j] + nseg[j];
+  // clusters: single-pair contractions reading the same packed A buffer (same
+  // M and K); every merged op is a cluster of its own
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [a](int x, int y) {
-    return reinterpret_cast<uintptr_t>(a[x].packA) < reinterpret_cast<uintptr_t>(a[y].packA);
-  });
+  auto keyA = [&](int j) { return nseg[j] > 1 ? (uintptr_t)-1 : reinterpret_cast<uintptr_t>(a[first[j]].packA); };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return keyA(x) < keyA(y); });
   ops.assign(n, TcGroupOp{});
+  segs.clear();
   clusters.clear();
   // K chunks of at most kMaxKt k-tiles: long enough that the atomic output
   // update of a chunk is small next to its MMAs, short enough that the items
@@ -811,14 +826,33 @@ int tc_group_build(const TcArgs* a, int n, std::vector<TcGroupOp>& ops, std::vec
   constexpr int kMaxKt = 128;
   int64_t t = 0;
   for (int q = 0; q < n; ++q) {
-    const TcArgs& x = a[order[q]];
-    if (!x.packA || !x.packB) return -1;  // both operands come packed
+    const int j = order[q];
+    const TcArgs& x = a[first[j]];
     TcGroupOp& o = ops[q];
     const int pbn = tc_pick_bn(x.N);
     const int bn = std::min(pbn, GBN);
-    const int64_t Mp = tc_pad(x.M, BM), Np = tc_pad(x.N, pbn), Kp = tc_pad(x.K, BK);
-    const int64_t inner = 3 * Kp;
-    if (!make_map(&o.ma, x.packA, inner, Mp, BM) || !make_map(&o.mb, x.packB, inner, Np, bn)) return -4;
+    const int64_t Mp = tc_pad(x.M, BM), Np = tc_pad(x.N, pbn);
+    int kt_all = 0;
+    for (int sgi = 0; sgi < nseg[j]; ++sgi) {
+      const TcArgs& y = a[first[j] + sgi];
+      if (!y.packA || !y.packB) return -1;  // both operands come packed
+      if (y.M != x.M || y.N != x.N) return -1;
+      const int64_t inner = 3 * tc_pad(y.K, BK);
+      CUtensorMap* pma = &o.ma;
+      CUtensorMap* pmb = &o.mb;
+      if (sgi > 0) {
+        segs.push_back(TcSeg{});
+        pma = &segs.back().ma;
+        pmb = &segs.back().mb;
+        segs.back().kt = (int)(inner / BK);
+      } else {
+        o.kt0 = (int)(inner / BK);
+        o.seg0 = (int)segs.size();
+      }
+      if (!make_map(pma, y.packA, inner, Mp, BM) || !make_map(pmb, y.packB, inner, Np, bn)) return -4;
+      kt_all += (int)(inner / BK);
+    }
+    o.nseg = nseg[j];
     o.C = x.C;
     o.tCM = x.tCM;
     o.tCN = x.tCN;
@@ -829,24 +863,25 @@ int tc_group_build(const TcArgs* a, int n, std::vector<TcGroupOp>& ops, std::vec
     o.bn = bn;
     o.alpha = (float)x.alpha;
     o.col_lanes = x.col_lanes;
-    const bool start = clusters.empty() || a[order[q - 1]].packA != x.packA;
+    const bool start = clusters.empty() || nseg[j] > 1 || keyA(order[q - 1]) != keyA(j);
     if (start) {
       TcCluster c{};
       c.begin = t;
       c.op0 = q;
       c.mt = (int)(Mp / BM);
-      c.kt_total = (int)(inner / BK);
+      c.kt_total = kt_all;
       const int ks = (c.kt_total + kMaxKt - 1) / kMaxKt;
       c.kps = (c.kt_total + ks - 1) / ks;
       c.ksplit = (c.kt_total + c.kps - 1) / c.kps;
       clusters.push_back(c);
     }
     TcCluster& c = clusters.back();
-    if (c.mt != (int)(Mp / BM) || c.kt_total != (int)(inner / BK)) return -1;  // shared A: same M and K
+    if (c.mt != (int)(Mp / BM) || c.kt_total != kt_all) return -1;  // shared A: same M and K
     o.wbegin = c.W;
     c.W += o.nt;
     c.nops += 1;
-    if (q + 1 == n || a[order[q + 1]].packA != x.packA) t += (int64_t)c.mt * c.ksplit * c.W;
+    const bool end = q + 1 == n || nseg[order[q + 1]] > 1 || nseg[j] > 1 || keyA(order[q + 1]) != keyA(j);
+    if (end) t += (int64_t)c.mt * c.ksplit * c.W;
   }
   *total = t;
   return 0;
@@ -873,11 +908,11 @@ int tc_pack_group_launch(const PackDesc* d, int nd, int64_t total, int sms, cuda
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int tc_group_launch(const TcGroupOp* d_ops, const TcCluster* d_cl, int ncl, int64_t total, int sms, int* err,
-                    cudaStream_t s) {
+int tc_group_launch(const TcGroupOp* d_ops, const TcSeg* d_segs, const TcCluster* d_cl, int ncl, int64_t total,
+                    int sms, int* err, cudaStream_t s) {
   if (ncl <= 0 || total <= 0) return 0;
   const int grid = (int)std::min<int64_t>(total, sms);
-  k_tc_grouped<<<grid, 64 + 32 * kEpiWarps, grouped_smem_bytes(), s>>>(d_ops, d_cl, ncl, total, err);
+  k_tc_grouped<<<grid, 64 + 32 * kEpiWarps, grouped_smem_bytes(), s>>>(d_ops, d_segs, d_cl, ncl, total, err);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

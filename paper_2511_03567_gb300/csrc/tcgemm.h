@@ -29,7 +29,10 @@ struct TcArgs {
 };
 
 // One contraction of a grouped tensor-core launch (device descriptor; the
-// tensor maps of its packed operands live here, in global memory).
+// tensor maps of its packed operands live here, in global memory).  A merged
+// op sums nseg contractions with the same outputs, extents and alpha: its own
+// operand pair (kt0 k-tiles) followed by nseg - 1 pairs at segs[seg0 ...],
+// their K ranges concatenated.
 struct alignas(64) TcGroupOp {
   CUtensorMap ma, mb;
   double* C;
@@ -37,7 +40,12 @@ struct alignas(64) TcGroupOp {
   const int64_t* tCN;
   int64_t cL, M, N;
   int nt, bn, col_lanes, wbegin;  // wbegin: first n-tile slot of this op in its cluster
+  int nseg, seg0, kt0;
   float alpha;
+};
+struct alignas(64) TcSeg {
+  CUtensorMap ma, mb;
+  int kt;  // k-tiles of this operand pair
 };
 // Contractions sharing one packed A operand: items (m tile, K chunk, slot)
 // with slot running over the n tiles of all member ops.
@@ -46,13 +54,14 @@ struct TcCluster {
   int op0, nops, mt, kt_total, kps, ksplit, W;
 };
 
-// Descriptors and clusters of a grouped launch over the contractions a[0..n)
-// (both operands of each already packed).  0 on success.
-int tc_group_build(const TcArgs* a, int n, std::vector<TcGroupOp>& ops, std::vector<TcCluster>& clusters,
-                   int64_t* total);
+// Descriptors, extra K segments and clusters of a grouped launch over n ops;
+// op j sums the nseg[j] consecutive contractions of a (outputs, extents and
+// alpha of its first one; both operands of each already packed).  0 on success.
+int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupOp>& ops, std::vector<TcSeg>& segs,
+                   std::vector<TcCluster>& clusters, int64_t* total);
 // Persistent launch over device copies of those arrays (one CTA per SM).
-int tc_group_launch(const TcGroupOp* d_ops, const TcCluster* d_cl, int ncl, int64_t total, int sms, int* err,
-                    cudaStream_t s);
+int tc_group_launch(const TcGroupOp* d_ops, const TcSeg* d_segs, const TcCluster* d_cl, int ncl, int64_t total,
+                    int sms, int* err, cudaStream_t s);
 
 // One operand buffer of a grouped packing launch (the tc_pack layout).
 struct PackDesc {

@@ -86,3 +86,28 @@ def test_grouped_tensor_core_launch_matches_per_op_launches():
     diff = max(np.abs(Ra[k] - Rb[k]).max() for k in Ra if Ra[k].size)
     assert diff < 1e-5 * scale, (diff, scale)
     assert abs(Ea - Eb) < 1e-7
+
+
+def test_mixed_solve_refines_to_fp64_fixed_point():
+    """Mixed precision as the solver runs it: tensor-core iterations until
+    max|dt| < refine_tol, then FP64 iterations to the FP64 criterion.  The
+    converged energy equals the FP64 solve's within the 1e-6 Eh target (in
+    practice far closer: the refinement converges to the FP64 fixed point).
+    The tile rule sends every GEMM-shaped contraction to the tensor cores so
+    that this small, convergent problem exercises them."""
+    import paper_2511_03567_gb300 as ric
+    nc, na, nv, nx = 3, 6, 16, 60
+    p = synthetic.make_problem(nc, na, nv, nx, 100, 0)
+    g = ric.RicMrcc(nc, na, nv, nx)
+    g.set_integrals(p.h, p.B)
+    g.set_rdms(p.G1, p.G2, p.G3)
+    g.semicanonicalize()
+    e64, st64 = g.solve(0.5, max_iter=60)
+    assert st64.converged == 1
+    g.set_tile_rule(1e3, True, True)
+    g.set_amplitudes(g.unpack(np.zeros(g.layout.t1_size), np.zeros(g.layout.t2_size)))  # restart from T = 0
+    em, stm = g.solve(0.5, max_iter=60, precision=ric.MIXED, refine_tol=1e-4)
+    assert stm.converged == 1
+    assert stm.mixed_iterations > 0 and stm.fp64_iterations > 0
+    assert g.plan_info().tc_contractions > 0
+    assert abs(em - e64) < 1e-6, (em, e64)
