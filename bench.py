@@ -154,7 +154,7 @@ def roofline(kind_ms, info, mixed, pk, fp64_peak, torch):
         roof = {"bound": "hbm", "achieved": gb / t / 1e9, "unit": "GB/s", "peak": pk.get("hbm_gbs", 6800.0),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), of measured",
                 "work": "bytes: packed operand buffers read once + 16 B (FP64 read+write) per output "
-                        "element per contraction",
+                        "element per launched (merged) op",
                 "tensor_tflops": 3.0 * work / t / 1e12,
                 "tensor_frac": 3.0 * work / t / 1e12 / pk.get("bf16_tflops_sustained", 1700.0),
                 "tensor_peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"}
@@ -266,7 +266,8 @@ def main():
         info = g.plan_info()
         print(json.dumps({"ncu_residual": args.ncu_residual, "workload": w["workload"], "precision": args.precision,
                           "tile_rule": g.get_tile_rule(), "energy": E,
-                          "graph_launches": int(info.graph_launches[1 if prec == ric.MIXED else 0])}))
+                          "graph_launches": int(info.graph_launches[1 if prec == ric.MIXED else 0]),
+                          "tc_gemm_bytes": info.tc_gemm_bytes, "tc_flops": info.tc_flops}))
         return 0
     if not args.no_tune and args.tile_rule is None and not args.ncu_largest:
         # tile rule for this workload, timed at representative (non-zero)

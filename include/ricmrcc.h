@@ -220,7 +220,8 @@ typedef struct {
   double kernel_work[7];
   /* algorithmic bytes of the tensor-core GEMMs per residual: every packed
    * operand buffer read once, every output element read and written once in
-   * FP64 per contraction (known once the tensor-core path is planned) */
+   * FP64 per launched op (contractions merged into one op count once; known
+   * once the tensor-core path is planned) */
   double tc_gemm_bytes;
 } ricmrcc_plan_info_t;
 

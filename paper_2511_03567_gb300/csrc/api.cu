@@ -9,6 +9,7 @@
 #include <array>
 #include <chrono>
 #include <memory>
+#include <set>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -1150,6 +1151,7 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
   out->step_launches = (gl ? gl : out->residual_launches) + 4;
   const bool mixed = h->precision == RICMRCC_MIXED;
   static const int slot[kGroupKinds] = {0, 1, 2, 5, 6};
+  std::set<std::string> out_keys;
   for (size_t i = 0; i < h->res_prog.ops.size(); ++i) {
     const ContractOp& op = h->res_prog.ops[i];
     out->kind_launches[op.kind] += 1;
@@ -1161,7 +1163,22 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
     const int k = mixed && tc_eligible(op, h->rule) ? 4 : slot[op_kind(op, h->rule)];
     out->kernel_ops[k] += 1;
     out->kernel_work[k] += op.flops;
-    if (h->tc_planned && tc_eligible(op, h->rule)) out->tc_gemm_bytes += 16.0 * (double)op.M * (double)op.N;
+    if (h->tc_planned && tc_eligible(op, h->rule) && h->rule.tc_grouped) {
+      // outputs are written once per merged op (contractions of one level
+      // with the same outputs and alpha share their output update)
+      const int64_t* th = h->res_prog.table.data() + op.tab;
+      std::string key(reinterpret_cast<const char*>(&op.level), sizeof(op.level));
+      key.append(reinterpret_cast<const char*>(&op.C), sizeof(op.C));
+      key.append(reinterpret_cast<const char*>(&op.alpha), sizeof(op.alpha));
+      const int64_t ext[3] = {op.L, op.M, op.N};
+      key.append(reinterpret_cast<const char*>(ext), sizeof(ext));
+      key.append(reinterpret_cast<const char*>(th + 2 * op.L), sizeof(int64_t) * op.L);
+      key.append(reinterpret_cast<const char*>(th + 3 * op.L + op.M), sizeof(int64_t) * op.M);
+      key.append(reinterpret_cast<const char*>(th + 3 * op.L + 2 * op.M + op.N), sizeof(int64_t) * op.N);
+      if (out_keys.insert(key).second) out->tc_gemm_bytes += 16.0 * (double)op.M * (double)op.N;
+    } else if (h->tc_planned && tc_eligible(op, h->rule)) {
+      out->tc_gemm_bytes += 16.0 * (double)op.M * (double)op.N;
+    }
   }
   // operand packing per evaluation: each amplitude-dependent buffer once
   // (read FP64 source, write three BF16 segments); constant ones are packed
