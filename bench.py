@@ -202,7 +202,11 @@ def run_reference(args):
     line = {"metric": METRIC, "value": res["s_per_iter"], "unit": "s/iter", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["s_per_iter"] * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": dict(WORKLOAD), "impl": "reference",
+            "data": "synthetic",
+            "config": dict(WORKLOAD, precision=args.precision, parallelism=f"replicas{args.gpus}",
+                           l2="inputs larger than L2 (2.7 GB integral tensor), no flush",
+                           reference="the FP64 oracle on the host cores, residual elements one by one"),
+            "impl": "reference",
             "cpu_baseline": {"value": res["s_per_iter"], "unit": "s/iter", "cores": res["cores"],
                              "kind": "oracle", "sample": res["sample"]},
             "e2e": {"value": res["s_per_iter"], "unit": "s/iter", "h2d_bytes_per_step": 0,
