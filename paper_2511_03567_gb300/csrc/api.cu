@@ -627,6 +627,8 @@ int capture_residual(ricmrcc_t* h, bool mixed) {
     return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: memset"));
   if (mixed && cudaMemsetAsync(h->d_err, 0, sizeof(int), s0) != cudaSuccess)
     return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: memset"));
+  if (cudaMemsetAsync(sc.counters, 0, sizeof(unsigned long long) * sc.ncounters, s0) != cudaSuccess)
+    return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: memset"));
   StreamTarget tgt(h->lane, h->lane_ev, h->tc_ev);
   int64_t launches = 0;
   const int rc = run_schedule(h, sc, inst, live, h->rule, mixed, tgt, h->tc_scratch, h->tc_scratch_bytes,
@@ -1298,6 +1300,7 @@ int ricmrcc_profile(ricmrcc_t* h, int reps, int mixed, double* kind_ms) {
     CK(cudaMemsetAsync(h->X, 0, sizeof(double) * h->ng, h->s));
     CK(cudaMemsetAsync(h->scal + 1, 0, sizeof(double), h->s));
     if (mixed) CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
+    CK(cudaMemsetAsync(sc.counters, 0, sizeof(unsigned long long) * sc.ncounters, h->s));
     ProfileTarget tgt(h->s);
     TRY(run_schedule(h, sc, inst, live, h->rule, mixed != 0, tgt, h->tc_scratch, h->tc_scratch_bytes, h->d_err,
                      nullptr));

@@ -137,6 +137,7 @@ int capture(ricmrcc_batch_t* b, const std::vector<char>& live, bool mixed) {
          cudaMemsetAsync(h->scal + 1, 0, sizeof(double), s0) == cudaSuccess;
   }
   if (ok && mixed) ok = cudaMemsetAsync(b->d_err, 0, sizeof(int), s0) == cudaSuccess;
+  if (ok) ok = cudaMemsetAsync(sc.counters, 0, sizeof(unsigned long long) * sc.ncounters, s0) == cudaSuccess;
   if (!ok) return abort_capture(bfail(b, RICMRCC_ECUDA, "graph capture: memset"));
   StreamTarget tgt(b->lane, b->lane_ev, b->tc_ev);
   const int rc = run_schedule(b->inst[0], sc, b->inst, live, b->rule, mixed, tgt, b->tc_scratch, b->tc_slice,

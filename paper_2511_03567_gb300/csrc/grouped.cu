@@ -26,6 +26,17 @@ __device__ __forceinline__ void red_add(double* p, double v) {
   asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "d"(v));
 }
 
+// Next work item of a persistent CTA: taken from the launch's counter when
+// there is one (CTAs that start late, e.g. while another kernel holds the SM,
+// then simply find less work), else strided by the grid.
+__device__ __forceinline__ int64_t next_item(unsigned long long* ctr, int64_t cur, bool first) {
+  if (!ctr) return first ? (int64_t)blockIdx.x : cur + gridDim.x;
+  __shared__ int64_t s_next;
+  if (threadIdx.x == 0) s_next = (int64_t)atomicAdd(ctr, 1ull);
+  __syncthreads();
+  return s_next;
+}
+
 __device__ __forceinline__ int find_op(const int64_t* __restrict__ begin, int nops, int64_t t) {
   int lo = 0, hi = nops - 1;
   while (lo < hi) {
@@ -38,7 +49,8 @@ __device__ __forceinline__ int find_op(const int64_t* __restrict__ begin, int no
 
 template <typename CT, int BM, int BN, int TM, int TN, int BK>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
-    k_grouped_tile(const GroupOp* __restrict__ ops, const int64_t* __restrict__ begin, int nops, int64_t total) {
+    k_grouped_tile(const GroupOp* __restrict__ ops, const int64_t* __restrict__ begin, int nops, int64_t total,
+                   unsigned long long* ctr) {
   constexpr int NT = (BM / TM) * (BN / TN);
   __shared__ CT As[BK][BM + 1];
   __shared__ CT Bs[BK][BN + 1];
@@ -46,7 +58,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN);
   const int ty = tid / (BN / TN);
-  for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+  for (int64_t tile = next_item(ctr, 0, true); tile < total; tile = next_item(ctr, tile, false)) {
     const int oi = find_op(begin, nops, tile);
     const GroupOp& op = ops[oi];
     const int64_t L = op.L, M = op.M, N = op.N, K = op.K;
@@ -172,8 +184,9 @@ __device__ CT gsum(CT v) {
 // (op, output element, K chunk), summed over the op's segments.
 template <typename CT>
 __global__ void __launch_bounds__(256)
-    k_grouped_dot(const GroupOp* __restrict__ ops, const int64_t* __restrict__ begin, int nops, int64_t total) {
-  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    k_grouped_dot(const GroupOp* __restrict__ ops, const int64_t* __restrict__ begin, int nops, int64_t total,
+                  unsigned long long* ctr) {
+  for (int64_t w = next_item(ctr, 0, true); w < total; w = next_item(ctr, w, false)) {
     const int oi = find_op(begin, nops, w);
     const GroupOp& op = ops[oi];
     const int64_t L = op.L, M = op.M, N = op.N, K = op.K;
@@ -255,7 +268,7 @@ int resident_per_sm(F kernel) {
 
 template <typename CT>
 void launch_typed(int kind, const GroupOp* ops, const int64_t* begin, int nops, int64_t total, int sms,
-                  cudaStream_t s) {
+                  unsigned long long* ctr, cudaStream_t s) {
   // persistent grid: every resident CTA slot of every SM (occupancy API)
   static int per_sm[kGroupKinds] = {0, 0, 0, 0, 0};
   if (!per_sm[kind]) {
@@ -270,21 +283,21 @@ void launch_typed(int kind, const GroupOp* ops, const int64_t* begin, int nops, 
   const int64_t slots = (int64_t)sms * per_sm[kind];
   const int g = (int)(total < slots ? total : slots);
   switch (kind) {
-    case 0: k_grouped_tile<CT, 64, 64, 4, 4, 16><<<g, 256, 0, s>>>(ops, begin, nops, total); break;
-    case 1: k_grouped_tile<CT, 16, 16, 1, 1, 16><<<g, 256, 0, s>>>(ops, begin, nops, total); break;
-    case 2: k_grouped_dot<CT><<<g, 256, 0, s>>>(ops, begin, nops, total); break;
-    case 3: k_grouped_tile<CT, 128, 16, 8, 1, 8><<<g, 256, 0, s>>>(ops, begin, nops, total); break;
-    default: k_grouped_tile<CT, 64, 32, 8, 1, 8><<<g, 256, 0, s>>>(ops, begin, nops, total); break;
+    case 0: k_grouped_tile<CT, 64, 64, 4, 4, 16><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
+    case 1: k_grouped_tile<CT, 16, 16, 1, 1, 16><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
+    case 2: k_grouped_dot<CT><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
+    case 3: k_grouped_tile<CT, 128, 16, 8, 1, 8><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
+    default: k_grouped_tile<CT, 64, 32, 8, 1, 8><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
   }
 }
 
 }  // namespace
 
 void launch_grouped(int kind, bool fp32, const GroupOp* ops, const int64_t* begin, int nops, int64_t total,
-                    int sms, cudaStream_t s) {
+                    int sms, unsigned long long* ctr, cudaStream_t s) {
   if (nops <= 0 || total <= 0 || kind < 0 || kind >= kGroupKinds) return;
   if (fp32)
-    launch_typed<float>(kind, ops, begin, nops, total, sms, s);
+    launch_typed<float>(kind, ops, begin, nops, total, sms, ctr, s);
   else
-    launch_typed<double>(kind, ops, begin, nops, total, sms, s);
+    launch_typed<double>(kind, ops, begin, nops, total, sms, ctr, s);
 }

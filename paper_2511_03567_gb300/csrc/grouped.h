@@ -36,6 +36,8 @@ int64_t group_units(const GroupOp& op, int kind);
 // kind: 0 = 64x64 FP64 tile, 1 = 16x16 tile, 2 = dot reduction,
 // 3 = 128x16 tile and 4 = 64x32 tile (tall-skinny ops; one column per thread).
 constexpr int kGroupKinds = 5;
-// fp32: compute in FP32 (mixed precision), else FP64.
+// fp32: compute in FP32 (mixed precision), else FP64.  ctr (nullable, zero
+// before the launch): work-item counter the CTAs take items from; without it
+// each CTA takes a fixed stride of items.
 void launch_grouped(int kind, bool fp32, const GroupOp* ops, const int64_t* begin, int nops, int64_t total,
-                    int sms, cudaStream_t s);
+                    int sms, unsigned long long* ctr, cudaStream_t s);

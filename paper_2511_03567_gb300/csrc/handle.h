@@ -167,6 +167,7 @@ struct Group {
   const int64_t* begin = nullptr;
   int nops = 0;
   int64_t total = 0;
+  unsigned long long* ctr = nullptr;  // work-item counter (in Schedule::counters)
 };
 // Upload `ops` (host) as one grouped launch of `kind`; the device arrays are
 // appended to `allocs` (owned by the caller).
@@ -191,6 +192,9 @@ struct TcLevel {
 };
 struct Schedule {
   int max_level = 0;
+  // work-item counters of the grouped launches; zero them before every run
+  unsigned long long* counters = nullptr;
+  int64_t ncounters = 0;
   std::vector<std::array<Group, kGroupKinds>> groups;  // per level and tile kind
   std::vector<TcLevel> tc;                             // per level (grouped tensor-core launches)
   double flops = 0.0, tc_flops = 0.0;

@@ -78,6 +78,15 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
         if (g.nseg > 1) group_split(g, k);
     for (int k = 0; k < kGroupKinds; ++k) TRY(make_group(eh, allocs, by_kind[k], k, &out->groups[lvl][k]));
   }
+  // one work-item counter per grouped launch
+  out->ncounters = (int64_t)(out->max_level + 1) * kGroupKinds;
+  void* dc = nullptr;
+  if (cudaMalloc(&dc, sizeof(unsigned long long) * out->ncounters) != cudaSuccess)
+    return fail(eh, RICMRCC_ENOMEM, "work counters");
+  allocs.push_back(dc);
+  out->counters = static_cast<unsigned long long*>(dc);
+  for (int lvl = 0; lvl <= out->max_level; ++lvl)
+    for (int k = 0; k < kGroupKinds; ++k) out->groups[lvl][k].ctr = out->counters + lvl * kGroupKinds + k;
   out->tc.assign(out->max_level + 1, {});
   if (!mixed) return RICMRCC_OK;
   // grouped packing launches (one per level)
@@ -188,38 +197,44 @@ int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*
                  void* scratch, size_t slice, int* err, int64_t* launches) {
   static const int slot[kGroupKinds] = {0, 1, 2, 5, 6};  // profile kernel index per tile kind
   int64_t n = 0;
-  for (int lvl = 0; lvl <= sc.max_level; ++lvl) {
-    tgt.fork();
+  auto grouped_fp = [&](int lvl) {
     for (int k = 0; k < kGroupKinds; ++k) {
       const Group& g = sc.groups[lvl][k];
       if (!g.nops) continue;
       tgt.mark(slot[k]);
-      launch_grouped(k, mixed, g.ops, g.begin, g.nops, g.total, eh->sms, tgt.lane(k));
+      launch_grouped(k, mixed, g.ops, g.begin, g.nops, g.total, eh->sms, g.ctr, tgt.lane(k));
       ++n;
     }
-    if (mixed) {
-      // one grouped packing launch on the first tensor-core lane, then the
-      // tensor-core launches behind it (same lane) or after the lanes meet
-      const TcLevel& tl = sc.tc[lvl];
-      int j = 0;
-      if (tl.npacks) {
-        tgt.mark(3);
-        if (tc_pack_group_launch(tl.packs, tl.npacks, tl.pack_total, eh->sms, tgt.lane(kTcLane0)) != 0)
-          return fail(eh, RICMRCC_ECUDA, "operand packing launch");
+  };
+  for (int lvl = 0; lvl <= sc.max_level; ++lvl) {
+    tgt.fork();
+    if (!mixed) {
+      grouped_fp(lvl);
+      tgt.join();
+      continue;
+    }
+    // mixed precision: the tensor-core chain is enqueued first, so that its
+    // one-CTA-per-SM launches hold their SMs while the FP32 tiles of the same
+    // level fill the remaining room (their CTAs take work from a counter)
+    const TcLevel& tl = sc.tc[lvl];
+    int j = 0;
+    if (tl.npacks) {
+      tgt.mark(3);
+      if (tc_pack_group_launch(tl.packs, tl.npacks, tl.pack_total, eh->sms, tgt.lane(kTcLane0)) != 0)
+        return fail(eh, RICMRCC_ECUDA, "operand packing launch");
+      ++n;
+      j = 1;
+    }
+    if (rule.tc_grouped) {
+      if (tl.nclusters) {
+        tgt.mark(4);
+        if (tc_group_launch(tl.ops, tl.segs, tl.clusters, tl.nclusters, tl.total, eh->sms, err,
+                            tgt.lane(kTcLane0)) != 0)
+          return fail(eh, RICMRCC_ECUDA, "grouped tensor-core launch");
         ++n;
-        j = 1;
       }
-      if (j && !rule.tc_grouped) tgt.tc_meet();
-      if (rule.tc_grouped) {
-        if (tl.nclusters) {
-          tgt.mark(4);
-          if (tc_group_launch(tl.ops, tl.segs, tl.clusters, tl.nclusters, tl.total, eh->sms, err, tgt.lane(kTcLane0)) != 0)
-            return fail(eh, RICMRCC_ECUDA, "grouped tensor-core launch");
-          ++n;
-        }
-        tgt.join();
-        continue;
-      }
+    } else {
+      if (j) tgt.tc_meet();
       j = 0;
       for (size_t i = 0; i < inst.size(); ++i) {
         if (!live[i]) continue;
@@ -241,6 +256,7 @@ int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*
         }
       }
     }
+    grouped_fp(lvl);
     tgt.join();
   }
   tgt.mark(-1);
