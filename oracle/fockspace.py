@@ -296,3 +296,63 @@ def reference_state(fs: FockSpace, n_core, n_act, n_el_act, seed=0):
             s |= 1 << p
         psi[s] = rng.normal()
     return psi / np.linalg.norm(psi)
+
+
+# ---------------------------------------------------------------------------
+# Spin multiplets (high-spin references, Sec. 2.3: spin-free RDMs of S > 0)
+# ---------------------------------------------------------------------------
+
+def spin_multiplet(n_orb, n_el, two_s, seed=0):
+    """All M_S components |S, M> (M = -S..S) of one random spin multiplet.
+
+    Spin orbitals are 2p + spin (spin 0 = alpha).  |S, 0> (or |S, 1/2>) is a
+    random unit vector in the S^2 = S(S+1) eigenspace of the lowest-|M_S|
+    sector with n_el electrons; the other components follow by S+ and S-.
+    Returns (fs, [psi_M for M ascending]).
+    """
+    m = 2 * n_orb
+    fs = FockSpace(m)
+    so = lambda p, s: 2 * p + s  # noqa: E731
+    splus = sum(fs.string([so(p, 0)], [so(p, 1)]) for p in range(n_orb))
+    sminus = splus.T
+    nalpha = np.array([sum((st >> so(p, 0)) & 1 for p in range(n_orb)) for st in range(fs.dim)])
+    nbeta = np.array([sum((st >> so(p, 1)) & 1 for p in range(n_orb)) for st in range(fs.dim)])
+    sz2 = nalpha - nbeta  # 2 M_S per determinant
+    low = two_s % 2  # lowest non-negative 2 M_S of the multiplet
+    sector = np.nonzero((fs.popcount == n_el) & (sz2 == low))[0]
+    s2 = sminus @ splus + np.diag(0.25 * sz2 ** 2 + 0.5 * sz2)
+    sub = s2[np.ix_(sector, sector)]
+    w, v = np.linalg.eigh(sub)
+    target = 0.25 * two_s * (two_s + 2)
+    space = v[:, np.abs(w - target) < 1e-8]
+    if space.shape[1] == 0:
+        raise ValueError("no such multiplet in this space")
+    c = space @ np.random.default_rng(seed).normal(size=space.shape[1])
+    psi = np.zeros(fs.dim)
+    psi[sector] = c / np.linalg.norm(c)
+    comps = {low: psi}
+    x = psi
+    for tm in range(low + 2, two_s + 1, 2):  # raise
+        x = splus @ x
+        x = x / np.linalg.norm(x)
+        comps[tm] = x
+    x = psi
+    for tm in range(low - 2, -two_s - 1, -2):  # lower
+        x = sminus @ x
+        x = x / np.linalg.norm(x)
+        comps[tm] = x
+    return fs, [comps[k] for k in sorted(comps)]
+
+
+def spin_trace(gso, n_orb, k):
+    """Spin-free RDM Gamma^{P..}_{Q..} = sum over spins of gamma^{(P,s)..}_{(Q,s)..}
+    (the E-operator convention: upper and lower index i carry the same spin)."""
+    out = np.zeros((n_orb,) * (2 * k))
+    for P in itertools.product(range(n_orb), repeat=k):
+        for Q in itertools.product(range(n_orb), repeat=k):
+            tot = 0.0
+            for spins in itertools.product((0, 1), repeat=k):
+                idx = tuple(2 * P[i] + spins[i] for i in range(k)) + tuple(2 * Q[i] + spins[i] for i in range(k))
+                tot += gso[idx]
+            out[P + Q] = tot
+    return out

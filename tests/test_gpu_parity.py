@@ -195,3 +195,23 @@ def test_mid_full_size_sampled_elements():
     ref = o.residual_elements(m, T, elems)
     for (name, idx), r in zip(elems, ref):
         assert abs(Rg[name][idx] - r) < RES_TOL, (name, idx, Rg[name][idx], r)
+
+
+@pytest.mark.parametrize("n_el,two_s", [(4, 2), (3, 1)])
+def test_residual_high_spin_reference(n_el, two_s):
+    """High-spin references (S = 1 with 4 active electrons, S = 1/2 with 3):
+    the library takes their spin-free RDMs, which stand for the M_S-averaged
+    ensemble (pinned in test_oracle_highspin.py); GPU and oracle agree."""
+    from oracle import fockspace as F
+    nc, na, nv, nx = 2, 4, 10, 48
+    fs, comps = F.spin_multiplet(na, n_el, two_s, seed=5)
+    G = [F.spin_trace(F.rdm(fs, comps[0], k), na, k) for k in (1, 2, 3)]
+    h, B = synthetic.make_integrals(nc, na, nv, nx, seed=7)
+    _, *rot = o.semicanonicalize(nc, na, nv, h, B, *G)
+    m = o.Model(nc, na, nv, *rot)
+    g = _gpu(nc, na, nv, nx, rot)
+    T = synthetic.make_amplitudes(nc, na, nv, seed=9, scale=0.05)
+    R, E = o.residual(m, T)
+    Rg, Eg = g.residual(T)
+    assert _compare(R, Rg) < RES_TOL
+    assert abs(E - Eg) < E_TOL
