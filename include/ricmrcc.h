@@ -355,6 +355,14 @@ RICMRCC_API int ricmrcc_batch_residual(ricmrcc_batch_t* b, int precision, double
  * (the per-instance outcome is in stats). */
 RICMRCC_API int ricmrcc_batch_solve(ricmrcc_batch_t* b, const ricmrcc_opts* opts, double* E_out,
                                     ricmrcc_stats* stats);
+/* ricmrcc_batch_solve with a flow value per instance (s[count], host; it
+ * replaces opts->s): a scan of the flow parameter over copies of one problem
+ * runs as one batch (the paper's accuracy-vs-s and non-convergence study,
+ * Sec. 4).  Per-instance outcomes (converged / diverged, iterations, max|dt|)
+ * are in stats; a diverged instance stops updating and does not stop the
+ * others. */
+RICMRCC_API int ricmrcc_batch_solve_flows(ricmrcc_batch_t* b, const double* s, const ricmrcc_opts* opts,
+                                          double* E_out, ricmrcc_stats* stats);
 /* n_steps batch iterations without convergence tests (restart != 0 resets the
  * DIIS histories).  E_out, max_dt_out: host [count], nullable. */
 RICMRCC_API int ricmrcc_batch_step(ricmrcc_batch_t* b, const ricmrcc_opts* opts, int n_steps, int restart,

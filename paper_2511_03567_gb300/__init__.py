@@ -139,6 +139,7 @@ def load_library():
         "ricmrcc_batch_set_rdms": ([vp, ctypes.c_int, vp, vp, vp, ctypes.c_int], ctypes.c_int),
         "ricmrcc_batch_residual": ([vp, ctypes.c_int, vp], ctypes.c_int),
         "ricmrcc_batch_solve": ([vp, ctypes.POINTER(Opts), vp, vp], ctypes.c_int),
+        "ricmrcc_batch_solve_flows": ([vp, vp, ctypes.POINTER(Opts), vp, vp], ctypes.c_int),
         "ricmrcc_batch_step": ([vp, ctypes.POINTER(Opts), ctypes.c_int, ctypes.c_int, vp, vp],
                                ctypes.c_int),
         "ricmrcc_batch_tune": ([vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Tuning)], ctypes.c_int),
@@ -443,6 +444,18 @@ class RicMrccBatch:
         e = np.zeros(self.count)
         st = (Stats * self.count)()
         rc = self.lib.ricmrcc_batch_solve(self.b, ctypes.byref(o), _ptr(e), ctypes.cast(st, ctypes.c_void_p))
+        self._check(rc, allow=(OK, NOT_CONVERGED, DIVERGED))
+        return e, list(st), rc
+
+    def solve_flows(self, s_values, **kw):
+        """Solve instance i with flow s_values[i] (a flow scan as one batch)."""
+        s_arr = np.ascontiguousarray(np.asarray(s_values, dtype=np.float64))
+        assert s_arr.size == self.count
+        o = RicMrcc.default_opts(**kw)
+        e = np.zeros(self.count)
+        st = (Stats * self.count)()
+        rc = self.lib.ricmrcc_batch_solve_flows(self.b, _ptr(s_arr), ctypes.byref(o), _ptr(e),
+                                                ctypes.cast(st, ctypes.c_void_p))
         self._check(rc, allow=(OK, NOT_CONVERGED, DIVERGED))
         return e, list(st), rc
 

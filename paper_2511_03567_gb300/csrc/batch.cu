@@ -195,7 +195,7 @@ int check_ready(ricmrcc_batch_t* b) {
 // One batch iteration over the instances in `upd` (graph over `live`, which
 // contains `upd`): residuals, then update / convergence test / DIIS per
 // instance.  conv[i], div[i] are set for the updated instances.
-int batch_iterate(ricmrcc_batch_t* b, const ricmrcc_opts& o, const std::vector<char>& live,
+int batch_iterate(ricmrcc_batch_t* b, const std::vector<ricmrcc_opts>& oi, const std::vector<char>& live,
                   const std::vector<char>& upd, bool mixed, bool check, std::vector<char>& conv,
                   std::vector<char>& div) {
   TRY(launch_residuals(b, live, mixed));
@@ -204,7 +204,7 @@ int batch_iterate(ricmrcc_batch_t* b, const ricmrcc_opts& o, const std::vector<c
     if (!upd[i]) continue;
     ricmrcc_t* h = b->inst[i];
     BCK(cudaStreamWaitEvent(h->s, b->done, 0));
-    ITRY(i, iter_update(h, o));
+    ITRY(i, iter_update(h, oi[i]));
   }
   std::vector<char> diis(b->count, 0);
   for (int i = 0; i < b->count; ++i) {
@@ -212,7 +212,7 @@ int batch_iterate(ricmrcc_batch_t* b, const ricmrcc_opts& o, const std::vector<c
     ricmrcc_t* h = b->inst[i];
     BCK(cudaStreamSynchronize(h->s));
     bool c = false, d = false, q = false;
-    ITRY(i, iter_check(h, o, check, &c, &d, &q));
+    ITRY(i, iter_check(h, oi[i], check, &c, &d, &q));
     conv[i] = c;
     div[i] = d;
     diis[i] = q;
@@ -220,7 +220,7 @@ int batch_iterate(ricmrcc_batch_t* b, const ricmrcc_opts& o, const std::vector<c
   for (int i = 0; i < b->count; ++i) {
     if (!diis[i]) continue;
     BCK(cudaStreamSynchronize(b->inst[i]->s));
-    ITRY(i, iter_finish(b->inst[i], o));
+    ITRY(i, iter_finish(b->inst[i], oi[i]));
   }
   return RICMRCC_OK;
 }
@@ -366,7 +366,7 @@ int ricmrcc_batch_step(ricmrcc_batch_t* b, const ricmrcc_opts* opts, int n_steps
     for (ricmrcc_t* h : b->inst) reset_iteration_state(h);
   bool diverged = false;
   for (int k = 0; k < n_steps && !diverged; ++k) {
-    TRY(batch_iterate(b, o, all, all, mixed, false, conv, div));
+    TRY(batch_iterate(b, std::vector<ricmrcc_opts>(b->count, o), all, all, mixed, false, conv, div));
     for (int i = 0; i < b->count; ++i) diverged = diverged || div[i];
   }
   for (int i = 0; i < b->count; ++i) {
@@ -377,22 +377,26 @@ int ricmrcc_batch_step(ricmrcc_batch_t* b, const ricmrcc_opts* opts, int n_steps
   return RICMRCC_OK;
 }
 
-int ricmrcc_batch_solve(ricmrcc_batch_t* b, const ricmrcc_opts* opts, double* E_out, ricmrcc_stats* stats) {
+static int batch_solve_impl(ricmrcc_batch_t* b, const ricmrcc_opts* opts, const double* s_each, double* E_out,
+                            ricmrcc_stats* stats) {
   if (!b) return RICMRCC_EINVAL;
   b->err.clear();
   ricmrcc_opts o;
   ricmrcc_opts_default(&o);
   if (opts) o = *opts;
-  TRY(check_batch_opts(b, o));
-  const auto t0 = std::chrono::steady_clock::now();
   const int n = b->count;
+  std::vector<ricmrcc_opts> oi(n, o);
+  if (s_each)
+    for (int i = 0; i < n; ++i) oi[i].s = s_each[i];
+  for (int i = 0; i < n; ++i) ITRY(i, check_opts(b->inst[i], oi[i]));
+  const auto t0 = std::chrono::steady_clock::now();
   for (ricmrcc_t* h : b->inst) reset_iteration_state(h);
   std::vector<char> live(n, 1), act(n, 1), conv(n, 0), div(n, 0), done_conv(n, 0), done_div(n, 0);
   std::vector<int> iters(n, 0), n_mixed(n, 0);
   bool mixed = o.precision == RICMRCC_MIXED;
   int n_live = n, n_act = n;
   for (int it = 1; it <= o.max_iter && n_act > 0; ++it) {
-    TRY(batch_iterate(b, o, live, act, mixed, !mixed, conv, div));
+    TRY(batch_iterate(b, oi, live, act, mixed, !mixed, conv, div));
     bool all_refined = true;
     for (int i = 0; i < n; ++i) {
       if (!act[i]) continue;
@@ -432,14 +436,24 @@ int ricmrcc_batch_solve(ricmrcc_batch_t* b, const ricmrcc_opts* opts, double* E_
       stats[i].seconds = secs;
     }
     h->solved = done_conv[i];
-    h->solved_s = o.s;
-    h->solved_opts = o;
+    h->solved_s = oi[i].s;
+    h->solved_opts = oi[i];
     all_conv = all_conv && done_conv[i];
     any_div = any_div || done_div[i];
   }
   if (any_div) return bfail(b, RICMRCC_DIVERGED, "an instance diverged (see stats)");
   if (!all_conv) return bfail(b, RICMRCC_NOT_CONVERGED, "max_iter reached (see stats)");
   return RICMRCC_OK;
+}
+
+int ricmrcc_batch_solve(ricmrcc_batch_t* b, const ricmrcc_opts* opts, double* E_out, ricmrcc_stats* stats) {
+  return batch_solve_impl(b, opts, nullptr, E_out, stats);
+}
+
+int ricmrcc_batch_solve_flows(ricmrcc_batch_t* b, const double* s, const ricmrcc_opts* opts, double* E_out,
+                              ricmrcc_stats* stats) {
+  if (!b || !s) return bfail(b, RICMRCC_EINVAL, "null flow array");
+  return batch_solve_impl(b, opts, s, E_out, stats);
 }
 
 int ricmrcc_batch_tune(ricmrcc_batch_t* b, int precision, int reps, ricmrcc_tuning* out) {

@@ -170,3 +170,21 @@ def test_batched_workload_full_size_matches_single_path():
         # carry ~1e-5 relative error (16 significant bits per operand); the
         # 1e-6 Eh criterion applies to the solve after its FP64 refinement
         assert abs(Es - Em[i]) < 1e-5, i
+
+
+def test_flow_scan_as_one_batch(small):
+    """Flow scan s in {0.1, 0.5, 2.0} over copies of one problem in one batch:
+    each instance's energy equals its own single solve at that s and the
+    oracle's; the energy changes with s (the RIC fixed point depends on the
+    flow)."""
+    import paper_2511_03567_gb300 as ric
+    rots, models = small
+    d = SMALL[0]
+    flows = [0.1, 0.5, 2.0]
+    b = _batch([d] * len(flows), [rots[0]] * len(flows))
+    E, stats, rc = b.solve_flows(flows)
+    assert rc == ric.OK and all(st.converged == 1 for st in stats)
+    for s_i, e_i in zip(flows, E):
+        ref = o.solve(models[0], s_i)
+        assert ref.converged and abs(e_i - ref.energy) < E_TOL, s_i
+    assert abs(E[0] - E[2]) > 1e-6
