@@ -119,7 +119,7 @@ def fp64_gemm_peak(torch):
 
 
 KERNEL_NAMES = ("grouped_tile_64x64", "grouped_tile_16x16", "grouped_dot", "tc_pack_split_bf16",
-                "tc_gemm_tcgen05_bf16x3", "grouped_tile_128x16", "grouped_tile_64x32")
+                "tc_gemm_tcgen05_bf16x3", "grouped_tile_128x16", "grouped_tile_64x32", "grouped_small_long_k")
 
 
 def fp32_peak_tflops(torch):

@@ -216,8 +216,8 @@ typedef struct {
   /* per kernel of ricmrcc_profile (same order), for the handle's precision and
    * tile rule: contractions and their FLOPs (tensor-core FLOPs FP64-equivalent;
    * [3], the packing, counts the packed operand buffers and their bytes) */
-  int64_t kernel_ops[7];
-  double kernel_work[7];
+  int64_t kernel_ops[8];
+  double kernel_work[8];
   /* algorithmic bytes of the tensor-core GEMMs per residual: every packed
    * operand buffer read once, every output element read and written once in
    * FP64 per launched op (contractions merged into one op count once; known
@@ -234,10 +234,10 @@ RICMRCC_API int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out);
  * the mean milliseconds per residual in kind_ms[RICMRCC_PROFILE_KINDS]
  * (host), per kernel: [0] 64x64 tile, [1] 16x16 tile, [2] dot reduction,
  * [3] tensor-core operand packing, [4] tcgen05 GEMM, [5] 128x16 tile,
- * [6] 64x32 tile.  The tiles compute in FP64, or in FP32 with mixed != 0,
+ * [6] 64x32 tile, [7] small-output long-K reduction.  The tiles compute in FP64, or in FP32 with mixed != 0,
  * which also routes the large contractions to the tensor cores ([3], [4]).
  * Diagnostic: the events serialise the launches. */
-#define RICMRCC_PROFILE_KINDS 7
+#define RICMRCC_PROFILE_KINDS 8
 RICMRCC_API int ricmrcc_profile(ricmrcc_t* h, int reps, int mixed, double* kind_ms);
 
 /* Split-precision BF16 tensor-core GEMM (the contraction engine of the

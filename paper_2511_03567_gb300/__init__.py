@@ -53,7 +53,7 @@ class PlanInfo(ctypes.Structure):
                 ("kind_launches", ctypes.c_int64 * 3), ("kind_flops", ctypes.c_double * 3),
                 ("tc_contractions", ctypes.c_int64), ("tc_flops", ctypes.c_double),
                 ("tc_pack_bytes", ctypes.c_double), ("graph_launches", ctypes.c_int64 * 2),
-                ("kernel_ops", ctypes.c_int64 * 7), ("kernel_work", ctypes.c_double * 7),
+                ("kernel_ops", ctypes.c_int64 * 8), ("kernel_work", ctypes.c_double * 8),
                 ("tc_gemm_bytes", ctypes.c_double)]
 
 
@@ -327,7 +327,8 @@ def _plan_info(self):
     return info
 
 
-PROFILE_KINDS = ("tile_64x64", "tile_16x16", "dot", "tc_pack", "tc_gemm", "tile_128x16", "tile_64x32")
+PROFILE_KINDS = ("tile_64x64", "tile_16x16", "dot", "tc_pack", "tc_gemm", "tile_128x16", "tile_64x32",
+                 "small_long_k")
 
 
 def _profile(self, reps=3, mixed=False):

@@ -191,6 +191,7 @@ bool tc_eligible(const ContractOp& op, const TileRule& r) {
 int op_kind(const ContractOp& op, const TileRule& r) {
   if (op.kind == 2) return 2;
   if (r.skinny && op.M >= 64 && op.N < 32) return op.N <= 16 ? 3 : 4;
+  if (r.skinny && op.M <= 16 && op.N <= 16 && op.K >= 4 * kSmallKC) return 5;  // small outputs, long K
   return op.kind;
 }
 
@@ -1152,7 +1153,7 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
   const int64_t gl = h->graph_launches[h->precision == RICMRCC_MIXED ? 1 : 0];
   out->step_launches = (gl ? gl : out->residual_launches) + 4;
   const bool mixed = h->precision == RICMRCC_MIXED;
-  static const int slot[kGroupKinds] = {0, 1, 2, 5, 6};
+  static const int slot[kGroupKinds] = {0, 1, 2, 5, 6, 7};
   std::set<std::string> out_keys;
   for (size_t i = 0; i < h->res_prog.ops.size(); ++i) {
     const ContractOp& op = h->res_prog.ops[i];

@@ -222,15 +222,93 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+
+// Small outputs (M, N <= 16), long K: one work item = one K chunk (kSmallKC)
+// of one op and one l.  The chunk of A (M rows) and B (N rows) is staged in
+// shared memory; thread t owns output t % (M N) and a 1/g share of the
+// chunk's K (g = 256 / (M N) threads per output); partial sums meet in
+// shared memory and one reduction per output goes to C.
+template <typename CT>
+__global__ void __launch_bounds__(256)
+    k_grouped_small(const GroupOp* __restrict__ ops, const int64_t* __restrict__ begin, int nops, int64_t total,
+                    unsigned long long* ctr) {
+  __shared__ CT As[16][kSmallKC + 1];
+  __shared__ CT Bs[16][kSmallKC + 1];
+  __shared__ CT part[256];
+  __shared__ int64_t sA[16], sB[16];
+  const int tid = threadIdx.x;
+  for (int64_t w = next_item(ctr, 0, true); w < total; w = next_item(ctr, w, false)) {
+    const int oi = find_op(begin, nops, w);
+    const GroupOp& op = ops[oi];
+    const int64_t L = op.L, M = op.M, N = op.N, K = op.K;
+    const int MN = (int)(M * N);
+    const int g = 256 / MN;  // threads per output (>= 1)
+    const int o = tid % MN, share = tid / MN;
+    const int m = o / (int)N, n = o % (int)N;
+    const int64_t* tCL = op.tab + 2 * L;
+    const int64_t* tCM = tCL + L + M;
+    const int64_t* tCN = tCM + M + N;
+    const int64_t r = w - begin[oi];
+    const int ks = (int)(r % op.ksplit);
+    const int64_t l = r / op.ksplit;
+    const int64_t kb = (int64_t)ks * op.kchunk;
+    const int64_t ke = kb + op.kchunk < K ? kb + op.kchunk : K;
+    CT acc = (CT)0;
+    for (int sgi = 0; sgi < op.nseg; ++sgi) {
+      const GroupSeg& sg = op.seg[sgi];
+      const int64_t lo = kb > sg.koff ? kb : sg.koff;
+      const int64_t hi = ke < sg.koff + sg.K ? ke : sg.koff + sg.K;
+      if (lo >= hi) continue;
+      const int64_t* tAL = sg.tab;
+      const int64_t* tBL = tAL + L;
+      const int64_t* tAM = tBL + 2 * L;
+      const int64_t* tBN = tAM + 2 * M;
+      const int64_t* tAK = tBN + 2 * N;
+      const int64_t* tBK = tAK + sg.K;
+      __syncthreads();  // previous stage fully consumed
+      if (tid < M) sA[tid] = tAL[l] + tAM[tid];
+      if (tid >= 16 && tid < 16 + N) sB[tid - 16] = tBL[l] + tBN[tid - 16];
+      __syncthreads();
+      const int len = (int)(hi - lo);
+      const int64_t k0 = lo - sg.koff;
+      const double alpha = sg.alpha;
+      for (int i = tid; i < M * len; i += 256) {
+        const int mm = i / len, kk = i % len;
+        As[mm][kk] = (CT)sg.A[sA[mm] + tAK[k0 + kk]];
+      }
+      for (int i = tid; i < N * len; i += 256) {
+        const int nn = i / len, kk = i % len;
+        Bs[nn][kk] = (CT)(alpha * sg.B[sB[nn] + tBK[k0 + kk]]);
+      }
+      __syncthreads();
+      if (share < g)
+        for (int kk = share; kk < len; kk += g) acc = fma(As[m][kk], Bs[n][kk], acc);
+    }
+    part[tid] = acc;
+    __syncthreads();
+    if (tid < MN) {
+      CT sum = part[tid];
+      for (int p = 1; p < g; ++p) sum += part[tid + p * MN];
+      if (sum != (CT)0) red_add(op.C + tCL[l] + tCM[m] + tCN[n], (double)sum);
+    }
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
 // Output tile (rows x columns) of each tile kind.
-constexpr int kTileM[5] = {64, 16, 1, 128, 64};
-constexpr int kTileN[5] = {64, 16, 1, 16, 32};
+constexpr int kTileM[kGroupKinds] = {64, 16, 1, 128, 64, 16};
+constexpr int kTileN[kGroupKinds] = {64, 16, 1, 16, 32, 16};
 
 void group_split(GroupOp& op, int kind) {
   const int64_t K = op.K;
   int64_t ks = 1;
+  if (kind == 5) {
+    op.ksplit = (int)((K + kSmallKC - 1) / kSmallKC);
+    op.kchunk = kSmallKC;
+    return;
+  }
   if (kind == 2) {
     ks = K / 4096;
     if (ks > 4096) ks = 4096;
@@ -270,14 +348,15 @@ template <typename CT>
 void launch_typed(int kind, const GroupOp* ops, const int64_t* begin, int nops, int64_t total, int sms,
                   unsigned long long* ctr, cudaStream_t s) {
   // persistent grid: every resident CTA slot of every SM (occupancy API)
-  static int per_sm[kGroupKinds] = {0, 0, 0, 0, 0};
+  static int per_sm[kGroupKinds] = {0, 0, 0, 0, 0, 0};
   if (!per_sm[kind]) {
     switch (kind) {
       case 0: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 64, 64, 4, 4, 16>); break;
       case 1: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 16, 16, 1, 1, 16>); break;
       case 2: per_sm[kind] = resident_per_sm(k_grouped_dot<CT>); break;
       case 3: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 128, 16, 8, 1, 8>); break;
-      default: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 64, 32, 8, 1, 8>); break;
+      case 4: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 64, 32, 8, 1, 8>); break;
+      default: per_sm[kind] = resident_per_sm(k_grouped_small<CT>); break;
     }
   }
   const int64_t slots = (int64_t)sms * per_sm[kind];
@@ -287,7 +366,8 @@ void launch_typed(int kind, const GroupOp* ops, const int64_t* begin, int nops, 
     case 1: k_grouped_tile<CT, 16, 16, 1, 1, 16><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
     case 2: k_grouped_dot<CT><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
     case 3: k_grouped_tile<CT, 128, 16, 8, 1, 8><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
-    default: k_grouped_tile<CT, 64, 32, 8, 1, 8><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
+    case 4: k_grouped_tile<CT, 64, 32, 8, 1, 8><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
+    default: k_grouped_small<CT><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
   }
 }
 

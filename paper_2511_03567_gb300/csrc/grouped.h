@@ -35,7 +35,10 @@ void group_split(GroupOp& op, int kind);
 int64_t group_units(const GroupOp& op, int kind);
 // kind: 0 = 64x64 FP64 tile, 1 = 16x16 tile, 2 = dot reduction,
 // 3 = 128x16 tile and 4 = 64x32 tile (tall-skinny ops; one column per thread).
-constexpr int kGroupKinds = 5;
+// 5 = small outputs (M, N <= 16) with long K: each work item reduces one
+// K chunk of all the op's outputs, the block's threads splitting K.
+constexpr int kGroupKinds = 6;
+constexpr int kSmallKC = 128;  // K chunk of kind 5
 // fp32: compute in FP32 (mixed precision), else FP64.  ctr (nullable, zero
 // before the launch): work-item counter the CTAs take items from; without it
 // each CTA takes a fixed stride of items.

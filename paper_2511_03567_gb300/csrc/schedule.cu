@@ -75,7 +75,7 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
     }
     for (int k = 0; k < kGroupKinds; ++k)
       for (GroupOp& g : by_kind[k])
-        if (g.nseg > 1) group_split(g, k);
+        if (g.nseg > 1 || k == 5) group_split(g, k);
     for (int k = 0; k < kGroupKinds; ++k) TRY(make_group(eh, allocs, by_kind[k], k, &out->groups[lvl][k]));
   }
   // one work-item counter per grouped launch
@@ -195,7 +195,7 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
 int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*>& inst,
                  const std::vector<char>& live, const TileRule& rule, bool mixed, ScheduleTarget& tgt,
                  void* scratch, size_t slice, int* err, int64_t* launches) {
-  static const int slot[kGroupKinds] = {0, 1, 2, 5, 6};  // profile kernel index per tile kind
+  static const int slot[kGroupKinds] = {0, 1, 2, 5, 6, 7};  // profile kernel index per tile kind
   int64_t n = 0;
   auto grouped_fp = [&](int lvl) {
     for (int k = 0; k < kGroupKinds; ++k) {
