@@ -188,9 +188,20 @@ bool tc_eligible(const ContractOp& op, const TileRule& r) {
 // FP64 kernel of an op: the planner's choice (64x64 tile, 16x16 tile or dot
 // reduction), with tall-skinny ops moved to the 128x16 / 64x32 tiles, whose
 // threads own one output column each and so write C rows contiguously.
-int op_kind(const ContractOp& op, const TileRule& r) {
+int op_kind(const ContractOp& op, const TileRule& r, const int64_t* th) {
   if (op.kind == 2) return 2;
-  if (r.skinny && op.M >= 64 && op.N < 32) return op.N <= 16 ? 3 : 4;
+  if (r.skinny && op.M >= 64 && op.N < 32) {
+    if (op.N > 16) return 4;
+    if (th) {  // lanes along whichever output index runs contiguously more often
+      const int64_t* tCM = th + 3 * op.L + op.M;
+      const int64_t* tCN = tCM + op.M + op.N;
+      int64_t um = 0, un = 0;
+      for (int64_t i = 1; i < op.M; ++i) um += tCM[i] - tCM[i - 1] == 1;
+      for (int64_t i = 1; i < op.N; ++i) un += tCN[i] - tCN[i - 1] == 1;
+      if ((double)um / (double)(op.M - 1) > (op.N > 1 ? (double)un / (double)(op.N - 1) : 0.0)) return 6;
+    }
+    return 3;
+  }
   if (r.skinny && op.M <= 16 && op.N <= 16 && op.K >= 4 * kSmallKC) return 5;  // small outputs, long K
   return op.kind;
 }
@@ -1153,7 +1164,7 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
   const int64_t gl = h->graph_launches[h->precision == RICMRCC_MIXED ? 1 : 0];
   out->step_launches = (gl ? gl : out->residual_launches) + 4;
   const bool mixed = h->precision == RICMRCC_MIXED;
-  static const int slot[kGroupKinds] = {0, 1, 2, 5, 6, 7};
+  static const int slot[kGroupKinds] = {0, 1, 2, 5, 6, 7, 5};
   std::set<std::string> out_keys;
   for (size_t i = 0; i < h->res_prog.ops.size(); ++i) {
     const ContractOp& op = h->res_prog.ops[i];
@@ -1163,7 +1174,9 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
       out->tc_contractions += 1;
       out->tc_flops += op.flops;
     }
-    const int k = mixed && tc_eligible(op, h->rule) ? 4 : slot[op_kind(op, h->rule)];
+    const int k = mixed && tc_eligible(op, h->rule)
+                      ? 4
+                      : slot[op_kind(op, h->rule, h->res_prog.table.data() + op.tab)];
     out->kernel_ops[k] += 1;
     out->kernel_work[k] += op.flops;
     if (h->tc_planned && tc_eligible(op, h->rule) && h->rule.tc_grouped) {

@@ -136,9 +136,9 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
         for (int kk = 0; kk < BK; ++kk) {
           CT a[TM], b[TN];
 #pragma unroll
-          for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+          for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + (BM / TM) * i];
 #pragma unroll
-          for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+          for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + (BN / TN) * j];
 #pragma unroll
           for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -150,11 +150,11 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
     double* C = op.C;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-      const int mm = ty * TM + i;
+      const int mm = ty + (BM / TM) * i;
       if (m0 + mm >= M) continue;
 #pragma unroll
       for (int j = 0; j < TN; ++j) {
-        const int nn = tx * TN + j;
+        const int nn = tx + (BN / TN) * j;
         if (n0 + nn >= N) continue;
         const CT v = acc[i][j];
         if (v != (CT)0) red_add(C + cL + sCM[mm] + sCN[nn], (double)v);
@@ -298,8 +298,8 @@ __global__ void __launch_bounds__(256)
 }  // namespace
 
 // Output tile (rows x columns) of each tile kind.
-constexpr int kTileM[kGroupKinds] = {64, 16, 1, 128, 64, 16};
-constexpr int kTileN[kGroupKinds] = {64, 16, 1, 16, 32, 16};
+constexpr int kTileM[kGroupKinds] = {64, 16, 1, 128, 64, 16, 128};
+constexpr int kTileN[kGroupKinds] = {64, 16, 1, 16, 32, 16, 16};
 
 void group_split(GroupOp& op, int kind) {
   const int64_t K = op.K;
@@ -348,7 +348,7 @@ template <typename CT>
 void launch_typed(int kind, const GroupOp* ops, const int64_t* begin, int nops, int64_t total, int sms,
                   unsigned long long* ctr, cudaStream_t s) {
   // persistent grid: every resident CTA slot of every SM (occupancy API)
-  static int per_sm[kGroupKinds] = {0, 0, 0, 0, 0, 0};
+  static int per_sm[kGroupKinds] = {0, 0, 0, 0, 0, 0, 0};
   if (!per_sm[kind]) {
     switch (kind) {
       case 0: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 64, 64, 4, 4, 16>); break;
@@ -356,7 +356,8 @@ void launch_typed(int kind, const GroupOp* ops, const int64_t* begin, int nops, 
       case 2: per_sm[kind] = resident_per_sm(k_grouped_dot<CT>); break;
       case 3: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 128, 16, 8, 1, 8>); break;
       case 4: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 64, 32, 8, 1, 8>); break;
-      default: per_sm[kind] = resident_per_sm(k_grouped_small<CT>); break;
+      case 5: per_sm[kind] = resident_per_sm(k_grouped_small<CT>); break;
+      default: per_sm[kind] = resident_per_sm(k_grouped_tile<CT, 128, 16, 1, 8, 8>); break;
     }
   }
   const int64_t slots = (int64_t)sms * per_sm[kind];
@@ -367,7 +368,8 @@ void launch_typed(int kind, const GroupOp* ops, const int64_t* begin, int nops, 
     case 2: k_grouped_dot<CT><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
     case 3: k_grouped_tile<CT, 128, 16, 8, 1, 8><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
     case 4: k_grouped_tile<CT, 64, 32, 8, 1, 8><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
-    default: k_grouped_small<CT><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
+    case 5: k_grouped_small<CT><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
+    default: k_grouped_tile<CT, 128, 16, 1, 8, 8><<<g, 256, 0, s>>>(ops, begin, nops, total, ctr); break;
   }
 }
 

@@ -37,7 +37,10 @@ int64_t group_units(const GroupOp& op, int kind);
 // 3 = 128x16 tile and 4 = 64x32 tile (tall-skinny ops; one column per thread).
 // 5 = small outputs (M, N <= 16) with long K: each work item reduces one
 // K chunk of all the op's outputs, the block's threads splitting K.
-constexpr int kGroupKinds = 6;
+// 6 = tall-skinny like 3 with lanes along rows (for outputs whose rows, not
+// columns, are contiguous, so that each reduction instruction covers
+// consecutive addresses).
+constexpr int kGroupKinds = 7;
 constexpr int kSmallKC = 128;  // K chunk of kind 5
 // fp32: compute in FP32 (mixed precision), else FP64.  ctr (nullable, zero
 // before the launch): work-item counter the CTAs take items from; without it

@@ -139,7 +139,9 @@ int leave(ricmrcc_t* h);
 
 // Kernel kind (grouped.h numbering) of an FP64 op under `r`, and whether the
 // op runs on the tensor cores in mixed precision.
-int op_kind(const ContractOp& op, const TileRule& r);
+// th: the op's host offset table (nullable) lets a tall-skinny op pick the
+// tile whose lanes follow its contiguous output index.
+int op_kind(const ContractOp& op, const TileRule& r, const int64_t* th = nullptr);
 bool tc_eligible(const ContractOp& op, const TileRule& r);
 // Plan the tensor-core path (eligible ops, operand cache, scratch size) ...
 int ensure_tc_plan(ricmrcc_t* h);

@@ -48,8 +48,8 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
           out->tc_flops += op.flops;
           continue;
         }
-        const int kind = op_kind(op, rule);
         const int64_t* th = p.table.data() + op.tab;
+        const int kind = op_kind(op, rule, th);
         std::string key(reinterpret_cast<const char*>(&op.C), sizeof(op.C));
         const int64_t ext[3] = {op.L, op.M, op.N};
         key.append(reinterpret_cast<const char*>(ext), sizeof(ext));
@@ -195,7 +195,7 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
 int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*>& inst,
                  const std::vector<char>& live, const TileRule& rule, bool mixed, ScheduleTarget& tgt,
                  void* scratch, size_t slice, int* err, int64_t* launches) {
-  static const int slot[kGroupKinds] = {0, 1, 2, 5, 6, 7};  // profile kernel index per tile kind
+  static const int slot[kGroupKinds] = {0, 1, 2, 5, 6, 7, 5};  // profile kernel index per tile kind
   int64_t n = 0;
   auto grouped_fp = [&](int lvl) {
     for (int k = 0; k < kGroupKinds; ++k) {
