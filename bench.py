@@ -271,7 +271,9 @@ def main():
         print(json.dumps({"ncu_residual": args.ncu_residual, "workload": w["workload"], "precision": args.precision,
                           "tile_rule": g.get_tile_rule(), "energy": E,
                           "graph_launches": int(info.graph_launches[1 if prec == ric.MIXED else 0]),
-                          "tc_gemm_bytes": info.tc_gemm_bytes, "tc_flops": info.tc_flops}))
+                          "tc_gemm_bytes": info.tc_gemm_bytes, "tc_flops": info.tc_flops,
+                          "tc_grouped_ops": int(info.tc_grouped_ops),
+                          "tc_weighted_ops": int(info.tc_weighted_ops)}))
         return 0
     if not args.no_tune and args.tile_rule is None and not args.ncu_largest:
         # tile rule for this workload, timed at representative (non-zero)
@@ -363,7 +365,8 @@ def main():
     roof = roofline(kind_ms, info, mixed, pk, fp64_peak, torch)
     tc = None
     if mixed:
-        tc = {"contractions": int(info.tc_contractions), "fp64_equiv_flops": info.tc_flops,
+        tc = {"contractions": int(info.tc_contractions), "grouped_ops": int(info.tc_grouped_ops),
+              "weighted_ops": int(info.tc_weighted_ops), "fp64_equiv_flops": info.tc_flops,
               "pack_bytes_per_residual": info.tc_pack_bytes,
               "bf16_flops": 3.0 * info.tc_flops,
               "gemm_tflops": 3.0 * info.tc_flops / (kind_ms[4] / 1e3) / 1e12 if kind_ms[4] else None,

@@ -223,6 +223,12 @@ typedef struct {
    * FP64 per launched op (contractions merged into one op count once; known
    * once the tensor-core path is planned) */
   double tc_gemm_bytes;
+  /* ops of the grouped tensor-core launches (merged contractions count once)
+   * and how many of them merge contractions of different alphas (+-2^e
+   * weights applied inside the MMA); 0 until the tensor-core path is planned
+   * with grouped launches */
+  int64_t tc_grouped_ops;
+  int64_t tc_weighted_ops;
 } ricmrcc_plan_info_t;
 
 /* Sizes of the contraction program planned for this handle. */

@@ -54,7 +54,8 @@ class PlanInfo(ctypes.Structure):
                 ("tc_contractions", ctypes.c_int64), ("tc_flops", ctypes.c_double),
                 ("tc_pack_bytes", ctypes.c_double), ("graph_launches", ctypes.c_int64 * 2),
                 ("kernel_ops", ctypes.c_int64 * 8), ("kernel_work", ctypes.c_double * 8),
-                ("tc_gemm_bytes", ctypes.c_double)]
+                ("tc_gemm_bytes", ctypes.c_double), ("tc_grouped_ops", ctypes.c_int64),
+                ("tc_weighted_ops", ctypes.c_int64)]
 
 
 class TileRule(ctypes.Structure):

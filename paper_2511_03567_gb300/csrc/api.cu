@@ -9,6 +9,7 @@
 #include <array>
 #include <chrono>
 #include <memory>
+#include <map>
 #include <set>
 #include <string>
 #include <unordered_map>
@@ -1165,7 +1166,13 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
   out->step_launches = (gl ? gl : out->residual_launches) + 4;
   const bool mixed = h->precision == RICMRCC_MIXED;
   static const int slot[kGroupKinds] = {0, 1, 2, 5, 6, 7, 5};
-  std::set<std::string> out_keys;
+  struct MergedOp {
+    int n = 0;          // contractions so far under this key
+    double alpha0 = 0;  // alpha of the current op's first contraction
+    int64_t op = -1;    // index of the current op
+  };
+  std::map<std::string, MergedOp> out_keys;
+  std::vector<char> weighted;  // per grouped op: merges different alphas
   for (size_t i = 0; i < h->res_prog.ops.size(); ++i) {
     const ContractOp& op = h->res_prog.ops[i];
     out->kind_launches[op.kind] += 1;
@@ -1181,17 +1188,26 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
     out->kernel_work[k] += op.flops;
     if (h->tc_planned && tc_eligible(op, h->rule) && h->rule.tc_grouped) {
       // outputs are written once per merged op (contractions of one level
-      // with the same outputs and alpha share their output update)
+      // with the same outputs and alpha class share their output update)
       const int64_t* th = h->res_prog.table.data() + op.tab;
       std::string key(reinterpret_cast<const char*>(&op.level), sizeof(op.level));
       key.append(reinterpret_cast<const char*>(&op.C), sizeof(op.C));
-      key.append(reinterpret_cast<const char*>(&op.alpha), sizeof(op.alpha));
+      tc_alpha_class(op.alpha, key);
       const int64_t ext[3] = {op.L, op.M, op.N};
       key.append(reinterpret_cast<const char*>(ext), sizeof(ext));
       key.append(reinterpret_cast<const char*>(th + 2 * op.L), sizeof(int64_t) * op.L);
       key.append(reinterpret_cast<const char*>(th + 3 * op.L + op.M), sizeof(int64_t) * op.M);
       key.append(reinterpret_cast<const char*>(th + 3 * op.L + 2 * op.M + op.N), sizeof(int64_t) * op.N);
-      if (out_keys.insert(key).second) out->tc_gemm_bytes += 16.0 * (double)op.M * (double)op.N;
+      // a merged op takes at most kTcMaxSeg contractions; the next one starts a new op
+      MergedOp& mo = out_keys[key];
+      if (mo.n++ % kTcMaxSeg == 0) {
+        out->tc_gemm_bytes += 16.0 * (double)op.M * (double)op.N;
+        mo.alpha0 = op.alpha;
+        mo.op = (int64_t)weighted.size();
+        weighted.push_back(0);
+      } else if (op.alpha != mo.alpha0) {
+        weighted[mo.op] = 1;
+      }
     } else if (h->tc_planned && tc_eligible(op, h->rule)) {
       out->tc_gemm_bytes += 16.0 * (double)op.M * (double)op.N;
     }
@@ -1200,6 +1216,8 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
   // (read FP64 source, write three BF16 segments); constant ones are packed
   // only when the integrals or RDMs change.  Known once the tensor-core path
   // is planned.
+  out->tc_grouped_ops = (int64_t)weighted.size();
+  for (char w : weighted) out->tc_weighted_ops += w;
   for (const PackedOperand& e : h->tc_cache) {
     out->tc_gemm_bytes += 6.0 * e.rows_pad * e.Kp;
     if (e.level < 0) continue;

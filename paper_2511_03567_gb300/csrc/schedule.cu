@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <array>
+#include <cmath>
 #include <map>
 #include <string>
 #include <vector>
@@ -126,10 +127,10 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
     out->tc[lvl].pack_total = total;
   }
   if (!rule.tc_grouped) return RICMRCC_OK;
-  constexpr int kTcMaxSeg = 8;
   for (int lvl = 0; lvl <= out->max_level; ++lvl) {
     // tensor-core contractions of one instance that add into the same output
-    // elements with the same alpha merge into one op (concatenated K)
+    // elements merge into one op (concatenated K) when their alphas are equal
+    // or all +-2^e (the kernel applies the sign and exponent per segment)
     std::vector<std::vector<TcArgs>> merged;
     for (size_t i = 0; i < inst.size(); ++i) {
       if (!live[i]) continue;
@@ -141,7 +142,7 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
         if (op.L == 0 || op.M == 0 || op.N == 0 || op.K == 0) continue;
         const int64_t* th = p.table.data() + op.tab;
         std::string key(reinterpret_cast<const char*>(&op.C), sizeof(op.C));
-        key.append(reinterpret_cast<const char*>(&op.alpha), sizeof(op.alpha));
+        tc_alpha_class(op.alpha, key);
         const int64_t ext[3] = {op.L, op.M, op.N};
         key.append(reinterpret_cast<const char*>(ext), sizeof(ext));
         key.append(reinterpret_cast<const char*>(th + 2 * op.L), sizeof(int64_t) * op.L);
@@ -159,7 +160,11 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
     if (merged.empty()) continue;
     std::vector<TcArgs> args;
     std::vector<int> nseg;
-    for (const auto& m : merged) {
+    for (auto& m : merged) {
+      // segments by increasing |alpha|: the kernel only scales its
+      // accumulator down at a segment boundary
+      std::stable_sort(m.begin(), m.end(),
+                       [](const TcArgs& x, const TcArgs& y) { return std::fabs(x.alpha) < std::fabs(y.alpha); });
       args.insert(args.end(), m.begin(), m.end());
       nseg.push_back((int)m.size());
     }

@@ -312,6 +312,48 @@ __device__ __forceinline__ uint32_t instr_desc_n(int bn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
+// Segment of a merged op holding k-tile kt (segment 0 = the op's own pair).
+__device__ __forceinline__ int seg_at(const TcGroupOp& op, const TcSeg* __restrict__ segs, int kt) {
+  int i = 0, off = 0, len = op.kt0;
+  while (kt >= off + len && i + 1 < op.nseg) {
+    off += len;
+    len = segs[op.seg0 + i].kt;
+    ++i;
+  }
+  return i;
+}
+
+// tcgen05.mma with the accumulator scaled by 2^-S before the product is added
+// (S is an immediate of the instruction, 1..15).
+template <int S>
+__device__ __forceinline__ void mma_scaled(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.eq.u32 p, %4, %4;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p, %5;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(0u), "n"(S));
+}
+__device__ __noinline__ void mma_scaled_any(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, int s) {
+  switch (s) {
+    case 1: mma_scaled<1>(d, ad, bd, idesc); break;
+    case 2: mma_scaled<2>(d, ad, bd, idesc); break;
+    case 3: mma_scaled<3>(d, ad, bd, idesc); break;
+    case 4: mma_scaled<4>(d, ad, bd, idesc); break;
+    case 5: mma_scaled<5>(d, ad, bd, idesc); break;
+    case 6: mma_scaled<6>(d, ad, bd, idesc); break;
+    case 7: mma_scaled<7>(d, ad, bd, idesc); break;
+    case 8: mma_scaled<8>(d, ad, bd, idesc); break;
+    case 9: mma_scaled<9>(d, ad, bd, idesc); break;
+    case 10: mma_scaled<10>(d, ad, bd, idesc); break;
+    case 11: mma_scaled<11>(d, ad, bd, idesc); break;
+    case 12: mma_scaled<12>(d, ad, bd, idesc); break;
+    case 13: mma_scaled<13>(d, ad, bd, idesc); break;
+    case 14: mma_scaled<14>(d, ad, bd, idesc); break;
+    default: mma_scaled<15>(d, ad, bd, idesc); break;
+  }
+}
+
+constexpr uint32_t kNegateA = 1u << 13;  // instruction descriptor: negate the A operand
+
 constexpr int kEpiWarps = 8;
 
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
@@ -388,13 +430,29 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     bool ok = true;
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++c) {
       const ItemPos p = item_pos(ops, cl, ncl, t);
-      const int bn = ops[p.oi].bn;
+      const TcGroupOp& op = ops[p.oi];
       const uint32_t b = c & 1;
       if (c >= 2 && !mbar_wait(tempty + b, ((c >> 1) - 1) & 1, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t idesc = instr_desc_n(bn);
+      // the accumulator holds the item's sum in units of its last segment's
+      // weight: segments of the other sign run with A negated, and each
+      // segment boundary scales the partial sum down by the exponent step
+      const uint32_t idesc0 = instr_desc_n(op.bn);
+      const uint32_t neg_last = op.scode[seg_at(op, segs, p.kt1 - 1)] & 1u;
+      int sidx = seg_at(op, segs, p.kt0);
+      int send = 0;  // first k-tile past segment sidx
+      for (int i = 0; i <= sidx; ++i) send += i == 0 ? op.kt0 : segs[op.seg0 + i - 1].kt;
+      uint32_t idesc = idesc0 | (((op.scode[sidx] & 1u) ^ neg_last) ? kNegateA : 0u);
       const uint32_t acc_tmem = tmem + b * GBN;
       for (int kt = p.kt0; kt < p.kt1; ++kt, ++g) {
+        int scale = 0;
+        if (kt >= send && sidx + 1 < op.nseg) {
+          const int e0 = op.scode[sidx] >> 1;
+          send += segs[op.seg0 + sidx].kt;
+          ++sidx;
+          scale = (op.scode[sidx] >> 1) - e0;
+          idesc = idesc0 | (((op.scode[sidx] & 1u) ^ neg_last) ? kNegateA : 0u);
+        }
         const uint32_t s = g % STAGES;
         if (!mbar_wait(full + s, (g / STAGES) & 1, err)) {
           ok = false;
@@ -408,10 +466,14 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
           const uint64_t ad = smem_desc(a0 + k * 32);
           const uint64_t bd = smem_desc(b0 + k * 32);
           const uint32_t accum = (kt > p.kt0 || k > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+          if (k == 0 && scale > 0) {
+            mma_scaled_any(acc_tmem, ad, bd, idesc, scale);  // kt > p.kt0 here: accumulating
+          } else {
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(empty + s))
@@ -446,7 +508,9 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
       double* const C = op.C + op.cL;
       const int64_t M = op.M, N = op.N;
       const int bn = op.bn, col_lanes = op.col_lanes;
-      const float alpha = op.alpha;
+      // weight of the item's last segment (the accumulator's unit)
+      const uint32_t code = op.scode[seg_at(op, segs, p.kt1 - 1)];
+      const float alpha = ((code & 1u) ? -op.alpha : op.alpha) * (float)(1u << (code >> 1));
       const int64_t* __restrict__ tCN = op.tCN;
       const int64_t m = (int64_t)p.mi * BM + q * 32 + lane;
       const int64_t cm = m < M ? op.tCM[m] : -1;
@@ -833,10 +897,21 @@ int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupO
     const int bn = std::min(pbn, GBN);
     const int64_t Mp = tc_pad(x.M, BM), Np = tc_pad(x.N, pbn);
     int kt_all = 0;
+    if (nseg[j] < 1 || nseg[j] > kTcMaxSeg || x.alpha == 0.0) return -1;
+    int e_prev = 0;
     for (int sgi = 0; sgi < nseg[j]; ++sgi) {
       const TcArgs& y = a[first[j] + sgi];
       if (!y.packA || !y.packB) return -1;  // both operands come packed
       if (y.M != x.M || y.N != x.N) return -1;
+      // weight relative to the first segment: a sign and 2^e, 0 <= e <= 15,
+      // e non-decreasing (the accumulator is only ever scaled down)
+      int e = 0;
+      const double ratio = std::fabs(y.alpha) / std::fabs(x.alpha);
+      if (std::frexp(ratio, &e) != 0.5) return -1;
+      e -= 1;
+      if (e < e_prev || e > kTcMaxExp) return -1;
+      e_prev = e;
+      o.scode[sgi] = (uint8_t)((e << 1) | (y.alpha < 0.0 ? 1 : 0));
       const int64_t inner = 3 * tc_pad(y.K, BK);
       CUtensorMap* pma = &o.ma;
       CUtensorMap* pmb = &o.mb;
@@ -861,7 +936,7 @@ int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupO
     o.N = x.N;
     o.nt = (int)(Np / bn);
     o.bn = bn;
-    o.alpha = (float)x.alpha;
+    o.alpha = (float)std::fabs(x.alpha);
     o.col_lanes = x.col_lanes;
     const bool start = clusters.empty() || nseg[j] > 1 || keyA(order[q - 1]) != keyA(j);
     if (start) {

@@ -6,6 +6,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <cmath>
+#include <string>
 #include <vector>
 
 struct TcArgs {
@@ -30,9 +32,15 @@ struct TcArgs {
 
 // One contraction of a grouped tensor-core launch (device descriptor; the
 // tensor maps of its packed operands live here, in global memory).  A merged
-// op sums nseg contractions with the same outputs, extents and alpha: its own
-// operand pair (kt0 k-tiles) followed by nseg - 1 pairs at segs[seg0 ...],
-// their K ranges concatenated.
+// op sums nseg <= kTcMaxSeg contractions with the same outputs and extents:
+// its own operand pair (kt0 k-tiles) followed by nseg - 1 pairs at
+// segs[seg0 ...], their K ranges concatenated.  Segment i is weighted by
+// (-1)^(scode[i] & 1) * 2^(scode[i] >> 1) * alpha (alpha > 0 when nseg > 1):
+// the MMAs of a segment with the other sign run with A negated, and at a
+// segment boundary the accumulator is scaled down by the exponent step
+// (tcgen05.mma's power-of-two input scale), so the partial sums stay exact.
+constexpr int kTcMaxSeg = 8;
+constexpr int kTcMaxExp = 15;  // largest exponent step the MMA's input scale takes
 struct alignas(64) TcGroupOp {
   CUtensorMap ma, mb;
   double* C;
@@ -42,6 +50,7 @@ struct alignas(64) TcGroupOp {
   int nt, bn, col_lanes, wbegin;  // wbegin: first n-tile slot of this op in its cluster
   int nseg, seg0, kt0;
   float alpha;
+  uint8_t scode[kTcMaxSeg];
 };
 struct alignas(64) TcSeg {
   CUtensorMap ma, mb;
@@ -54,9 +63,30 @@ struct TcCluster {
   int op0, nops, mt, kt_total, kps, ksplit, W;
 };
 
+// Merge class of a contraction's alpha: contractions of one output whose
+// alphas are +-2^e with e in the same 16-wide window can share one op (the
+// sign and the exponent step are applied inside the MMA); any other alpha
+// merges only with itself.  Appends the class to a merge key.
+inline void tc_alpha_class(double alpha, std::string& key) {
+  int e = 0;
+  const double m = std::frexp(std::fabs(alpha), &e);
+  if (m == 0.5) {
+    // alpha = 2^(e - 1); windows [16 w - 8, 16 w + 7] (w = 0 holds 2^-8 .. 2^7)
+    const int k = e - 1 + 8;
+    const int window = k >= 0 ? k / 16 : -((-k + 15) / 16);
+    key.push_back('p');
+    key.append(reinterpret_cast<const char*>(&window), sizeof(window));
+  } else {
+    key.push_back('a');
+    key.append(reinterpret_cast<const char*>(&alpha), sizeof(alpha));
+  }
+}
+
 // Descriptors, extra K segments and clusters of a grouped launch over n ops;
-// op j sums the nseg[j] consecutive contractions of a (outputs, extents and
-// alpha of its first one; both operands of each already packed).  0 on success.
+// op j sums the nseg[j] consecutive contractions of a (outputs and extents of
+// its first one; both operands of each already packed; alphas all equal, or
+// all +-2^e with e non-decreasing over the segments and within kTcMaxExp of
+// the first).  0 on success.
 int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupOp>& ops, std::vector<TcSeg>& segs,
                    std::vector<TcCluster>& clusters, int64_t* total);
 // Persistent launch over device copies of those arrays (one CTA per SM).

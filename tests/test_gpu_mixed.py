@@ -75,7 +75,13 @@ def test_grouped_tensor_core_launch_matches_per_op_launches():
         g.set_tile_rule(3e6, True, grouped)
         assert g.get_tile_rule()["tc_grouped"] == grouped
         out[grouped] = g.residual(T)
-        assert g.plan_info().tc_contractions > 0
+        info = g.plan_info()
+        assert info.tc_contractions > 0
+        if grouped:
+            # merged ops include ones whose contractions carry different
+            # alphas (sign and power-of-two step applied inside the MMA)
+            assert 0 < info.tc_grouped_ops < info.tc_contractions
+            assert info.tc_weighted_ops > 0
     scale = max(np.abs(R64[k]).max() for k in R64 if R64[k].size)
     for grouped, (Rm, Em) in out.items():
         worst = max(np.abs(R64[k] - Rm[k]).max() for k in R64 if R64[k].size)
