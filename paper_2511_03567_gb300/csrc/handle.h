@@ -184,8 +184,7 @@ void tc_lanes_meet(cudaStream_t* lanes, cudaEvent_t* ev);
 struct TcLevel {
   const TcGroupOp* ops = nullptr;
   const TcSeg* segs = nullptr;
-  const TcCluster* clusters = nullptr;
-  int nclusters = 0;
+  const TcItem* items = nullptr;  // work items of the grouped launch (total of them)
   int64_t total = 0;
   // amplitude-dependent operand buffers first consumed at this level
   const PackDesc* packs = nullptr;

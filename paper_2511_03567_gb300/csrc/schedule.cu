@@ -170,29 +170,27 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
     }
     std::vector<TcGroupOp> ops;
     std::vector<TcSeg> segs;
-    std::vector<TcCluster> cl;
-    int64_t total = 0;
-    if (tc_group_build(args.data(), nseg.data(), (int)nseg.size(), ops, segs, cl, &total) != 0)
+    std::vector<TcItem> items;
+    if (tc_group_build(args.data(), nseg.data(), (int)nseg.size(), ops, segs, items) != 0)
       return fail(eh, RICMRCC_ECUDA, "grouped tensor-core descriptors");
-    void *dops = nullptr, *dcl = nullptr, *dsg = nullptr;
+    void *dops = nullptr, *dit = nullptr, *dsg = nullptr;
     if (cudaMalloc(&dops, sizeof(TcGroupOp) * ops.size()) != cudaSuccess) return fail(eh, RICMRCC_ENOMEM, "descriptors");
     allocs.push_back(dops);
-    if (cudaMalloc(&dcl, sizeof(TcCluster) * cl.size()) != cudaSuccess) return fail(eh, RICMRCC_ENOMEM, "descriptors");
-    allocs.push_back(dcl);
+    if (cudaMalloc(&dit, sizeof(TcItem) * items.size()) != cudaSuccess) return fail(eh, RICMRCC_ENOMEM, "descriptors");
+    allocs.push_back(dit);
     if (cudaMalloc(&dsg, sizeof(TcSeg) * std::max<size_t>(segs.size(), 1)) != cudaSuccess)
       return fail(eh, RICMRCC_ENOMEM, "descriptors");
     allocs.push_back(dsg);
     if (cudaMemcpy(dops, ops.data(), sizeof(TcGroupOp) * ops.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(dcl, cl.data(), sizeof(TcCluster) * cl.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(dit, items.data(), sizeof(TcItem) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         (!segs.empty() &&
          cudaMemcpy(dsg, segs.data(), sizeof(TcSeg) * segs.size(), cudaMemcpyHostToDevice) != cudaSuccess))
       return fail(eh, RICMRCC_ECUDA, "descriptor upload");
-    out->tc[lvl].segs = static_cast<const TcSeg*>(dsg);
     TcLevel& tl = out->tc[lvl];
+    tl.segs = static_cast<const TcSeg*>(dsg);
     tl.ops = static_cast<const TcGroupOp*>(dops);
-    tl.clusters = static_cast<const TcCluster*>(dcl);
-    tl.nclusters = (int)cl.size();
-    tl.total = total;
+    tl.items = static_cast<const TcItem*>(dit);
+    tl.total = (int64_t)items.size();
   }
   return RICMRCC_OK;
 }
@@ -231,10 +229,9 @@ int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*
       j = 1;
     }
     if (rule.tc_grouped) {
-      if (tl.nclusters) {
+      if (tl.total) {
         tgt.mark(4);
-        if (tc_group_launch(tl.ops, tl.segs, tl.clusters, tl.nclusters, tl.total, eh->sms, err,
-                            tgt.lane(kTcLane0)) != 0)
+        if (tc_group_launch(tl.ops, tl.segs, tl.items, tl.total, eh->sms, err, tgt.lane(kTcLane0)) != 0)
           return fail(eh, RICMRCC_ECUDA, "grouped tensor-core launch");
         ++n;
       }

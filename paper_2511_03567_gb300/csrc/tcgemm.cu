@@ -276,51 +276,23 @@ __global__ void __launch_bounds__(128, 1)
 // freed only after every issued MMA has completed.
 constexpr int GBN = 128;  // largest N tile; B stages are sized for it (wider ops take more N tiles)
 
-// Work items of one cluster (contractions that share their packed A operand)
-// are ordered (m tile, K chunk) major and (op, n tile) minor: items reading the
+// Work items come from a table built on the host (TcItem), read one item
+// ahead by every role so that decoding an item costs no dependent loads.  The
+// items of one cluster (contractions sharing their packed A operand) are
+// ordered (m tile, K chunk) major and (op, n tile) minor: items reading the
 // same A tile are adjacent, so concurrent CTAs fetch it from HBM once and from
 // L2 after that.
-struct ItemPos {
-  int oi, mi, ni, kt0, kt1;
-};
-
-__device__ __forceinline__ ItemPos item_pos(const TcGroupOp* __restrict__ ops, const TcCluster* __restrict__ cl,
-                                            int ncl, int64_t t) {
-  int lo = 0, hi = ncl - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (cl[mid].begin <= t) lo = mid;
-    else hi = mid - 1;
+__device__ __forceinline__ TcItem load_item(const TcItem* __restrict__ items, int64_t t, int64_t total) {
+  TcItem it{};
+  if (t < total) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(items + t));
+    memcpy(&it, &v, sizeof(it));
   }
-  const TcCluster& c = cl[lo];
-  const int64_t r = t - c.begin;
-  const int w = (int)(r % c.W);
-  const int64_t u = r / c.W;
-  const int ks = (int)(u % c.ksplit);
-  ItemPos p;
-  p.mi = (int)(u / c.ksplit);
-  int j = c.op0;
-  while (j + 1 < c.op0 + c.nops && ops[j + 1].wbegin <= w) ++j;
-  p.oi = j;
-  p.ni = w - ops[j].wbegin;
-  p.kt0 = ks * c.kps;
-  p.kt1 = min(c.kt_total, p.kt0 + c.kps);
-  return p;
+  return it;
 }
 
 __device__ __forceinline__ uint32_t instr_desc_n(int bn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-}
-
-// Segment of a merged op holding k-tile kt (segment 0 = the op's own pair).
-__device__ __forceinline__ int seg_at(const TcGroupOp& op, const TcSeg* __restrict__ segs, int kt) {
-  int i = 0, off = 0, len = op.kt0;
-  while (kt >= off + len && i + 1 < op.nseg) {
-    off += len;
-    len = segs[op.seg0 + i].kt;
-    ++i;
-  }
-  return i;
 }
 
 // tcgen05.mma with the accumulator scaled by 2^-S before the product is added
@@ -357,8 +329,8 @@ constexpr uint32_t kNegateA = 1u << 13;  // instruction descriptor: negate the A
 constexpr int kEpiWarps = 8;
 
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
-    k_tc_grouped(const TcGroupOp* __restrict__ ops, const TcSeg* __restrict__ segs, const TcCluster* __restrict__ cl,
-                 int ncl, int64_t total, int* err) {
+    k_tc_grouped(const TcGroupOp* __restrict__ ops, const TcSeg* __restrict__ segs,
+                 const TcItem* __restrict__ items, int64_t total, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
@@ -398,21 +370,25 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     // TMA producer
     uint32_t g = 0;
     bool ok = true;
+    TcItem nx = load_item(items, blockIdx.x, total);
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
-      const ItemPos p = item_pos(ops, cl, ncl, t);
-      const TcGroupOp& op = ops[p.oi];
+      const TcItem it = nx;
+      nx = load_item(items, t + gridDim.x, total);
+      const TcGroupOp& op = ops[it.oi];
       // K segments: the op's own operand pair, then op.nseg - 1 more from segs
-      const CUtensorMap* ma = &op.ma;
-      const CUtensorMap* mb = &op.mb;
-      int sidx = 0, off = 0, len = op.kt0;
-      for (int kt = p.kt0; kt < p.kt1; ++kt, ++g) {
-        while (kt >= off + len && sidx + 1 < op.nseg) {
-          off += len;
+      int sidx = it.s0, send = it.send;
+      const TcSeg* sg0 = sidx ? segs + op.seg0 + sidx - 1 : nullptr;
+      const CUtensorMap* ma = sg0 ? &sg0->ma : &op.ma;
+      const CUtensorMap* mb = sg0 ? &sg0->mb : &op.mb;
+      int off = send - (sg0 ? sg0->kt : op.kt0);
+      for (int kt = it.kt0; kt < it.kt1; ++kt, ++g) {
+        if (kt >= send && sidx + 1 < op.nseg) {
           const TcSeg& sg = segs[op.seg0 + sidx];
           ++sidx;
           ma = &sg.ma;
           mb = &sg.mb;
-          len = sg.kt;
+          off = send;
+          send += sg.kt;
         }
         const uint32_t s = g % STAGES;
         if (g >= STAGES && !mbar_wait(empty + s, ((g / STAGES) - 1) & 1, err)) {
@@ -420,17 +396,19 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
           break;
         }
         mbar_expect_tx(full + s, (uint32_t)(BM + op.bn) * BK * 2);
-        tma_load_2d(sA + s * BM * BK * 2, ma, (kt - off) * BK, p.mi * BM, full + s);
-        tma_load_2d(sB + s * GBN * BK * 2, mb, (kt - off) * BK, p.ni * op.bn, full + s);
+        tma_load_2d(sA + s * BM * BK * 2, ma, (kt - off) * BK, it.mi * BM, full + s);
+        tma_load_2d(sB + s * GBN * BK * 2, mb, (kt - off) * BK, it.ni * op.bn, full + s);
       }
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     uint32_t g = 0, c = 0;
     bool ok = true;
+    TcItem nx = load_item(items, blockIdx.x, total);
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++c) {
-      const ItemPos p = item_pos(ops, cl, ncl, t);
-      const TcGroupOp& op = ops[p.oi];
+      const TcItem it = nx;
+      nx = load_item(items, t + gridDim.x, total);
+      const TcGroupOp& op = ops[it.oi];
       const uint32_t b = c & 1;
       if (c >= 2 && !mbar_wait(tempty + b, ((c >> 1) - 1) & 1, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -438,13 +416,11 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
       // weight: segments of the other sign run with A negated, and each
       // segment boundary scales the partial sum down by the exponent step
       const uint32_t idesc0 = instr_desc_n(op.bn);
-      const uint32_t neg_last = op.scode[seg_at(op, segs, p.kt1 - 1)] & 1u;
-      int sidx = seg_at(op, segs, p.kt0);
-      int send = 0;  // first k-tile past segment sidx
-      for (int i = 0; i <= sidx; ++i) send += i == 0 ? op.kt0 : segs[op.seg0 + i - 1].kt;
+      const uint32_t neg_last = op.scode[it.s1] & 1u;
+      int sidx = it.s0, send = it.send;
       uint32_t idesc = idesc0 | (((op.scode[sidx] & 1u) ^ neg_last) ? kNegateA : 0u);
       const uint32_t acc_tmem = tmem + b * GBN;
-      for (int kt = p.kt0; kt < p.kt1; ++kt, ++g) {
+      for (int kt = it.kt0; kt < it.kt1; ++kt, ++g) {
         int scale = 0;
         if (kt >= send && sidx + 1 < op.nseg) {
           const int e0 = op.scode[sidx] >> 1;
@@ -465,9 +441,9 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         for (int k = 0; k < BK / 16; ++k) {
           const uint64_t ad = smem_desc(a0 + k * 32);
           const uint64_t bd = smem_desc(b0 + k * 32);
-          const uint32_t accum = (kt > p.kt0 || k > 0) ? 1u : 0u;
+          const uint32_t accum = (kt > it.kt0 || k > 0) ? 1u : 0u;
           if (k == 0 && scale > 0) {
-            mma_scaled_any(acc_tmem, ad, bd, idesc, scale);  // kt > p.kt0 here: accumulating
+            mma_scaled_any(acc_tmem, ad, bd, idesc, scale);  // kt > it.kt0 here: accumulating
           } else {
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -495,8 +471,10 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     const int half = (warp - 2) >> 2;
     float* tile = etile + (warp - 2) * 32 * 33;
     uint32_t c = 0;
+    TcItem nx = load_item(items, blockIdx.x, total);
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++c) {
-      const ItemPos p = item_pos(ops, cl, ncl, t);
+      const TcItem p = nx;
+      nx = load_item(items, t + gridDim.x, total);
       const TcGroupOp& op = ops[p.oi];
       const uint32_t b = c & 1;
       // warp-uniform decision (tcgen05.ld below needs the whole warp)
@@ -509,7 +487,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
       const int64_t M = op.M, N = op.N;
       const int bn = op.bn, col_lanes = op.col_lanes;
       // weight of the item's last segment (the accumulator's unit)
-      const uint32_t code = op.scode[seg_at(op, segs, p.kt1 - 1)];
+      const uint32_t code = op.scode[p.s1];
       const float alpha = ((code & 1u) ? -op.alpha : op.alpha) * (float)(1u << (code >> 1));
       const int64_t* __restrict__ tCN = op.tCN;
       const int64_t m = (int64_t)p.mi * BM + q * 32 + lane;
@@ -871,7 +849,8 @@ int tc_pack(const double* X, int64_t xL, const int64_t* tR, const int64_t* tK, i
 }
 
 int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupOp>& ops, std::vector<TcSeg>& segs,
-                   std::vector<TcCluster>& clusters, int64_t* total) {
+                   std::vector<TcItem>& items) {
+  std::vector<TcCluster> clusters;
   if (!get_encode()) return -2;
   std::vector<int> first(n + 1, 0);  // op j's operand pairs: a[first[j] .. first[j + 1])
   for (int j = 0; j < n; ++j) first[j + 1] = first[j] + nseg[j];
@@ -958,8 +937,43 @@ int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupO
     const bool end = q + 1 == n || nseg[order[q + 1]] > 1 || nseg[j] > 1 || keyA(order[q + 1]) != keyA(j);
     if (end) t += (int64_t)c.mt * c.ksplit * c.W;
   }
-  *total = t;
-  return 0;
+  // the work items, cluster by cluster: (m tile, K chunk) major, slot minor
+  items.clear();
+  items.reserve((size_t)t);
+  for (const TcCluster& c : clusters) {
+    for (int64_t u = 0; u < (int64_t)c.mt * c.ksplit; ++u) {
+      const int mi = (int)(u / c.ksplit), ks = (int)(u % c.ksplit);
+      const int kt0 = ks * c.kps, kt1 = std::min(c.kt_total, kt0 + c.kps);
+      for (int q = c.op0; q < c.op0 + c.nops; ++q) {
+        const TcGroupOp& o = ops[q];
+        // segment bounds of this op's concatenated K
+        int s0 = 0, s1 = 0, send = 0, beg = 0;
+        for (int sgi = 0; sgi < o.nseg; ++sgi) {
+          const int end = beg + (sgi == 0 ? o.kt0 : segs[o.seg0 + sgi - 1].kt);
+          if (kt0 >= beg && kt0 < end) {
+            s0 = sgi;
+            send = end;
+          }
+          if (kt1 - 1 >= beg && kt1 - 1 < end) s1 = sgi;
+          beg = end;
+        }
+        if (mi > 0xffff || o.nt > 0x10000 || kt1 > 0xffff || send > 0xffff) return -1;  // 16-bit item fields
+        for (int ni = 0; ni < o.nt; ++ni) {
+          TcItem it{};
+          it.oi = q;
+          it.mi = (uint16_t)mi;
+          it.ni = (uint16_t)ni;
+          it.kt0 = (uint16_t)kt0;
+          it.kt1 = (uint16_t)kt1;
+          it.s0 = (uint8_t)s0;
+          it.s1 = (uint8_t)s1;
+          it.send = (uint16_t)send;
+          items.push_back(it);
+        }
+      }
+    }
+  }
+  return (int64_t)items.size() == t ? 0 : -1;
 }
 
 int tc_pack_group_build(const PackDesc* in, int n, std::vector<PackDesc>& out, int64_t* total) {
@@ -983,11 +997,11 @@ int tc_pack_group_launch(const PackDesc* d, int nd, int64_t total, int sms, cuda
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int tc_group_launch(const TcGroupOp* d_ops, const TcSeg* d_segs, const TcCluster* d_cl, int ncl, int64_t total,
-                    int sms, int* err, cudaStream_t s) {
-  if (ncl <= 0 || total <= 0) return 0;
+int tc_group_launch(const TcGroupOp* d_ops, const TcSeg* d_segs, const TcItem* d_items, int64_t total, int sms,
+                    int* err, cudaStream_t s) {
+  if (total <= 0) return 0;
   const int grid = (int)std::min<int64_t>(total, sms);
-  k_tc_grouped<<<grid, 64 + 32 * kEpiWarps, grouped_smem_bytes(), s>>>(d_ops, d_segs, d_cl, ncl, total, err);
+  k_tc_grouped<<<grid, 64 + 32 * kEpiWarps, grouped_smem_bytes(), s>>>(d_ops, d_segs, d_items, total, err);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

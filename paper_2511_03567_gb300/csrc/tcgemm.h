@@ -57,11 +57,22 @@ struct alignas(64) TcSeg {
   int kt;  // k-tiles of this operand pair
 };
 // Contractions sharing one packed A operand: items (m tile, K chunk, slot)
-// with slot running over the n tiles of all member ops.
+// with slot running over the n tiles of all member ops (host-side ordering).
 struct TcCluster {
   int64_t begin;  // first work item
   int op0, nops, mt, kt_total, kps, ksplit, W;
 };
+// One work item of a grouped launch, decoded on the host so that the
+// kernel's roles read it with a single 16-byte load: op, tile, K chunk and
+// the merged op's segments at both ends of the chunk.
+struct alignas(16) TcItem {
+  int32_t oi;
+  uint16_t mi, ni;    // 128-row tile, BN-column tile
+  uint16_t kt0, kt1;  // k-tiles [kt0, kt1) of the op's concatenated K
+  uint8_t s0, s1;     // segments holding kt0 and kt1 - 1
+  uint16_t send;      // first k-tile past segment s0
+};
+static_assert(sizeof(TcItem) == 16, "one 16-byte load per item");
 
 // Merge class of a contraction's alpha: contractions of one output whose
 // alphas are +-2^e with e in the same 16-wide window can share one op (the
@@ -82,16 +93,16 @@ inline void tc_alpha_class(double alpha, std::string& key) {
   }
 }
 
-// Descriptors, extra K segments and clusters of a grouped launch over n ops;
+// Descriptors, extra K segments and work items of a grouped launch over n ops;
 // op j sums the nseg[j] consecutive contractions of a (outputs and extents of
 // its first one; both operands of each already packed; alphas all equal, or
 // all +-2^e with e non-decreasing over the segments and within kTcMaxExp of
 // the first).  0 on success.
 int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupOp>& ops, std::vector<TcSeg>& segs,
-                   std::vector<TcCluster>& clusters, int64_t* total);
+                   std::vector<TcItem>& items);
 // Persistent launch over device copies of those arrays (one CTA per SM).
-int tc_group_launch(const TcGroupOp* d_ops, const TcSeg* d_segs, const TcCluster* d_cl, int ncl, int64_t total,
-                    int sms, int* err, cudaStream_t s);
+int tc_group_launch(const TcGroupOp* d_ops, const TcSeg* d_segs, const TcItem* d_items, int64_t total, int sms,
+                    int* err, cudaStream_t s);
 
 // One operand buffer of a grouped packing launch (the tc_pack layout).
 struct PackDesc {
