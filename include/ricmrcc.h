@@ -299,11 +299,16 @@ RICMRCC_API int ricmrcc_get_residual(ricmrcc_t* h, double* R1, double* R2);
  *                 128x16 / 64x32 tiles, else the 16x16 tile.
  *   tc_grouped    nonzero: the tensor-core contractions of a dependency level
  *                 run as one persistent grouped launch, else one launch each.
+ *   tc_min_n      smallest output width N sent to the tensor cores (values
+ *                 <= 1 admit every N); narrower contractions stay on the
+ *                 CUDA-core tiles, where a 128-row MMA tile would be mostly
+ *                 padding.
  * The result does not depend on the rule beyond rounding. */
 typedef struct {
   double tc_min_flops;
   int skinny;
   int tc_grouped;
+  int tc_min_n;
 } ricmrcc_tile_rule;
 
 #define RICMRCC_TUNE_MAX 8

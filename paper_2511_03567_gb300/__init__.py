@@ -59,7 +59,8 @@ class PlanInfo(ctypes.Structure):
 
 
 class TileRule(ctypes.Structure):
-    _fields_ = [("tc_min_flops", ctypes.c_double), ("skinny", ctypes.c_int), ("tc_grouped", ctypes.c_int)]
+    _fields_ = [("tc_min_flops", ctypes.c_double), ("skinny", ctypes.c_int), ("tc_grouped", ctypes.c_int),
+                ("tc_min_n", ctypes.c_int)]
 
 
 TUNE_MAX = 8
@@ -357,20 +358,22 @@ def _get_residual(self):
     return r1, r2
 
 
-def _set_tile_rule(self, tc_min_flops=1e7, skinny=True, tc_grouped=True):
-    r = TileRule(float(tc_min_flops), int(bool(skinny)), int(bool(tc_grouped)))
+def _set_tile_rule(self, tc_min_flops=1e7, skinny=True, tc_grouped=True, tc_min_n=1):
+    r = TileRule(float(tc_min_flops), int(bool(skinny)), int(bool(tc_grouped)), int(tc_min_n))
     self._check(self.lib.ricmrcc_set_tile_rule(self.h, ctypes.byref(r)))
 
 
 def _get_tile_rule(self):
     r = TileRule()
     self._check(self.lib.ricmrcc_get_tile_rule(self.h, ctypes.byref(r)))
-    return {"tc_min_flops": r.tc_min_flops, "skinny": bool(r.skinny), "tc_grouped": bool(r.tc_grouped)}
+    return {"tc_min_flops": r.tc_min_flops, "skinny": bool(r.skinny), "tc_grouped": bool(r.tc_grouped),
+            "tc_min_n": r.tc_min_n}
 
 
 def _tuning_dict(t):
     cands = [{"tc_min_flops": t.rule[i].tc_min_flops, "skinny": bool(t.rule[i].skinny),
-              "tc_grouped": bool(t.rule[i].tc_grouped), "ms": t.ms[i]} for i in range(t.n_candidates)]
+              "tc_grouped": bool(t.rule[i].tc_grouped), "tc_min_n": t.rule[i].tc_min_n, "ms": t.ms[i]}
+             for i in range(t.n_candidates)]
     return {"candidates": cands, "chosen": t.chosen}
 
 

@@ -183,7 +183,7 @@ int plan(ricmrcc_t* h) {
 // 8/8/120 size).  M and K are padded to the 128 x 64 tile, so ops with M >= 64
 // and K >= 32 waste at most half of each.
 bool tc_eligible(const ContractOp& op, const TileRule& r) {
-  return op.kind != 2 && op.L == 1 && op.M >= 64 && op.K >= 32 && op.flops >= r.tc_min_flops;
+  return op.kind != 2 && op.L == 1 && op.M >= 64 && op.K >= 32 && op.N >= r.tc_min_n && op.flops >= r.tc_min_flops;
 }
 
 // FP64 kernel of an op: the planner's choice (64x64 tile, 16x16 tile or dot
@@ -393,12 +393,19 @@ std::vector<TileRule> tune_candidates(const TileRule& cur, bool mixed) {
     return c;
   }
   // tensor-core threshold sweep (tall-skinny tiles, grouped tensor-core
-  // launches), plus one point without the skinny tiles and one with a
-  // tensor-core launch per contraction
-  const double tc[6] = {3e6, 1e7, 3e7, 1e8, 3e8, 1e9};
+  // launches), one point with the N < 16 contractions kept on the CUDA
+  // cores, one without the skinny tiles and one with a tensor-core launch per
+  // contraction
+  const double tc[5] = {1e6, 3e6, 1e7, 3e7, 1e8};
   for (double f : tc) {
     TileRule r;
     r.tc_min_flops = f;
+    c.push_back(r);
+  }
+  {
+    TileRule r;
+    r.tc_min_flops = 3e6;
+    r.tc_min_n = 16;
     c.push_back(r);
   }
   TileRule r;
@@ -411,7 +418,8 @@ std::vector<TileRule> tune_candidates(const TileRule& cur, bool mixed) {
 }
 
 int set_rule(ricmrcc_t* h, const TileRule& r) {
-  if (r.tc_min_flops == h->rule.tc_min_flops && r.skinny == h->rule.skinny && r.tc_grouped == h->rule.tc_grouped)
+  if (r.tc_min_flops == h->rule.tc_min_flops && r.skinny == h->rule.skinny && r.tc_grouped == h->rule.tc_grouped &&
+      r.tc_min_n == h->rule.tc_min_n)
     return RICMRCC_OK;
   CK(cudaStreamSynchronize(h->s));
   release_tc(h);
@@ -1373,6 +1381,7 @@ int ricmrcc_set_tile_rule(ricmrcc_t* h, const ricmrcc_tile_rule* rule) {
   r.tc_min_flops = rule->tc_min_flops;
   r.skinny = rule->skinny ? 1 : 0;
   r.tc_grouped = rule->tc_grouped ? 1 : 0;
+  r.tc_min_n = rule->tc_min_n > 1 ? rule->tc_min_n : 1;
   return set_rule(h, r);
 }
 
@@ -1381,6 +1390,7 @@ int ricmrcc_get_tile_rule(const ricmrcc_t* h, ricmrcc_tile_rule* rule) {
   rule->tc_min_flops = h->rule.tc_min_flops;
   rule->skinny = h->rule.skinny;
   rule->tc_grouped = h->rule.tc_grouped;
+  rule->tc_min_n = h->rule.tc_min_n;
   return RICMRCC_OK;
 }
 
@@ -1412,6 +1422,7 @@ int ricmrcc_tune(ricmrcc_t* h, int precision, int reps, ricmrcc_tuning* out) {
     res.rule[c].tc_min_flops = cand[c].tc_min_flops;
     res.rule[c].skinny = cand[c].skinny;
     res.rule[c].tc_grouped = cand[c].tc_grouped;
+    res.rule[c].tc_min_n = cand[c].tc_min_n;
     res.ms[c] = ms / reps;
     if (res.ms[c] < best) {
       best = res.ms[c];

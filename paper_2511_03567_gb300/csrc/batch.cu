@@ -486,6 +486,7 @@ int ricmrcc_batch_tune(ricmrcc_batch_t* b, int precision, int reps, ricmrcc_tuni
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     res.rule[c].tc_min_flops = cand[c].tc_min_flops;
+    res.rule[c].tc_min_n = cand[c].tc_min_n;
     res.rule[c].skinny = cand[c].skinny;
     res.rule[c].tc_grouped = cand[c].tc_grouped;
     res.ms[c] = ms / reps;

@@ -22,6 +22,7 @@ struct TileRule {
   double tc_min_flops = 1e7;  // mixed precision: smallest op on the tensor cores
   int skinny = 1;             // 1: tall-skinny ops (N < 32, M >= 64) use the 128x16 / 64x32 tiles
   int tc_grouped = 1;         // 1: one persistent tensor-core launch per level, 0: one per op
+  int tc_min_n = 1;           // mixed precision: narrowest output (N) on the tensor cores
 };
 
 // A packed BF16 [hi|hi|lo] (A side) or [hi|lo|hi] (B side) operand kept

@@ -56,23 +56,33 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
                : "memory");
 }
-// Bounded wait for the phase with the given parity; false on timeout.
+// Bounded wait for the phase with the given parity; false on timeout.  The
+// first try_wait is the fast path (no timer read); while waiting, the error
+// flag (set by a role that gave up) and the clock are checked every 32 tries
+// only, so that a completed phase is seen within one try_wait, not after a
+// global-memory round trip.
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
   const uint32_t a = smem_u32(b);
+  if (mbar_try(a, parity)) return true;
   const uint64_t t0 = gtime();
-  while (true) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-    if (*(volatile int*)err) return false;
-    if (gtime() - t0 > kWaitNs) {
-      atomicExch(err, 1);
-      return false;
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try(a, parity)) return true;
+    if ((i & 31) == 0) {
+      if (*(volatile int*)err) return false;
+      if (gtime() - t0 > kWaitNs) {
+        atomicExch(err, 1);
+        return false;
+      }
     }
   }
 }
@@ -270,11 +280,15 @@ __global__ void __launch_bounds__(128, 1)
 //               TMEM lane quarter, alternating 32-column chunks, so that
 //               enough atomics are in flight to cover their latency
 // The two accumulators (2 x 256 TMEM columns) let the MMAs of item c+1 run
-// while the epilogue drains item c; the 4-stage ring lets the producer run
+// while the epilogue drains item c; the 6-stage ring lets the producer run
 // ahead across item boundaries.  Every wait is bounded (kWaitNs) and sets the
 // error flag on timeout; the MMA issuer's final commit guarantees that TMEM is
 // freed only after every issued MMA has completed.
 constexpr int GBN = 128;  // largest N tile; B stages are sized for it (wider ops take more N tiles)
+// Ring depth of the grouped kernel: six 32 KB stages (plus the epilogue's
+// transpose tiles) fill the 227 KB of shared memory a CTA can have; the
+// deeper ring covers more of the TMA and MMA-completion latency per stage.
+constexpr int GSTAGES = 6;
 
 // Work items come from a table built on the host (TcItem), read one item
 // ahead by every role so that decoding an item costs no dependent loads.  The
@@ -334,18 +348,18 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;
-  uint8_t* sB = sA + STAGES * BM * BK * 2;
-  float* etile = reinterpret_cast<float*>(sB + STAGES * GBN * BK * 2);  // kEpiWarps x 32 x 33 floats
+  uint8_t* sB = sA + GSTAGES * BM * BK * 2;
+  float* etile = reinterpret_cast<float*>(sB + GSTAGES * GBN * BK * 2);  // kEpiWarps x 32 x 33 floats
   uint64_t* full = reinterpret_cast<uint64_t*>(etile + kEpiWarps * 32 * 33);
-  uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;   // [2] accumulator ready for the epilogue
+  uint64_t* empty = full + GSTAGES;
+  uint64_t* tfull = empty + GSTAGES;   // [2] accumulator ready for the epilogue
   uint64_t* tempty = tfull + 2;       // [2] accumulator drained by the epilogue
   uint64_t* fin = tempty + 2;         // every issued MMA has completed
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < GSTAGES; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
@@ -390,8 +404,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
           off = send;
           send += sg.kt;
         }
-        const uint32_t s = g % STAGES;
-        if (g >= STAGES && !mbar_wait(empty + s, ((g / STAGES) - 1) & 1, err)) {
+        const uint32_t s = g % GSTAGES;
+        if (g >= GSTAGES && !mbar_wait(empty + s, ((g / GSTAGES) - 1) & 1, err)) {
           ok = false;
           break;
         }
@@ -429,8 +443,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
           scale = (op.scode[sidx] >> 1) - e0;
           idesc = idesc0 | (((op.scode[sidx] & 1u) ^ neg_last) ? kNegateA : 0u);
         }
-        const uint32_t s = g % STAGES;
-        if (!mbar_wait(full + s, (g / STAGES) & 1, err)) {
+        const uint32_t s = g % GSTAGES;
+        if (!mbar_wait(full + s, (g / GSTAGES) & 1, err)) {
           ok = false;
           break;
         }
@@ -558,7 +572,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 }
 
 size_t grouped_smem_bytes() {
-  return 1024 + (size_t)STAGES * (BM + GBN) * BK * 2 + kEpiWarps * 32 * 33 * 4 + (2 * STAGES + 5) * 8 + 128;
+  return 1024 + (size_t)GSTAGES * (BM + GBN) * BK * 2 + kEpiWarps * 32 * 33 * 4 + (2 * GSTAGES + 5) * 8 + 128;
 }
 
 // Split two values into BF16 hi parts and BF16 lo parts (the rounding error of

@@ -94,6 +94,31 @@ def test_grouped_tensor_core_launch_matches_per_op_launches():
     assert abs(Ea - Eb) < 1e-7
 
 
+def test_tile_rule_min_n_keeps_narrow_contractions_off_tensor_cores():
+    """tc_min_n moves the narrow (N < 16) contractions from the tensor cores
+    to the CUDA-core tiles; the residual stays within the mixed tolerance."""
+    import paper_2511_03567_gb300 as ric
+    p = _prof_problem()
+    g = ric.RicMrcc(p.n_core, p.n_act, p.n_virt, p.n_aux)
+    g.set_integrals(p.h, p.B)
+    g.set_rdms(p.G1, p.G2, p.G3)
+    g.semicanonicalize()
+    T = synthetic.make_amplitudes(p.n_core, p.n_act, p.n_virt, seed=3, scale=0.02)
+    R64, E64 = g.residual(T)
+    g.set_precision(ric.MIXED)
+    n_tc = {}
+    for min_n in (1, 16):
+        g.set_tile_rule(3e6, True, True, min_n)
+        assert g.get_tile_rule()["tc_min_n"] == min_n
+        Rm, Em = g.residual(T)
+        n_tc[min_n] = g.plan_info().tc_contractions
+        scale = max(np.abs(R64[k]).max() for k in R64 if R64[k].size)
+        worst = max(np.abs(R64[k] - Rm[k]).max() for k in R64 if R64[k].size)
+        assert worst < 1e-4 * scale, (min_n, worst, scale)
+        assert abs(E64 - Em) < 1e-6
+    assert 0 < n_tc[16] < n_tc[1]
+
+
 def test_mixed_solve_refines_to_fp64_fixed_point():
     """Mixed precision as the solver runs it: tensor-core iterations until
     max|dt| < refine_tol, then FP64 iterations to the FP64 criterion.  The
