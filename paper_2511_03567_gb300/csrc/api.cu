@@ -396,7 +396,7 @@ std::vector<TileRule> tune_candidates(const TileRule& cur, bool mixed) {
   // launches), one point with the N < 16 contractions kept on the CUDA
   // cores, one without the skinny tiles and one with a tensor-core launch per
   // contraction
-  const double tc[5] = {1e6, 3e6, 1e7, 3e7, 1e8};
+  const double tc[5] = {3e5, 1e6, 3e6, 1e7, 3e7};
   for (double f : tc) {
     TileRule r;
     r.tc_min_flops = f;

@@ -94,6 +94,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_2d_u(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
 // 128 bytes, 8-row swizzle atoms 1024 bytes apart.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
@@ -340,6 +347,37 @@ __device__ __noinline__ void mma_scaled_any(uint32_t d, uint64_t ad, uint64_t bd
 
 constexpr uint32_t kNegateA = 1u << 13;  // instruction descriptor: negate the A operand
 
+// The four K = 16 MMAs of one 64-wide k-tile.  ad / bd describe the stage's
+// first 16 columns; the next ones start 32 bytes further, i.e. +2 in the
+// descriptor's address field (addresses stay below 256 KB, so no carry).
+// The first MMA accumulates if `accum`, the other three always.
+__device__ __forceinline__ void mma_ktile(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p, q;\n .reg .b64 a1, a2, a3, b1, b2, b3;\n"
+      " setp.ne.b32 p, %4, 0;\n setp.eq.u32 q, %3, %3;\n"
+      " add.s64 a1, %1, 2;\n add.s64 a2, %1, 4;\n add.s64 a3, %1, 6;\n"
+      " add.s64 b1, %2, 2;\n add.s64 b2, %2, 4;\n add.s64 b3, %2, 6;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, q;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+}
+// Same, the first MMA scaling the accumulator by 2^-scale (segment boundary).
+__device__ __noinline__ void mma_ktile_scaled(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, int scale) {
+  mma_scaled_any(d, ad, bd, idesc, scale);
+  asm volatile(
+      "{\n .reg .pred q;\n .reg .b64 a1, a2, a3, b1, b2, b3;\n"
+      " setp.eq.u32 q, %3, %3;\n"
+      " add.s64 a1, %1, 2;\n add.s64 a2, %1, 4;\n add.s64 a3, %1, 6;\n"
+      " add.s64 b1, %2, 2;\n add.s64 b2, %2, 4;\n add.s64 b3, %2, 6;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, q;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc));
+}
+static_assert(BK == 64, "mma_ktile issues four K = 16 MMAs per k-tile");
+
 constexpr int kEpiWarps = 8;
 
 __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
@@ -381,9 +419,10 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // TMA producer
-    uint32_t g = 0;
-    bool ok = true;
+    // TMA producer (stage st, phase ph of the ring; primed once it wrapped)
+    uint32_t st = 0, ph = 0;
+    bool primed = false, ok = true;
+    const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB), full0 = smem_u32(full);
     TcItem nx = load_item(items, blockIdx.x, total);
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
       const TcItem it = nx;
@@ -395,7 +434,9 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
       const CUtensorMap* ma = sg0 ? &sg0->ma : &op.ma;
       const CUtensorMap* mb = sg0 ? &sg0->mb : &op.mb;
       int off = send - (sg0 ? sg0->kt : op.kt0);
-      for (int kt = it.kt0; kt < it.kt1; ++kt, ++g) {
+      const uint32_t tx = (uint32_t)(BM + op.bn) * BK * 2;
+      const int ya = it.mi * BM, yb = it.ni * op.bn;
+      for (int kt = it.kt0; kt < it.kt1; ++kt) {
         if (kt >= send && sidx + 1 < op.nseg) {
           const TcSeg& sg = segs[op.seg0 + sidx];
           ++sidx;
@@ -404,20 +445,27 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
           off = send;
           send += sg.kt;
         }
-        const uint32_t s = g % GSTAGES;
-        if (g >= GSTAGES && !mbar_wait(empty + s, ((g / GSTAGES) - 1) & 1, err)) {
+        if (primed && !mbar_wait(empty + st, ph ^ 1u, err)) {
           ok = false;
           break;
         }
-        mbar_expect_tx(full + s, (uint32_t)(BM + op.bn) * BK * 2);
-        tma_load_2d(sA + s * BM * BK * 2, ma, (kt - off) * BK, it.mi * BM, full + s);
-        tma_load_2d(sB + s * GBN * BK * 2, mb, (kt - off) * BK, it.ni * op.bn, full + s);
+        const uint32_t fb = full0 + st * 8;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(tx) : "memory");
+        tma_load_2d_u(sA0 + st * (BM * BK * 2), ma, (kt - off) * BK, ya, fb);
+        tma_load_2d_u(sB0 + st * (GBN * BK * 2), mb, (kt - off) * BK, yb, fb);
+        if (++st == GSTAGES) {
+          st = 0;
+          ph ^= 1u;
+          primed = true;
+        }
       }
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    uint32_t g = 0, c = 0;
+    // MMA issuer (stage st, phase ph of the ring)
+    uint32_t st = 0, ph = 0, c = 0;
     bool ok = true;
+    const uint64_t adesc0 = smem_desc(smem_u32(sA)), bdesc0 = smem_desc(smem_u32(sB));
+    const uint32_t empty0 = smem_u32(empty);
     TcItem nx = load_item(items, blockIdx.x, total);
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++c) {
       const TcItem it = nx;
@@ -434,7 +482,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
       int sidx = it.s0, send = it.send;
       uint32_t idesc = idesc0 | (((op.scode[sidx] & 1u) ^ neg_last) ? kNegateA : 0u);
       const uint32_t acc_tmem = tmem + b * GBN;
-      for (int kt = it.kt0; kt < it.kt1; ++kt, ++g) {
+      for (int kt = it.kt0; kt < it.kt1; ++kt) {
         int scale = 0;
         if (kt >= send && sidx + 1 < op.nseg) {
           const int e0 = op.scode[sidx] >> 1;
@@ -443,31 +491,25 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
           scale = (op.scode[sidx] >> 1) - e0;
           idesc = idesc0 | (((op.scode[sidx] & 1u) ^ neg_last) ? kNegateA : 0u);
         }
-        const uint32_t s = g % GSTAGES;
-        if (!mbar_wait(full + s, (g / GSTAGES) & 1, err)) {
+        if (!mbar_wait(full + st, ph, err)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(sA + s * BM * BK * 2);
-        const uint32_t b0 = smem_u32(sB + s * GBN * BK * 2);
-#pragma unroll
-        for (int k = 0; k < BK / 16; ++k) {
-          const uint64_t ad = smem_desc(a0 + k * 32);
-          const uint64_t bd = smem_desc(b0 + k * 32);
-          const uint32_t accum = (kt > it.kt0 || k > 0) ? 1u : 0u;
-          if (k == 0 && scale > 0) {
-            mma_scaled_any(acc_tmem, ad, bd, idesc, scale);  // kt > it.kt0 here: accumulating
-          } else {
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc_tmem),
-                "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-          }
+        const uint64_t ad = adesc0 + st * ((BM * BK * 2) >> 4);
+        const uint64_t bd = bdesc0 + st * ((GBN * BK * 2) >> 4);
+        if (scale > 0) {
+          mma_ktile_scaled(acc_tmem, ad, bd, idesc, scale);  // kt > it.kt0 here: accumulating
+        } else {
+          mma_ktile(acc_tmem, ad, bd, idesc, kt > it.kt0 ? 1u : 0u);
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(empty + s))
+                         empty0 + st * 8)
                      : "memory");
+        if (++st == GSTAGES) {
+          st = 0;
+          ph ^= 1u;
+        }
       }
       if (!ok) break;
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
