@@ -703,12 +703,22 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_pack_grouped(const PackDesc* __restrict__ d, int nd, int64_t total) {
   __shared__ float tile[64][33];
+  // first tiles of the buffers, copied once per CTA when they fit, so that
+  // finding a tile's buffer is a search in shared memory, not a chain of
+  // dependent global loads across the descriptors
+  constexpr int kSmemDesc = 1024;
+  __shared__ int64_t sbeg[kSmemDesc];
+  const bool in_smem = nd <= kSmemDesc;
+  if (in_smem) {
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) sbeg[i] = d[i].begin;
+    __syncthreads();
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int64_t t = blockIdx.x; t < total; t += gridDim.x) {
     int lo = 0, hi = nd - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (d[mid].begin <= t) lo = mid;
+      if ((in_smem ? sbeg[mid] : d[mid].begin) <= t) lo = mid;
       else hi = mid - 1;
     }
     const PackDesc& e = d[lo];
