@@ -144,7 +144,7 @@ def roofline(kind_ms, info, mixed, pk, fp64_peak, torch):
     if c == 3:
         roof = {"bound": "hbm", "achieved": work / t / 1e9, "unit": "GB/s", "peak": pk.get("hbm_gbs", 6800.0),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), of measured",
-                "work": "bytes: FP64 source read + three BF16 segments written, per packed buffer"}
+                "work": "bytes: FP64 source read + BF16 hi and lo halves written, per packed buffer"}
     elif c == 4:
         # the tensor-core GEMMs read every packed operand once and update every
         # output in FP64: 3 x 2MNK BF16 FLOPs over these bytes is ~94 FLOP/B at

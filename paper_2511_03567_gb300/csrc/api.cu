@@ -282,7 +282,6 @@ int ensure_tc_plan(ricmrcc_t* h) {
       e.K = op.K;
       e.rows_pad = side ? tc_pad(op.N, tc_pick_bn(op.N)) : tc_pad(op.M, 128);
       e.Kp = tc_pad(op.K, 64);
-      e.pat = side ? 0b010 : 0b100;
       e.level = constant_operand(h, e.X) ? -1 : op.level;
       const int64_t* hR = side ? tBN : tAM;
       const int64_t* hK = side ? tBK : tAK;
@@ -295,14 +294,13 @@ int ensure_tc_plan(ricmrcc_t* h) {
       k = fnv(k, &e.rows, sizeof(e.rows));
       k = fnv(k, &e.K, sizeof(e.K));
       k = fnv(k, &e.rows_pad, sizeof(e.rows_pad));
-      k = fnv(k, &e.pat, sizeof(e.pat));
       k = fnv(k, hR, sizeof(int64_t) * e.rows);
       k = fnv(k, hK, sizeof(int64_t) * e.K);
       int found = -1;
       for (const Key& q : keys[k]) {
         const PackedOperand& o = h->tc_cache[q.entry];
         if (o.X == e.X && o.xL == e.xL && o.rows == e.rows && o.K == e.K && o.rows_pad == e.rows_pad &&
-            o.pat == e.pat && !memcmp(q.hR, hR, sizeof(int64_t) * e.rows) &&
+            !memcmp(q.hR, hR, sizeof(int64_t) * e.rows) &&
             !memcmp(q.hK, hK, sizeof(int64_t) * e.K)) {
           found = q.entry;
           break;
@@ -310,7 +308,7 @@ int ensure_tc_plan(ricmrcc_t* h) {
       }
       if (found < 0) {
         e.rows_fast = rows_fast(hR, e.rows, hK, e.K);
-        const size_t bytes = (size_t)e.rows_pad * 3 * e.Kp * 2;
+        const size_t bytes = (size_t)e.rows_pad * 2 * e.Kp * 2;
         cudaError_t err = cudaMalloc(&e.data, bytes);
         if (err != cudaSuccess) {
           cudaGetLastError();
@@ -334,7 +332,7 @@ int ensure_tc_plan(ricmrcc_t* h) {
 }
 
 int pack_entry(const PackedOperand& e, cudaStream_t s) {
-  return tc_pack(e.X, e.xL, e.tR, e.tK, e.rows, e.K, e.rows_pad, e.Kp, e.pat, e.rows_fast, e.data, s);
+  return tc_pack(e.X, e.xL, e.tR, e.tK, e.rows, e.K, e.rows_pad, e.Kp, e.rows_fast, e.data, s);
 }
 
 int ensure_tc(ricmrcc_t* h) {
@@ -1221,15 +1219,15 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
     }
   }
   // operand packing per evaluation: each amplitude-dependent buffer once
-  // (read FP64 source, write three BF16 segments); constant ones are packed
-  // only when the integrals or RDMs change.  Known once the tensor-core path
-  // is planned.
+  // (read FP64 source, write the BF16 hi and lo halves); constant ones are
+  // packed only when the integrals or RDMs change.  Known once the
+  // tensor-core path is planned.
   out->tc_grouped_ops = (int64_t)weighted.size();
   for (char w : weighted) out->tc_weighted_ops += w;
   for (const PackedOperand& e : h->tc_cache) {
-    out->tc_gemm_bytes += 6.0 * e.rows_pad * e.Kp;
+    out->tc_gemm_bytes += 4.0 * e.rows_pad * e.Kp;
     if (e.level < 0) continue;
-    const double bytes = 8.0 * e.rows * e.K + 6.0 * e.rows_pad * e.Kp;
+    const double bytes = 8.0 * e.rows * e.K + 4.0 * e.rows_pad * e.Kp;
     out->tc_pack_bytes += bytes;
     if (mixed) {
       out->kernel_ops[3] += 1;

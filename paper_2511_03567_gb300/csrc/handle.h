@@ -25,7 +25,7 @@ struct TileRule {
   int tc_min_n = 1;           // mixed precision: narrowest output (N) on the tensor cores
 };
 
-// A packed BF16 [hi|hi|lo] (A side) or [hi|lo|hi] (B side) operand kept
+// A packed split-BF16 operand ([hi | lo] per row, either GEMM side) kept
 // across residual evaluations.
 struct PackedOperand {
   const double* X = nullptr;  // source tensor
@@ -33,10 +33,9 @@ struct PackedOperand {
   const int64_t* tR = nullptr;  // device row / K offset tables
   const int64_t* tK = nullptr;
   int64_t rows = 0, K = 0, rows_pad = 0, Kp = 0;
-  int pat = 0;
   int level = -1;     // -1: constant (packed on refresh); else packed in the graph at this level
   int rows_fast = 0;  // gather with lanes along rows (else along K)
-  void* data = nullptr;  // rows_pad x 3 Kp BF16
+  void* data = nullptr;  // rows_pad x 2 Kp BF16: [hi | lo]
 };
 
 constexpr int kLanes = 10;  // concurrent streams of a captured residual

@@ -106,7 +106,6 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
         pd.K = e.K;
         pd.rows_pad = e.rows_pad;
         pd.Kp = e.Kp;
-        pd.pat = e.pat;
         pd.rows_fast = e.rows_fast;
         pd.out = static_cast<__nv_bfloat16*>(e.data);
         in.push_back(pd);

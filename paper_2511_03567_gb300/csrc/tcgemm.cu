@@ -3,13 +3,14 @@
 // C[l?, m, n] += alpha * sum_k A[m, k] B[n, k] for one planned contraction:
 //  1. pack: A and B are gathered through the contraction's offset tables into
 //     K-major BF16 matrices.  Each FP64 value x is split x = hi + lo (hi =
-//     bf16(x), lo = bf16(x - hi)); the K axis holds three segments, A as
-//     [hi | hi | lo] and B as [hi | lo | hi], so one GEMM of depth 3K gives
-//     hi*hi + hi*lo + lo*hi (the split-precision product; lo*lo is dropped).
-//  2. GEMM: TMA loads 128 x 64 (A) and BN x 64 (B) BF16 tiles with the 128-byte
-//     swizzle into a 4-stage shared-memory ring; one thread issues
-//     tcgen05.mma (M = 128, N = BN, K = 16) into an FP32 accumulator in TMEM;
-//     tcgen05.commit releases stages back to the TMA producer.
+//     bf16(x), lo = bf16(x - hi)); every packed row holds [hi | lo], Kp
+//     columns each, the same layout for both operands.
+//  2. GEMM: per 64-wide K block, TMA loads the hi and lo 128 x 64 tiles of A
+//     and BN x 64 tiles of B (128-byte swizzle) into one stage of a
+//     shared-memory ring; one thread issues the three products hi*hi, hi*lo
+//     and lo*hi (tcgen05.mma, M = 128, N = BN, K = 16, four per product) into
+//     an FP32 accumulator in TMEM (the split-precision product; lo*lo is
+//     dropped); tcgen05.commit releases the stage back to the TMA producer.
 //  3. epilogue: four warps read the accumulator with tcgen05.ld (one TMEM lane
 //     per output row) and add alpha * C to the FP64 destination through the
 //     output offset tables (atomic, so split-K CTAs and terms accumulate).
@@ -38,7 +39,12 @@ __device__ __forceinline__ void red_add(double* p, double v) {
 
 constexpr int BM = 128;
 constexpr int BK = 64;  // 64 BF16 = 128 bytes: one swizzle atom row
-constexpr int STAGES = 4;
+// Ring depth of the per-contraction kernel: stages of A_hi, A_lo, B_hi, B_lo
+// tiles (2 (128 + BN) x 64 BF16) within ~192 KB of shared memory.
+template <int BN>
+__host__ __device__ constexpr int tc_stages() {
+  return BN >= 256 ? 2 : (BN >= 128 ? 3 : 4);
+}
 constexpr uint64_t kWaitNs = 4000000000ull;  // 4 s bound on every wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -123,17 +129,80 @@ __device__ __forceinline__ uint32_t instr_desc() {
          | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
+// tcgen05.mma with the accumulator scaled by 2^-S before the product is added
+// (S is an immediate of the instruction, 1..15).
+template <int S>
+__device__ __forceinline__ void mma_scaled(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.eq.u32 p, %4, %4;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p, %5;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(0u), "n"(S));
+}
+__device__ __noinline__ void mma_scaled_any(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, int s) {
+  switch (s) {
+    case 1: mma_scaled<1>(d, ad, bd, idesc); break;
+    case 2: mma_scaled<2>(d, ad, bd, idesc); break;
+    case 3: mma_scaled<3>(d, ad, bd, idesc); break;
+    case 4: mma_scaled<4>(d, ad, bd, idesc); break;
+    case 5: mma_scaled<5>(d, ad, bd, idesc); break;
+    case 6: mma_scaled<6>(d, ad, bd, idesc); break;
+    case 7: mma_scaled<7>(d, ad, bd, idesc); break;
+    case 8: mma_scaled<8>(d, ad, bd, idesc); break;
+    case 9: mma_scaled<9>(d, ad, bd, idesc); break;
+    case 10: mma_scaled<10>(d, ad, bd, idesc); break;
+    case 11: mma_scaled<11>(d, ad, bd, idesc); break;
+    case 12: mma_scaled<12>(d, ad, bd, idesc); break;
+    case 13: mma_scaled<13>(d, ad, bd, idesc); break;
+    case 14: mma_scaled<14>(d, ad, bd, idesc); break;
+    default: mma_scaled<15>(d, ad, bd, idesc); break;
+  }
+}
+
+constexpr uint32_t kNegateA = 1u << 13;  // instruction descriptor: negate the A operand
+
+// The four K = 16 MMAs of one 64-wide k-tile.  ad / bd describe the stage's
+// first 16 columns; the next ones start 32 bytes further, i.e. +2 in the
+// descriptor's address field (addresses stay below 256 KB, so no carry).
+// The first MMA accumulates if `accum`, the other three always.
+__device__ __forceinline__ void mma_ktile(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p, q;\n .reg .b64 a1, a2, a3, b1, b2, b3;\n"
+      " setp.ne.b32 p, %4, 0;\n setp.eq.u32 q, %3, %3;\n"
+      " add.s64 a1, %1, 2;\n add.s64 a2, %1, 4;\n add.s64 a3, %1, 6;\n"
+      " add.s64 b1, %2, 2;\n add.s64 b2, %2, 4;\n add.s64 b3, %2, 6;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, q;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+}
+// Same, the first MMA scaling the accumulator by 2^-scale (segment boundary).
+__device__ __noinline__ void mma_ktile_scaled(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, int scale) {
+  mma_scaled_any(d, ad, bd, idesc, scale);
+  asm volatile(
+      "{\n .reg .pred q;\n .reg .b64 a1, a2, a3, b1, b2, b3;\n"
+      " setp.eq.u32 q, %3, %3;\n"
+      " add.s64 a1, %1, 2;\n add.s64 a2, %1, 4;\n add.s64 a3, %1, 6;\n"
+      " add.s64 b1, %2, 2;\n add.s64 b2, %2, 4;\n add.s64 b3, %2, 6;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, q;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, q;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc));
+}
+static_assert(BK == 64, "mma_ktile issues four K = 16 MMAs per k-tile");
+
 template <int BN>
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               int kt_per_split, int kt_total, int64_t M, int64_t N, int mtiles, int ntiles,
               double* __restrict__ C, const int64_t* __restrict__ tCM, const int64_t* __restrict__ tCN,
               int64_t cL, double alpha, int col_lanes, int* err) {
+  constexpr int STAGES = tc_stages<BN>();
+  constexpr uint32_t kA = BM * BK * 2, kB = BN * BK * 2, kStage = 2 * (kA + kB);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * BM * BK * 2;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * BN * BK * 2);
+  uint8_t* sA = smem;  // stage s: A_hi | A_lo | B_hi | B_lo at smem + s * kStage
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * kStage);
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
@@ -144,7 +213,7 @@ __global__ void __launch_bounds__(128, 1)
   t /= mtiles;
   const int ni = t % ntiles;
   const int ks = t / ntiles;
-  const int kt0 = ks * kt_per_split;
+  const int kt0 = ks * kt_per_split;  // K blocks of 64 columns
   const int kt1 = min(kt_total, kt0 + kt_per_split);
   const int nkt = kt1 - kt0;
 
@@ -168,18 +237,24 @@ __global__ void __launch_bounds__(128, 1)
 
   if (nkt > 0) {
     if (warp == 0 && lane == 0) {
-      // TMA producer
+      // TMA producer: hi and lo tiles of both operands per K block (the lo
+      // half of a packed row starts kt_total blocks in)
+      const int lo_x = kt_total * BK;
       for (int i = 0; i < nkt; ++i) {
         const int s = i % STAGES;
         if (i >= STAGES && !mbar_wait(empty + s, ((i / STAGES) - 1) & 1, err)) break;
-        mbar_expect_tx(full + s, (BM + BN) * BK * 2);
+        mbar_expect_tx(full + s, kStage);
         const int kx = (kt0 + i) * BK;
-        tma_load_2d(sA + s * BM * BK * 2, &tmA, kx, mi * BM, full + s);
-        tma_load_2d(sB + s * BN * BK * 2, &tmB, kx, ni * BN, full + s);
+        uint8_t* st = smem + s * kStage;
+        tma_load_2d(st, &tmA, kx, mi * BM, full + s);
+        tma_load_2d(st + kA, &tmA, lo_x + kx, mi * BM, full + s);
+        tma_load_2d(st + 2 * kA, &tmB, kx, ni * BN, full + s);
+        tma_load_2d(st + 2 * kA + kB, &tmB, lo_x + kx, ni * BN, full + s);
       }
     } else if (warp == 1 && lane == 0) {
-      // MMA issuer
+      // MMA issuer: hi*hi, hi*lo, lo*hi per K block
       const uint32_t idesc = instr_desc<BN>();
+      const uint64_t d0 = smem_desc(smem_u32(smem));
       bool ok = true;
       for (int i = 0; i < nkt; ++i) {
         const int s = i % STAGES;
@@ -188,18 +263,11 @@ __global__ void __launch_bounds__(128, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(sA + s * BM * BK * 2);
-        const uint32_t b0 = smem_u32(sB + s * BN * BK * 2);
-#pragma unroll
-        for (int k = 0; k < BK / 16; ++k) {
-          const uint64_t ad = smem_desc(a0 + k * 32);
-          const uint64_t bd = smem_desc(b0 + k * 32);
-          const uint32_t acc = (i > 0 || k > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-        }
+        const uint64_t ahi = d0 + ((s * kStage) >> 4), alo = ahi + (kA >> 4);
+        const uint64_t bhi = ahi + ((2 * kA) >> 4), blo = bhi + (kB >> 4);
+        mma_ktile(tmem, ahi, bhi, idesc, i > 0 ? 1u : 0u);
+        mma_ktile(tmem, ahi, blo, idesc, 1u);
+        mma_ktile(tmem, alo, bhi, idesc, 1u);
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(empty + s))
                      : "memory");
@@ -287,15 +355,16 @@ __global__ void __launch_bounds__(128, 1)
 //               TMEM lane quarter, alternating 32-column chunks, so that
 //               enough atomics are in flight to cover their latency
 // The two accumulators (2 x 256 TMEM columns) let the MMAs of item c+1 run
-// while the epilogue drains item c; the 6-stage ring lets the producer run
+// while the epilogue drains item c; the 3-stage ring lets the producer run
 // ahead across item boundaries.  Every wait is bounded (kWaitNs) and sets the
 // error flag on timeout; the MMA issuer's final commit guarantees that TMEM is
 // freed only after every issued MMA has completed.
 constexpr int GBN = 128;  // largest N tile; B stages are sized for it (wider ops take more N tiles)
-// Ring depth of the grouped kernel: six 32 KB stages (plus the epilogue's
-// transpose tiles) fill the 227 KB of shared memory a CTA can have; the
-// deeper ring covers more of the TMA and MMA-completion latency per stage.
-constexpr int GSTAGES = 6;
+// Ring of the grouped kernel: three 64 KB stages (A_hi | A_lo | B_hi | B_lo
+// of one 64-wide K block, B sized for GBN rows) plus the epilogue's transpose
+// tiles fill the 227 KB of shared memory a CTA can have.
+constexpr int GSTAGES = 3;
+constexpr uint32_t kGA = BM * BK * 2, kGB = GBN * BK * 2, kGStage = 2 * (kGA + kGB);
 
 // Work items come from a table built on the host (TcItem), read one item
 // ahead by every role so that decoding an item costs no dependent loads.  The
@@ -316,67 +385,6 @@ __device__ __forceinline__ uint32_t instr_desc_n(int bn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-// tcgen05.mma with the accumulator scaled by 2^-S before the product is added
-// (S is an immediate of the instruction, 1..15).
-template <int S>
-__device__ __forceinline__ void mma_scaled(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.eq.u32 p, %4, %4;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p, %5;\n}\n" ::"r"(d),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(0u), "n"(S));
-}
-__device__ __noinline__ void mma_scaled_any(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, int s) {
-  switch (s) {
-    case 1: mma_scaled<1>(d, ad, bd, idesc); break;
-    case 2: mma_scaled<2>(d, ad, bd, idesc); break;
-    case 3: mma_scaled<3>(d, ad, bd, idesc); break;
-    case 4: mma_scaled<4>(d, ad, bd, idesc); break;
-    case 5: mma_scaled<5>(d, ad, bd, idesc); break;
-    case 6: mma_scaled<6>(d, ad, bd, idesc); break;
-    case 7: mma_scaled<7>(d, ad, bd, idesc); break;
-    case 8: mma_scaled<8>(d, ad, bd, idesc); break;
-    case 9: mma_scaled<9>(d, ad, bd, idesc); break;
-    case 10: mma_scaled<10>(d, ad, bd, idesc); break;
-    case 11: mma_scaled<11>(d, ad, bd, idesc); break;
-    case 12: mma_scaled<12>(d, ad, bd, idesc); break;
-    case 13: mma_scaled<13>(d, ad, bd, idesc); break;
-    case 14: mma_scaled<14>(d, ad, bd, idesc); break;
-    default: mma_scaled<15>(d, ad, bd, idesc); break;
-  }
-}
-
-constexpr uint32_t kNegateA = 1u << 13;  // instruction descriptor: negate the A operand
-
-// The four K = 16 MMAs of one 64-wide k-tile.  ad / bd describe the stage's
-// first 16 columns; the next ones start 32 bytes further, i.e. +2 in the
-// descriptor's address field (addresses stay below 256 KB, so no carry).
-// The first MMA accumulates if `accum`, the other three always.
-__device__ __forceinline__ void mma_ktile(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p, q;\n .reg .b64 a1, a2, a3, b1, b2, b3;\n"
-      " setp.ne.b32 p, %4, 0;\n setp.eq.u32 q, %3, %3;\n"
-      " add.s64 a1, %1, 2;\n add.s64 a2, %1, 4;\n add.s64 a3, %1, 6;\n"
-      " add.s64 b1, %2, 2;\n add.s64 b2, %2, 4;\n add.s64 b3, %2, 6;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, q;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, q;\n}\n" ::"r"(d),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-}
-// Same, the first MMA scaling the accumulator by 2^-scale (segment boundary).
-__device__ __noinline__ void mma_ktile_scaled(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, int scale) {
-  mma_scaled_any(d, ad, bd, idesc, scale);
-  asm volatile(
-      "{\n .reg .pred q;\n .reg .b64 a1, a2, a3, b1, b2, b3;\n"
-      " setp.eq.u32 q, %3, %3;\n"
-      " add.s64 a1, %1, 2;\n add.s64 a2, %1, 4;\n add.s64 a3, %1, 6;\n"
-      " add.s64 b1, %2, 2;\n add.s64 b2, %2, 4;\n add.s64 b3, %2, 6;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, q;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, q;\n}\n" ::"r"(d),
-      "l"(ad), "l"(bd), "r"(idesc));
-}
-static_assert(BK == 64, "mma_ktile issues four K = 16 MMAs per k-tile");
 
 constexpr int kEpiWarps = 8;
 
@@ -385,9 +393,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
                  const TcItem* __restrict__ items, int64_t total, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = smem;
-  uint8_t* sB = sA + GSTAGES * BM * BK * 2;
-  float* etile = reinterpret_cast<float*>(sB + GSTAGES * GBN * BK * 2);  // kEpiWarps x 32 x 33 floats
+  uint8_t* sA = smem;  // stage s at smem + s * kGStage
+  float* etile = reinterpret_cast<float*>(smem + GSTAGES * kGStage);  // kEpiWarps x 32 x 33 floats
   uint64_t* full = reinterpret_cast<uint64_t*>(etile + kEpiWarps * 32 * 33);
   uint64_t* empty = full + GSTAGES;
   uint64_t* tfull = empty + GSTAGES;   // [2] accumulator ready for the epilogue
@@ -419,10 +426,12 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // TMA producer (stage st, phase ph of the ring; primed once it wrapped)
+    // TMA producer (stage st, phase ph of the ring; primed once it wrapped):
+    // hi and lo tiles of both operands per K block; the lo half of a packed
+    // row starts one segment width (its K blocks x 64) in
     uint32_t st = 0, ph = 0;
     bool primed = false, ok = true;
-    const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB), full0 = smem_u32(full);
+    const uint32_t s0 = smem_u32(sA), full0 = smem_u32(full);
     TcItem nx = load_item(items, blockIdx.x, total);
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
       const TcItem it = nx;
@@ -433,8 +442,9 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
       const TcSeg* sg0 = sidx ? segs + op.seg0 + sidx - 1 : nullptr;
       const CUtensorMap* ma = sg0 ? &sg0->ma : &op.ma;
       const CUtensorMap* mb = sg0 ? &sg0->mb : &op.mb;
-      int off = send - (sg0 ? sg0->kt : op.kt0);
-      const uint32_t tx = (uint32_t)(BM + op.bn) * BK * 2;
+      int len = sg0 ? sg0->kt : op.kt0;
+      int off = send - len;
+      const uint32_t bytes = 2u * (uint32_t)(BM + op.bn) * BK * 2;
       const int ya = it.mi * BM, yb = it.ni * op.bn;
       for (int kt = it.kt0; kt < it.kt1; ++kt) {
         if (kt >= send && sidx + 1 < op.nseg) {
@@ -443,6 +453,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
           ma = &sg.ma;
           mb = &sg.mb;
           off = send;
+          len = sg.kt;
           send += sg.kt;
         }
         if (primed && !mbar_wait(empty + st, ph ^ 1u, err)) {
@@ -450,9 +461,13 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
           break;
         }
         const uint32_t fb = full0 + st * 8;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(tx) : "memory");
-        tma_load_2d_u(sA0 + st * (BM * BK * 2), ma, (kt - off) * BK, ya, fb);
-        tma_load_2d_u(sB0 + st * (GBN * BK * 2), mb, (kt - off) * BK, yb, fb);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes) : "memory");
+        const uint32_t sb = s0 + st * kGStage;
+        const int x = (kt - off) * BK, xl = x + len * BK;
+        tma_load_2d_u(sb, ma, x, ya, fb);
+        tma_load_2d_u(sb + kGA, ma, xl, ya, fb);
+        tma_load_2d_u(sb + 2 * kGA, mb, x, yb, fb);
+        tma_load_2d_u(sb + 2 * kGA + kGB, mb, xl, yb, fb);
         if (++st == GSTAGES) {
           st = 0;
           ph ^= 1u;
@@ -464,7 +479,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     // MMA issuer (stage st, phase ph of the ring)
     uint32_t st = 0, ph = 0, c = 0;
     bool ok = true;
-    const uint64_t adesc0 = smem_desc(smem_u32(sA)), bdesc0 = smem_desc(smem_u32(sB));
+    const uint64_t desc0 = smem_desc(smem_u32(sA));
     const uint32_t empty0 = smem_u32(empty);
     TcItem nx = load_item(items, blockIdx.x, total);
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++c) {
@@ -496,13 +511,16 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t ad = adesc0 + st * ((BM * BK * 2) >> 4);
-        const uint64_t bd = bdesc0 + st * ((GBN * BK * 2) >> 4);
+        // hi*hi (scaling the accumulator at a segment boundary), hi*lo, lo*hi
+        const uint64_t ahi = desc0 + st * (kGStage >> 4), alo = ahi + (kGA >> 4);
+        const uint64_t bhi = ahi + ((2 * kGA) >> 4), blo = bhi + (kGB >> 4);
         if (scale > 0) {
-          mma_ktile_scaled(acc_tmem, ad, bd, idesc, scale);  // kt > it.kt0 here: accumulating
+          mma_ktile_scaled(acc_tmem, ahi, bhi, idesc, scale);  // kt > it.kt0 here: accumulating
         } else {
-          mma_ktile(acc_tmem, ad, bd, idesc, kt > it.kt0 ? 1u : 0u);
+          mma_ktile(acc_tmem, ahi, bhi, idesc, kt > it.kt0 ? 1u : 0u);
         }
+        mma_ktile(acc_tmem, ahi, blo, idesc, 1u);
+        mma_ktile(acc_tmem, alo, bhi, idesc, 1u);
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          empty0 + st * 8)
                      : "memory");
@@ -614,7 +632,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 }
 
 size_t grouped_smem_bytes() {
-  return 1024 + (size_t)GSTAGES * (BM + GBN) * BK * 2 + kEpiWarps * 32 * 33 * 4 + (2 * GSTAGES + 5) * 8 + 128;
+  return 1024 + (size_t)GSTAGES * kGStage + kEpiWarps * 32 * 33 * 4 + (2 * GSTAGES + 5) * 8 + 128;
 }
 
 // Split two values into BF16 hi parts and BF16 lo parts (the rounding error of
@@ -630,14 +648,14 @@ __device__ __forceinline__ void split_bf16(float x0, float x1, __nv_bfloat162* h
 }
 
 // Gather one operand through offset tables and split it into BF16 hi/lo:
-// out[r][seg * Kp + k], r < rows_pad, three segments with pattern `pat`
-// (bit s set: segment s holds lo, else hi).  Pad rows/columns are zero.
+// out[r][k] = hi, out[r][Kp + k] = lo, r < rows_pad.  Pad rows/columns are
+// zero.
 // Work items are (row, 64-wide K chunk) pairs, one per warp and step, two K
 // elements per lane (Kp is a multiple of 64), so short-and-wide operands
 // spread over the whole GPU as well as tall ones.
 __global__ void __launch_bounds__(256)
     k_pack_split(const double* __restrict__ X, int64_t xL, const int64_t* __restrict__ tR,
-                 const int64_t* __restrict__ tK, int64_t rows, int64_t K, int64_t rows_pad, int64_t Kp, int pat,
+                 const int64_t* __restrict__ tK, int64_t rows, int64_t K, int64_t rows_pad, int64_t Kp,
                  __nv_bfloat16* __restrict__ out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nkc = Kp >> 6, items = rows_pad * nkc, seg = Kp >> 1;
@@ -649,11 +667,10 @@ __global__ void __launch_bounds__(256)
     const float x1 = (live && k + 1 < K) ? (float)X[base + tK[k + 1]] : 0.f;
     __nv_bfloat162 hi, lo;
     split_bf16(x0, x1, &hi, &lo);
-    __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(out + r * 3 * Kp);
+    __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(out + r * 2 * Kp);
     const int64_t c = k >> 1;
-    row[c] = (pat & 1) ? lo : hi;
-    row[seg + c] = (pat & 2) ? lo : hi;
-    row[2 * seg + c] = (pat & 4) ? lo : hi;
+    row[c] = hi;
+    row[seg + c] = lo;
   }
 }
 
@@ -664,7 +681,7 @@ __global__ void __launch_bounds__(256)
 __global__ void __launch_bounds__(256)
     k_pack_split_rows(const double* __restrict__ X, int64_t xL, const int64_t* __restrict__ tR,
                       const int64_t* __restrict__ tK, int64_t rows, int64_t K, int64_t rows_pad, int64_t Kp,
-                      int pat, __nv_bfloat16* __restrict__ out) {
+                      __nv_bfloat16* __restrict__ out) {
   __shared__ float tile[64][33];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nkt = Kp / 64, ntiles = (rows_pad / 32) * nkt;
@@ -686,11 +703,10 @@ __global__ void __launch_bounds__(256)
       const int rr = warp + 8 * j;
       __nv_bfloat162 hi, lo;
       split_bf16(tile[2 * lane][rr], tile[2 * lane + 1][rr], &hi, &lo);
-      __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(out + (r0 + rr) * 3 * Kp);
+      __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(out + (r0 + rr) * 2 * Kp);
       const int64_t c = (k0 >> 1) + lane;
-      row[c] = (pat & 1) ? lo : hi;
-      row[seg + c] = (pat & 2) ? lo : hi;
-      row[2 * seg + c] = (pat & 4) ? lo : hi;
+      row[c] = hi;
+      row[seg + c] = lo;
     }
     __syncthreads();
   }
@@ -740,11 +756,10 @@ __global__ void __launch_bounds__(256)
         const int rr = warp + 8 * j;
         __nv_bfloat162 h2, l2;
         split_bf16(tile[2 * lane][rr], tile[2 * lane + 1][rr], &h2, &l2);
-        __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(e.out + (r0 + rr) * 3 * e.Kp);
+        __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(e.out + (r0 + rr) * 2 * e.Kp);
         const int64_t c = (k0 >> 1) + lane;
-        row[c] = (e.pat & 1) ? l2 : h2;
-        row[seg + c] = (e.pat & 2) ? l2 : h2;
-        row[2 * seg + c] = (e.pat & 4) ? l2 : h2;
+        row[c] = h2;
+        row[seg + c] = l2;
       }
       __syncthreads();
     } else {
@@ -758,27 +773,26 @@ __global__ void __launch_bounds__(256)
         const float x1 = (live && k + 1 < e.K) ? (float)e.X[base + e.tK[k + 1]] : 0.f;
         __nv_bfloat162 h2, l2;
         split_bf16(x0, x1, &h2, &l2);
-        __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(e.out + r * 3 * e.Kp);
+        __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(e.out + r * 2 * e.Kp);
         const int64_t c = k >> 1;
-        row[c] = (e.pat & 1) ? l2 : h2;
-        row[seg + c] = (e.pat & 2) ? l2 : h2;
-        row[2 * seg + c] = (e.pat & 4) ? l2 : h2;
+        row[c] = h2;
+        row[seg + c] = l2;
       }
     }
   }
 }
 
 void pack_launch(const double* X, int64_t xL, const int64_t* tR, const int64_t* tK, int64_t rows, int64_t K,
-                 int64_t rows_pad, int64_t Kp, int pat, int rows_fast, __nv_bfloat16* out, cudaStream_t s) {
+                 int64_t rows_pad, int64_t Kp, int rows_fast, __nv_bfloat16* out, cudaStream_t s) {
   if (rows_fast && rows_pad % 32 == 0) {
     const int64_t tiles = (rows_pad / 32) * (Kp / 64);
     const int64_t blocks = std::min<int64_t>(tiles, 152 * 8);
-    k_pack_split_rows<<<(int)blocks, 256, 0, s>>>(X, xL, tR, tK, rows, K, rows_pad, Kp, pat, out);
+    k_pack_split_rows<<<(int)blocks, 256, 0, s>>>(X, xL, tR, tK, rows, K, rows_pad, Kp, out);
     return;
   }
   const int64_t items = rows_pad * (Kp / 64);
   const int64_t blocks = std::min<int64_t>((items + 7) / 8, 152 * 16);
-  k_pack_split<<<(int)blocks, 256, 0, s>>>(X, xL, tR, tK, rows, K, rows_pad, Kp, pat, out);
+  k_pack_split<<<(int)blocks, 256, 0, s>>>(X, xL, tR, tK, rows, K, rows_pad, Kp, out);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -808,7 +822,7 @@ bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, i
 
 template <int BN>
 size_t smem_bytes() {
-  return 1024 + (size_t)STAGES * (BM + BN) * BK * 2 + (2 * STAGES + 1) * 8 + 16;
+  return 1024 + (size_t)tc_stages<BN>() * 2 * (BM + BN) * BK * 2 + (2 * tc_stages<BN>() + 1) * 8 + 16;
 }
 
 template <int BN>
@@ -817,9 +831,9 @@ int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int64_t M, int64_t N
               int col_lanes, int* err, cudaStream_t s) {
   const int mt = (int)(Mp / BM), nt = (int)(Np / BN);
   const int tiles = mt * nt;
-  // split K only while every split keeps kMinKt k-tiles: each split adds a
+  // split K only while every split keeps kMinKt K blocks: each split adds a
   // full tile of atomic output updates, which costs more than its MMAs
-  constexpr int kMinKt = 12;
+  constexpr int kMinKt = 4;
   int ksplit = 1;
   if (tiles < 2 * 152) ksplit = (2 * 152 + tiles - 1) / tiles;
   ksplit = std::min(ksplit, std::max(1, kt_total / kMinKt));
@@ -877,7 +891,7 @@ int tc_contract_timed(const TcArgs& a, cudaStream_t s, cudaEvent_t* mid) {
   }
   const int bn = tc_pick_bn(a.N);
   const int64_t Mp = tc_pad(a.M, BM), Np = tc_pad(a.N, bn), Kp = tc_pad(a.K, BK);
-  const int64_t inner = 3 * Kp;
+  const int64_t inner = 2 * Kp;  // [hi | lo]
   // scratch for the sides packed here (none when both come packed)
   if ((size_t)((a.packA ? 0 : Mp) + (a.packB ? 0 : Np)) * inner * 2 > a.scratch_bytes) return -3;
   // operands packed by the caller are used as given; the others are packed
@@ -887,18 +901,18 @@ int tc_contract_timed(const TcArgs& a, cudaStream_t s, cudaEvent_t* mid) {
   if (a.packA) {
     pa = reinterpret_cast<__nv_bfloat16*>(const_cast<void*>(a.packA));
   } else {
-    pack_launch(a.A, a.aL, a.tAM, a.tAK, a.M, a.K, Mp, Kp, 0b100, 0, pa, s);
+    pack_launch(a.A, a.aL, a.tAM, a.tAK, a.M, a.K, Mp, Kp, 0, pa, s);
     free_at += Mp * inner;
   }
   __nv_bfloat16* pb = free_at;
   if (a.packB)
     pb = reinterpret_cast<__nv_bfloat16*>(const_cast<void*>(a.packB));
   else
-    pack_launch(a.B, a.bL, a.tBN, a.tBK, a.N, a.K, Np, Kp, 0b010, 0, pb, s);
+    pack_launch(a.B, a.bL, a.tBN, a.tBK, a.N, a.K, Np, Kp, 0, pb, s);
   if (mid) cudaEventRecord(*mid, s);
   CUtensorMap ma, mb;
   if (!make_map(&ma, pa, inner, Mp, BM) || !make_map(&mb, pb, inner, Np, bn)) return -4;
-  const int kt_total = (int)(inner / BK);
+  const int kt_total = (int)(Kp / BK);  // K blocks
   switch (bn) {
     case 32: return launch_tc<32>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.col_lanes, a.err, s);
     case 64: return launch_tc<64>(ma, mb, a.M, a.N, Mp, Np, kt_total, a.C, a.tCM, a.tCN, a.cL, a.alpha, a.col_lanes, a.err, s);
@@ -908,9 +922,9 @@ int tc_contract_timed(const TcArgs& a, cudaStream_t s, cudaEvent_t* mid) {
 }
 
 int tc_pack(const double* X, int64_t xL, const int64_t* tR, const int64_t* tK, int64_t rows, int64_t K,
-            int64_t rows_pad, int64_t Kp, int pat, int rows_fast, void* out, cudaStream_t s) {
+            int64_t rows_pad, int64_t Kp, int rows_fast, void* out, cudaStream_t s) {
   if (!X || !tR || !tK || !out || rows < 0 || rows > rows_pad || K < 0 || K > Kp || Kp % BK) return -1;
-  pack_launch(X, xL, tR, tK, rows, K, rows_pad, Kp, pat, rows_fast, static_cast<__nv_bfloat16*>(out), s);
+  pack_launch(X, xL, tR, tK, rows, K, rows_pad, Kp, rows_fast, static_cast<__nv_bfloat16*>(out), s);
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -929,10 +943,10 @@ int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupO
   ops.assign(n, TcGroupOp{});
   segs.clear();
   clusters.clear();
-  // K chunks of at most kMaxKt k-tiles: long enough that the atomic output
-  // update of a chunk is small next to its MMAs, short enough that the items
-  // of a launch have similar length
-  constexpr int kMaxKt = 128;
+  // K chunks of at most kMaxKt K blocks (three 64-deep products each): long
+  // enough that the atomic output update of a chunk is small next to its
+  // MMAs, short enough that the items of a launch have similar length
+  constexpr int kMaxKt = 43;
   int64_t t = 0;
   for (int q = 0; q < n; ++q) {
     const int j = order[q];
@@ -957,20 +971,20 @@ int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupO
       if (e < e_prev || e > kTcMaxExp) return -1;
       e_prev = e;
       o.scode[sgi] = (uint8_t)((e << 1) | (y.alpha < 0.0 ? 1 : 0));
-      const int64_t inner = 3 * tc_pad(y.K, BK);
+      const int64_t inner = 2 * tc_pad(y.K, BK);  // [hi | lo]
       CUtensorMap* pma = &o.ma;
       CUtensorMap* pmb = &o.mb;
       if (sgi > 0) {
         segs.push_back(TcSeg{});
         pma = &segs.back().ma;
         pmb = &segs.back().mb;
-        segs.back().kt = (int)(inner / BK);
+        segs.back().kt = (int)(inner / 2 / BK);
       } else {
-        o.kt0 = (int)(inner / BK);
+        o.kt0 = (int)(inner / 2 / BK);
         o.seg0 = (int)segs.size();
       }
       if (!make_map(pma, y.packA, inner, Mp, BM) || !make_map(pmb, y.packB, inner, Np, bn)) return -4;
-      kt_all += (int)(inner / BK);
+      kt_all += (int)(inner / 2 / BK);
     }
     o.nseg = nseg[j];
     o.C = x.C;
@@ -1073,13 +1087,13 @@ int tc_group_launch(const TcGroupOp* d_ops, const TcSeg* d_segs, const TcItem* d
 
 size_t tc_scratch_bytes(int64_t M, int64_t N, int64_t K) {
   const int bn = tc_pick_bn(N);
-  return (size_t)(tc_pad(M, BM) + tc_pad(N, bn)) * 3 * tc_pad(K, BK) * 2;
+  return (size_t)(tc_pad(M, BM) + tc_pad(N, bn)) * 2 * tc_pad(K, BK) * 2;
 }
 
 double tc_pack_bytes(int64_t M, int64_t N, int64_t K) {
   // algorithmic bytes of the packing step: read both FP64 operands once,
-  // write the padded three-segment BF16 copies
+  // write the padded [hi | lo] BF16 copies
   const int bn = tc_pick_bn(N);
   return 8.0 * (double)(M + N) * (double)K +
-         2.0 * 3.0 * (double)(tc_pad(M, BM) + tc_pad(N, bn)) * (double)tc_pad(K, BK);
+         2.0 * 2.0 * (double)(tc_pad(M, BM) + tc_pad(N, bn)) * (double)tc_pad(K, BK);
 }

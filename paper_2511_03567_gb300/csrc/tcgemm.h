@@ -111,7 +111,7 @@ struct PackDesc {
   const int64_t* tR;
   const int64_t* tK;
   int64_t rows, K, rows_pad, Kp;
-  int pat, rows_fast;
+  int rows_fast;
   __nv_bfloat16* out;
   int64_t begin;  // first work item (filled by tc_pack_group_build)
 };
@@ -125,12 +125,12 @@ bool tc_available();
 int tc_pick_bn(int64_t N);  // N tile of the GEMM for an N extent
 int64_t tc_pad(int64_t x, int64_t m);
 // Gather X[xL + tR[r] + tK[k]] (r < rows, k < K) into the packed split-BF16
-// layout of one operand: rows_pad rows of three Kp segments, segment s the lo
-// part where bit s of `pat` is set, else the hi part (A side 0b100, B side
-// 0b010).  rows_fast != 0 reads with lanes along rows (for operands whose
-// rows are contiguous in X), else along K.  0 on success.
+// layout of one operand (either side of a GEMM): rows_pad rows of [hi | lo],
+// Kp BF16 columns each (zero padded).  rows_fast != 0 reads with lanes along
+// rows (for operands whose rows are contiguous in X), else along K.  0 on
+// success.
 int tc_pack(const double* X, int64_t xL, const int64_t* tR, const int64_t* tK, int64_t rows, int64_t K,
-            int64_t rows_pad, int64_t Kp, int pat, int rows_fast, void* out, cudaStream_t s);
+            int64_t rows_pad, int64_t Kp, int rows_fast, void* out, cudaStream_t s);
 // Set the GEMM kernels' shared-memory attribute; call outside graph capture.
 bool tc_prepare();
 size_t tc_scratch_bytes(int64_t M, int64_t N, int64_t K);
