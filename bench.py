@@ -170,7 +170,7 @@ def roofline(kind_ms, info, mixed, pk, fp64_peak, torch):
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
     roof["traffic"] = None
     roof["traffic_note"] = ("not captured at this size; on the 4/CAS(4,4)/64/200 case the tensor-core "
-                            "launches moved 0.92x their algorithmic bytes (profiles/tc_grouped_prof_full.md)")
+                            "launches moved 0.86x their algorithmic bytes (profiles/tc_grouped_prof_full.md)")
     roof["contractions_per_residual"] = int(info.kernel_ops[c])
     roof["ms_per_residual"] = float(kind_ms[c])
     roof["profile_ms_per_residual"] = {n: float(x) for n, x in zip(KERNEL_NAMES, kind_ms)}
