@@ -956,21 +956,15 @@ int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupO
     const int bn = std::min(pbn, GBN);
     const int64_t Mp = tc_pad(x.M, BM), Np = tc_pad(x.N, pbn);
     int kt_all = 0;
-    if (nseg[j] < 1 || nseg[j] > kTcMaxSeg || x.alpha == 0.0) return -1;
-    int e_prev = 0;
+    if (nseg[j] < 1 || nseg[j] > kTcMaxSeg) return -1;
+    // weights relative to the first segment: a sign and 2^e, 0 <= e <= 15
+    double alphas[kTcMaxSeg];
+    for (int sgi = 0; sgi < nseg[j]; ++sgi) alphas[sgi] = a[first[j] + sgi].alpha;
+    if (!tc_segment_weights(alphas, nseg[j], o.scode, &o.alpha)) return -1;
     for (int sgi = 0; sgi < nseg[j]; ++sgi) {
       const TcArgs& y = a[first[j] + sgi];
       if (!y.packA || !y.packB) return -1;  // both operands come packed
       if (y.M != x.M || y.N != x.N) return -1;
-      // weight relative to the first segment: a sign and 2^e, 0 <= e <= 15,
-      // e non-decreasing (the accumulator is only ever scaled down)
-      int e = 0;
-      const double ratio = std::fabs(y.alpha) / std::fabs(x.alpha);
-      if (std::frexp(ratio, &e) != 0.5) return -1;
-      e -= 1;
-      if (e < e_prev || e > kTcMaxExp) return -1;
-      e_prev = e;
-      o.scode[sgi] = (uint8_t)((e << 1) | (y.alpha < 0.0 ? 1 : 0));
       const int64_t inner = 2 * tc_pad(y.K, BK);  // [hi | lo]
       CUtensorMap* pma = &o.ma;
       CUtensorMap* pmb = &o.mb;
@@ -995,7 +989,6 @@ int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupO
     o.N = x.N;
     o.nt = (int)(Np / bn);
     o.bn = bn;
-    o.alpha = (float)std::fabs(x.alpha);
     o.col_lanes = x.col_lanes;
     const bool start = clusters.empty() || nseg[j] > 1 || keyA(order[q - 1]) != keyA(j);
     if (start) {
@@ -1018,41 +1011,8 @@ int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupO
     if (end) t += (int64_t)c.mt * c.ksplit * c.W;
   }
   // the work items, cluster by cluster: (m tile, K chunk) major, slot minor
-  items.clear();
   items.reserve((size_t)t);
-  for (const TcCluster& c : clusters) {
-    for (int64_t u = 0; u < (int64_t)c.mt * c.ksplit; ++u) {
-      const int mi = (int)(u / c.ksplit), ks = (int)(u % c.ksplit);
-      const int kt0 = ks * c.kps, kt1 = std::min(c.kt_total, kt0 + c.kps);
-      for (int q = c.op0; q < c.op0 + c.nops; ++q) {
-        const TcGroupOp& o = ops[q];
-        // segment bounds of this op's concatenated K
-        int s0 = 0, s1 = 0, send = 0, beg = 0;
-        for (int sgi = 0; sgi < o.nseg; ++sgi) {
-          const int end = beg + (sgi == 0 ? o.kt0 : segs[o.seg0 + sgi - 1].kt);
-          if (kt0 >= beg && kt0 < end) {
-            s0 = sgi;
-            send = end;
-          }
-          if (kt1 - 1 >= beg && kt1 - 1 < end) s1 = sgi;
-          beg = end;
-        }
-        if (mi > 0xffff || o.nt > 0x10000 || kt1 > 0xffff || send > 0xffff) return -1;  // 16-bit item fields
-        for (int ni = 0; ni < o.nt; ++ni) {
-          TcItem it{};
-          it.oi = q;
-          it.mi = (uint16_t)mi;
-          it.ni = (uint16_t)ni;
-          it.kt0 = (uint16_t)kt0;
-          it.kt1 = (uint16_t)kt1;
-          it.s0 = (uint8_t)s0;
-          it.s1 = (uint8_t)s1;
-          it.send = (uint16_t)send;
-          items.push_back(it);
-        }
-      }
-    }
-  }
+  if (!tc_expand_items(clusters, ops, segs, items)) return -1;  // 16-bit item fields
   return (int64_t)items.size() == t ? 0 : -1;
 }
 

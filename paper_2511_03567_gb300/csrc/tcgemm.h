@@ -74,6 +74,68 @@ struct alignas(16) TcItem {
 };
 static_assert(sizeof(TcItem) == 16, "one 16-byte load per item");
 
+// Segment weights of a merged op (host side): alpha[i] = (-1)^(code[i] & 1)
+// * 2^(code[i] >> 1) * base with base = |alpha[0]| > 0; the exponents must be
+// non-decreasing and at most kTcMaxExp (the MMA only scales its accumulator
+// down).  false if the alphas do not have that form.
+inline bool tc_segment_weights(const double* alpha, int n, uint8_t* code, float* base) {
+  if (n < 1 || n > kTcMaxSeg || !(alpha[0] != 0.0)) return false;
+  int e_prev = 0;
+  for (int i = 0; i < n; ++i) {
+    int e = 0;
+    if (std::frexp(std::fabs(alpha[i]) / std::fabs(alpha[0]), &e) != 0.5) return false;
+    e -= 1;
+    if (e < e_prev || e > kTcMaxExp) return false;
+    e_prev = e;
+    code[i] = (uint8_t)((e << 1) | (alpha[i] < 0.0 ? 1 : 0));
+  }
+  *base = (float)std::fabs(alpha[0]);
+  return true;
+}
+
+// Work items of a grouped launch from its clusters (host side): per cluster,
+// (m tile, K chunk) major and (op, n tile) minor, each item with the merged
+// op's segments at both ends of its K chunk (s0 holds kt0, s1 holds
+// kt1 - 1; send ends segment s0).  K counts are in the ops' K-block units.
+// false if a field does not fit the item's 16-bit slots.
+inline bool tc_expand_items(const std::vector<TcCluster>& clusters, const std::vector<TcGroupOp>& ops,
+                            const std::vector<TcSeg>& segs, std::vector<TcItem>& items) {
+  items.clear();
+  for (const TcCluster& c : clusters) {
+    for (int64_t u = 0; u < (int64_t)c.mt * c.ksplit; ++u) {
+      const int mi = (int)(u / c.ksplit), ks = (int)(u % c.ksplit);
+      const int kt0 = ks * c.kps, kt1 = kt0 + c.kps < c.kt_total ? kt0 + c.kps : c.kt_total;
+      for (int q = c.op0; q < c.op0 + c.nops; ++q) {
+        const TcGroupOp& o = ops[q];
+        int s0 = 0, s1 = 0, send = 0, beg = 0;
+        for (int sgi = 0; sgi < o.nseg; ++sgi) {
+          const int end = beg + (sgi == 0 ? o.kt0 : segs[o.seg0 + sgi - 1].kt);
+          if (kt0 >= beg && kt0 < end) {
+            s0 = sgi;
+            send = end;
+          }
+          if (kt1 - 1 >= beg && kt1 - 1 < end) s1 = sgi;
+          beg = end;
+        }
+        if (mi > 0xffff || o.nt > 0x10000 || kt1 > 0xffff || send > 0xffff) return false;
+        for (int ni = 0; ni < o.nt; ++ni) {
+          TcItem it{};
+          it.oi = q;
+          it.mi = (uint16_t)mi;
+          it.ni = (uint16_t)ni;
+          it.kt0 = (uint16_t)kt0;
+          it.kt1 = (uint16_t)kt1;
+          it.s0 = (uint8_t)s0;
+          it.s1 = (uint8_t)s1;
+          it.send = (uint16_t)send;
+          items.push_back(it);
+        }
+      }
+    }
+  }
+  return true;
+}
+
 // Merge class of a contraction's alpha: contractions of one output whose
 // alphas are +-2^e with e in the same 16-wide window can share one op (the
 // sign and the exponent step are applied inside the MMA); any other alpha
