@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # the BASELINE Mid configuration (first flow value)
+    # Mid: 8 core, CAS(8,8), 120 virtual, n_aux 400, 512 determinants (first flow value)
     "mid": {"workload": "mid", "n_core": 8, "n_act": 8, "n_virt": 120, "n_aux": 400, "n_det": 512,
             "s": 0.1, "seed": 0},
     # small case for profiler captures (integral tensor 215 MB > L2)
