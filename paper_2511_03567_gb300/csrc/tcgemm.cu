@@ -160,7 +160,7 @@ __device__ __noinline__ void mma_scaled_any(uint32_t d, uint64_t ad, uint64_t bd
 
 constexpr uint32_t kNegateA = 1u << 13;  // instruction descriptor: negate the A operand
 
-// The four K = 16 MMAs of one 64-wide k-tile.  ad / bd describe the stage's
+// The four K = 16 MMAs of one product over a 64-wide K block.  ad / bd describe the stage's
 // first 16 columns; the next ones start 32 bytes further, i.e. +2 in the
 // descriptor's address field (addresses stay below 256 KB, so no carry).
 // The first MMA accumulates if `accum`, the other three always.
@@ -189,7 +189,7 @@ __device__ __noinline__ void mma_ktile_scaled(uint32_t d, uint64_t ad, uint64_t 
       " tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, q;\n}\n" ::"r"(d),
       "l"(ad), "l"(bd), "r"(idesc));
 }
-static_assert(BK == 64, "mma_ktile issues four K = 16 MMAs per k-tile");
+static_assert(BK == 64, "mma_ktile issues four K = 16 MMAs per 64-wide K block");
 
 template <int BN>
 __global__ void __launch_bounds__(128, 1)

@@ -33,7 +33,7 @@ struct TcArgs {
 // One contraction of a grouped tensor-core launch (device descriptor; the
 // tensor maps of its packed operands live here, in global memory).  A merged
 // op sums nseg <= kTcMaxSeg contractions with the same outputs and extents:
-// its own operand pair (kt0 k-tiles) followed by nseg - 1 pairs at
+// its own operand pair (kt0 K blocks of 64) followed by nseg - 1 pairs at
 // segs[seg0 ...], their K ranges concatenated.  Segment i is weighted by
 // (-1)^(scode[i] & 1) * 2^(scode[i] >> 1) * alpha (alpha > 0 when nseg > 1):
 // the MMAs of a segment with the other sign run with A negated, and at a
@@ -54,7 +54,7 @@ struct alignas(64) TcGroupOp {
 };
 struct alignas(64) TcSeg {
   CUtensorMap ma, mb;
-  int kt;  // k-tiles of this operand pair
+  int kt;  // K blocks (64 columns) of this operand pair
 };
 // Contractions sharing one packed A operand: items (m tile, K chunk, slot)
 // with slot running over the n tiles of all member ops (host-side ordering).
@@ -68,9 +68,9 @@ struct TcCluster {
 struct alignas(16) TcItem {
   int32_t oi;
   uint16_t mi, ni;    // 128-row tile, BN-column tile
-  uint16_t kt0, kt1;  // k-tiles [kt0, kt1) of the op's concatenated K
+  uint16_t kt0, kt1;  // K blocks [kt0, kt1) of the op's concatenated K
   uint8_t s0, s1;     // segments holding kt0 and kt1 - 1
-  uint16_t send;      // first k-tile past segment s0
+  uint16_t send;      // first K block past segment s0
 };
 static_assert(sizeof(TcItem) == 16, "one 16-byte load per item");
 
