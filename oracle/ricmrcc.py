@@ -534,28 +534,33 @@ def _clip(arr, sl):
     return arr[tuple(sl)]
 
 
-_TERMS = None
+_TERMS = {}
+METHODS = ("ric", "full")
 
 
-def terms(merged=True):
-    """The RIC term lists; `merged` sums terms that are the same tensor network."""
-    global _TERMS
-    if _TERMS is None:
-        raw = wick.ric_terms()
-        _TERMS = {"raw": raw, "merged": {k: wick.simplify(v) for k, v in raw.items()}}
-    return _TERMS["merged" if merged else "raw"]
+def terms(merged=True, method="ric"):
+    """The term lists of `method`: "ric" (the RIC neglect rules of Sec. 2.2)
+    or "full" (the same BCH expansion without them, lambda_4 dropped);
+    `merged` sums terms that are the same tensor network."""
+    if method not in METHODS:
+        raise ValueError(f"method must be one of {METHODS}")
+    if method not in _TERMS:
+        raw = wick.ric_terms() if method == "ric" else wick.full_terms()
+        _TERMS[method] = {"raw": raw, "merged": {k: wick.simplify(v) for k, v in raw.items()}}
+    return _TERMS[method]["merged" if merged else "raw"]
 
 
-def residual(model: Model, T, ev: Evaluator | None = None, merged=True):
+def residual(model: Model, T, ev: Evaluator | None = None, merged=True, method="ric"):
     """Spin-free residual blocks {class: array} and the energy.
 
     R1[k,c] = r^{c alpha}_{k alpha}; R2[k,l,c,d] = r^{c alpha d beta}_{k alpha l beta}
     with r the antisymmetrised (Eq. antisym) many-body residual of
-    H + [H,T] + 1/2 [[H,T],T] under the RIC neglect rules (Sec. 2.2).
+    H + [H,T] + 1/2 [[H,T],T] under the RIC neglect rules (Sec. 2.2), or
+    without them for method="full".
     """
     model.set_amplitudes(T)
     ev = ev or Evaluator(model)
-    tl = terms(merged)
+    tl = terms(merged, method)
     res_terms = tl["lin"] + tl["quad_res"]
     out = {}
     for name, ks, cs in T1_CLASSES:
@@ -573,10 +578,10 @@ def residual(model: Model, T, ev: Evaluator | None = None, merged=True):
     return out, energy
 
 
-def energy(model: Model, T, ev: Evaluator | None = None):
+def energy(model: Model, T, ev: Evaluator | None = None, method="ric"):
     model.set_amplitudes(T)
     ev = ev or Evaluator(model)
-    tl = terms()
+    tl = terms(method=method)
     return model.E0 + ev.scalar(tl["lin"]) + ev.scalar(tl["quad_en"])
 
 
@@ -640,11 +645,12 @@ def zero_amplitudes(sp: Spaces):
 
 
 def solve(model: Model, s, max_iter=100, e_tol=1e-10, t_tol=1e-9, diis_size=8,
-          diis_start=3, T0=None):
+          diis_start=3, T0=None, method="ric"):
     """DIIS-accelerated renormalised iteration from T = 0.
 
     DIIS (Pulay) extrapolates the amplitudes with error vectors t_new - t over
-    every class jointly; it starts at iteration `diis_start`.
+    every class jointly; it starts at iteration `diis_start`.  `method`
+    selects the residual (see `terms`).
     """
     eps = np.diag(model.fock_spinfree())
     D = denominators(model.sp, eps)
@@ -654,7 +660,7 @@ def solve(model: Model, s, max_iter=100, e_tol=1e-10, t_tol=1e-9, diis_size=8,
     e_old = None
     vecs, errs, hist = [], [], []
     for it in range(1, max_iter + 1):
-        R, E = residual(model, T, ev)
+        R, E = residual(model, T, ev, method=method)
         Tn = renormalized_update(T, R, D, s)
         err = _flat(Tn, keys) - _flat(T, keys)
         hist.append((E, float(np.abs(err).max()) if err.size else 0.0))

@@ -370,6 +370,25 @@ def ric_terms():
     return {"lin": lin, "quad_res": quad_res, "quad_en": quad_en}
 
 
+def full_terms():
+    """The same truncated BCH expansion without the RIC neglect rules of
+    Sec. 2.2: every pair of amplitude classes and the two-body cumulant are
+    kept in 1/2 [[H,T],T], for the residual (ranks 1-2) and the energy (rank
+    0).  Cumulants stop at lambda_3 (the four-body cumulant is dropped, as in
+    the RIC expansion, since the method's inputs end at the three-body RDM).
+    'lin' is the RIC list's: H + [H,T] has no neglect rule."""
+    h = hamiltonian()
+    t_all = cluster_operator()
+    half = Fraction(1, 2)
+    lin = list(h) + commutator(h, t_all, max_open=4)
+    c_all = commutator(h, t_all, max_open=6)
+    quad_res, quad_en = [], []
+    for term in commutator(c_all, t_all, max_open=4):
+        scaled = Term(term.coeff * half, term.factors, term.ops, term.sp, term.tags)
+        (quad_res if term.rank >= 1 else quad_en).append(scaled)
+    return {"lin": lin, "quad_res": quad_res, "quad_en": quad_en}
+
+
 # ---------------------------------------------------------------------------
 # Merging identical tensor networks
 # ---------------------------------------------------------------------------
