@@ -101,9 +101,9 @@ def _term_c(t):
         len(t.factors), len(labels), ",".join(map(str, masks)), ",".join(facs))
 
 
-def write(path):
+def write(path, exact=True):
     t0 = time.time()
-    res, en = sf.derive()
+    res, en = sf.derive(exact)
     res = restrict(res)
     en = restrict(en)
     cum = restrict(sf.cumulant3_terms())

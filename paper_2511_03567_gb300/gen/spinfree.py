@@ -163,10 +163,73 @@ def _canon(t: SFTerm):
             tuple(sorted((lab[x], m) for x, m in sp.items())))
 
 
-def merge(terms):
+def _wl_signatures(t: SFTerm):
+    """Label-independent signatures of a term's indices (index space, output
+    position, tensor slots; refined three times by the neighbours' ones)."""
+    sp = dict(t.space)
+    outpos = {x: i for i, x in enumerate(t.out_idx)}
+    occ = {x: [] for x in sp}
+    for nm, ix in t.factors:
+        n = _RANK[nm]
+        for p, x in enumerate(ix):
+            occ[x].append((nm, "u" if p < n else "l"))
+    sig = {x: repr((sp[x], outpos.get(x, -1), sorted(occ[x]))) for x in sp}
+    for _ in range(3):
+        new = {}
+        for x in sp:
+            nb = []
+            for nm, ix in t.factors:
+                if x in ix:
+                    nb.append((nm, sorted(sig[y] for y in ix if y != x)))
+            new[x] = repr((sig[x], sorted(nb)))
+        sig = new
+    return sig
+
+
+def _key(t: SFTerm, order):
+    sp = dict(t.space)
+    lab = {x: i for i, x in enumerate(order)}
+    facs = []
+    for nm, ix in t.factors:
+        n = _RANK[nm]
+        cols = sorted(zip([lab[x] for x in ix[:n]], [lab[x] for x in ix[n:]]))
+        facs.append((nm, tuple(c[0] for c in cols) + tuple(c[1] for c in cols)))
+    facs.sort()
+    return (t.out, tuple(lab[x] for x in t.out_idx), tuple(facs),
+            tuple(sorted((lab[x], m) for x, m in sp.items())))
+
+
+def _canon_exact(t: SFTerm, limit=720):
+    """Canonical form under relabeling: the smallest key over every order of
+    the indices that keeps the signature order (indices with equal
+    signatures are tried in all their orders).  Terms whose ties allow more
+    than `limit` orders get the label-order tie break of `_canon`."""
+    sig = _wl_signatures(t)
+    groups = {}
+    for x in sorted(sig, key=lambda x: (sig[x], x)):
+        groups.setdefault(sig[x], []).append(x)
+    classes = [groups[k] for k in sorted(groups)]
+    n_orders = 1
+    for c in classes:
+        for i in range(2, len(c) + 1):
+            n_orders *= i
+    if n_orders > limit:
+        return _canon(t)
+    best = None
+    for choice in itertools.product(*[itertools.permutations(c) for c in classes]):
+        k = _key(t, [x for c in choice for x in c])
+        if best is None or k < best:
+            best = k
+    return best
+
+
+def merge(terms, exact=False):
+    """Sum the terms that are the same tensor network (`exact`: with the
+    complete canonical form, else the faster signature-and-label one)."""
+    canon = _canon_exact if exact else _canon
     acc = {}
     for t in terms:
-        k = _canon(t)
+        k = canon(t)
         acc[k] = acc.get(k, Fraction(0)) + t.coef
     out = []
     for (o, oi, facs, sp), c in acc.items():
@@ -192,11 +255,12 @@ def drop_zero_blocks(terms):
     return out
 
 
-def derive():
-    """All spin-free terms: residual (R1, X2) and energy (E, without E0)."""
+def derive(exact=True):
+    """All spin-free terms: residual (R1, X2) and energy (E, without E0);
+    `exact` merges with the complete canonical form."""
     h = al.ric_hbar()
-    res = merge(spinfree_residual(h["res"]))
-    en = merge(spinfree_energy(h["energy"]))
+    res = merge(spinfree_residual(h["res"]), exact)
+    en = merge(spinfree_energy(h["energy"]), exact)
     return res, en
 
 
