@@ -298,3 +298,17 @@ def ric_hbar():
     en += scale(commutator(HT, T, 0), half)
     en += scale(commutator(HT3, T3, 0), -half)
     return {"res": res, "energy": en}
+
+
+def full_hbar():
+    """Spin-orbital pieces of Hbar = H + [H,T] + 1/2[[H,T],T] without the RIC
+    neglect rules of Sec. 2.2: every pair of amplitude classes and the
+    two-body cumulant kept in the double commutator; cumulants end at
+    lambda_3.  Same layout as `ric_hbar`."""
+    H = hamiltonian()
+    T = cluster(ALL)
+    lin = H + commutator(H, T, 2)
+    quad = scale(commutator(commutator(H, T, 3), T, 2), Fraction(1, 2))
+    res = [t for t in lin if t.rank >= 1] + [t for t in quad if t.rank >= 1]
+    en = [t for t in lin if t.rank == 0] + [t for t in quad if t.rank == 0]
+    return {"res": res, "energy": en}

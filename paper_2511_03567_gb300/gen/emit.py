@@ -1,7 +1,8 @@
 """Write the spin-free term tables as a C include (build-time tool).
 
 Run `python -m paper_2511_03567_gb300.gen.emit` to regenerate
-`paper_2511_03567_gb300/csrc/ric_terms.inc`.  The tables depend only on the
+`paper_2511_03567_gb300/csrc/ric_terms.inc`, and with `--full` the unfiltered
+BCH-2 tables `csrc/ric_terms_full.inc.gz`.  The tables depend only on the
 method (not on problem sizes); the runtime planner turns them into binary
 contractions for the actual dimensions.
 """
@@ -79,7 +80,7 @@ def restrict(terms):
     return out
 
 
-def _term_c(t):
+def _term_c(t, max_labels=16, max_factors=7):
     sp = dict(t.space)
     labels = {}
     for x in list(t.out_idx) + [x for _, ix in t.factors for x in ix]:
@@ -92,10 +93,10 @@ def _term_c(t):
     for nm, ix in t.factors:
         idx = [labels[x] for x in ix] + [0] * (6 - len(ix))
         facs.append("{%d,%d,{%s}}" % (TENSOR_ID[nm], len(ix), ",".join(map(str, idx))))
-    while len(facs) < 7:
+    while len(facs) < max_factors:
         facs.append("{0,0,{0,0,0,0,0,0}}")
     outl = [labels[x] for x in t.out_idx] + [0] * (6 - len(t.out_idx))
-    masks += [0] * (16 - len(masks))
+    masks += [0] * (max_labels - len(masks))
     return "{%.17g,%d,%d,{%s},%d,%d,{%s},{%s}}" % (
         float(t.coef), OUT_ID[t.out], len(t.out_idx), ",".join(map(str, outl)),
         len(t.factors), len(labels), ",".join(map(str, masks)), ",".join(facs))
@@ -137,6 +138,45 @@ def write(path, exact=True):
           f"{len(gradt)} dT, {len(gradh)} d(F,V) terms in {time.time() - t0:.1f}s", file=sys.stderr)
 
 
+def write_full(path, processes=8):
+    """The unfiltered BCH-2 tables (Sec. 2.2 without the neglect rules),
+    gzip-compressed, in the same entry format: kFullResidualTerms and
+    kFullEnergyTerms.  Not compiled into the library (about 15 MB as text)."""
+    import gzip
+
+    t0 = time.time()
+    res, en = sf.derive_full(processes)
+    res = restrict(res)
+    en = restrict(en)
+    # more labels and factors per term than the RIC tables' 16 / 7
+    nlab = max(len({x for _, ix in t.factors for x in ix} | set(t.out_idx)) for t in res + en)
+    nfac = max(len(t.factors) for t in res + en)
+    nlab, nfac = max(nlab, 16), max(nfac, 7)
+    fmt = lambda t: _term_c(t, nlab, nfac)
+    res.sort(key=fmt)
+    en.sort(key=fmt)
+    lines = [
+        "// Generated by paper_2511_03567_gb300/gen/emit.py (write_full) -- do not edit.",
+        "// Spin-free terms of H + [H,T] + 1/2[[H,T],T] without the RIC neglect rules",
+        "// (Sec. 2.2; cumulants up to lambda_3); entry format of ric_terms.inc with",
+        f"// up to {nlab} index labels and {nfac} factors per term",
+        f"#define RIC_FULL_MAX_LABELS {nlab}",
+        f"#define RIC_FULL_MAX_FACTORS {nfac}",
+        "static const RicTermDesc kFullResidualTerms[] = {",
+    ]
+    lines += ["  " + fmt(t) + "," for t in res]
+    lines += ["};", "static const RicTermDesc kFullEnergyTerms[] = {"]
+    lines += ["  " + fmt(t) + "," for t in en]
+    lines += ["};", ""]
+    with gzip.open(path, "wt", compresslevel=9) as f:
+        f.write("\n".join(lines))
+    print(f"wrote {path}: {len(res)} residual, {len(en)} energy terms in {time.time() - t0:.1f}s",
+          file=sys.stderr)
+
+
 if __name__ == "__main__":
     here = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    write(os.path.join(here, "csrc", "ric_terms.inc"))
+    if "--full" in sys.argv:
+        write_full(os.path.join(here, "csrc", "ric_terms_full.inc.gz"))
+    else:
+        write(os.path.join(here, "csrc", "ric_terms.inc"))

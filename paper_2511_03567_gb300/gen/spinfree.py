@@ -255,6 +255,39 @@ def drop_zero_blocks(terms):
     return out
 
 
+def _spin_sum_and_merge(job):
+    """Worker of `derive_full`: spin-sum one share of the spin-orbital terms
+    and sum equal tensor networks (complete canonical form)."""
+    kind, so_terms = job
+    terms = spinfree_residual(so_terms) if kind == "res" else spinfree_energy(so_terms)
+    acc = {}
+    for t in terms:
+        k = _canon_exact(t)
+        acc[k] = acc.get(k, Fraction(0)) + t.coef
+    return kind, acc
+
+
+def derive_full(processes=8, shares=64):
+    """Spin-free terms of the unfiltered BCH-2 expansion (`al.full_hbar`):
+    residual (R1, X2) and energy (E, without E0).  The ~120 000 spin-orbital
+    terms are spin-summed and merged in `processes` worker processes."""
+    import multiprocessing as mp
+
+    h = al.full_hbar()
+    jobs = [("res", h["res"][i::shares]) for i in range(shares)]
+    jobs += [("en", h["energy"][i::8]) for i in range(8)]
+    with mp.get_context("spawn").Pool(processes) as pool:
+        parts = pool.map(_spin_sum_and_merge, jobs, chunksize=1)
+    acc = {"res": {}, "en": {}}
+    for kind, part in parts:
+        for k, c in part.items():
+            acc[kind][k] = acc[kind].get(k, Fraction(0)) + c
+
+    def build(d):
+        return [SFTerm(c, facs, o, oi, sp) for (o, oi, facs, sp), c in d.items() if c != 0]
+    return build(acc["res"]), build(acc["en"])
+
+
 def derive(exact=True):
     """All spin-free terms: residual (R1, X2) and energy (E, without E0);
     `exact` merges with the complete canonical form."""
