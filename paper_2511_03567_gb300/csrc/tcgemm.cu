@@ -354,7 +354,7 @@ __global__ void __launch_bounds__(128, 1)
 //               scatter through the output offset tables); two warps per
 //               TMEM lane quarter, alternating 32-column chunks, so that
 //               enough atomics are in flight to cover their latency
-// The two accumulators (2 x 256 TMEM columns) let the MMAs of item c+1 run
+// The two accumulators (2 x 128 TMEM columns) let the MMAs of item c+1 run
 // while the epilogue drains item c; the 3-stage ring lets the producer run
 // ahead across item boundaries.  Every wait is bounded (kWaitNs) and sets the
 // error flag on timeout; the MMA issuer's final commit guarantees that TMEM is
@@ -384,7 +384,6 @@ __device__ __forceinline__ TcItem load_item(const TcItem* __restrict__ items, in
 __device__ __forceinline__ uint32_t instr_desc_n(int bn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
-
 
 constexpr int kEpiWarps = 8;
 
