@@ -30,6 +30,7 @@ What it computes (Sec. 2-3 of the paper), step by step and unfactorised:
 from __future__ import annotations
 
 import itertools
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -546,7 +547,8 @@ def terms(merged=True, method="ric"):
         raise ValueError(f"method must be one of {METHODS}")
     if method not in _TERMS:
         raw = wick.ric_terms() if method == "ric" else wick.full_terms()
-        _TERMS[method] = {"raw": raw, "merged": {k: wick.simplify(v) for k, v in raw.items()}}
+        procs = min(os.cpu_count() or 1, 16)
+        _TERMS[method] = {"raw": raw, "merged": {k: wick.simplify(v, procs) for k, v in raw.items()}}
     return _TERMS[method]["merged" if merged else "raw"]
 
 

@@ -450,8 +450,8 @@ def canonical(t: Term):
     return (tuple(facs), ops, sps), sign
 
 
-def simplify(terms):
-    """Merge terms with equal canonical keys (summing coefficients)."""
+def _keyed_sum(terms):
+    """Coefficient sums and a representative term per canonical key."""
     acc = {}
     rep = {}
     for t in terms:
@@ -459,6 +459,26 @@ def simplify(terms):
         acc[key] = acc.get(key, Fraction(0)) + sign * t.coeff
         if key not in rep:
             rep[key] = t
+    return acc, rep
+
+
+def simplify(terms, processes=1):
+    """Merge terms with equal canonical keys (summing coefficients).  With
+    processes > 1 the keys of large lists are computed in that many spawned
+    worker processes (the sums are the same)."""
+    if processes > 1 and len(terms) > 20000:
+        import multiprocessing as mp
+
+        chunks = [terms[i::processes * 4] for i in range(processes * 4)]
+        with mp.get_context("spawn").Pool(processes) as pool:
+            parts = pool.map(_keyed_sum, chunks)
+        acc, rep = {}, {}
+        for a, r in parts:
+            for key, c in a.items():
+                acc[key] = acc.get(key, Fraction(0)) + c
+                rep.setdefault(key, r[key])
+    else:
+        acc, rep = _keyed_sum(terms)
     out = []
     for key, c in acc.items():
         if c == 0:
