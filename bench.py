@@ -54,7 +54,9 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples during the timed region."""
+    """nvidia-smi clock / throttle samples (every 50 ms) from before the
+    warm-up to after the timed region; mark() records when the timed region
+    starts and ends so the summary can single out its samples."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -62,22 +64,26 @@ class ClockSampler:
     def __init__(self, gpu=0):
         self.gpu = gpu
         self.rows = []
+        self.marks = {}
         self.proc = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except FileNotFoundError:
             self.proc = None
         return self
 
+    def mark(self, name):
+        self.marks[name] = time.perf_counter()
+
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
 
     def __exit__(self, *a):
         if self.proc:
@@ -87,16 +93,28 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    @staticmethod
+    def _stats(rows):
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].lower().startswith("active")})
+        return sm, mx, reasons
+
     def summary(self):
         if not self.rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4)
-                          if len(r) > 5 + i and r[5 + i].lower().startswith("active")})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+        t0 = self.marks.get("timed_start", -1e30)
+        t1 = self.marks.get("timed_end", 1e30)
+        timed = [r for t, r in self.rows if t0 <= t <= t1]
+        sm, mx, reasons = self._stats([r for _, r in self.rows])
+        tsm, _, treasons = self._stats(timed)
+        return {"sm_mhz": float(np.median(tsm)) if tsm else (float(np.median(sm)) if sm else None),
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(set(reasons) | set(treasons)),
+                "samples": len(self.rows), "samples_timed": len(timed),
+                "sm_mhz_median_all": float(np.median(sm)) if sm else None,
+                "window": "warm-up and timed region; sm_mhz is the timed region's median when it has samples"}
 
 
 def fp64_gemm_peak(torch):
@@ -188,28 +206,45 @@ def dist_init():
     return None, rank, ws, local
 
 
-def cpu_baseline_run(steps_budget_s=20.0):
+def cpu_baseline_run(budget_s=40.0):
     """Oracle on a bounded sample of the Mid workload (host cores)."""
     from oracle import sampled
-    return sampled.time_sampled_iteration(WORKLOAD, budget_s=steps_budget_s)
+    res = sampled.time_sampled_iteration(WORKLOAD, budget_s=budget_s)
+    res["host"] = sampled.host_description()
+    return res
 
 
 def run_reference(args):
+    """The oracle (FP64, host cores) on the same workload: each step evaluates
+    one sample of it at full size (the energy, or one whole residual row of a
+    class, the classes in turn) and the steps' samples are extrapolated to one
+    iteration; `ms_per_step` is the measured time per sample."""
     dist, rank, ws, local = dist_init()
     if rank != 0:
         return 0
-    res = cpu_baseline_run(steps_budget_s=max(10.0, 20.0 * max(args.steps, 1) / 5))
-    line = {"metric": METRIC, "value": res["s_per_iter"], "unit": "s/iter", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["s_per_iter"] * 1e3,
+    from oracle import sampled
+    smp = sampled.RowSampler(WORKLOAD)
+    cheapest = smp.order[-1]
+    for _ in range(args.warmup):
+        smp.run(cheapest, record=False)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        smp.run(smp.schedule(i))
+    secs = time.perf_counter() - t0
+    per_iter, desc = smp.estimate()
+    host = sampled.host_description()
+    line = {"metric": METRIC, "value": per_iter, "unit": "s/iter", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / max(args.steps, 1) * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": dict(WORKLOAD, precision=args.precision, parallelism=f"replicas{args.gpus}",
-                           l2="inputs larger than L2 (2.7 GB integral tensor), no flush",
-                           reference="the FP64 oracle on the host cores, residual elements one by one"),
+            "data": "synthetic", "extrapolated": True,
+            "step": "one sample of the workload (the energy, or one whole residual row of a class); "
+                    "value is the iteration time extrapolated from the steps' samples",
+            "config": dict(WORKLOAD, precision="fp64", parallelism="host cores",
+                           reference="the FP64 oracle on the host cores"),
             "impl": "reference",
-            "cpu_baseline": {"value": res["s_per_iter"], "unit": "s/iter", "cores": res["cores"],
-                             "kind": "oracle", "sample": res["sample"]},
-            "e2e": {"value": res["s_per_iter"], "unit": "s/iter", "h2d_bytes_per_step": 0,
+            "cpu_baseline": {"value": per_iter, "unit": "s/iter", "cores": sampled.threads(),
+                             "kind": "oracle", "sample": desc, "host": host},
+            "e2e": {"value": per_iter, "unit": "s/iter", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -226,6 +261,8 @@ def main():
                     help="skip timing the FP64 path beside the mixed one")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile rule")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-converging", action="store_true",
+                    help="skip the mixed-against-FP64 solves of the converging Mid-sized problem")
     ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
     ap.add_argument("--ncu-largest", type=int, default=0,
                     help="profiler mode: one residual, then only the N largest contractions")
@@ -295,19 +332,24 @@ def main():
                           "residual_flops": info.residual_flops}))
         return 0
 
-    # warm-up, then exactly K timed iterations (DIIS history continues)
-    g.step(s=w["s"], n_steps=max(args.warmup, 1), restart=True, precision=prec)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # Warm-up from the initial guess T = 0; the amplitudes it reaches are the
+    # starting state of every timed block.  The synthetic Mid iteration does
+    # not converge (every <ij|ab> is O(0.05)), so timed iterations run in
+    # blocks of at most BLOCK from this state and never far enough along the
+    # trajectory to overflow; each block is timed with CUDA events on the
+    # library's stream and the blocks' times are summed (exactly K iterations).
+    lay = g.layout
+    snap = (torch.empty(lay.t1_size, dtype=torch.float64, device="cuda"),
+            torch.empty(lay.t2_size, dtype=torch.float64, device="cuda"))
     with ClockSampler(local) as clk:
-        e0.record(stream)
-        E, dt = g.step(s=w["s"], n_steps=args.steps, restart=False, precision=prec)
-        e1.record(stream)
+        g.step(s=w["s"], n_steps=max(args.warmup, 1), restart=True, precision=prec)
+        g.get_amplitudes_dev(*snap)
         torch.cuda.synchronize()
-    secs = e0.elapsed_time(e1) / 1e3
+        if dist:
+            dist.barrier()
+        clk.mark("timed_start")
+        secs, E = timed_blocks(torch, g, stream, w["s"], prec, args.steps, snap)
+        clk.mark("timed_end")
     if dist:
         t = torch.tensor([secs], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -316,50 +358,55 @@ def main():
     ms_per_step = secs / args.steps * 1e3
     info = g.plan_info()  # graph launch counts are known once captured
 
+    # mixed against FP64 for one evaluation at the warm amplitudes
+    acc = None
+    if prec == ric.MIXED:
+        acc = eval_mixed_vs_fp64(torch, g, snap)
+
     fp64_line = None
     if prec == ric.MIXED and not args.no_fp64_compare:
-        # the FP64 path on the same handle, same amplitudes' history
+        # the FP64 path on the same handle from the same warm amplitudes
         g.set_precision(ric.FP64)
-        g.step(s=w["s"], n_steps=max(args.warmup, 1), restart=True, precision=ric.FP64)
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        g.step(s=w["s"], n_steps=args.steps, restart=False, precision=ric.FP64)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        f_secs = f0.elapsed_time(f1) / 1e3 / args.steps
+        restore(g, w["s"], ric.FP64, snap)
+        g.step(s=w["s"], n_steps=1, restart=False, precision=ric.FP64)  # capture + warm-up
+        f_secs, _ = timed_blocks(torch, g, stream, w["s"], ric.FP64, args.steps, snap)
+        f_secs /= args.steps
         fp64_line = {"s_per_iter": f_secs, "tflops": info.residual_flops / f_secs / 1e12,
                      "speedup_mixed": f_secs / (ms_per_step / 1e3)}
         g.set_precision(ric.MIXED)
-        g.step(s=w["s"], n_steps=1, restart=True, precision=ric.MIXED)
 
-    # end to end through the public host API: pinned host amplitudes in,
-    # one iteration, amplitudes out
-    lay = g.layout
-    t1 = torch.empty(lay.t1_size, dtype=torch.float64).pin_memory().numpy()
-    t2 = torch.empty(lay.t2_size, dtype=torch.float64).pin_memory().numpy()
-    cur = g.get_amplitudes()
-    a1, a2 = g.pack(cur)
-    t1[:] = a1
-    t2[:] = a2
+    # end to end through the public host API: each iteration copies the
+    # amplitudes in from pinned host memory, iterates and copies them out
+    t1 = torch.empty(lay.t1_size, dtype=torch.float64).pin_memory()
+    t2 = torch.empty(lay.t2_size, dtype=torch.float64).pin_memory()
+    t1.copy_(snap[0].cpu())
+    t2.copy_(snap[1].cpu())
+    t1n, t2n = t1.numpy(), t2.numpy()
+    restore(g, w["s"], prec, snap)
     torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, min(args.steps, BLOCK))
     c0 = time.perf_counter()
     for _ in range(e2e_steps):
-        g.lib.ricmrcc_set_amplitudes(g.h, ric._ptr(t1), ric._ptr(t2))
+        g.lib.ricmrcc_set_amplitudes(g.h, ric._ptr(t1n), ric._ptr(t2n))
         g.step(s=w["s"], n_steps=1, restart=False, precision=prec)
-        g.lib.ricmrcc_get_amplitudes(g.h, ric._ptr(t1), ric._ptr(t2))
+        g.lib.ricmrcc_get_amplitudes(g.h, ric._ptr(t1n), ric._ptr(t2n))
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - c0) / e2e_steps
 
     # roofline of the dominant kernel (per-kernel CUDA-event profile after the
-    # timed region, on the library's stream)
+    # timed region, on the library's stream, at the warm amplitudes)
     mixed = prec == ric.MIXED
+    restore(g, w["s"], prec, snap)
     kind_ms = g.profile(reps=2, mixed=mixed)
     info = g.plan_info()
     pk = peaks()
     fp64_peak = fp64_gemm_peak(torch) if rank == 0 else None
+
+    # a converging problem of the same sizes: mixed solve (with its FP64
+    # refinement) against the FP64 solve
+    conv = None
+    if mixed and not args.no_converging and rank == 0:
+        conv = converging_mid(g, p, w)
     if rank != 0:
         return 0
     roof = roofline(kind_ms, info, mixed, pk, fp64_peak, torch)
@@ -378,24 +425,116 @@ def main():
             "dtype": "f64" if prec == ric.FP64 else "bf16x3(f32 acc)+f64",
             "data": "synthetic",
             "config": dict(WORKLOAD, precision=args.precision, parallelism=f"replicas{ws}",
-                           l2="inputs larger than L2 (2.7 GB integral tensor), no flush"),
+                           l2="inputs larger than L2 (2.7 GB integral tensor), no flush",
+                           converged=False,
+                           timing=f"iterations in blocks of <= {BLOCK} from the amplitudes after "
+                                  f"{max(args.warmup, 1)} warm-up iterations from T = 0; CUDA events "
+                                  "per block, summed"),
             "tflops": info.residual_flops / (ms_per_step / 1e3) / 1e12,
             "residual_flops": info.residual_flops, "energy_last": E,
             "e2e": {"value": e2e_s, "unit": "s/iter", "h2d_bytes_per_step": 8 * (lay.t1_size + lay.t2_size),
-                    "d2h_bytes_per_step": 8 * (lay.t1_size + lay.t2_size)},
+                    "d2h_bytes_per_step": 8 * (lay.t1_size + lay.t2_size), "steps": e2e_steps},
             "gpu_launches": int(info.step_launches) * args.steps,
             "roofline": roof, "clocks": clk.summary(), "tensor_core": tc, "fp64_path": fp64_line,
+            "accuracy": {"mixed_vs_fp64_one_evaluation": acc, "converging_mid": conv},
             "tile_rule": g.get_tile_rule(), "tuning": tuning}
     if not args.no_cpu_baseline and ws == 1 and args.workload == "mid":
         try:
             cb = cpu_baseline_run()
             line["cpu_baseline"] = {"value": cb["s_per_iter"], "unit": "s/iter", "cores": cb["cores"],
-                                    "kind": "oracle", "sample": cb["sample"]}
+                                    "kind": "oracle", "sample": cb["sample"], "host": cb["host"]}
         except Exception as ex:  # the oracle is optional on the bench path
             line["cpu_baseline"] = {"value": None, "unit": "s/iter", "cores": os.cpu_count(),
                                     "kind": "oracle", "sample": f"failed: {ex}"}
     print(json.dumps(line))
     return 0
+
+
+# iterations per timed block (see main)
+BLOCK = 20
+
+
+def restore(g, s, prec, snap):
+    """Back to the warm amplitudes with an empty DIIS history (not timed)."""
+    g.step(s=s, n_steps=0, restart=True, precision=prec)
+    g.set_amplitudes_dev(*snap)
+
+
+def timed_blocks(torch, g, stream, s, prec, steps, snap):
+    """Exactly `steps` solver iterations in blocks of <= BLOCK, each block
+    started from `snap`; returns (seconds summed over the blocks' CUDA-event
+    times, energy of the last iteration)."""
+    secs, done, E = 0.0, 0, None
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    while done < steps:
+        k = min(BLOCK, steps - done)
+        restore(g, s, prec, snap)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        E, _ = g.step(s=s, n_steps=k, restart=False, precision=prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        secs += e0.elapsed_time(e1) / 1e3
+        done += k
+    return secs, E
+
+
+def eval_mixed_vs_fp64(torch, g, snap):
+    """One residual + energy in FP64 and in the mixed path at the same amplitudes."""
+    import paper_2511_03567_gb300 as ric
+    lay = g.layout
+    out = {}
+    for prec in (ric.FP64, ric.MIXED):
+        g.set_precision(prec)
+        r1 = torch.empty(lay.t1_size, dtype=torch.float64, device="cuda")
+        r2 = torch.empty(lay.t2_size, dtype=torch.float64, device="cuda")
+        e = torch.zeros(1, dtype=torch.float64, device="cuda")
+        g.residual_dev(snap[0], snap[1], r1, r2, e)
+        torch.cuda.synchronize()
+        out[prec] = (torch.cat([r1, r2]), float(e.item()))
+    g.set_precision(ric.MIXED)
+    rf, ef = out[ric.FP64]
+    rm, em = out[ric.MIXED]
+    return {"amplitudes": "the warm amplitudes every timed block starts from",
+            "energy_fp64": ef, "energy_mixed": em, "abs_dE": abs(em - ef),
+            "max_abs_dR": float((rm - rf).abs().max()), "max_abs_R": float(rf.abs().max()),
+            "rel_dR": float((rm - rf).abs().max() / rf.abs().max())}
+
+
+# B scale of the converging problem: B ~ N(0, 0.05 * CONV_B_SCALE), every
+# other input as the Mid workload
+CONV_B_SCALE = 0.2
+
+
+def converging_mid(g, p, w):
+    """Mid sizes with a smaller density-fitting factor, so that the iteration
+    converges: the mixed solve (tensor-core iterations, then FP64 refinement)
+    against the FP64 solve, energies and times.  Changes the handle's
+    integrals (run after everything else on the Mid workload)."""
+    import paper_2511_03567_gb300 as ric
+    g.set_integrals(p.h, np.ascontiguousarray(p.B * CONV_B_SCALE))
+    g.set_rdms(p.G1, p.G2, p.G3)  # the handle holds them in its rotated basis
+    g.semicanonicalize()
+    out = {"inputs": f"Mid workload with B scaled by {CONV_B_SCALE} (B ~ N(0, {0.05 * CONV_B_SCALE:g}))",
+           "s": w["s"]}
+    res = {}
+    for name, prec in (("fp64", ric.FP64), ("mixed", ric.MIXED)):
+        g.set_precision(prec)
+        g.step(s=w["s"], n_steps=0, restart=True, precision=prec)  # T = 0
+        try:
+            E, st = g.solve(s=w["s"], precision=prec, max_iter=80)
+            res[name] = {"energy": E, "converged": bool(st.converged), "iterations": st.iterations,
+                         "mixed_iterations": st.mixed_iterations, "fp64_iterations": st.fp64_iterations,
+                         "seconds": st.seconds, "e0": st.e0}
+        except ric.RicMrccError as ex:
+            res[name] = {"error": str(ex)}
+    out.update(res)
+    if "energy" in res.get("fp64", {}) and "energy" in res.get("mixed", {}):
+        out["abs_dE_mixed_vs_fp64"] = abs(res["mixed"]["energy"] - res["fp64"]["energy"])
+        out["within_1e-6"] = out["abs_dE_mixed_vs_fp64"] <= 1e-6
+    g.set_precision(ric.MIXED)
+    return out
 
 
 def run_batched(args):

@@ -181,21 +181,27 @@ RICMRCC_API int ricmrcc_residual_dev(ricmrcc_t* h, const double* T1, const doubl
 /* Fill opts with the defaults listed in ricmrcc_opts. */
 RICMRCC_API int ricmrcc_opts_default(ricmrcc_opts* opts);
 
-/* Solve the amplitude equations with the renormalized update of Eq.
- * ric-update, t <- (t Delta + r)(1 - exp(-s Delta^2)) / Delta with
+/* Solve the amplitude equations at flow s [Eh^-2] (s >= 0; it replaces
+ * opts->s) with the renormalized update of Eq. ric-update,
+ * t <- (t Delta + r)(1 - exp(-s Delta^2)) / Delta with
  * Delta = sum eps(holes) - sum eps(particles), eps = diag f (Eq. cc-update),
  * DIIS-accelerated (Sec. 2.2).  Starts from the stored amplitudes (zero after
- * set_rdms, or those given by ricmrcc_set_amplitudes).  E_out (nullable) and
+ * set_rdms, or those given by ricmrcc_set_amplitudes).  opts (nullable:
+ * defaults) sets the thresholds, DIIS and precision.  E_out (nullable) and
  * stats (nullable) receive the result.  Returns OK, NOT_CONVERGED (max_iter
- * reached; amplitudes and energy of the last iterate are kept) or DIVERGED
- * (non-finite numbers). */
-RICMRCC_API int ricmrcc_solve(ricmrcc_t* h, const ricmrcc_opts* opts, double* E_out, ricmrcc_stats* stats);
+ * reached; amplitudes and energy of the last iterate are kept), DIVERGED
+ * (non-finite energy or amplitude change; the amplitudes are left as they
+ * were when it was detected) or EINVAL (bad s or options). */
+RICMRCC_API int ricmrcc_solve(ricmrcc_t* h, double s, const ricmrcc_opts* opts, double* E_out,
+                              ricmrcc_stats* stats);
 
 /* Run n_steps iterations of the solver loop of ricmrcc_solve (residual and
- * energy, Eq. ric-update, DIIS) without the convergence test, continuing the
- * DIIS history of earlier calls unless restart != 0.  E_out / max_dt_out
- * (nullable, host) receive the energy at the last evaluated amplitudes and
- * the last max |t_new - t|.  Returns OK or DIVERGED. */
+ * energy, Eq. ric-update, DIIS) at flow opts->s without the convergence test,
+ * continuing from the stored amplitudes and the DIIS history of earlier
+ * calls.  restart != 0 first returns to the solver's initial guess: T = 0
+ * and an empty DIIS history.  E_out / max_dt_out (nullable, host) receive
+ * the energy at the last evaluated amplitudes and the last max |t_new - t|.
+ * Returns OK or DIVERGED. */
 RICMRCC_API int ricmrcc_step(ricmrcc_t* h, const ricmrcc_opts* opts, int n_steps, int restart,
                              double* E_out, double* max_dt_out);
 
@@ -277,9 +283,15 @@ RICMRCC_API int ricmrcc_run_largest_ops(ricmrcc_t* h, int count);
 RICMRCC_API int ricmrcc_energy_backward(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds);
 
 /* Copy the stored amplitudes out / in (flat class layout, host pointers);
- * set_amplitudes allows warm starts and resuming an interrupted solve. */
+ * set_amplitudes allows warm starts and resuming an interrupted solve.
+ * set_amplitudes rejects non-finite values (EINVAL). */
 RICMRCC_API int ricmrcc_get_amplitudes(ricmrcc_t* h, double* T1, double* T2);
 RICMRCC_API int ricmrcc_set_amplitudes(ricmrcc_t* h, const double* T1, const double* T2);
+/* Same with device pointers (T1-sized and T2-sized device arrays), enqueued
+ * on the handle's stream.  The device variant does not inspect the values:
+ * a non-finite amplitude makes the next solver iteration return DIVERGED. */
+RICMRCC_API int ricmrcc_get_amplitudes_dev(ricmrcc_t* h, double* T1, double* T2);
+RICMRCC_API int ricmrcc_set_amplitudes_dev(ricmrcc_t* h, const double* T1, const double* T2);
 
 /* Residual of the last evaluation (ricmrcc_residual, ricmrcc_step,
  * ricmrcc_solve or ricmrcc_batch_residual / _step / _solve on a batch that

@@ -458,7 +458,7 @@ class Evaluator:
             ops.append(self._operand(name, ix, fixed, spmap))
             subs.append("".join(letters[x] for x in ix))
         spec = ",".join(subs) + "->" + "".join(letters[x] for x in out_idx)
-        key = (id(t), tuple(sorted((k, v[:2]) for k, v in fixed.items())), tuple(out_idx))
+        key = (id(t), tuple(sorted((k, v[:2], len(v) > 2) for k, v in fixed.items())), tuple(out_idx))
         path = self._paths.get(key)
         if path is None:
             path = np.einsum_path(spec, *ops, optimize="greedy")[0]
@@ -741,42 +741,69 @@ def residual_elements(model: Model, T, elements, ev: Evaluator | None = None):
     """
     model.set_amplitudes(T)
     ev = ev or Evaluator(model)
+    out = [float(_residual_piece(ev, name, idx)[0]) for name, idx in elements]
+    return np.array(out)
+
+
+def residual_rows(model: Model, T, rows, ev: Evaluator | None = None):
+    """Rows of the spin-free residual: every element that shares all but one
+    index.
+
+    rows: list of (class name, index tuple in the class array order with
+    exactly one entry None), e.g. ("IJAB", (k, l, c, None)) for R2[k, l, c, :].
+    Same definition as `residual`, with the other orbitals fixed and one left
+    open, so one evaluation serves a whole row.  Returns one 1-d array per row.
+    """
+    model.set_amplitudes(T)
+    ev = ev or Evaluator(model)
+    out = []
+    for name, idx in rows:
+        if sum(x is None for x in idx) != 1:
+            raise ValueError("a row leaves exactly one index open")
+        out.append(_residual_piece(ev, name, tuple(idx)))
+    return out
+
+
+def _fixed(space, spin, index):
+    """Evaluator spec of an open (index None) or fixed orbital of one spin."""
+    return (space, spin) if index is None else (space, spin, index)
+
+
+def _residual_piece(ev: Evaluator, name, idx):
+    """Residual elements of class `name` at idx (one entry may be None: then
+    the whole row along that index), as a 1-d array."""
     tl = terms()
     res_terms = tl["lin"] + tl["quad_res"]
     t1c = {c[0]: c[1:] for c in T1_CLASSES}
     t2c = {c[0]: c[1:] for c in T2_CLASSES}
-    out = []
-    for name, idx in elements:
-        if name in t1c:
-            ks, cs = t1c[name]
-            k, c = idx
-            val = 0.0
-            for t in res_terms:
-                if t.rank != 1:
-                    continue
-                (p,), (q,) = t.upper(), t.lower()
-                r = ev.term(t, {p: (cs, 0, c), q: (ks, 0, k)}, (p, q))
-                if r is not None:
-                    val += float(np.sum(r))
-            out.append(val)
-            continue
-        ks, ls, cs, ds = t2c[name]
-        k, l, c, d = idx
-        A, B = 0, 1
-        variants = (  # Eq. antisym for the alpha-beta component
-            (+1, [(cs, A, c), (ds, B, d)], [(ks, A, k), (ls, B, l)]),
-            (-1, [(cs, A, c), (ds, B, d)], [(ls, B, l), (ks, A, k)]),
-            (-1, [(ds, B, d), (cs, A, c)], [(ks, A, k), (ls, B, l)]),
-            (+1, [(ds, B, d), (cs, A, c)], [(ls, B, l), (ks, A, k)]),
-        )
+    if name in t1c:
+        ks, cs = t1c[name]
+        k, c = idx
         val = 0.0
-        for sgn, up, lo in variants:
-            for t in res_terms:
-                if t.rank != 2:
-                    continue
-                (p1, p2), (q1, q2) = t.upper(), t.lower()
-                r = ev.term(t, {p1: up[0], p2: up[1], q1: lo[0], q2: lo[1]}, (p1, p2, q1, q2))
-                if r is not None:
-                    val += sgn * float(np.sum(r))
-        out.append(val)
-    return np.array(out)
+        for t in res_terms:
+            if t.rank != 1:
+                continue
+            (p,), (q,) = t.upper(), t.lower()
+            r = ev.term(t, {p: _fixed(cs, 0, c), q: _fixed(ks, 0, k)}, (p, q))
+            if r is not None:
+                val = val + np.asarray(r).reshape(-1)
+        return np.atleast_1d(val)
+    ks, ls, cs, ds = t2c[name]
+    k, l, c, d = idx
+    A, B = 0, 1
+    up1 = [_fixed(cs, A, c), _fixed(ds, B, d)]
+    up2 = [_fixed(ds, B, d), _fixed(cs, A, c)]
+    lo1 = [_fixed(ks, A, k), _fixed(ls, B, l)]
+    lo2 = [_fixed(ls, B, l), _fixed(ks, A, k)]
+    variants = ((+1, up1, lo1), (-1, up1, lo2), (-1, up2, lo1), (+1, up2, lo2))  # Eq. antisym
+    val = 0.0
+    for sgn, up, lo in variants:
+        for t in res_terms:
+            if t.rank != 2:
+                continue
+            (p1, p2), (q1, q2) = t.upper(), t.lower()
+            r = ev.term(t, {p1: up[0], p2: up[1], q1: lo[0], q2: lo[1]}, (p1, p2, q1, q2))
+            if r is not None:
+                # at most one open index: its axis is the only one longer than 1
+                val = val + sgn * np.asarray(r).reshape(-1)
+    return np.atleast_1d(val)

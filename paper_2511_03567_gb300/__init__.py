@@ -117,7 +117,10 @@ def load_library():
         "ricmrcc_residual": ([vp] * 6, ctypes.c_int),
         "ricmrcc_residual_dev": ([vp] * 6, ctypes.c_int),
         "ricmrcc_opts_default": ([ctypes.POINTER(Opts)], ctypes.c_int),
-        "ricmrcc_solve": ([vp, ctypes.POINTER(Opts), vp, ctypes.POINTER(Stats)], ctypes.c_int),
+        "ricmrcc_solve": ([vp, ctypes.c_double, ctypes.POINTER(Opts), vp, ctypes.POINTER(Stats)],
+                          ctypes.c_int),
+        "ricmrcc_get_amplitudes_dev": ([vp, vp, vp], ctypes.c_int),
+        "ricmrcc_set_amplitudes_dev": ([vp, vp, vp], ctypes.c_int),
         "ricmrcc_get_amplitudes": ([vp, vp, vp], ctypes.c_int),
         "ricmrcc_step": ([vp, ctypes.POINTER(Opts), ctypes.c_int, ctypes.c_int, vp, vp], ctypes.c_int),
         "ricmrcc_plan_info": ([vp, ctypes.POINTER(PlanInfo)], ctypes.c_int),
@@ -295,6 +298,14 @@ class RicMrcc:
         t1, t2 = self.pack(T)
         self._check(self.lib.ricmrcc_set_amplitudes(self.h, _ptr(t1), _ptr(t2)))
 
+    def get_amplitudes_dev(self, t1, t2):
+        """Stored amplitudes into flat device arrays (torch CUDA float64 tensors)."""
+        self._check(self.lib.ricmrcc_get_amplitudes_dev(self.h, _ptr(t1), _ptr(t2)))
+
+    def set_amplitudes_dev(self, t1, t2):
+        """Flat device arrays (torch CUDA float64 tensors) into the stored amplitudes."""
+        self._check(self.lib.ricmrcc_set_amplitudes_dev(self.h, _ptr(t1), _ptr(t2)))
+
     # ------------------------------------------------------------------ solve
     @staticmethod
     def default_opts(**kw):
@@ -308,7 +319,7 @@ class RicMrcc:
         o = self.default_opts(s=s, **kw)
         st = Stats()
         e = ctypes.c_double()
-        rc = self.lib.ricmrcc_solve(self.h, ctypes.byref(o), ctypes.byref(e), ctypes.byref(st))
+        rc = self.lib.ricmrcc_solve(self.h, float(s), ctypes.byref(o), ctypes.byref(e), ctypes.byref(st))
         self._check(rc, allow=(OK, NOT_CONVERGED))
         return e.value, st
 

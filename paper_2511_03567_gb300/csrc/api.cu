@@ -1092,11 +1092,12 @@ int check_opts(ricmrcc_t* h, const ricmrcc_opts& o) {
 
 extern "C" {
 
-int ricmrcc_solve(ricmrcc_t* h, const ricmrcc_opts* opts, double* E_out, ricmrcc_stats* stats) {
+int ricmrcc_solve(ricmrcc_t* h, double s, const ricmrcc_opts* opts, double* E_out, ricmrcc_stats* stats) {
   if (!h) return RICMRCC_EINVAL;
   ricmrcc_opts o;
   ricmrcc_opts_default(&o);
   if (opts) o = *opts;
+  o.s = s;
   TRY(check_opts(h, o));
   TRY(enter(h));
   const auto t0 = std::chrono::steady_clock::now();
@@ -1145,7 +1146,12 @@ int ricmrcc_step(ricmrcc_t* h, const ricmrcc_opts* opts, int n_steps, int restar
   if (n_steps < 0) return fail(h, RICMRCC_EINVAL, "n_steps < 0");
   TRY(check_opts(h, o));
   TRY(enter(h));
-  if (restart) reset_iteration_state(h);
+  if (restart) {
+    // back to the initial guess T = 0 with an empty DIIS history
+    reset_iteration_state(h);
+    CK(cudaMemsetAsync(h->T, 0, sizeof(double) * h->ng, h->s));
+    h->solved = false;
+  }
   bool conv = false, div = false;
   const bool mixed = o.precision == RICMRCC_MIXED || h->precision == RICMRCC_MIXED;
   for (int i = 0; i < n_steps && !div; ++i) TRY(iterate(h, o, false, mixed, &conv, &div));
@@ -1433,6 +1439,24 @@ int ricmrcc_tune(ricmrcc_t* h, int precision, int reps, ricmrcc_tuning* out) {
   res.chosen = bi;
   TRY(set_rule(h, cand[bi]));
   if (out) *out = res;
+  return leave(h);
+}
+
+int ricmrcc_get_amplitudes_dev(ricmrcc_t* h, double* T1, double* T2) {
+  if (!h || !T1 || !T2) return fail(h, RICMRCC_EINVAL, "null pointer");
+  TRY(enter(h));
+  launch_gather(T1, h->T + h->n2g, h->pack1, nullptr, h->t1_size, h->s);
+  launch_gather(T2, h->T, h->pack2, nullptr, h->t2_size, h->s);
+  CK(cudaPeekAtLastError());
+  return leave(h);
+}
+
+int ricmrcc_set_amplitudes_dev(ricmrcc_t* h, const double* T1, const double* T2) {
+  if (!h || !T1 || !T2) return fail(h, RICMRCC_EINVAL, "null pointer");
+  h->solved = false;
+  TRY(enter(h));
+  scatter_amplitudes(h, T1, T2);
+  CK(cudaPeekAtLastError());
   return leave(h);
 }
 

@@ -363,7 +363,13 @@ int ricmrcc_batch_step(ricmrcc_batch_t* b, const ricmrcc_opts* opts, int n_steps
   const std::vector<char> all(b->count, 1);
   std::vector<char> conv(b->count, 0), div(b->count, 0);
   if (restart)
-    for (ricmrcc_t* h : b->inst) reset_iteration_state(h);
+    for (ricmrcc_t* h : b->inst) {
+      // back to the initial guess T = 0 with an empty DIIS history
+      reset_iteration_state(h);
+      BCK(cudaMemsetAsync(h->T, 0, sizeof(double) * h->ng, h->s));
+      BCK(cudaStreamSynchronize(h->s));
+      h->solved = false;
+    }
   bool diverged = false;
   for (int k = 0; k < n_steps && !diverged; ++k) {
     TRY(batch_iterate(b, std::vector<ricmrcc_opts>(b->count, o), all, all, mixed, false, conv, div));
