@@ -104,6 +104,7 @@ typedef struct {
   int converged;      /* 1 if both thresholds were met */
   int fp64_iterations;
   int mixed_iterations;
+  int diverged;       /* 1 if the iteration produced non-finite numbers */
   double energy;      /* E = E0 + Hbar_0 at the returned amplitudes */
   double e0;          /* reference energy <Psi0|H|Psi0> */
   double max_dt;      /* last max |t_new - t| */
@@ -404,6 +405,76 @@ typedef struct {
   int64_t kernel_launches; /* kernel launches of one batch residual graph */
 } ricmrcc_batch_info_t;
 RICMRCC_API int ricmrcc_batch_info(const ricmrcc_batch_t* b, ricmrcc_batch_info_t* out);
+
+/* ---- Density-fitted particle-particle ladder -------------------------------
+ *
+ * The linear vvvv term of the doubles residual (Sec. 2.2; the contraction
+ * Sec. 4.3 names rate-limiting), with the integrals rebuilt from the
+ * density-fitting factor inside the call:
+ *   R^{ab}_{kl} += sum_{e,f virtual} (ae|bf) T^{ef}_{kl},  (ae|bf) = sum_Q B[Q][a][e] B[Q][b][f]
+ * for all hole pairs (k, l) (core and active: n_hole = n_core + n_act) and
+ * virtual a, b.  For systems whose integral tensor does not fit in memory
+ * (v^4 numbers): the integrals exist only one slab of pairs (a, b) at a time.
+ * Arithmetic: split-precision BF16 products (hi*hi + hi*lo + lo*hi, about 16
+ * significant bits per operand) with FP32 accumulation on the tcgen05 tensor
+ * cores, both for the integral rebuild and for the ladder; R accumulates in
+ * FP64.  The amplitudes must be pair-symmetric, T^{ef}_{kl} = T^{fe}_{lk}
+ * (Eq. spinfree-perm-sym); the work uses the (e,f)-symmetric and
+ * -antisymmetric parts, a quarter of the unpacked products.
+ *
+ * Layouts (row-major FP64): Bvv[n_aux][n_virt][n_virt] (the virtual-virtual
+ * block of ricmrcc_set_integrals' B, symmetric in the orbital pair);
+ * T and R [n_hole][n_hole][n_virt][n_virt], element [k][l][e][f] = T^{ef}_{kl}.
+ * The handle owns its device workspace (ricmrcc_ladder_info reports it;
+ * ENOMEM at create if it does not fit). */
+typedef struct ricmrcc_ladder ricmrcc_ladder_t;
+typedef struct {
+  int slabs;                      /* slabs of pairs (a, b) per application */
+  int64_t slab_rows;              /* largest slab (pairs a <= b) */
+  double rebuild_flops;           /* algorithmic: 2 n_aux per integral (ae|bf), a <= b: n_aux v^3 (v+1) */
+  double ladder_flops;            /* algorithmic, symmetric/antisymmetric packed products */
+  double rebuild_flops_executed;  /* BF16 tensor-core FLOPs issued (3 products, padding) */
+  double ladder_flops_executed;
+  double workspace_bytes;
+  /* milliseconds of the last application, per phase (CUDA events on the
+   * handle's stream; filled by ricmrcc_ladder_finish) */
+  double ms_pack, ms_rebuild, ms_symmetrise, ms_ladder, ms_unpack;
+} ricmrcc_ladder_info_t;
+
+/* n_hole, n_virt, n_aux >= 1; slab_rows = largest number of pairs (a <= b)
+ * per slab (0: 16384).  Uses the current CUDA device.  Errors: EINVAL,
+ * ENOMEM, ENOTSUP (no tensor-map support), ECUDA. */
+RICMRCC_API int ricmrcc_ladder_create(int n_hole, int n_virt, int n_aux, int64_t slab_rows,
+                                      ricmrcc_ladder_t** out);
+RICMRCC_API void ricmrcc_ladder_destroy(ricmrcc_ladder_t* L);
+RICMRCC_API const char* ricmrcc_ladder_last_error(const ricmrcc_ladder_t* L);
+/* Stream the calls are ordered after and before (NULL = legacy default). */
+RICMRCC_API int ricmrcc_ladder_set_stream(ricmrcc_ladder_t* L, void* stream);
+/* Pack the factor (kept until the next call).  Device pointer; enqueued. */
+RICMRCC_API int ricmrcc_ladder_set_factor_dev(ricmrcc_ladder_t* L, const double* Bvv);
+/* R += ladder(T).  Device pointers; enqueued: ricmrcc_ladder_finish waits
+ * for it and reports its status.  Errors: ESTATE (no factor), EINVAL. */
+RICMRCC_API int ricmrcc_ladder_apply_dev(ricmrcc_ladder_t* L, const double* T, double* R);
+/* Wait for the enqueued work; out (nullable) receives the sizes and the
+ * phase times of the last application.  Returns ECUDA if a tensor-core
+ * pipeline wait timed out (the kernels stopped; the context stays usable). */
+RICMRCC_API int ricmrcc_ladder_finish(ricmrcc_ladder_t* L, ricmrcc_ladder_info_t* out);
+/* Sizes and algorithmic work (no waiting). */
+RICMRCC_API int ricmrcc_ladder_info(ricmrcc_ladder_t* L, ricmrcc_ladder_info_t* out);
+/* Host-pointer variants (copy in and out; blocking). */
+RICMRCC_API int ricmrcc_ladder_set_factor(ricmrcc_ladder_t* L, const double* Bvv);
+RICMRCC_API int ricmrcc_ladder_apply(ricmrcc_ladder_t* L, const double* T, double* R);
+
+/* Time bound of every wait inside the tensor-core kernels (seconds, > 0;
+ * default 4).  A wait that runs out sets the call's error status (ECUDA,
+ * "tensor-core pipeline wait timed out"); the kernels stop after their
+ * copies and MMAs in flight have landed, so the context stays usable.
+ * stall_test != 0 makes every tensor-core kernel launched afterwards first
+ * wait on a barrier that nothing completes, so that wait runs out after
+ * `seconds`: a test of that error path without any fault (0 for normal
+ * work).  Applies to kernels launched afterwards on the current device; call
+ * it outside stream capture. */
+RICMRCC_API int ricmrcc_set_wait_limit(double seconds, int stall_test);
 
 /* Allocation-free eigensolver for one symmetric block (no counterpart in the
  * paper; it is the eigen-step of ricmrcc_semicanonicalize offered on its own).

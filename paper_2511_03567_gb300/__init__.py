@@ -42,7 +42,7 @@ class Opts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("fp64_iterations", ctypes.c_int), ("mixed_iterations", ctypes.c_int),
-                ("energy", ctypes.c_double), ("e0", ctypes.c_double),
+                ("diverged", ctypes.c_int), ("energy", ctypes.c_double), ("e0", ctypes.c_double),
                 ("max_dt", ctypes.c_double), ("seconds", ctypes.c_double)]
 
 
@@ -75,6 +75,17 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("waves", ctypes.c_int), ("grouped_launches", ctypes.c_int64),
                 ("tc_contractions", ctypes.c_int64), ("flops", ctypes.c_double),
                 ("tc_flops", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+class LadderInfo(ctypes.Structure):
+    _fields_ = [("slabs", ctypes.c_int), ("slab_rows", ctypes.c_int64), ("rebuild_flops", ctypes.c_double),
+                ("ladder_flops", ctypes.c_double), ("rebuild_flops_executed", ctypes.c_double),
+                ("ladder_flops_executed", ctypes.c_double), ("workspace_bytes", ctypes.c_double),
+                ("ms_pack", ctypes.c_double), ("ms_rebuild", ctypes.c_double), ("ms_symmetrise", ctypes.c_double),
+                ("ms_ladder", ctypes.c_double), ("ms_unpack", ctypes.c_double)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class RicMrccError(RuntimeError):
@@ -132,6 +143,18 @@ def load_library():
                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, vp],
                                 ctypes.c_int),
         "ricmrcc_block_eigh_noalloc": ([vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "ricmrcc_ladder_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(vp)],
+                                  ctypes.c_int),
+        "ricmrcc_ladder_destroy": ([vp], None),
+        "ricmrcc_ladder_last_error": ([vp], ctypes.c_char_p),
+        "ricmrcc_ladder_set_stream": ([vp, vp], ctypes.c_int),
+        "ricmrcc_ladder_set_factor_dev": ([vp, vp], ctypes.c_int),
+        "ricmrcc_ladder_apply_dev": ([vp, vp, vp], ctypes.c_int),
+        "ricmrcc_ladder_finish": ([vp, ctypes.POINTER(LadderInfo)], ctypes.c_int),
+        "ricmrcc_ladder_info": ([vp, ctypes.POINTER(LadderInfo)], ctypes.c_int),
+        "ricmrcc_ladder_set_factor": ([vp, vp], ctypes.c_int),
+        "ricmrcc_ladder_apply": ([vp, vp, vp], ctypes.c_int),
+        "ricmrcc_set_wait_limit": ([ctypes.c_double, ctypes.c_int], ctypes.c_int),
         "ricmrcc_get_residual": ([vp, vp, vp], ctypes.c_int),
         "ricmrcc_set_tile_rule": ([vp, ctypes.POINTER(TileRule)], ctypes.c_int),
         "ricmrcc_get_tile_rule": ([vp, ctypes.POINTER(TileRule)], ctypes.c_int),
@@ -494,6 +517,77 @@ class RicMrccBatch:
         return {"waves": i.waves, "grouped_launches": i.grouped_launches,
                 "tc_contractions": i.tc_contractions, "flops": i.flops, "tc_flops": i.tc_flops,
                 "kernel_launches": i.kernel_launches}
+
+
+class Ladder:
+    """Density-fitted particle-particle ladder (ricmrcc_ladder_*):
+    R[k,l,a,b] += sum_{e,f} (ae|bf) T[k,l,e,f] with (ae|bf) = sum_Q B[Q,a,e] B[Q,b,f]."""
+
+    def __init__(self, n_hole, n_virt, n_aux, slab_rows=0):
+        self.lib = load_library()
+        self.dims = (n_hole, n_virt, n_aux)
+        L = ctypes.c_void_p()
+        rc = self.lib.ricmrcc_ladder_create(n_hole, n_virt, n_aux, int(slab_rows), ctypes.byref(L))
+        if rc != OK:
+            raise RicMrccError(rc, "ricmrcc_ladder_create failed")
+        self.L = L
+
+    def _check(self, rc, allow=(OK,)):
+        if rc not in allow:
+            raise RicMrccError(rc, self.lib.ricmrcc_ladder_last_error(self.L).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "L", None):
+            self.lib.ricmrcc_ladder_destroy(self.L)
+            self.L = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr):
+        self._check(self.lib.ricmrcc_ladder_set_stream(self.L, stream_ptr))
+
+    def set_factor(self, Bvv):
+        """Bvv [n_aux, n_virt, n_virt]: a CUDA float64 tensor or a host array."""
+        if hasattr(Bvv, "is_cuda") and Bvv.is_cuda:
+            self._check(self.lib.ricmrcc_ladder_set_factor_dev(self.L, _ptr(Bvv)))
+        else:
+            b = _host(Bvv)
+            self._check(self.lib.ricmrcc_ladder_set_factor(self.L, _ptr(b)))
+
+    def apply_dev(self, T, R):
+        """R += ladder(T) for CUDA float64 tensors [n_hole, n_hole, n_virt, n_virt] (enqueued)."""
+        self._check(self.lib.ricmrcc_ladder_apply_dev(self.L, _ptr(T), _ptr(R)))
+
+    def finish(self):
+        """Wait for the enqueued work; sizes and phase times of the last application."""
+        info = LadderInfo()
+        self._check(self.lib.ricmrcc_ladder_finish(self.L, ctypes.byref(info)))
+        return info.as_dict()
+
+    def apply(self, T, R):
+        """Host arrays: returns R + ladder(T) (R is not modified)."""
+        t = _host(T)
+        r = _host(R).copy()
+        self._check(self.lib.ricmrcc_ladder_apply(self.L, _ptr(t), _ptr(r)))
+        return r
+
+    def info(self):
+        info = LadderInfo()
+        self._check(self.lib.ricmrcc_ladder_info(self.L, ctypes.byref(info)))
+        return info.as_dict()
+
+
+def set_wait_limit(seconds, stall_test=False):
+    """Time bound of every wait inside the tensor-core kernels (default 4 s);
+    stall_test makes each kernel wait once on a barrier nothing completes."""
+    rc = load_library().ricmrcc_set_wait_limit(float(seconds), int(bool(stall_test)))
+    if rc != OK:
+        raise RicMrccError(rc, "ricmrcc_set_wait_limit failed")
 
 
 def header_symbols(header=None):

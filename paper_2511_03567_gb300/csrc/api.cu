@@ -685,7 +685,12 @@ int check_tc_error(ricmrcc_t* h) {
   int e = 0;
   CK(cudaMemcpyAsync(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
   CK(cudaStreamSynchronize(h->s));
-  if (e) return fail(h, RICMRCC_ECUDA, "tensor-core pipeline wait timed out");
+  if (e) {
+    // clear the flag: the kernels that gave up have returned, the context is usable
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return fail(h, RICMRCC_ECUDA, "tensor-core pipeline wait timed out");
+  }
   return RICMRCC_OK;
 }
 
@@ -956,6 +961,17 @@ int ricmrcc_residual_dev(ricmrcc_t* h, const double* T1, const double* T2, doubl
   return residual_impl(h, T1, T2, R1, R2, E_out, true);
 }
 
+int ricmrcc_set_wait_limit(double seconds, int stall_test) {
+  if (!(seconds > 0.0) || !(seconds < 1e6)) return RICMRCC_EINVAL;
+  const uint64_t ns = (uint64_t)(seconds * 1e9) > 0 ? (uint64_t)(seconds * 1e9) : 1;
+  const int st = stall_test ? 1 : 0;
+  if (tc_set_wait_ns(ns, st) != 0 || ladder_set_wait_ns(ns, st) != 0) {
+    cudaGetLastError();
+    return RICMRCC_ECUDA;
+  }
+  return RICMRCC_OK;
+}
+
 int ricmrcc_opts_default(ricmrcc_opts* o) {
   if (!o) return RICMRCC_EINVAL;
   o->s = 0.5;
@@ -1123,6 +1139,7 @@ int ricmrcc_solve(ricmrcc_t* h, double s, const ricmrcc_opts* opts, double* E_ou
     stats->converged = converged ? 1 : 0;
     stats->fp64_iterations = it - n_mixed;
     stats->mixed_iterations = n_mixed;
+    stats->diverged = diverged ? 1 : 0;
     stats->energy = h->last_E;
     stats->e0 = h->E0;
     stats->max_dt = h->last_dt;

@@ -436,6 +436,7 @@ static int batch_solve_impl(ricmrcc_batch_t* b, const ricmrcc_opts* opts, const 
       stats[i].converged = done_conv[i] ? 1 : 0;
       stats[i].fp64_iterations = iters[i] - n_mixed[i];
       stats[i].mixed_iterations = n_mixed[i];
+      stats[i].diverged = done_div[i] ? 1 : 0;
       stats[i].energy = h->last_E;
       stats[i].e0 = h->E0;
       stats[i].max_dt = h->last_dt;

@@ -1,0 +1,825 @@
+// Density-fitted particle-particle ladder on the tcgen05 tensor cores.
+//
+//   R^{ab}_{kl} += sum_{e,f in V} (ae|bf) T^{ef}_{kl},   (ae|bf) = sum_Q B_Qae B_Qbf
+//
+// for every hole pair (k, l) (core or active) and virtual a, b: the linear
+// vvvv term of the doubles residual of Sec. 2.2, the contraction Sec. 4.3
+// names rate-limiting.  The integrals are rebuilt from the density-fitting
+// factor inside the call, slab by slab, and never stored whole (they would
+// take v^4 numbers).
+//
+// With T pair-symmetric (T^{ef}_{kl} = T^{fe}_{lk}) the contraction splits
+// into a part symmetric and a part antisymmetric in (e, f), which is also
+// symmetric / antisymmetric in (a, b) and in (k, l):
+//   S^{ab}_{ef} = (V^{ab}_{ef} + V^{ab}_{fe}) / 2,  A^{ab}_{ef} = (V^{ab}_{ef} - V^{ab}_{fe}) / 2,
+//   V^{ab}_{ef} = (ae|bf),
+//   R+^{ab}_{kl} = sum_{e<=f} S^{ab}_{ef} Tp^{ef}_{kl},  Tp = T^{ef}_{kl} + T^{fe}_{kl} (e < f), T^{ee}_{kl}
+//   R-^{ab}_{kl} = sum_{e<f}  A^{ab}_{ef} Tm^{ef}_{kl},  Tm = T^{ef}_{kl} - T^{fe}_{kl}
+//   R^{ab}_{kl}  = R+^{ab}_{kl} + R-^{ab}_{kl}
+// so only a <= b, e <= f, k <= l (and the strict triangles for the minus
+// part) are formed: a quarter of the unpacked work.
+//
+// Per slab of pairs (a, b) with a in [a0, a1), b >= a:
+//   1. rebuild GEMM  V[(a,e)][(b,f)] = sum_Q Bp[(a,e)][Q] Bp[(b,f)][Q]   (rows a in the slab, columns b >= a0)
+//   2. symmetrise    W+[(ab)][(ef)] = S, W-[(ab)][(ef)] = A               (split into BF16 hi / lo)
+//   3. ladder GEMMs  D+[(kl)][(ab)] = sum_(ef) Tp[(kl)][(ef)] W+[(ab)][(ef)], D- likewise
+//   4. unpack        R[k][l][a][b] += D+ +- D-
+// Both GEMMs run in one persistent tcgen05 kernel (k_gemm3): split-precision
+// BF16 operands [hi | lo] (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM),
+// 128 x 256 output tiles, TMA-fed two-stage shared-memory ring, two TMEM
+// accumulators so that a tile's write-out overlaps the next tile's MMAs.
+// Every wait is bounded (tc_ptx.h); a timeout sets the error flag, which the
+// host reads after the call.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ricmrcc.h"
+#include "tc_ptx.h"
+
+using namespace tcptx;
+
+namespace {
+
+constexpr int LBM = 128, LBN = 256, LBK = 64, LSTAGES = 2;
+constexpr uint32_t kLA = LBM * LBK * 2;            // 16 KB: one 128 x 64 BF16 tile
+constexpr uint32_t kLB = LBN * LBK * 2;            // 32 KB: one 256 x 64 BF16 tile
+constexpr uint32_t kLStage = 2 * (kLA + kLB);      // A_hi | A_lo | B_hi | B_lo
+constexpr int kLEpi = 4;                           // epilogue warps (one per TMEM lane quarter)
+constexpr int kLThreads = 64 + 32 * kLEpi;
+
+__device__ __forceinline__ uint32_t idesc_128x256() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(LBN >> 3) << 17) | ((uint32_t)(LBM >> 4) << 24);
+}
+
+struct TileMap {
+  int mt, nt, group;
+  __device__ __forceinline__ void at(int64_t t, int* mi, int* ni) const {
+    // groups of `group` n tiles, n fastest inside a group, then m: the CTAs of
+    // one wave share a few A and B tiles through L2
+    const int64_t per = (int64_t)group * mt;
+    const int g = (int)(t / per);
+    const int r = (int)(t - (int64_t)g * per);
+    const int gw = min(group, nt - g * group);
+    *mi = r / gw;
+    *ni = g * group + r % gw;
+  }
+};
+
+// D[m][n] = sum_k A[ya0 + m][k] B[yb0 + n][k] for m < M, n < N (FP32, row-major,
+// ldd).  A and B are packed [hi | lo] BF16 rows of 2 * kt * 64 elements.
+__global__ void __launch_bounds__(kLThreads, 1)
+    k_gemm3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int ya0, int yb0,
+            int64_t M, int64_t N, int kt, float* __restrict__ D, int64_t ldd, TileMap tm, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  float* etile = reinterpret_cast<float*>(smem + LSTAGES * kLStage);  // kLEpi x 32 x 33
+  uint64_t* full = reinterpret_cast<uint64_t*>(etile + kLEpi * 32 * 33);
+  uint64_t* empty = full + LSTAGES;
+  uint64_t* tfull = empty + LSTAGES;  // [2]
+  uint64_t* tempty = tfull + 2;       // [2]
+  uint64_t* fin = tempty + 2;
+  uint64_t* never = fin + 1;  // completed by nothing (error-path test)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t total = (int64_t)tm.mt * tm.nt;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < LSTAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);
+      mbar_init(tempty + b, kLEpi);
+    }
+    mbar_init(fin, 1);
+    mbar_init(never, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * LBN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer: stage st, phase ph of the ring; load i goes to stage
+    // i % LSTAGES with phase (i / LSTAGES) & 1
+    uint32_t st = 0, ph = 0;
+    int64_t issued = 0;
+    bool ok = true;
+    const uint32_t s0 = smem_u32(smem), full0 = smem_u32(full);
+    const int lo_x = kt * LBK;
+    for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      int mi, ni;
+      tm.at(t, &mi, &ni);
+      const int ya = ya0 + mi * LBM, yb = yb0 + ni * LBN;
+      for (int k = 0; k < kt; ++k) {
+        if (issued >= LSTAGES && !mbar_wait(empty + st, ph ^ 1u, err)) {
+          ok = false;
+          break;
+        }
+        const uint32_t fb = full0 + st * 8;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kLStage) : "memory");
+        const uint32_t sb = s0 + st * kLStage;
+        const int x = k * LBK;
+        tma_load_2d_u(sb, &tmA, x, ya, fb);
+        tma_load_2d_u(sb + kLA, &tmA, lo_x + x, ya, fb);
+        tma_load_2d_u(sb + 2 * kLA, &tmB, x, yb, fb);
+        tma_load_2d_u(sb + 2 * kLA + kLB, &tmB, lo_x + x, yb, fb);
+        ++issued;
+        if (++st == LSTAGES) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    // copies still in flight land before the CTA exits
+    for (int64_t i = issued > LSTAGES ? issued - LSTAGES : 0; i < issued; ++i)
+      mbar_wait_drain(full + i % LSTAGES, (uint32_t)(i / LSTAGES) & 1u, err);
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: per K block hi*hi, hi*lo, lo*hi into accumulator c & 1
+    uint32_t st = 0, ph = 0, c = 0;
+    bool ok = true;
+    const uint64_t desc0 = smem_desc(smem_u32(smem));
+    const uint32_t empty0 = smem_u32(empty);
+    const uint32_t idesc = idesc_128x256();
+    ok = stall_test_wait(never, err);
+    for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++c) {
+      const uint32_t b = c & 1;
+      if (c >= 2 && !mbar_wait(tempty + b, ((c >> 1) - 1) & 1, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t acc = tmem + b * LBN;
+      for (int k = 0; k < kt; ++k) {
+        if (!mbar_wait(full + st, ph, err)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t ahi = desc0 + st * (kLStage >> 4), alo = ahi + (kLA >> 4);
+        const uint64_t bhi = ahi + ((2 * kLA) >> 4), blo = bhi + (kLB >> 4);
+        mma_ktile(acc, ahi, bhi, idesc, k > 0 ? 1u : 0u);
+        mma_ktile(acc, ahi, blo, idesc, 1u);
+        mma_ktile(acc, alo, bhi, idesc, 1u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         empty0 + st * 8)
+                     : "memory");
+        if (++st == LSTAGES) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+      if (!ok) break;
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(tfull + b))
+                   : "memory");
+    }
+    // completion of everything issued (also after a timeout)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(fin))
+                 : "memory");
+  } else if (warp >= 2) {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (output rows) in
+    // 32-column chunks and writes them through a 32 x 33 shared tile, one
+    // output row per store instruction (lanes along columns)
+    const int q = warp & 3;
+    float* tile = etile + (warp - 2) * 32 * 33;
+    uint32_t c = 0;
+    for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++c) {
+      int mi, ni;
+      tm.at(t, &mi, &ni);
+      const uint32_t b = c & 1;
+      const bool ready = __all_sync(0xffffffffu, mbar_wait(tfull + b, (c >> 1) & 1, err));
+      if (!ready) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t m0 = (int64_t)mi * LBM + q * 32;
+#pragma unroll 1
+      for (int ch = 0; ch < LBN / 32; ++ch) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + b * LBN + (uint32_t)(ch * 32);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+              "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+              "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+              "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        const int64_t n = (int64_t)ni * LBN + ch * 32 + lane;
+        if (n < N) {
+#pragma unroll 4
+          for (int rr = 0; rr < 32; ++rr) {
+            const int64_t m = m0 + rr;
+            if (m < M) D[m * ldd + n] = tile[rr * 33 + lane];
+          }
+        }
+        __syncwarp();
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty + b)) : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    mbar_wait_drain(fin, 0, err);  // every issued MMA has completed
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * LBN));
+  }
+}
+
+size_t gemm3_smem_bytes() {
+  return 1024 + (size_t)LSTAGES * kLStage + kLEpi * 32 * 33 * 4 + (2 * LSTAGES + 6) * 8 + 16;
+}
+
+// ---------------------------------------------------------------------------
+// Packing and element-wise kernels (CUDA cores)
+
+__device__ __forceinline__ void store_split(__nv_bfloat16* row, int64_t Kp, int64_t c, float x) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  row[c] = h;
+  row[Kp + c] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+// Bp[(a vp + e)][Q] = B[Q][a][e] as [hi | lo] rows (Q padded to Kp; rows
+// e >= v stay zero from the buffer's initial clear).  Tiles of 32 (a, e) x 64 Q
+// are read with lanes along (a, e) and written with lanes along Q.
+__global__ void __launch_bounds__(256)
+    k_pack_factor(const double* __restrict__ B, int X, int v, int vp, int64_t Kp, __nv_bfloat16* __restrict__ out) {
+  __shared__ float tile[64][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t vv = (int64_t)v * v, nst = (vv + 31) / 32, nqt = Kp / 64;
+  for (int64_t t = blockIdx.x; t < nst * nqt; t += gridDim.x) {
+    const int64_t s0 = (t / nqt) * 32, q0 = (t % nqt) * 64;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int qq = warp + 8 * j;
+      const int64_t Q = q0 + qq, s = s0 + lane;
+      tile[qq][lane] = (Q < X && s < vv) ? (float)B[Q * vv + s] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int rr = warp + 8 * j;
+      const int64_t s = s0 + rr;
+      if (s < vv) {
+        const int64_t a = s / v, e = s - a * v;
+        __nv_bfloat162 hi, lo;
+        split_bf16(tile[2 * lane][rr], tile[2 * lane + 1][rr], &hi, &lo);
+        __nv_bfloat162* row = reinterpret_cast<__nv_bfloat162*>(out + (a * vp + e) * 2 * Kp);
+        const int64_t cc = (q0 >> 1) + lane;
+        row[cc] = hi;
+        row[(Kp >> 1) + cc] = lo;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int64_t tri_index(int64_t n, int64_t i, int64_t j, int strict) {
+  // position of (i, j), i <= j (i < j when strict), in the row-major packed
+  // upper triangle of an n x n matrix
+  return strict ? i * (2 * n - i - 1) / 2 + (j - i - 1) : i * (2 * n - i + 1) / 2 + (j - i);
+}
+
+// Pairs (i, j) of a packed triangle from their index (host builds the 32 x 32
+// tile pairs; this inverts a pair index of the hole pairs).
+__device__ __forceinline__ void tri_pair(int64_t n, int64_t p, int strict, int* i, int* j) {
+  // smallest i with tri_index(n, i, i + strict, strict) > p, minus one
+  int lo = 0, hi = (int)n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tri_index(n, mid, mid + strict, strict) <= p) lo = mid;
+    else hi = mid - 1;
+  }
+  *i = lo;
+  *j = (int)(p - tri_index(n, lo, lo + strict, strict)) + lo + strict;
+}
+
+// Tp / Tm rows: for each hole pair (k <= l, or k < l for the minus part) the
+// packed triangle of T[k][l] +- its transpose (diagonal once for plus).
+// Work items: (pair, 32 x 32 tile pair (E, F), F >= E); both tiles are read
+// with lanes along rows, combined through shared memory.
+__global__ void __launch_bounds__(256)
+    k_pack_amplitudes(const double* __restrict__ T, int nh, int v, int strict, int64_t npairs, int64_t Kp,
+                      const int2* __restrict__ tiles, int ntiles, __nv_bfloat16* __restrict__ out) {
+  __shared__ float t1[32][33], t2[32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t vv = (int64_t)v * v;
+  for (int64_t it = blockIdx.x; it < npairs * ntiles; it += gridDim.x) {
+    const int64_t p = it / ntiles;
+    const int2 EF = tiles[it - p * ntiles];
+    int k, l;
+    tri_pair(nh, p, strict, &k, &l);
+    const double* M = T + ((int64_t)k * nh + l) * vv;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = warp + 8 * j;
+      const int e1 = EF.x + i, f1 = EF.y + lane;
+      t1[i][lane] = (e1 < v && f1 < v) ? (float)M[(int64_t)e1 * v + f1] : 0.f;
+      const int e2 = EF.y + i, f2 = EF.x + lane;
+      t2[i][lane] = (e2 < v && f2 < v) ? (float)M[(int64_t)e2 * v + f2] : 0.f;
+    }
+    __syncthreads();
+    __nv_bfloat16* row = out + p * 2 * Kp;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = warp + 8 * j;
+      const int e = EF.x + i, f = EF.y + lane;
+      if (e < v && f < v && (strict ? f > e : f >= e)) {
+        const float x = strict ? t1[i][lane] - t2[lane][i] : (f == e ? t1[i][lane] : t1[i][lane] + t2[lane][i]);
+        store_split(row, Kp, tri_index(v, e, f, strict), x);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Row of the slab's pair (a, b), a in [a0, a1), b >= a (b > a when strict).
+__device__ __forceinline__ int64_t slab_row(int v, int a0, int a, int b, int strict) {
+  // sum over a' in [a0, a) of (v - a' - strict), plus b - a - strict
+  const int64_t n = a - a0;
+  return n * (2 * (int64_t)(v - strict) - a0 - a + 1) / 2 + (b - a - strict);
+}
+
+// W+ / W- rows of the slab from the rebuilt integrals V (FP32, rows (a - a0) vp
+// + e, columns (b - a0) vp + f): S = (V^{ab}_{ef} + V^{ab}_{fe}) / 2 for
+// e <= f, A = (V^{ab}_{ef} - V^{ab}_{fe}) / 2 for e < f (a < b).
+__global__ void __launch_bounds__(256)
+    k_symmetrise(const float* __restrict__ V, int64_t ldv, int v, int vp, int a0, int a1, int64_t npairs,
+                 const int2* __restrict__ tiles, int ntiles, int64_t Kp, int64_t Km, __nv_bfloat16* __restrict__ Wp,
+                 __nv_bfloat16* __restrict__ Wm) {
+  __shared__ float t1[32][33], t2[32][33];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t it = blockIdx.x; it < npairs * ntiles; it += gridDim.x) {
+    const int64_t p = it / ntiles;
+    const int2 EF = tiles[it - p * ntiles];
+    // pair p -> (a, b): rows of a' hold v - a' pairs
+    int a = a0;
+    int64_t base = 0;
+    while (base + (v - a) <= p) {
+      base += v - a;
+      ++a;
+    }
+    const int b = a + (int)(p - base);
+    const float* Vab = V + (int64_t)(a - a0) * vp * ldv + (int64_t)(b - a0) * vp;  // V^{ab}_{ef} = Vab[e ldv + f]
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = warp + 8 * j;
+      const int e1 = EF.x + i, f1 = EF.y + lane;
+      t1[i][lane] = (e1 < v && f1 < v) ? Vab[(int64_t)e1 * ldv + f1] : 0.f;
+      const int e2 = EF.y + i, f2 = EF.x + lane;
+      t2[i][lane] = (e2 < v && f2 < v) ? Vab[(int64_t)e2 * ldv + f2] : 0.f;
+    }
+    __syncthreads();
+    __nv_bfloat16* rp = Wp + slab_row(v, a0, a, b, 0) * 2 * Kp;
+    __nv_bfloat16* rm = b > a ? Wm + slab_row(v, a0, a, b, 1) * 2 * Km : nullptr;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int i = warp + 8 * j;
+      const int e = EF.x + i, f = EF.y + lane;
+      if (e < v && f < v && f >= e) {
+        const float x1 = t1[i][lane], x2 = t2[lane][i];  // V^{ab}_{ef}, V^{ab}_{fe}
+        store_split(rp, Kp, tri_index(v, e, f, 0), 0.5f * (x1 + x2));
+        if (rm && f > e) store_split(rm, Km, tri_index(v, e, f, 1), 0.5f * (x1 - x2));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// R[k][l][a][b] += D+[(kl)][(ab)] + sgn D-[(kl)][(ab)] for the pairs of the
+// slab (min(a, b) in [a0, a1)); sgn = -1 when exactly one of a > b, k > l.
+// Work items (k, l, a) with threads along b.
+__global__ void __launch_bounds__(256)
+    k_unpack(const float* __restrict__ Dp, const float* __restrict__ Dm, int64_t ldd, int nh, int v, int a0, int a1,
+             double* __restrict__ R) {
+  const int64_t na = v - a0, items = (int64_t)nh * nh * na;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int a = a0 + (int)(it % na);
+    const int64_t kl = it / na;
+    const int k = (int)(kl / nh), l = (int)(kl % nh);
+    const int kk = min(k, l), ll = max(k, l);
+    const int64_t pp = tri_index(nh, kk, ll, 0);
+    const int64_t pm = kk < ll ? tri_index(nh, kk, ll, 1) : -1;
+    const float* dp = Dp + pp * ldd;
+    const float* dm = pm >= 0 ? Dm + pm * ldd : nullptr;
+    const float ks = k < l ? 1.f : -1.f;
+    double* Rrow = R + (kl * v + a) * (int64_t)v;
+    const int bend = a < a1 ? v : a1;
+    for (int b = a0 + threadIdx.x; b < bend; b += blockDim.x) {
+      const int lo = min(a, b), hi = max(a, b);
+      float x = dp[slab_row(v, a0, lo, hi, 0)];
+      if (dm && lo < hi) x += (a < b ? ks : -ks) * dm[slab_row(v, a0, lo, hi, 1)];
+      Rrow[b] += (double)x;
+    }
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
+
+bool encode_fn() {
+  if (g_enc) return true;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess || !fn ||
+      q != cudaDriverEntryPointSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  g_enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return true;
+}
+
+// Tensor map of a packed [hi | lo] operand: rows of `inner` BF16, tiles of
+// 64 columns x box_rows rows, 128-byte swizzle (rows past `rows` read zero).
+bool packed_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, int box_rows) {
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(inner * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)LBK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return g_enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int64_t pad_to(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Handle
+
+struct ricmrcc_ladder {
+  int nh = 0, v = 0, X = 0, vp = 0, sms = 0;
+  int64_t kx = 0;                // padded n_aux (K of the rebuild GEMM)
+  int64_t nkp = 0, nkm = 0;      // hole pairs k <= l, k < l
+  int64_t nep = 0, nem = 0;      // virtual pairs e <= f, e < f
+  int64_t Kp = 0, Km = 0;        // padded K of the plus / minus ladder GEMMs
+  int64_t slab_rows = 0;         // max pairs (a, b) per slab
+  int64_t ldv = 0, ldd = 0;
+  std::vector<int> slabs;        // a0 of each slab, then v
+  cudaStream_t user = nullptr, s = nullptr;
+  cudaEvent_t ev_user = nullptr;
+  __nv_bfloat16 *Bp = nullptr, *Tp = nullptr, *Tm = nullptr, *Wp = nullptr, *Wm = nullptr;
+  float *V = nullptr, *Dp = nullptr, *Dm = nullptr;
+  int2* tiles = nullptr;         // 32 x 32 tile pairs (E, F), F >= E
+  int ntiles = 0;
+  int* d_err = nullptr;
+  bool have_factor = false;
+  std::vector<cudaEvent_t> ev;   // per slab: 5 boundaries (rebuild, symmetrise, ladder +, ladder -, unpack)
+  cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // amplitude packing
+  ricmrcc_ladder_info_t info{};
+  std::string err;
+};
+
+namespace {
+
+int lfail(ricmrcc_ladder_t* L, int code, const std::string& m) {
+  if (L) L->err = m;
+  return code;
+}
+
+#define LCK(call)                                                                  \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) return lfail(L, RICMRCC_ECUDA, cudaGetErrorString(e_)); \
+  } while (0)
+
+int launch_gemm3(ricmrcc_ladder_t* L, const CUtensorMap& ma, const CUtensorMap& mb, int ya0, int yb0, int64_t M,
+                 int64_t N, int kt, float* D, int64_t ldd) {
+  TileMap tm;
+  tm.mt = (int)((M + LBM - 1) / LBM);
+  tm.nt = (int)((N + LBN - 1) / LBN);
+  tm.group = std::min(tm.nt, 8);
+  const int64_t total = (int64_t)tm.mt * tm.nt;
+  if (total <= 0 || kt <= 0) return RICMRCC_OK;
+  const int grid = (int)std::min<int64_t>(total, L->sms);
+  k_gemm3<<<grid, kLThreads, gemm3_smem_bytes(), L->s>>>(ma, mb, ya0, yb0, M, N, kt, D, ldd, tm, L->d_err);
+  LCK(cudaGetLastError());
+  return RICMRCC_OK;
+}
+
+void free_all(ricmrcc_ladder_t* L) {
+  for (void* p : {(void*)L->Bp, (void*)L->Tp, (void*)L->Tm, (void*)L->Wp, (void*)L->Wm, (void*)L->V, (void*)L->Dp,
+                  (void*)L->Dm, (void*)L->tiles, (void*)L->d_err})
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : L->ev) cudaEventDestroy(e);
+  if (L->ev_t0) cudaEventDestroy(L->ev_t0);
+  if (L->ev_t1) cudaEventDestroy(L->ev_t1);
+  if (L->ev_user) cudaEventDestroy(L->ev_user);
+  if (L->s) cudaStreamDestroy(L->s);
+}
+
+int enter(ricmrcc_ladder_t* L) {
+  L->err.clear();
+  if (L->user) {
+    LCK(cudaEventRecord(L->ev_user, L->user));
+    LCK(cudaStreamWaitEvent(L->s, L->ev_user, 0));
+  }
+  return RICMRCC_OK;
+}
+int leave(ricmrcc_ladder_t* L) {
+  if (L->user) {
+    LCK(cudaEventRecord(L->ev_user, L->s));
+    LCK(cudaStreamWaitEvent(L->user, L->ev_user, 0));
+  }
+  return RICMRCC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ricmrcc_ladder_create(int n_hole, int n_virt, int n_aux, int64_t slab_rows, ricmrcc_ladder_t** out) {
+  if (!out) return RICMRCC_EINVAL;
+  *out = nullptr;
+  if (n_hole < 1 || n_virt < 1 || n_aux < 1 || slab_rows < 0) return RICMRCC_EINVAL;
+  if ((int64_t)n_virt * pad_to(n_virt, 8) >= (1ll << 31)) return RICMRCC_ENOTSUP;  // TMA row coordinates
+  if (!encode_fn()) return RICMRCC_ENOTSUP;
+  ricmrcc_ladder_t* L = new ricmrcc_ladder_t();
+  L->nh = n_hole;
+  L->v = n_virt;
+  L->X = n_aux;
+  L->vp = (int)pad_to(n_virt, 8);
+  L->kx = pad_to(n_aux, LBK);
+  L->nkp = (int64_t)n_hole * (n_hole + 1) / 2;
+  L->nkm = (int64_t)n_hole * (n_hole - 1) / 2;
+  L->nep = (int64_t)n_virt * (n_virt + 1) / 2;
+  L->nem = (int64_t)n_virt * (n_virt - 1) / 2;
+  L->Kp = pad_to(L->nep, LBK);
+  L->Km = pad_to(std::max<int64_t>(L->nem, 1), LBK);
+  const int64_t v = n_virt;
+  // slabs: consecutive a with at most slab_rows pairs (a, b >= a) each (one
+  // a at least)
+  const int64_t target = slab_rows > 0 ? slab_rows : 16384;
+  L->slab_rows = 0;
+  for (int a = 0; a < n_virt;) {
+    L->slabs.push_back(a);
+    int64_t rows = 0;
+    int b = a;
+    while (b < n_virt && (rows == 0 || rows + (v - b) <= target)) {
+      rows += v - b;
+      ++b;
+    }
+    L->slab_rows = std::max(L->slab_rows, rows);
+    a = b;
+  }
+  L->slabs.push_back(n_virt);
+  int64_t vrows = 0, vcols = 0;
+  for (size_t i = 0; i + 1 < L->slabs.size(); ++i) {
+    vrows = std::max<int64_t>(vrows, (int64_t)(L->slabs[i + 1] - L->slabs[i]) * L->vp);
+    vcols = std::max<int64_t>(vcols, (v - L->slabs[i]) * L->vp);
+  }
+  L->ldv = pad_to(vcols, 4);
+  L->ldd = pad_to(L->slab_rows, 4);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&L->sms, cudaDevAttrMultiProcessorCount, dev);
+  // 32 x 32 tile pairs of the v x v triangle
+  std::vector<int2> tp;
+  for (int E = 0; E < n_virt; E += 32)
+    for (int F = E; F < n_virt; F += 32) tp.push_back(make_int2(E, F));
+  L->ntiles = (int)tp.size();
+  bool ok = cudaStreamCreateWithFlags(&L->s, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&L->ev_user, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreate(&L->ev_t0) == cudaSuccess && cudaEventCreate(&L->ev_t1) == cudaSuccess;
+  const size_t nslab = L->slabs.size() - 1;
+  L->ev.assign(nslab * 6, nullptr);
+  for (auto& e : L->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+  auto alloc = [&](void** p, size_t bytes, bool clear) {
+    if (!ok) return;
+    ok = cudaMalloc(p, bytes) == cudaSuccess;
+    if (ok && clear) ok = cudaMemset(*p, 0, bytes) == cudaSuccess;
+  };
+  alloc((void**)&L->Bp, (size_t)v * L->vp * 2 * L->kx * 2, true);
+  alloc((void**)&L->Tp, (size_t)L->nkp * 2 * L->Kp * 2, true);
+  alloc((void**)&L->Tm, (size_t)std::max<int64_t>(L->nkm, 1) * 2 * L->Km * 2, true);
+  alloc((void**)&L->Wp, (size_t)L->slab_rows * 2 * L->Kp * 2, true);
+  alloc((void**)&L->Wm, (size_t)L->slab_rows * 2 * L->Km * 2, true);
+  alloc((void**)&L->V, (size_t)vrows * L->ldv * 4, false);
+  alloc((void**)&L->Dp, (size_t)L->nkp * L->ldd * 4, false);
+  alloc((void**)&L->Dm, (size_t)std::max<int64_t>(L->nkm, 1) * L->ldd * 4, false);
+  alloc((void**)&L->tiles, tp.size() * sizeof(int2), false);
+  alloc((void**)&L->d_err, sizeof(int), true);
+  if (ok) ok = cudaMemcpy(L->tiles, tp.data(), tp.size() * sizeof(int2), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok)
+    ok = cudaFuncSetAttribute(k_gemm3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm3_smem_bytes()) ==
+         cudaSuccess;
+  if (!ok) {
+    const cudaError_t e = cudaGetLastError();
+    free_all(L);
+    delete L;
+    return e == cudaErrorMemoryAllocation ? RICMRCC_ENOMEM : RICMRCC_ECUDA;
+  }
+  // algorithmic work of one application
+  ricmrcc_ladder_info_t& in = L->info;
+  in.slabs = (int)nslab;
+  in.slab_rows = L->slab_rows;
+  in.rebuild_flops = (double)n_aux * (double)v * (double)v * (double)v * (double)(v + 1);  // 2 X (v^2 (v+1)/2) v
+  in.ladder_flops = 2.0 * ((double)L->nkp * L->nep * L->nep + (double)L->nkm * L->nem * L->nem);
+  double reb = 0.0;
+  for (size_t i = 0; i < nslab; ++i)
+    reb += 2.0 * (double)(L->slabs[i + 1] - L->slabs[i]) * L->vp * (double)(v - L->slabs[i]) * L->vp * L->kx;
+  in.rebuild_flops_executed = 3.0 * reb;
+  in.ladder_flops_executed = 3.0 * 2.0 *
+                             ((double)pad_to(L->nkp, LBM) * (double)L->Kp * (double)L->nep +
+                              (double)pad_to(std::max<int64_t>(L->nkm, 1), LBM) * (double)L->Km * (double)L->nem);
+  in.workspace_bytes = (double)v * L->vp * 2 * L->kx * 2 + (double)L->nkp * 2 * L->Kp * 2 +
+                       (double)L->nkm * 2 * L->Km * 2 + (double)L->slab_rows * 2 * (L->Kp + L->Km) * 2 +
+                       (double)vrows * L->ldv * 4 + (double)(L->nkp + L->nkm) * L->ldd * 4;
+  *out = L;
+  return RICMRCC_OK;
+}
+
+void ricmrcc_ladder_destroy(ricmrcc_ladder_t* L) {
+  if (!L) return;
+  if (L->s) cudaStreamSynchronize(L->s);
+  free_all(L);
+  delete L;
+}
+
+const char* ricmrcc_ladder_last_error(const ricmrcc_ladder_t* L) { return L ? L->err.c_str() : ""; }
+
+int ricmrcc_ladder_set_stream(ricmrcc_ladder_t* L, void* stream) {
+  if (!L) return RICMRCC_EINVAL;
+  L->user = static_cast<cudaStream_t>(stream);
+  return RICMRCC_OK;
+}
+
+int ricmrcc_ladder_set_factor_dev(ricmrcc_ladder_t* L, const double* Bvv) {
+  if (!L) return RICMRCC_EINVAL;
+  if (!Bvv) return lfail(L, RICMRCC_EINVAL, "null pointer");
+  int rc = enter(L);
+  if (rc) return rc;
+  const int64_t tiles = ((int64_t)L->v * L->v + 31) / 32 * (L->kx / 64);
+  k_pack_factor<<<(int)std::min<int64_t>(tiles, (int64_t)L->sms * 8), 256, 0, L->s>>>(Bvv, L->X, L->v, L->vp, L->kx,
+                                                                                        L->Bp);
+  LCK(cudaGetLastError());
+  L->have_factor = true;
+  return leave(L);
+}
+
+int ricmrcc_ladder_apply_dev(ricmrcc_ladder_t* L, const double* T, double* R) {
+  if (!L) return RICMRCC_EINVAL;
+  if (!T || !R) return lfail(L, RICMRCC_EINVAL, "null pointer");
+  if (!L->have_factor) return lfail(L, RICMRCC_ESTATE, "set the density-fitting factor first");
+  int rc = enter(L);
+  if (rc) return rc;
+  const int v = L->v, vp = L->vp;
+  const int grid = L->sms * 8;
+  LCK(cudaMemsetAsync(L->d_err, 0, sizeof(int), L->s));
+  LCK(cudaEventRecord(L->ev_t0, L->s));
+  k_pack_amplitudes<<<(int)std::min<int64_t>(L->nkp * L->ntiles, grid), 256, 0, L->s>>>(
+      T, L->nh, v, 0, L->nkp, L->Kp, L->tiles, L->ntiles, L->Tp);
+  if (L->nkm > 0)
+    k_pack_amplitudes<<<(int)std::min<int64_t>(L->nkm * L->ntiles, grid), 256, 0, L->s>>>(
+        T, L->nh, v, 1, L->nkm, L->Km, L->tiles, L->ntiles, L->Tm);
+  LCK(cudaGetLastError());
+  LCK(cudaEventRecord(L->ev_t1, L->s));
+  CUtensorMap mB, mTp, mTm, mWp, mWm;
+  const int64_t bp_rows = (int64_t)v * vp;
+  if (!packed_map(&mB, L->Bp, 2 * L->kx, bp_rows, LBM) || !packed_map(&mTp, L->Tp, 2 * L->Kp, L->nkp, LBM) ||
+      !packed_map(&mTm, L->Tm, 2 * L->Km, std::max<int64_t>(L->nkm, 1), LBM))
+    return lfail(L, RICMRCC_ECUDA, "tensor map encoding failed");
+  // the B-side map of the rebuild GEMM (256-row boxes over the same buffer)
+  CUtensorMap mB256;
+  if (!packed_map(&mB256, L->Bp, 2 * L->kx, bp_rows, LBN)) return lfail(L, RICMRCC_ECUDA, "tensor map encoding failed");
+  const size_t nslab = L->slabs.size() - 1;
+  for (size_t i = 0; i < nslab; ++i) {
+    const int a0 = L->slabs[i], a1 = L->slabs[i + 1];
+    int64_t np = 0, nm = 0;
+    for (int a = a0; a < a1; ++a) {
+      np += v - a;
+      nm += v - a - 1;
+    }
+    cudaEvent_t* e = &L->ev[i * 6];
+    LCK(cudaEventRecord(e[0], L->s));
+    // 1. V[(a,e)][(b,f)] for a in the slab, b >= a0
+    rc = launch_gemm3(L, mB, mB256, a0 * vp, a0 * vp, (int64_t)(a1 - a0) * vp, (int64_t)(v - a0) * vp,
+                      (int)(L->kx / LBK), L->V, L->ldv);
+    if (rc) return rc;
+    LCK(cudaEventRecord(e[1], L->s));
+    // 2. W+ / W- rows of the slab
+    k_symmetrise<<<(int)std::min<int64_t>(np * L->ntiles, grid), 256, 0, L->s>>>(
+        L->V, L->ldv, v, vp, a0, a1, np, L->tiles, L->ntiles, L->Kp, L->Km, L->Wp, L->Wm);
+    LCK(cudaGetLastError());
+    LCK(cudaEventRecord(e[2], L->s));
+    // 3. ladder GEMMs: D+[(kl)][(ab)], D-[(kl)][(ab)]
+    if (!packed_map(&mWp, L->Wp, 2 * L->Kp, np, LBN) || !packed_map(&mWm, L->Wm, 2 * L->Km, std::max<int64_t>(nm, 1), LBN))
+      return lfail(L, RICMRCC_ECUDA, "tensor map encoding failed");
+    rc = launch_gemm3(L, mTp, mWp, 0, 0, L->nkp, np, (int)(L->Kp / LBK), L->Dp, L->ldd);
+    if (rc) return rc;
+    LCK(cudaEventRecord(e[3], L->s));
+    if (L->nkm > 0 && nm > 0) {
+      rc = launch_gemm3(L, mTm, mWm, 0, 0, L->nkm, nm, (int)(L->Km / LBK), L->Dm, L->ldd);
+      if (rc) return rc;
+    }
+    LCK(cudaEventRecord(e[4], L->s));
+    // 4. R += D+ +- D-
+    const int64_t items = (int64_t)L->nh * L->nh * (v - a0);
+    k_unpack<<<(int)std::min<int64_t>(items, grid), 256, 0, L->s>>>(L->Dp, L->Dm, L->ldd, L->nh, v, a0, a1, R);
+    LCK(cudaGetLastError());
+    LCK(cudaEventRecord(e[5], L->s));
+  }
+  return leave(L);
+}
+
+int ricmrcc_ladder_info(ricmrcc_ladder_t* L, ricmrcc_ladder_info_t* out) {
+  if (!L || !out) return RICMRCC_EINVAL;
+  *out = L->info;
+  return RICMRCC_OK;
+}
+
+int ricmrcc_ladder_finish(ricmrcc_ladder_t* L, ricmrcc_ladder_info_t* out) {
+  if (!L) return RICMRCC_EINVAL;
+  LCK(cudaStreamSynchronize(L->s));
+  int e = 0;
+  LCK(cudaMemcpy(&e, L->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  ricmrcc_ladder_info_t& in = L->info;
+  float ms = 0.f;
+  in.ms_pack = 0.0;
+  if (cudaEventElapsedTime(&ms, L->ev_t0, L->ev_t1) == cudaSuccess) in.ms_pack = ms;
+  in.ms_rebuild = in.ms_symmetrise = in.ms_ladder = in.ms_unpack = 0.0;
+  for (size_t i = 0; i + 1 < L->slabs.size(); ++i) {
+    cudaEvent_t* ev = &L->ev[i * 6];
+    double t[5] = {0, 0, 0, 0, 0};
+    for (int j = 0; j < 5; ++j)
+      if (cudaEventElapsedTime(&ms, ev[j], ev[j + 1]) == cudaSuccess) t[j] = ms;
+    in.ms_rebuild += t[0];
+    in.ms_symmetrise += t[1];
+    in.ms_ladder += t[2] + t[3];
+    in.ms_unpack += t[4];
+  }
+  cudaGetLastError();
+  if (out) *out = in;
+  if (e) {
+    cudaMemset(L->d_err, 0, sizeof(int));
+    return lfail(L, RICMRCC_ECUDA, "tensor-core pipeline wait timed out");
+  }
+  return RICMRCC_OK;
+}
+
+int ricmrcc_ladder_set_factor(ricmrcc_ladder_t* L, const double* Bvv) {
+  if (!L || !Bvv) return lfail(L, RICMRCC_EINVAL, "null pointer");
+  double* d = nullptr;
+  const size_t bytes = (size_t)L->X * L->v * L->v * sizeof(double);
+  if (cudaMalloc(&d, bytes) != cudaSuccess) return lfail(L, RICMRCC_ENOMEM, "device allocation failed");
+  int rc = cudaMemcpy(d, Bvv, bytes, cudaMemcpyHostToDevice) == cudaSuccess ? RICMRCC_OK : RICMRCC_ECUDA;
+  if (!rc) rc = ricmrcc_ladder_set_factor_dev(L, d);
+  if (!rc && cudaStreamSynchronize(L->s) != cudaSuccess) rc = RICMRCC_ECUDA;
+  cudaFree(d);
+  return rc == RICMRCC_ECUDA && L->err.empty() ? lfail(L, rc, "CUDA error") : rc;
+}
+
+int ricmrcc_ladder_apply(ricmrcc_ladder_t* L, const double* T, double* R) {
+  if (!L || !T || !R) return lfail(L, RICMRCC_EINVAL, "null pointer");
+  const size_t bytes = (size_t)L->nh * L->nh * L->v * L->v * sizeof(double);
+  double *dT = nullptr, *dR = nullptr;
+  if (cudaMalloc(&dT, bytes) != cudaSuccess) return lfail(L, RICMRCC_ENOMEM, "device allocation failed");
+  if (cudaMalloc(&dR, bytes) != cudaSuccess) {
+    cudaFree(dT);
+    return lfail(L, RICMRCC_ENOMEM, "device allocation failed");
+  }
+  int rc = cudaMemcpy(dT, T, bytes, cudaMemcpyHostToDevice) == cudaSuccess &&
+                   cudaMemcpy(dR, R, bytes, cudaMemcpyHostToDevice) == cudaSuccess
+               ? RICMRCC_OK
+               : lfail(L, RICMRCC_ECUDA, "copy to the device failed");
+  if (!rc) rc = ricmrcc_ladder_apply_dev(L, dT, dR);
+  if (!rc) rc = ricmrcc_ladder_finish(L, nullptr);
+  if (!rc && cudaMemcpy(R, dR, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = lfail(L, RICMRCC_ECUDA, "copy from the device failed");
+  cudaFree(dT);
+  cudaFree(dR);
+  return rc;
+}
+
+}  // extern "C"
+
+// Bound of every pipeline wait of this unit's kernels (nanoseconds) and the
+// error-path test switch (tc_ptx.h).
+int ladder_set_wait_ns(uint64_t ns, int stall_test) {
+  return cudaMemcpyToSymbol(tcptx::g_wait_ns, &ns, sizeof(ns)) == cudaSuccess &&
+                 cudaMemcpyToSymbol(tcptx::g_stall_test, &stall_test, sizeof(int)) == cudaSuccess
+             ? 0
+             : -1;
+}

@@ -28,8 +28,11 @@
 
 #include "internal.h"
 #include "tcgemm.h"
+#include "tc_ptx.h"
 
 namespace {
+
+using namespace tcptx;
 
 // Fire-and-forget FP64 reduction into global memory (PTX red: no value comes
 // back, so consecutive updates do not wait on each other's completion).
@@ -44,79 +47,6 @@ constexpr int BK = 64;  // 64 BF16 = 128 bytes: one swizzle atom row
 template <int BN>
 __host__ __device__ constexpr int tc_stages() {
   return BN >= 256 ? 2 : (BN >= 128 ? 3 : 4);
-}
-constexpr uint64_t kWaitNs = 4000000000ull;  // 4 s bound on every wait
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t gtime() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
-               : "memory");
-}
-// Bounded wait for the phase with the given parity; false on timeout.  The
-// first try_wait is the fast path (no timer read); while waiting, the error
-// flag (set by a role that gave up) and the clock are checked every 32 tries
-// only, so that a completed phase is seen within one try_wait, not after a
-// global-memory round trip.
-__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(a), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
-  const uint32_t a = smem_u32(b);
-  if (mbar_try(a, parity)) return true;
-  const uint64_t t0 = gtime();
-  for (uint32_t i = 1;; ++i) {
-    if (mbar_try(a, parity)) return true;
-    if ((i & 31) == 0) {
-      if (*(volatile int*)err) return false;
-      if (gtime() - t0 > kWaitNs) {
-        atomicExch(err, 1);
-        return false;
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d_u(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
-// 128 bytes, 8-row swizzle atoms 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFF) >> 4);      // start address
-  d |= (uint64_t)1 << 16;                      // leading byte offset (unused with swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: next 8-row group
-  d |= (uint64_t)1 << 46;                      // descriptor version
-  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
-  return d;
 }
 
 // Instruction descriptor of tcgen05.mma kind::f16: BF16 x BF16 -> FP32, both
@@ -160,22 +90,6 @@ __device__ __noinline__ void mma_scaled_any(uint32_t d, uint64_t ad, uint64_t bd
 
 constexpr uint32_t kNegateA = 1u << 13;  // instruction descriptor: negate the A operand
 
-// The four K = 16 MMAs of one product over a 64-wide K block.  ad / bd describe the stage's
-// first 16 columns; the next ones start 32 bytes further, i.e. +2 in the
-// descriptor's address field (addresses stay below 256 KB, so no carry).
-// The first MMA accumulates if `accum`, the other three always.
-__device__ __forceinline__ void mma_ktile(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
-  asm volatile(
-      "{\n .reg .pred p, q;\n .reg .b64 a1, a2, a3, b1, b2, b3;\n"
-      " setp.ne.b32 p, %4, 0;\n setp.eq.u32 q, %3, %3;\n"
-      " add.s64 a1, %1, 2;\n add.s64 a2, %1, 4;\n add.s64 a3, %1, 6;\n"
-      " add.s64 b1, %2, 2;\n add.s64 b2, %2, 4;\n add.s64 b3, %2, 6;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], a2, b2, %3, q;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], a3, b3, %3, q;\n}\n" ::"r"(d),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-}
 // Same, the first MMA scaling the accumulator by 2^-scale (segment boundary).
 __device__ __noinline__ void mma_ktile_scaled(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, int scale) {
   mma_scaled_any(d, ad, bd, idesc, scale);
@@ -205,7 +119,8 @@ __global__ void __launch_bounds__(128, 1)
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * kStage);
   uint64_t* empty = full + STAGES;
   uint64_t* done = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* never = done + 1;  // completed by nothing (error-path test)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int t = blockIdx.x;
@@ -223,6 +138,7 @@ __global__ void __launch_bounds__(128, 1)
       mbar_init(empty + s, 1);
     }
     mbar_init(done, 1);
+    mbar_init(never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -240,7 +156,8 @@ __global__ void __launch_bounds__(128, 1)
       // TMA producer: hi and lo tiles of both operands per K block (the lo
       // half of a packed row starts kt_total blocks in)
       const int lo_x = kt_total * BK;
-      for (int i = 0; i < nkt; ++i) {
+      int issued = 0;
+      for (int i = 0; i < nkt; ++i, ++issued) {
         const int s = i % STAGES;
         if (i >= STAGES && !mbar_wait(empty + s, ((i / STAGES) - 1) & 1, err)) break;
         mbar_expect_tx(full + s, kStage);
@@ -251,12 +168,15 @@ __global__ void __launch_bounds__(128, 1)
         tma_load_2d(st + 2 * kA, &tmB, kx, ni * BN, full + s);
         tma_load_2d(st + 2 * kA + kB, &tmB, lo_x + kx, ni * BN, full + s);
       }
+      // copies still in flight land before the CTA exits
+      for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i)
+        mbar_wait_drain(full + i % STAGES, (i / STAGES) & 1, err);
     } else if (warp == 1 && lane == 0) {
       // MMA issuer: hi*hi, hi*lo, lo*hi per K block
       const uint32_t idesc = instr_desc<BN>();
       const uint64_t d0 = smem_desc(smem_u32(smem));
-      bool ok = true;
-      for (int i = 0; i < nkt; ++i) {
+      bool ok = stall_test_wait(never, err);
+      for (int i = 0; i < nkt && ok; ++i) {
         const int s = i % STAGES;
         if (!mbar_wait(full + s, (i / STAGES) & 1, err)) {
           ok = false;
@@ -339,6 +259,9 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
+    if (nkt > 0) mbar_wait_drain(done, 0, err);  // every issued MMA has completed
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
   }
 }
@@ -356,7 +279,7 @@ __global__ void __launch_bounds__(128, 1)
 //               enough atomics are in flight to cover their latency
 // The two accumulators (2 x 128 TMEM columns) let the MMAs of item c+1 run
 // while the epilogue drains item c; the 3-stage ring lets the producer run
-// ahead across item boundaries.  Every wait is bounded (kWaitNs) and sets the
+// ahead across item boundaries.  Every wait is bounded (g_wait_ns) and sets the
 // error flag on timeout; the MMA issuer's final commit guarantees that TMEM is
 // freed only after every issued MMA has completed.
 constexpr int GBN = 128;  // largest N tile; B stages are sized for it (wider ops take more N tiles)
@@ -399,7 +322,8 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
   uint64_t* tfull = empty + GSTAGES;   // [2] accumulator ready for the epilogue
   uint64_t* tempty = tfull + 2;       // [2] accumulator drained by the epilogue
   uint64_t* fin = tempty + 2;         // every issued MMA has completed
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  uint64_t* never = fin + 1;          // completed by nothing (error-path test)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -412,6 +336,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
       mbar_init(tempty + b, kEpiWarps);
     }
     mbar_init(fin, 1);
+    mbar_init(never, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -429,6 +354,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
     // hi and lo tiles of both operands per K block; the lo half of a packed
     // row starts one segment width (its K blocks x 64) in
     uint32_t st = 0, ph = 0;
+    int64_t issued = 0;  // stage loads issued (load i: stage i % GSTAGES, phase (i / GSTAGES) & 1)
     bool primed = false, ok = true;
     const uint32_t s0 = smem_u32(sA), full0 = smem_u32(full);
     TcItem nx = load_item(items, blockIdx.x, total);
@@ -467,6 +393,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         tma_load_2d_u(sb + kGA, ma, xl, ya, fb);
         tma_load_2d_u(sb + 2 * kGA, mb, x, yb, fb);
         tma_load_2d_u(sb + 2 * kGA + kGB, mb, xl, yb, fb);
+        ++issued;
         if (++st == GSTAGES) {
           st = 0;
           ph ^= 1u;
@@ -474,10 +401,13 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
         }
       }
     }
+    // copies still in flight land before the CTA exits
+    for (int64_t i = issued > GSTAGES ? issued - GSTAGES : 0; i < issued; ++i)
+      mbar_wait_drain(full + i % GSTAGES, (uint32_t)(i / GSTAGES) & 1u, err);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer (stage st, phase ph of the ring)
     uint32_t st = 0, ph = 0, c = 0;
-    bool ok = true;
+    bool ok = stall_test_wait(never, err);
     const uint64_t desc0 = smem_desc(smem_u32(sA));
     const uint32_t empty0 = smem_u32(empty);
     TcItem nx = load_item(items, blockIdx.x, total);
@@ -623,7 +553,7 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
-    mbar_wait(fin, 0, err);  // bounded: every issued MMA has completed
+    mbar_wait_drain(fin, 0, err);  // bounded: every issued MMA has completed
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * GBN));
@@ -632,18 +562,6 @@ __global__ void __launch_bounds__(64 + 32 * kEpiWarps, 1)
 
 size_t grouped_smem_bytes() {
   return 1024 + (size_t)GSTAGES * kGStage + kEpiWarps * 32 * 33 * 4 + (2 * GSTAGES + 5) * 8 + 128;
-}
-
-// Split two values into BF16 hi parts and BF16 lo parts (the rounding error of
-// hi).  The operand is first rounded to FP32 (one conversion on the narrow FP64
-// pipe); hi and lo then come from FP32 arithmetic, and hi + lo keeps about 16
-// significant bits, well inside FP32's 24.
-__device__ __forceinline__ void split_bf16(float x0, float x1, __nv_bfloat162* hi, __nv_bfloat162* lo) {
-  const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-  const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-  const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-  *hi = __halves2bfloat162(h0, h1);
-  *lo = __halves2bfloat162(l0, l1);
 }
 
 // Gather one operand through offset tables and split it into BF16 hi/lo:
@@ -821,7 +739,7 @@ bool make_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, i
 
 template <int BN>
 size_t smem_bytes() {
-  return 1024 + (size_t)tc_stages<BN>() * 2 * (BM + BN) * BK * 2 + (2 * tc_stages<BN>() + 1) * 8 + 16;
+  return 1024 + (size_t)tc_stages<BN>() * 2 * (BM + BN) * BK * 2 + (2 * tc_stages<BN>() + 2) * 8 + 16;
 }
 
 template <int BN>
@@ -1055,4 +973,13 @@ double tc_pack_bytes(int64_t M, int64_t N, int64_t K) {
   const int bn = tc_pick_bn(N);
   return 8.0 * (double)(M + N) * (double)K +
          2.0 * 2.0 * (double)(tc_pad(M, BM) + tc_pad(N, bn)) * (double)tc_pad(K, BK);
+}
+
+// Bound of every pipeline wait of this unit's kernels (nanoseconds) and the
+// error-path test switch (tc_ptx.h).
+int tc_set_wait_ns(uint64_t ns, int stall_test) {
+  return cudaMemcpyToSymbol(tcptx::g_wait_ns, &ns, sizeof(ns)) == cudaSuccess &&
+                 cudaMemcpyToSymbol(tcptx::g_stall_test, &stall_test, sizeof(int)) == cudaSuccess
+             ? 0
+             : -1;
 }

@@ -184,6 +184,11 @@ int tc_pack_group_build(const PackDesc* in, int n, std::vector<PackDesc>& out, i
 int tc_pack_group_launch(const PackDesc* d, int nd, int64_t total, int sms, cudaStream_t s);
 
 bool tc_available();
+// Bound of every tensor-core pipeline wait (ns) and the error-path test
+// switch (a wait on a barrier nothing completes), tcgemm.cu kernels.
+int tc_set_wait_ns(uint64_t ns, int stall_test);
+// Same for the ladder kernels (ladder.cu).
+int ladder_set_wait_ns(uint64_t ns, int stall_test);
 int tc_pick_bn(int64_t N);  // N tile of the GEMM for an N extent
 int64_t tc_pad(int64_t x, int64_t m);
 // Gather X[xL + tR[r] + tK[k]] (r < rows, k < K) into the packed split-BF16

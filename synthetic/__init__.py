@@ -318,3 +318,41 @@ def batched_dims(count=48, seed=0):
         v = int(rng.integers(40, 121))
         dims.append((o, a, v, 4 * (o + a + v)))
     return dims
+
+
+# ---------------------------------------------------------------------------
+# Inputs of the density-fitted particle-particle ladder alone
+# ---------------------------------------------------------------------------
+
+def make_ladder_inputs(n_hole, n_virt, n_aux, seed=0, b_sigma=0.05, t_sigma=0.02):
+    """(Bvv [n_aux, v, v], T [h, h, v, v]) for the ladder: Bvv ~ N(0, b_sigma)
+    symmetrised in its orbital pair (the virtual block of the factor B above),
+    T ~ N(0, t_sigma) made pair-symmetric, T[k,l,e,f] = T[l,k,f,e]."""
+    rng = np.random.default_rng([seed, 21])
+    B = rng.normal(0.0, b_sigma, (n_aux, n_virt, n_virt))
+    B = 0.5 * (B + B.transpose(0, 2, 1))
+    G = rng.normal(0.0, t_sigma, (n_hole, n_hole, n_virt, n_virt))
+    T = 0.5 * (G + G.transpose(1, 0, 3, 2))
+    return np.ascontiguousarray(B), np.ascontiguousarray(T)
+
+
+def make_ladder_inputs_device(n_hole, n_virt, n_aux, seed=0, b_sigma=0.05, t_sigma=0.02, device="cuda"):
+    """Same recipe drawn with torch's generator directly in device memory, for
+    sizes whose host copies would be too large (tens of GB): returns torch
+    float64 tensors (Bvv, T)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) * 1000003 + 21)
+    B = torch.empty((n_aux, n_virt, n_virt), dtype=torch.float64, device=device)
+    for q0 in range(0, n_aux, 64):
+        x = torch.randn((min(64, n_aux - q0), n_virt, n_virt), generator=g, dtype=torch.float64, device=device)
+        B[q0:q0 + x.shape[0]] = 0.5 * (x + x.transpose(1, 2)) * b_sigma
+    T = torch.empty((n_hole, n_hole, n_virt, n_virt), dtype=torch.float64, device=device)
+    for k in range(n_hole):
+        # T[k, l] for l >= k, and T[l, k] = T[k, l] transposed (pair symmetry)
+        x = torch.randn((n_hole - k, n_virt, n_virt), generator=g, dtype=torch.float64, device=device) * t_sigma
+        x[0] = 0.5 * (x[0] + x[0].T)
+        T[k, k:] = x
+        T[k:, k] = x.transpose(1, 2)
+    return B, T
+
