@@ -442,7 +442,7 @@ typedef struct {
 } ricmrcc_ladder_info_t;
 
 /* n_hole, n_virt, n_aux >= 1; slab_rows = largest number of pairs (a <= b)
- * per slab (0: 16384).  Uses the current CUDA device.  Errors: EINVAL,
+ * per slab (0: 12288; a slab also spans at most 24 values of a).  Uses the current CUDA device.  Errors: EINVAL,
  * ENOMEM, ENOTSUP (no tensor-map support), ECUDA. */
 RICMRCC_API int ricmrcc_ladder_create(int n_hole, int n_virt, int n_aux, int64_t slab_rows,
                                       ricmrcc_ladder_t** out);

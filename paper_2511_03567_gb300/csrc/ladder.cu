@@ -54,6 +54,9 @@ constexpr uint32_t kLB = LBN * LBK * 2;            // 32 KB: one 256 x 64 BF16 t
 constexpr uint32_t kLStage = 2 * (kLA + kLB);      // A_hi | A_lo | B_hi | B_lo
 constexpr int kLEpi = 4;                           // epilogue warps (one per TMEM lane quarter)
 constexpr int kLThreads = 64 + 32 * kLEpi;
+// K products a tensor-core accumulation runs over before its FP32 sum is
+// added into the output (the rebuild GEMM's K, n_aux, stays below it)
+constexpr int kLadderChunk = 16384;
 
 __device__ __forceinline__ uint32_t idesc_128x256() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(LBN >> 3) << 17) | ((uint32_t)(LBM >> 4) << 24);
@@ -61,6 +64,16 @@ __device__ __forceinline__ uint32_t idesc_128x256() {
 
 struct TileMap {
   int mt, nt, group;
+  int kchunk, nchunk;  // K blocks per chunk, chunks per tile
+  // work item t -> (tile, K chunk): chunk-major, so that the CTAs of one wave
+  // work on the same K range of neighbouring tiles
+  __device__ __forceinline__ void item(int64_t t, int* mi, int* ni, int* k0, int* k1, int kt) const {
+    const int64_t tiles = (int64_t)mt * nt;
+    const int ch = (int)(t / tiles);
+    at(t - (int64_t)ch * tiles, mi, ni);
+    *k0 = ch * kchunk;
+    *k1 = min(kt, *k0 + kchunk);
+  }
   __device__ __forceinline__ void at(int64_t t, int* mi, int* ni) const {
     // groups of `group` n tiles, n fastest inside a group, then m: the CTAs of
     // one wave share a few A and B tiles through L2
@@ -75,6 +88,12 @@ struct TileMap {
 
 // D[m][n] = sum_k A[ya0 + m][k] B[yb0 + n][k] for m < M, n < N (FP32, row-major,
 // ldd).  A and B are packed [hi | lo] BF16 rows of 2 * kt * 64 elements.
+// With tm.nchunk > 1 every tile's K range is cut into chunks of tm.kchunk
+// blocks, each its own work item, whose sums are added into D with FP32
+// reductions (D starts at zero): the tensor cores' FP32 accumulation then runs
+// over at most kchunk * 64 products before its result is rounded into D,
+// which bounds the accumulation's drift on very long K (the plain store path,
+// nchunk = 1, is for K of a few thousand).
 __global__ void __launch_bounds__(kLThreads, 1)
     k_gemm3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int ya0, int yb0,
             int64_t M, int64_t N, int kt, float* __restrict__ D, int64_t ldd, TileMap tm, int* err) {
@@ -90,7 +109,8 @@ __global__ void __launch_bounds__(kLThreads, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t total = (int64_t)tm.mt * tm.nt;
+  const int64_t total = (int64_t)tm.mt * tm.nt * tm.nchunk;
+  const bool reduce = tm.nchunk > 1;
   if (threadIdx.x == 0) {
     for (int s = 0; s < LSTAGES; ++s) {
       mbar_init(full + s, 1);
@@ -123,10 +143,10 @@ __global__ void __launch_bounds__(kLThreads, 1)
     const uint32_t s0 = smem_u32(smem), full0 = smem_u32(full);
     const int lo_x = kt * LBK;
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
-      int mi, ni;
-      tm.at(t, &mi, &ni);
+      int mi, ni, k0, k1;
+      tm.item(t, &mi, &ni, &k0, &k1, kt);
       const int ya = ya0 + mi * LBM, yb = yb0 + ni * LBN;
-      for (int k = 0; k < kt; ++k) {
+      for (int k = k0; k < k1; ++k) {
         if (issued >= LSTAGES && !mbar_wait(empty + st, ph ^ 1u, err)) {
           ok = false;
           break;
@@ -162,7 +182,9 @@ __global__ void __launch_bounds__(kLThreads, 1)
       if (c >= 2 && !mbar_wait(tempty + b, ((c >> 1) - 1) & 1, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t acc = tmem + b * LBN;
-      for (int k = 0; k < kt; ++k) {
+      int mi, ni, k0, k1;
+      tm.item(t, &mi, &ni, &k0, &k1, kt);
+      for (int k = k0; k < k1; ++k) {
         if (!mbar_wait(full + st, ph, err)) {
           ok = false;
           break;
@@ -170,7 +192,7 @@ __global__ void __launch_bounds__(kLThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint64_t ahi = desc0 + st * (kLStage >> 4), alo = ahi + (kLA >> 4);
         const uint64_t bhi = ahi + ((2 * kLA) >> 4), blo = bhi + (kLB >> 4);
-        mma_ktile(acc, ahi, bhi, idesc, k > 0 ? 1u : 0u);
+        mma_ktile(acc, ahi, bhi, idesc, k > k0 ? 1u : 0u);
         mma_ktile(acc, ahi, blo, idesc, 1u);
         mma_ktile(acc, alo, bhi, idesc, 1u);
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -198,8 +220,8 @@ __global__ void __launch_bounds__(kLThreads, 1)
     float* tile = etile + (warp - 2) * 32 * 33;
     uint32_t c = 0;
     for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++c) {
-      int mi, ni;
-      tm.at(t, &mi, &ni);
+      int mi, ni, k0, k1;
+      tm.item(t, &mi, &ni, &k0, &k1, kt);
       const uint32_t b = c & 1;
       const bool ready = __all_sync(0xffffffffu, mbar_wait(tfull + b, (c >> 1) & 1, err));
       if (!ready) break;
@@ -227,7 +249,13 @@ __global__ void __launch_bounds__(kLThreads, 1)
 #pragma unroll 4
           for (int rr = 0; rr < 32; ++rr) {
             const int64_t m = m0 + rr;
-            if (m < M) D[m * ldd + n] = tile[rr * 33 + lane];
+            if (m >= M) break;
+            if (reduce) {
+              asm volatile("red.global.add.f32 [%0], %1;" ::"l"(__cvta_generic_to_global(D + m * ldd + n)),
+                           "f"(tile[rr * 33 + lane]));
+            } else {
+              D[m * ldd + n] = tile[rr * 33 + lane];
+            }
           }
         }
         __syncwarp();
@@ -364,74 +392,125 @@ __device__ __forceinline__ int64_t slab_row(int v, int a0, int a, int b, int str
 // W+ / W- rows of the slab from the rebuilt integrals V (FP32, rows (a - a0) vp
 // + e, columns (b - a0) vp + f): S = (V^{ab}_{ef} + V^{ab}_{fe}) / 2 for
 // e <= f, A = (V^{ab}_{ef} - V^{ab}_{fe}) / 2 for e < f (a < b).
+// Work items: (pair, 64 x 64 tile pair (E, F), F >= E).  Both tiles are read
+// with 16-byte loads (lanes along f) into registers one item ahead, so the
+// next item's loads are in flight while this item is combined through
+// shared memory and written out.
+struct SymItem {
+  const float* Vab;
+  int a, b, E, F;
+};
+
+__device__ __forceinline__ SymItem sym_item(const float* V, int64_t ldv, int v, int vp, int a0, int64_t it, int ntiles,
+                                            const int2* tiles) {
+  const int64_t p = it / ntiles;
+  const int2 EF = tiles[it - p * ntiles];
+  // pair p -> (a, b): row a of the slab holds v - a pairs
+  int a = a0;
+  int64_t base = 0;
+  while (base + (v - a) <= p) {
+    base += v - a;
+    ++a;
+  }
+  SymItem s;
+  s.a = a;
+  s.b = a + (int)(p - base);
+  s.E = EF.x;
+  s.F = EF.y;
+  s.Vab = V + (int64_t)(a - a0) * vp * ldv + (int64_t)(s.b - a0) * vp;  // V^{ab}_{ef} = Vab[e ldv + f]
+  return s;
+}
+
+// 16 floats of each tile per thread: rows r = tid / 16 + 16 j, columns
+// 4 (tid % 16) .. +3; rows past v and columns past the padded block vp are zero
+__device__ __forceinline__ void sym_load(const SymItem& s, int64_t ldv, int v, int vp, float4* x1, float4* x2) {
+  const int r0 = threadIdx.x >> 4, c = (threadIdx.x & 15) * 4;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int r = r0 + 16 * j;
+    const int e1 = s.E + r, f1 = s.F + c;
+    x1[j] = (e1 < v && f1 < vp) ? __ldg(reinterpret_cast<const float4*>(s.Vab + (int64_t)e1 * ldv + f1))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int e2 = s.F + r, f2 = s.E + c;
+    x2[j] = (e2 < v && f2 < vp) ? __ldg(reinterpret_cast<const float4*>(s.Vab + (int64_t)e2 * ldv + f2))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
 __global__ void __launch_bounds__(256)
     k_symmetrise(const float* __restrict__ V, int64_t ldv, int v, int vp, int a0, int a1, int64_t npairs,
                  const int2* __restrict__ tiles, int ntiles, int64_t Kp, int64_t Km, __nv_bfloat16* __restrict__ Wp,
                  __nv_bfloat16* __restrict__ Wm) {
-  __shared__ float t1[32][33], t2[32][33];
+  __shared__ float t1[64][65], t2[64][65];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int64_t it = blockIdx.x; it < npairs * ntiles; it += gridDim.x) {
-    const int64_t p = it / ntiles;
-    const int2 EF = tiles[it - p * ntiles];
-    // pair p -> (a, b): rows of a' hold v - a' pairs
-    int a = a0;
-    int64_t base = 0;
-    while (base + (v - a) <= p) {
-      base += v - a;
-      ++a;
-    }
-    const int b = a + (int)(p - base);
-    const float* Vab = V + (int64_t)(a - a0) * vp * ldv + (int64_t)(b - a0) * vp;  // V^{ab}_{ef} = Vab[e ldv + f]
+  const int64_t total = npairs * ntiles;
+  int64_t it = blockIdx.x;
+  if (it >= total) return;
+  float4 x1[4], x2[4];
+  SymItem cur = sym_item(V, ldv, v, vp, a0, it, ntiles, tiles);
+  sym_load(cur, ldv, v, vp, x1, x2);
+  const int r0 = threadIdx.x >> 4, c0 = (threadIdx.x & 15) * 4;
+  for (; it < total; it += gridDim.x) {
+    __syncthreads();  // the previous item's reads of the tiles are done
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int i = warp + 8 * j;
-      const int e1 = EF.x + i, f1 = EF.y + lane;
-      t1[i][lane] = (e1 < v && f1 < v) ? Vab[(int64_t)e1 * ldv + f1] : 0.f;
-      const int e2 = EF.y + i, f2 = EF.x + lane;
-      t2[i][lane] = (e2 < v && f2 < v) ? Vab[(int64_t)e2 * ldv + f2] : 0.f;
+      const int r = r0 + 16 * j;
+      t1[r][c0] = x1[j].x, t1[r][c0 + 1] = x1[j].y, t1[r][c0 + 2] = x1[j].z, t1[r][c0 + 3] = x1[j].w;
+      t2[r][c0] = x2[j].x, t2[r][c0 + 1] = x2[j].y, t2[r][c0 + 2] = x2[j].z, t2[r][c0 + 3] = x2[j].w;
     }
     __syncthreads();
-    __nv_bfloat16* rp = Wp + slab_row(v, a0, a, b, 0) * 2 * Kp;
-    __nv_bfloat16* rm = b > a ? Wm + slab_row(v, a0, a, b, 1) * 2 * Km : nullptr;
+    const SymItem s = cur;
+    const int64_t nx = it + gridDim.x;
+    if (nx < total) {
+      cur = sym_item(V, ldv, v, vp, a0, nx, ntiles, tiles);
+      sym_load(cur, ldv, v, vp, x1, x2);  // in flight while this item is written
+    }
+    __nv_bfloat16* rp = Wp + slab_row(v, a0, s.a, s.b, 0) * 2 * Kp;
+    __nv_bfloat16* rm = s.b > s.a ? Wm + slab_row(v, a0, s.a, s.b, 1) * 2 * Km : nullptr;
+#pragma unroll 2
+    for (int q = 0; q < 8; ++q) {
+      const int i = warp + 8 * q, e = s.E + i;
+      if (e >= v) break;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int i = warp + 8 * j;
-      const int e = EF.x + i, f = EF.y + lane;
-      if (e < v && f < v && f >= e) {
-        const float x1 = t1[i][lane], x2 = t2[lane][i];  // V^{ab}_{ef}, V^{ab}_{fe}
-        store_split(rp, Kp, tri_index(v, e, f, 0), 0.5f * (x1 + x2));
-        if (rm && f > e) store_split(rm, Km, tri_index(v, e, f, 1), 0.5f * (x1 - x2));
+      for (int h = 0; h < 2; ++h) {
+        const int j = lane + 32 * h, f = s.F + j;
+        if (f < v && f >= e) {
+          const float y1 = t1[i][j], y2 = t2[j][i];  // V^{ab}_{ef}, V^{ab}_{fe}
+          store_split(rp, Kp, tri_index(v, e, f, 0), 0.5f * (y1 + y2));
+          if (rm && f > e) store_split(rm, Km, tri_index(v, e, f, 1), 0.5f * (y1 - y2));
+        }
       }
     }
-    __syncthreads();
   }
 }
 
 // R[k][l][a][b] += D+[(kl)][(ab)] + sgn D-[(kl)][(ab)] for the pairs of the
 // slab (min(a, b) in [a0, a1)); sgn = -1 when exactly one of a > b, k > l.
-// Work items (k, l, a) with threads along b.
+// Per (k, l) the slab's outputs are rows a in [a0, a1) with b in [a0, v) and
+// rows a in [a1, v) with b in [a0, a1); one thread per output, consecutive
+// threads along b.
 __global__ void __launch_bounds__(256)
     k_unpack(const float* __restrict__ Dp, const float* __restrict__ Dm, int64_t ldd, int nh, int v, int a0, int a1,
              double* __restrict__ R) {
-  const int64_t na = v - a0, items = (int64_t)nh * nh * na;
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
-    const int a = a0 + (int)(it % na);
-    const int64_t kl = it / na;
-    const int k = (int)(kl / nh), l = (int)(kl % nh);
-    const int kk = min(k, l), ll = max(k, l);
-    const int64_t pp = tri_index(nh, kk, ll, 0);
-    const int64_t pm = kk < ll ? tri_index(nh, kk, ll, 1) : -1;
-    const float* dp = Dp + pp * ldd;
-    const float* dm = pm >= 0 ? Dm + pm * ldd : nullptr;
-    const float ks = k < l ? 1.f : -1.f;
-    double* Rrow = R + (kl * v + a) * (int64_t)v;
-    const int bend = a < a1 ? v : a1;
-    for (int b = a0 + threadIdx.x; b < bend; b += blockDim.x) {
-      const int lo = min(a, b), hi = max(a, b);
-      float x = dp[slab_row(v, a0, lo, hi, 0)];
-      if (dm && lo < hi) x += (a < b ? ks : -ks) * dm[slab_row(v, a0, lo, hi, 1)];
-      Rrow[b] += (double)x;
+  const int64_t w = a1 - a0, wide = (int64_t)w * (v - a0), per = wide + (int64_t)(v - a1) * w;
+  const int64_t total = (int64_t)nh * nh * per;
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t kl = x / per, j = x - kl * per;
+    int a, b;
+    if (j < wide) {
+      a = a0 + (int)(j / (v - a0));
+      b = a0 + (int)(j % (v - a0));
+    } else {
+      const int64_t jj = j - wide;
+      a = a1 + (int)(jj / w);
+      b = a0 + (int)(jj % w);
     }
+    const int k = (int)(kl / nh), l = (int)(kl - (int64_t)k * nh);
+    const int kk = min(k, l), ll = max(k, l), lo = min(a, b), hi = max(a, b);
+    float y = Dp[tri_index(nh, kk, ll, 0) * ldd + slab_row(v, a0, lo, hi, 0)];
+    if (kk < ll && lo < hi)
+      y += ((a < b) == (k < l) ? 1.f : -1.f) * Dm[tri_index(nh, kk, ll, 1) * ldd + slab_row(v, a0, lo, hi, 1)];
+    R[(kl * v + a) * (int64_t)v + b] += (double)y;
   }
 }
 
@@ -476,14 +555,16 @@ struct ricmrcc_ladder {
   int64_t nep = 0, nem = 0;      // virtual pairs e <= f, e < f
   int64_t Kp = 0, Km = 0;        // padded K of the plus / minus ladder GEMMs
   int64_t slab_rows = 0;         // max pairs (a, b) per slab
-  int64_t ldv = 0, ldd = 0;
+  int64_t ldd = 0;
   std::vector<int> slabs;        // a0 of each slab, then v
   cudaStream_t user = nullptr, s = nullptr;
   cudaEvent_t ev_user = nullptr;
   __nv_bfloat16 *Bp = nullptr, *Tp = nullptr, *Tm = nullptr, *Wp = nullptr, *Wm = nullptr;
   float *V = nullptr, *Dp = nullptr, *Dm = nullptr;
-  int2* tiles = nullptr;         // 32 x 32 tile pairs (E, F), F >= E
+  int2* tiles = nullptr;         // 32 x 32 tile pairs (E, F), F >= E (amplitude packing)
   int ntiles = 0;
+  int2* tiles64 = nullptr;       // 64 x 64 tile pairs (symmetrisation)
+  int ntiles64 = 0;
   int* d_err = nullptr;
   bool have_factor = false;
   std::vector<cudaEvent_t> ev;   // per slab: 5 boundaries (rebuild, symmetrise, ladder +, ladder -, unpack)
@@ -505,13 +586,17 @@ int lfail(ricmrcc_ladder_t* L, int code, const std::string& m) {
     if (e_ != cudaSuccess) return lfail(L, RICMRCC_ECUDA, cudaGetErrorString(e_)); \
   } while (0)
 
+// kchunk = 0: whole K per tile, D stored; else chunks of kchunk K blocks
+// reduced into D (which the caller has zeroed).
 int launch_gemm3(ricmrcc_ladder_t* L, const CUtensorMap& ma, const CUtensorMap& mb, int ya0, int yb0, int64_t M,
-                 int64_t N, int kt, float* D, int64_t ldd) {
+                 int64_t N, int kt, float* D, int64_t ldd, int kchunk) {
   TileMap tm;
   tm.mt = (int)((M + LBM - 1) / LBM);
   tm.nt = (int)((N + LBN - 1) / LBN);
   tm.group = std::min(tm.nt, 8);
-  const int64_t total = (int64_t)tm.mt * tm.nt;
+  tm.kchunk = kchunk > 0 && kchunk < kt ? kchunk : kt;
+  tm.nchunk = (kt + tm.kchunk - 1) / tm.kchunk;
+  const int64_t total = (int64_t)tm.mt * tm.nt * tm.nchunk;
   if (total <= 0 || kt <= 0) return RICMRCC_OK;
   const int grid = (int)std::min<int64_t>(total, L->sms);
   k_gemm3<<<grid, kLThreads, gemm3_smem_bytes(), L->s>>>(ma, mb, ya0, yb0, M, N, kt, D, ldd, tm, L->d_err);
@@ -521,7 +606,7 @@ int launch_gemm3(ricmrcc_ladder_t* L, const CUtensorMap& ma, const CUtensorMap& 
 
 void free_all(ricmrcc_ladder_t* L) {
   for (void* p : {(void*)L->Bp, (void*)L->Tp, (void*)L->Tm, (void*)L->Wp, (void*)L->Wm, (void*)L->V, (void*)L->Dp,
-                  (void*)L->Dm, (void*)L->tiles, (void*)L->d_err})
+                  (void*)L->Dm, (void*)L->tiles, (void*)L->tiles64, (void*)L->d_err})
     if (p) cudaFree(p);
   for (cudaEvent_t e : L->ev) cudaEventDestroy(e);
   if (L->ev_t0) cudaEventDestroy(L->ev_t0);
@@ -569,15 +654,18 @@ int ricmrcc_ladder_create(int n_hole, int n_virt, int n_aux, int64_t slab_rows, 
   L->Kp = pad_to(L->nep, LBK);
   L->Km = pad_to(std::max<int64_t>(L->nem, 1), LBK);
   const int64_t v = n_virt;
-  // slabs: consecutive a with at most slab_rows pairs (a, b >= a) each (one
-  // a at least)
-  const int64_t target = slab_rows > 0 ? slab_rows : 16384;
+  // slabs: consecutive a with at most slab_rows pairs (a, b >= a) and at
+  // most kMaxSlabA values of a each (one a at least).  The rebuild GEMM of a
+  // slab forms the rectangle of rows a in [a0, a1) and columns b in [a0, v),
+  // so its part b < a is not used: the bound on a1 - a0 keeps that small.
+  constexpr int kMaxSlabA = 24;
+  const int64_t target = slab_rows > 0 ? slab_rows : 12288;
   L->slab_rows = 0;
   for (int a = 0; a < n_virt;) {
     L->slabs.push_back(a);
     int64_t rows = 0;
     int b = a;
-    while (b < n_virt && (rows == 0 || rows + (v - b) <= target)) {
+    while (b < n_virt && (rows == 0 || (rows + (v - b) <= target && b - a < kMaxSlabA))) {
       rows += v - b;
       ++b;
     }
@@ -585,12 +673,12 @@ int ricmrcc_ladder_create(int n_hole, int n_virt, int n_aux, int64_t slab_rows, 
     a = b;
   }
   L->slabs.push_back(n_virt);
-  int64_t vrows = 0, vcols = 0;
+  int64_t vrows = 0, vsize = 0;  // largest slab of V: rows x its leading dimension
   for (size_t i = 0; i + 1 < L->slabs.size(); ++i) {
-    vrows = std::max<int64_t>(vrows, (int64_t)(L->slabs[i + 1] - L->slabs[i]) * L->vp);
-    vcols = std::max<int64_t>(vcols, (v - L->slabs[i]) * L->vp);
+    const int64_t r = (int64_t)(L->slabs[i + 1] - L->slabs[i]) * L->vp;
+    vrows = std::max(vrows, r);
+    vsize = std::max(vsize, r * pad_to((v - L->slabs[i]) * L->vp, 4));
   }
-  L->ldv = pad_to(vcols, 4);
   L->ldd = pad_to(L->slab_rows, 4);
   int dev = 0;
   cudaGetDevice(&dev);
@@ -600,6 +688,10 @@ int ricmrcc_ladder_create(int n_hole, int n_virt, int n_aux, int64_t slab_rows, 
   for (int E = 0; E < n_virt; E += 32)
     for (int F = E; F < n_virt; F += 32) tp.push_back(make_int2(E, F));
   L->ntiles = (int)tp.size();
+  std::vector<int2> tp64;
+  for (int E = 0; E < n_virt; E += 64)
+    for (int F = E; F < n_virt; F += 64) tp64.push_back(make_int2(E, F));
+  L->ntiles64 = (int)tp64.size();
   bool ok = cudaStreamCreateWithFlags(&L->s, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&L->ev_user, cudaEventDisableTiming) == cudaSuccess &&
             cudaEventCreate(&L->ev_t0) == cudaSuccess && cudaEventCreate(&L->ev_t1) == cudaSuccess;
@@ -616,12 +708,15 @@ int ricmrcc_ladder_create(int n_hole, int n_virt, int n_aux, int64_t slab_rows, 
   alloc((void**)&L->Tm, (size_t)std::max<int64_t>(L->nkm, 1) * 2 * L->Km * 2, true);
   alloc((void**)&L->Wp, (size_t)L->slab_rows * 2 * L->Kp * 2, true);
   alloc((void**)&L->Wm, (size_t)L->slab_rows * 2 * L->Km * 2, true);
-  alloc((void**)&L->V, (size_t)vrows * L->ldv * 4, false);
+  alloc((void**)&L->V, (size_t)vsize * 4, false);
   alloc((void**)&L->Dp, (size_t)L->nkp * L->ldd * 4, false);
   alloc((void**)&L->Dm, (size_t)std::max<int64_t>(L->nkm, 1) * L->ldd * 4, false);
   alloc((void**)&L->tiles, tp.size() * sizeof(int2), false);
+  alloc((void**)&L->tiles64, tp64.size() * sizeof(int2), false);
   alloc((void**)&L->d_err, sizeof(int), true);
   if (ok) ok = cudaMemcpy(L->tiles, tp.data(), tp.size() * sizeof(int2), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok)
+    ok = cudaMemcpy(L->tiles64, tp64.data(), tp64.size() * sizeof(int2), cudaMemcpyHostToDevice) == cudaSuccess;
   if (ok)
     ok = cudaFuncSetAttribute(k_gemm3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm3_smem_bytes()) ==
          cudaSuccess;
@@ -646,7 +741,7 @@ int ricmrcc_ladder_create(int n_hole, int n_virt, int n_aux, int64_t slab_rows, 
                               (double)pad_to(std::max<int64_t>(L->nkm, 1), LBM) * (double)L->Km * (double)L->nem);
   in.workspace_bytes = (double)v * L->vp * 2 * L->kx * 2 + (double)L->nkp * 2 * L->Kp * 2 +
                        (double)L->nkm * 2 * L->Km * 2 + (double)L->slab_rows * 2 * (L->Kp + L->Km) * 2 +
-                       (double)vrows * L->ldv * 4 + (double)(L->nkp + L->nkm) * L->ldd * 4;
+                       (double)vsize * 4 + (double)(L->nkp + L->nkm) * L->ldd * 4;
   *out = L;
   return RICMRCC_OK;
 }
@@ -715,29 +810,33 @@ int ricmrcc_ladder_apply_dev(ricmrcc_ladder_t* L, const double* T, double* R) {
     cudaEvent_t* e = &L->ev[i * 6];
     LCK(cudaEventRecord(e[0], L->s));
     // 1. V[(a,e)][(b,f)] for a in the slab, b >= a0
+    const int64_t ldv = pad_to((int64_t)(v - a0) * vp, 4);
     rc = launch_gemm3(L, mB, mB256, a0 * vp, a0 * vp, (int64_t)(a1 - a0) * vp, (int64_t)(v - a0) * vp,
-                      (int)(L->kx / LBK), L->V, L->ldv);
+                      (int)(L->kx / LBK), L->V, ldv, (int)(kLadderChunk / LBK));
     if (rc) return rc;
     LCK(cudaEventRecord(e[1], L->s));
     // 2. W+ / W- rows of the slab
-    k_symmetrise<<<(int)std::min<int64_t>(np * L->ntiles, grid), 256, 0, L->s>>>(
-        L->V, L->ldv, v, vp, a0, a1, np, L->tiles, L->ntiles, L->Kp, L->Km, L->Wp, L->Wm);
+    k_symmetrise<<<(int)std::min<int64_t>(np * L->ntiles64, (int64_t)L->sms * 6), 256, 0, L->s>>>(
+        L->V, ldv, v, vp, a0, a1, np, L->tiles64, L->ntiles64, L->Kp, L->Km, L->Wp, L->Wm);
     LCK(cudaGetLastError());
     LCK(cudaEventRecord(e[2], L->s));
     // 3. ladder GEMMs: D+[(kl)][(ab)], D-[(kl)][(ab)]
     if (!packed_map(&mWp, L->Wp, 2 * L->Kp, np, LBN) || !packed_map(&mWm, L->Wm, 2 * L->Km, std::max<int64_t>(nm, 1), LBN))
       return lfail(L, RICMRCC_ECUDA, "tensor map encoding failed");
-    rc = launch_gemm3(L, mTp, mWp, 0, 0, L->nkp, np, (int)(L->Kp / LBK), L->Dp, L->ldd);
+    LCK(cudaMemsetAsync(L->Dp, 0, sizeof(float) * L->nkp * L->ldd, L->s));
+    rc = launch_gemm3(L, mTp, mWp, 0, 0, L->nkp, np, (int)(L->Kp / LBK), L->Dp, L->ldd, (int)(kLadderChunk / LBK));
     if (rc) return rc;
     LCK(cudaEventRecord(e[3], L->s));
     if (L->nkm > 0 && nm > 0) {
-      rc = launch_gemm3(L, mTm, mWm, 0, 0, L->nkm, nm, (int)(L->Km / LBK), L->Dm, L->ldd);
+      LCK(cudaMemsetAsync(L->Dm, 0, sizeof(float) * L->nkm * L->ldd, L->s));
+      rc = launch_gemm3(L, mTm, mWm, 0, 0, L->nkm, nm, (int)(L->Km / LBK), L->Dm, L->ldd, (int)(kLadderChunk / LBK));
       if (rc) return rc;
     }
     LCK(cudaEventRecord(e[4], L->s));
     // 4. R += D+ +- D-
-    const int64_t items = (int64_t)L->nh * L->nh * (v - a0);
-    k_unpack<<<(int)std::min<int64_t>(items, grid), 256, 0, L->s>>>(L->Dp, L->Dm, L->ldd, L->nh, v, a0, a1, R);
+    const int64_t outs = (int64_t)L->nh * L->nh * (a1 - a0) * (2 * (int64_t)v - a0 - a1);
+    k_unpack<<<(int)std::min<int64_t>((outs + 255) / 256, grid), 256, 0, L->s>>>(L->Dp, L->Dm, L->ldd, L->nh, v, a0,
+                                                                                   a1, R);
     LCK(cudaGetLastError());
     LCK(cudaEventRecord(e[5], L->s));
   }
