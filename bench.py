@@ -261,6 +261,8 @@ def main():
                     help="skip timing the FP64 path beside the mixed one")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile rule")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ladder", action="store_true", help="skip the Large-size density-fitted ladder")
+    ap.add_argument("--ladder-steps", type=int, default=2, help="timed applications of the Large ladder")
     ap.add_argument("--no-converging", action="store_true",
                     help="skip the mixed-against-FP64 solves of the converging Mid-sized problem")
     ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
@@ -402,6 +404,12 @@ def main():
     pk = peaks()
     fp64_peak = fp64_gemm_peak(torch) if rank == 0 else None
 
+    # the density-fitted vvvv ladder at the Large sizes (90 core + 12 active
+    # holes, 707 virtual, n_aux 2400), the contraction the Mid path takes from
+    # the stored integral tensor
+    ladder = None
+    if not args.no_ladder and rank == 0:
+        ladder = ladder_large(torch, stream, pk, steps=args.ladder_steps)
     # a converging problem of the same sizes: mixed solve (with its FP64
     # refinement) against the FP64 solve
     conv = None
@@ -437,6 +445,7 @@ def main():
             "gpu_launches": int(info.step_launches) * args.steps,
             "roofline": roof, "clocks": clk.summary(), "tensor_core": tc, "fp64_path": fp64_line,
             "accuracy": {"mixed_vs_fp64_one_evaluation": acc, "converging_mid": conv},
+            "ladder_large": ladder,
             "tile_rule": g.get_tile_rule(), "tuning": tuning}
     if not args.no_cpu_baseline and ws == 1 and args.workload == "mid":
         try:
@@ -500,6 +509,67 @@ def eval_mixed_vs_fp64(torch, g, snap):
             "energy_fp64": ef, "energy_mixed": em, "abs_dE": abs(em - ef),
             "max_abs_dR": float((rm - rf).abs().max()), "max_abs_R": float(rf.abs().max()),
             "rel_dR": float((rm - rf).abs().max() / rf.abs().max())}
+
+
+LADDER_LARGE = {"n_hole": 102, "n_virt": 707, "n_aux": 2400,
+                "sizes": "holes = 90 core + 12 active, 707 virtual, n_aux 2400 (the Large configuration)"}
+
+
+def ladder_large(torch, stream, pk, steps=2, warmup=1):
+    """R += sum_ef (ae|bf) T^{ef}_{kl} at the Large sizes through
+    ricmrcc_ladder_apply_dev: seconds per application (CUDA events on the
+    library's stream), the phases' times, and the ladder GEMM against the
+    BF16 tensor peak.  Inputs (B 9.6 GB, T and R 42 GB each in FP64) are
+    drawn on the device."""
+    import paper_2511_03567_gb300 as ric
+    import synthetic
+    w = LADDER_LARGE
+    nh, nv, nx = w["n_hole"], w["n_virt"], w["n_aux"]
+    Bv, T = synthetic.make_ladder_inputs_device(nh, nv, nx, seed=0)
+    R = torch.zeros_like(T)
+    L = ric.Ladder(nh, nv, nx)
+    L.set_stream(stream.cuda_stream)
+    L.set_factor(Bv)
+    for _ in range(max(warmup, 1)):
+        L.apply_dev(T, R)
+        L.finish()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    secs, phases = 0.0, {}
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        L.apply_dev(T, R)
+        e1.record(stream)
+        info = L.finish()
+        torch.cuda.synchronize()
+        secs += e0.elapsed_time(e1) / 1e3
+        for k in ("ms_pack", "ms_rebuild", "ms_symmetrise", "ms_ladder", "ms_unpack"):
+            phases[k] = phases.get(k, 0.0) + info[k] / steps
+    s_app = secs / steps
+    t_lad = phases["ms_ladder"] / 1e3
+    t_reb = phases["ms_rebuild"] / 1e3
+    peak = pk.get("bf16_tflops_sustained", 1700.0)
+    achieved = 3.0 * info["ladder_flops"] / t_lad / 1e12
+    out = {"workload": w["sizes"], "steps": steps, "s_per_application": s_app,
+           "method_flops": info["ladder_flops"] + info["rebuild_flops"],
+           "tflops_method": (info["ladder_flops"] + info["rebuild_flops"]) / s_app / 1e12,
+           "phases_ms": phases, "slabs": info["slabs"], "workspace_gb": info["workspace_bytes"] / 1e9,
+           "dtype": "bf16x3 (f32 acc) -> f64",
+           "roofline": {"bound": "tensor", "kernel": "k_gemm3 (ladder GEMMs)", "achieved": achieved,
+                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured",
+                        "frac_of_burst": achieved / pk.get("bf16_tflops", 1900.0),
+                        "work": "3 x 2 MNK per packed ladder GEMM (the split products hi*hi, hi*lo, lo*hi "
+                                "counted; M, N, K without padding): 3 x ladder_flops",
+                        "traffic": None},
+           "rebuild": {"kernel": "k_gemm3 (integral rebuild)",
+                       "tflops_bf16": 3.0 * info["rebuild_flops"] / t_reb / 1e12,
+                       "tflops_bf16_executed": info["rebuild_flops_executed"] / t_reb / 1e12,
+                       "work": "3 x n_aux v^3 (v+1): the integrals (ae|bf) with a <= b, split products counted"}}
+    del L, Bv, T, R
+    torch.cuda.empty_cache()
+    return out
 
 
 # B scale of the converging problem: B ~ N(0, 0.05 * CONV_B_SCALE), every

@@ -26,8 +26,9 @@
 //   4. unpack        R[k][l][a][b] += D+ +- D-
 // Both GEMMs run in one persistent tcgen05 kernel (k_gemm3): split-precision
 // BF16 operands [hi | lo] (hi*hi + hi*lo + lo*hi, FP32 accumulation in TMEM),
-// 128 x 256 output tiles, TMA-fed two-stage shared-memory ring, two TMEM
-// accumulators so that a tile's write-out overlaps the next tile's MMAs.
+// 128 x 256 output tiles, a TMA-fed shared-memory ring (two stages of 64-wide
+// or four of 32-wide K blocks), two TMEM accumulators so that a tile's
+// write-out overlaps the next tile's MMAs.
 // Every wait is bounded (tc_ptx.h); a timeout sets the error flag, which the
 // host reads after the call.
 #include <cuda.h>
@@ -48,10 +49,58 @@ using namespace tcptx;
 
 namespace {
 
-constexpr int LBM = 128, LBN = 256, LBK = 64, LSTAGES = 2;
-constexpr uint32_t kLA = LBM * LBK * 2;            // 16 KB: one 128 x 64 BF16 tile
-constexpr uint32_t kLB = LBN * LBK * 2;            // 32 KB: one 256 x 64 BF16 tile
-constexpr uint32_t kLStage = 2 * (kLA + kLB);      // A_hi | A_lo | B_hi | B_lo
+constexpr int LBM = 128, LBN = 256;
+
+// Ring shapes of the GEMM kernel, by K-block width BK:
+//  BK = 64: 128-byte rows, 128-byte swizzle, two 96 KB stages;
+//  BK = 32: 64-byte rows, 64-byte swizzle, four 48 KB stages (the producer
+//           runs three K blocks ahead).
+// The integral rebuild (operands mostly from L2) runs faster with BK = 32,
+// the ladder (both operands streamed from HBM, rows 1 MB apart) with BK = 64.
+template <int BK>
+struct Ring {
+  static constexpr int kStages = BK == 32 ? 4 : 2;
+  static constexpr uint32_t kA = LBM * BK * 2;          // one A tile (hi or lo)
+  static constexpr uint32_t kB = LBN * BK * 2;          // one B tile
+  static constexpr uint32_t kStage = 2 * (kA + kB);     // A_hi | A_lo | B_hi | B_lo
+  static constexpr uint32_t kRowBytes = BK * 2;
+  static constexpr uint64_t kSwizzle = BK == 32 ? 4 : 2;  // descriptor codes: 64-byte / 128-byte swizzle
+};
+
+// Shared-memory matrix descriptor: K-major operand, swizzled rows of
+// BK * 2 bytes, 8-row swizzle atoms 8 rows apart.
+template <int BK>
+__device__ __forceinline__ uint64_t smem_desc_bk(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);                   // start address
+  d |= (uint64_t)1 << 16;                                   // leading byte offset (unused with swizzle)
+  d |= (uint64_t)((8 * Ring<BK>::kRowBytes) >> 4) << 32;    // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;                                   // descriptor version
+  d |= Ring<BK>::kSwizzle << 61;
+  return d;
+}
+
+// The two K = 16 MMAs of one product over a 32-wide K block (the second 16
+// columns start 32 bytes further: +2 in the descriptor's address field).
+__device__ __forceinline__ void mma_k32(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p, q;\n .reg .b64 a1, b1;\n"
+      " setp.ne.b32 p, %4, 0;\n setp.eq.u32 q, %3, %3;\n"
+      " add.s64 a1, %1, 2;\n add.s64 b1, %2, 2;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], a1, b1, %3, q;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+}
+
+template <int BK>
+__device__ __forceinline__ void mma_kblock(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  if constexpr (BK == 32) {
+    mma_k32(d, ad, bd, idesc, accum);
+  } else {
+    mma_ktile(d, ad, bd, idesc, accum);
+  }
+}
+
 constexpr int kLEpi = 4;                           // epilogue warps (one per TMEM lane quarter)
 constexpr int kLThreads = 64 + 32 * kLEpi;
 // K products a tensor-core accumulation runs over before its FP32 sum is
@@ -87,16 +136,19 @@ struct TileMap {
 };
 
 // D[m][n] = sum_k A[ya0 + m][k] B[yb0 + n][k] for m < M, n < N (FP32, row-major,
-// ldd).  A and B are packed [hi | lo] BF16 rows of 2 * kt * 64 elements.
+// ldd).  A and B are packed [hi | lo] BF16 rows of 2 * kt * BK elements.
 // With tm.nchunk > 1 every tile's K range is cut into chunks of tm.kchunk
 // blocks, each its own work item, whose sums are added into D with FP32
 // reductions (D starts at zero): the tensor cores' FP32 accumulation then runs
-// over at most kchunk * 64 products before its result is rounded into D,
+// over at most kchunk * BK products before its result is rounded into D,
 // which bounds the accumulation's drift on very long K (the plain store path,
 // nchunk = 1, is for K of a few thousand).
+template <int BK>
 __global__ void __launch_bounds__(kLThreads, 1)
     k_gemm3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int ya0, int yb0,
             int64_t M, int64_t N, int kt, float* __restrict__ D, int64_t ldd, TileMap tm, int* err) {
+  constexpr int LSTAGES = Ring<BK>::kStages, LBK = BK;
+  constexpr uint32_t kLA = Ring<BK>::kA, kLB = Ring<BK>::kB, kLStage = Ring<BK>::kStage;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   float* etile = reinterpret_cast<float*>(smem + LSTAGES * kLStage);  // kLEpi x 32 x 33
@@ -173,7 +225,7 @@ __global__ void __launch_bounds__(kLThreads, 1)
     // MMA issuer: per K block hi*hi, hi*lo, lo*hi into accumulator c & 1
     uint32_t st = 0, ph = 0, c = 0;
     bool ok = true;
-    const uint64_t desc0 = smem_desc(smem_u32(smem));
+    const uint64_t desc0 = smem_desc_bk<BK>(smem_u32(smem));
     const uint32_t empty0 = smem_u32(empty);
     const uint32_t idesc = idesc_128x256();
     ok = stall_test_wait(never, err);
@@ -192,9 +244,9 @@ __global__ void __launch_bounds__(kLThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint64_t ahi = desc0 + st * (kLStage >> 4), alo = ahi + (kLA >> 4);
         const uint64_t bhi = ahi + ((2 * kLA) >> 4), blo = bhi + (kLB >> 4);
-        mma_ktile(acc, ahi, bhi, idesc, k > k0 ? 1u : 0u);
-        mma_ktile(acc, ahi, blo, idesc, 1u);
-        mma_ktile(acc, alo, bhi, idesc, 1u);
+        mma_kblock<BK>(acc, ahi, bhi, idesc, k > k0 ? 1u : 0u);
+        mma_kblock<BK>(acc, ahi, blo, idesc, 1u);
+        mma_kblock<BK>(acc, alo, bhi, idesc, 1u);
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          empty0 + st * 8)
                      : "memory");
@@ -275,8 +327,10 @@ __global__ void __launch_bounds__(kLThreads, 1)
   }
 }
 
+template <int BK>
 size_t gemm3_smem_bytes() {
-  return 1024 + (size_t)LSTAGES * kLStage + kLEpi * 32 * 33 * 4 + (2 * LSTAGES + 6) * 8 + 16;
+  return 1024 + (size_t)Ring<BK>::kStages * Ring<BK>::kStage + kLEpi * 32 * 33 * 4 + (2 * Ring<BK>::kStages + 6) * 8 +
+         16;
 }
 
 // ---------------------------------------------------------------------------
@@ -530,14 +584,15 @@ bool encode_fn() {
 }
 
 // Tensor map of a packed [hi | lo] operand: rows of `inner` BF16, tiles of
-// 64 columns x box_rows rows, 128-byte swizzle (rows past `rows` read zero).
-bool packed_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, int box_rows) {
+// bk columns x box_rows rows, bk * 2-byte swizzle (rows past `rows` read zero).
+bool packed_map(CUtensorMap* map, const void* base, int64_t inner, int64_t rows, int box_rows, int bk) {
   cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(inner * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)LBK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
   return g_enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, bk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -586,8 +641,9 @@ int lfail(ricmrcc_ladder_t* L, int code, const std::string& m) {
     if (e_ != cudaSuccess) return lfail(L, RICMRCC_ECUDA, cudaGetErrorString(e_)); \
   } while (0)
 
-// kchunk = 0: whole K per tile, D stored; else chunks of kchunk K blocks
-// reduced into D (which the caller has zeroed).
+// kt K blocks of BK; kchunk = 0 or >= kt: whole K per tile, D stored; else
+// chunks of kchunk K blocks reduced into D (which the caller has zeroed).
+template <int BK>
 int launch_gemm3(ricmrcc_ladder_t* L, const CUtensorMap& ma, const CUtensorMap& mb, int ya0, int yb0, int64_t M,
                  int64_t N, int kt, float* D, int64_t ldd, int kchunk) {
   TileMap tm;
@@ -599,7 +655,7 @@ int launch_gemm3(ricmrcc_ladder_t* L, const CUtensorMap& ma, const CUtensorMap& 
   const int64_t total = (int64_t)tm.mt * tm.nt * tm.nchunk;
   if (total <= 0 || kt <= 0) return RICMRCC_OK;
   const int grid = (int)std::min<int64_t>(total, L->sms);
-  k_gemm3<<<grid, kLThreads, gemm3_smem_bytes(), L->s>>>(ma, mb, ya0, yb0, M, N, kt, D, ldd, tm, L->d_err);
+  k_gemm3<BK><<<grid, kLThreads, gemm3_smem_bytes<BK>(), L->s>>>(ma, mb, ya0, yb0, M, N, kt, D, ldd, tm, L->d_err);
   LCK(cudaGetLastError());
   return RICMRCC_OK;
 }
@@ -646,13 +702,13 @@ int ricmrcc_ladder_create(int n_hole, int n_virt, int n_aux, int64_t slab_rows, 
   L->v = n_virt;
   L->X = n_aux;
   L->vp = (int)pad_to(n_virt, 8);
-  L->kx = pad_to(n_aux, LBK);
+  L->kx = pad_to(n_aux, 64);
   L->nkp = (int64_t)n_hole * (n_hole + 1) / 2;
   L->nkm = (int64_t)n_hole * (n_hole - 1) / 2;
   L->nep = (int64_t)n_virt * (n_virt + 1) / 2;
   L->nem = (int64_t)n_virt * (n_virt - 1) / 2;
-  L->Kp = pad_to(L->nep, LBK);
-  L->Km = pad_to(std::max<int64_t>(L->nem, 1), LBK);
+  L->Kp = pad_to(L->nep, 64);
+  L->Km = pad_to(std::max<int64_t>(L->nem, 1), 64);
   const int64_t v = n_virt;
   // slabs: consecutive a with at most slab_rows pairs (a, b >= a) and at
   // most kMaxSlabA values of a each (one a at least).  The rebuild GEMM of a
@@ -718,8 +774,10 @@ int ricmrcc_ladder_create(int n_hole, int n_virt, int n_aux, int64_t slab_rows, 
   if (ok)
     ok = cudaMemcpy(L->tiles64, tp64.data(), tp64.size() * sizeof(int2), cudaMemcpyHostToDevice) == cudaSuccess;
   if (ok)
-    ok = cudaFuncSetAttribute(k_gemm3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm3_smem_bytes()) ==
-         cudaSuccess;
+    ok = cudaFuncSetAttribute(k_gemm3<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)gemm3_smem_bytes<32>()) == cudaSuccess &&
+         cudaFuncSetAttribute(k_gemm3<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)gemm3_smem_bytes<64>()) == cudaSuccess;
   if (!ok) {
     const cudaError_t e = cudaGetLastError();
     free_all(L);
@@ -793,12 +851,15 @@ int ricmrcc_ladder_apply_dev(ricmrcc_ladder_t* L, const double* T, double* R) {
   LCK(cudaEventRecord(L->ev_t1, L->s));
   CUtensorMap mB, mTp, mTm, mWp, mWm;
   const int64_t bp_rows = (int64_t)v * vp;
-  if (!packed_map(&mB, L->Bp, 2 * L->kx, bp_rows, LBM) || !packed_map(&mTp, L->Tp, 2 * L->Kp, L->nkp, LBM) ||
-      !packed_map(&mTm, L->Tm, 2 * L->Km, std::max<int64_t>(L->nkm, 1), LBM))
+  // the rebuild GEMM runs with 32-wide K blocks, the ladder GEMMs with 64-wide ones
+  if (!packed_map(&mB, L->Bp, 2 * L->kx, bp_rows, LBM, 32) ||
+      !packed_map(&mTp, L->Tp, 2 * L->Kp, L->nkp, LBM, 64) ||
+      !packed_map(&mTm, L->Tm, 2 * L->Km, std::max<int64_t>(L->nkm, 1), LBM, 64))
     return lfail(L, RICMRCC_ECUDA, "tensor map encoding failed");
   // the B-side map of the rebuild GEMM (256-row boxes over the same buffer)
   CUtensorMap mB256;
-  if (!packed_map(&mB256, L->Bp, 2 * L->kx, bp_rows, LBN)) return lfail(L, RICMRCC_ECUDA, "tensor map encoding failed");
+  if (!packed_map(&mB256, L->Bp, 2 * L->kx, bp_rows, LBN, 32))
+    return lfail(L, RICMRCC_ECUDA, "tensor map encoding failed");
   const size_t nslab = L->slabs.size() - 1;
   for (size_t i = 0; i < nslab; ++i) {
     const int a0 = L->slabs[i], a1 = L->slabs[i + 1];
@@ -811,8 +872,8 @@ int ricmrcc_ladder_apply_dev(ricmrcc_ladder_t* L, const double* T, double* R) {
     LCK(cudaEventRecord(e[0], L->s));
     // 1. V[(a,e)][(b,f)] for a in the slab, b >= a0
     const int64_t ldv = pad_to((int64_t)(v - a0) * vp, 4);
-    rc = launch_gemm3(L, mB, mB256, a0 * vp, a0 * vp, (int64_t)(a1 - a0) * vp, (int64_t)(v - a0) * vp,
-                      (int)(L->kx / LBK), L->V, ldv, (int)(kLadderChunk / LBK));
+    rc = launch_gemm3<32>(L, mB, mB256, a0 * vp, a0 * vp, (int64_t)(a1 - a0) * vp, (int64_t)(v - a0) * vp,
+                          (int)(L->kx / 32), L->V, ldv, 0);
     if (rc) return rc;
     LCK(cudaEventRecord(e[1], L->s));
     // 2. W+ / W- rows of the slab
@@ -821,15 +882,16 @@ int ricmrcc_ladder_apply_dev(ricmrcc_ladder_t* L, const double* T, double* R) {
     LCK(cudaGetLastError());
     LCK(cudaEventRecord(e[2], L->s));
     // 3. ladder GEMMs: D+[(kl)][(ab)], D-[(kl)][(ab)]
-    if (!packed_map(&mWp, L->Wp, 2 * L->Kp, np, LBN) || !packed_map(&mWm, L->Wm, 2 * L->Km, std::max<int64_t>(nm, 1), LBN))
+    if (!packed_map(&mWp, L->Wp, 2 * L->Kp, np, LBN, 64) ||
+        !packed_map(&mWm, L->Wm, 2 * L->Km, std::max<int64_t>(nm, 1), LBN, 64))
       return lfail(L, RICMRCC_ECUDA, "tensor map encoding failed");
     LCK(cudaMemsetAsync(L->Dp, 0, sizeof(float) * L->nkp * L->ldd, L->s));
-    rc = launch_gemm3(L, mTp, mWp, 0, 0, L->nkp, np, (int)(L->Kp / LBK), L->Dp, L->ldd, (int)(kLadderChunk / LBK));
+    rc = launch_gemm3<64>(L, mTp, mWp, 0, 0, L->nkp, np, (int)(L->Kp / 64), L->Dp, L->ldd, kLadderChunk / 64);
     if (rc) return rc;
     LCK(cudaEventRecord(e[3], L->s));
     if (L->nkm > 0 && nm > 0) {
       LCK(cudaMemsetAsync(L->Dm, 0, sizeof(float) * L->nkm * L->ldd, L->s));
-      rc = launch_gemm3(L, mTm, mWm, 0, 0, L->nkm, nm, (int)(L->Km / LBK), L->Dm, L->ldd, (int)(kLadderChunk / LBK));
+      rc = launch_gemm3<64>(L, mTm, mWm, 0, 0, L->nkm, nm, (int)(L->Km / 64), L->Dm, L->ldd, kLadderChunk / 64);
       if (rc) return rc;
     }
     LCK(cudaEventRecord(e[4], L->s));
