@@ -41,6 +41,12 @@ WORKLOADS = {
 }
 WORKLOADS["batched"] = {"workload": "batched", "instances": 48, "s": 0.5, "seed": 0,
                         "sizes": "core U{2..10}, CAS(4,4)/(6,6)/(8,8), virtual U{40..120}, n_aux 4n"}
+# the density-fitted vvvv ladder alone: at the Large sizes, and a small case
+# for profiler captures (operands ~1 GB, larger than L2)
+WORKLOADS["ladder"] = {"workload": "ladder", "n_hole": 102, "n_virt": 707, "n_aux": 2400,
+                       "sizes": "holes = 90 core + 12 active, 707 virtual, n_aux 2400 (the Large configuration)"}
+WORKLOADS["ladder_prof"] = {"workload": "ladder_prof", "n_hole": 34, "n_virt": 300, "n_aux": 800,
+                            "sizes": "34 holes, 300 virtual, n_aux 800 (profiling case)"}
 WORKLOAD = WORKLOADS["mid"]
 METRIC = "RIC-MRCCSD s/iter (Mid, one GB300)"
 METRIC_BATCHED = "RIC-MRCCSD s/iter (Batched, 48 instances per iteration, one GB300)"
@@ -280,6 +286,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload in ("ladder", "ladder_prof"):
+        return run_ladder(args)
 
     import torch
     dist, rank, ws, local = dist_init()
@@ -515,7 +523,31 @@ LADDER_LARGE = {"n_hole": 102, "n_virt": 707, "n_aux": 2400,
                 "sizes": "holes = 90 core + 12 active, 707 virtual, n_aux 2400 (the Large configuration)"}
 
 
-def ladder_large(torch, stream, pk, steps=2, warmup=1):
+def run_ladder(args):
+    """The vvvv ladder alone (`--workload ladder` / `ladder_prof`): one step =
+    one application R += sum_ef (ae|bf) T^{ef}_{kl}."""
+    import torch
+    dist, rank, ws, local = dist_init()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    with ClockSampler(local) as clk:
+        clk.mark("timed_start")
+        out = ladder_large(torch, stream, peaks(), steps=max(args.steps, 1), warmup=args.warmup, w=WORKLOAD)
+        clk.mark("timed_end")
+    if rank != 0:
+        return 0
+    line = {"metric": "density-fitted vvvv ladder, s per application", "value": out["s_per_application"],
+            "unit": "s/application", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["s_per_application"] * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": out["dtype"], "data": "synthetic",
+            "config": {"workload": WORKLOAD["workload"], "sizes": WORKLOAD["sizes"],
+                       "l2": "operands larger than L2, no flush"},
+            "roofline": out["roofline"], "clocks": clk.summary(), "ladder": out}
+    print(json.dumps(line))
+    return 0
+
+
+def ladder_large(torch, stream, pk, steps=2, warmup=1, w=None):
     """R += sum_ef (ae|bf) T^{ef}_{kl} at the Large sizes through
     ricmrcc_ladder_apply_dev: seconds per application (CUDA events on the
     library's stream), the phases' times, and the ladder GEMM against the
@@ -523,7 +555,7 @@ def ladder_large(torch, stream, pk, steps=2, warmup=1):
     drawn on the device."""
     import paper_2511_03567_gb300 as ric
     import synthetic
-    w = LADDER_LARGE
+    w = w or LADDER_LARGE
     nh, nv, nx = w["n_hole"], w["n_virt"], w["n_aux"]
     Bv, T = synthetic.make_ladder_inputs_device(nh, nv, nx, seed=0)
     R = torch.zeros_like(T)

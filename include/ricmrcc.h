@@ -491,9 +491,15 @@ RICMRCC_API int ricmrcc_set_wait_limit(double seconds, int stall_test);
  * eigenvalues: device [n], ascending.  eigenvectors: device [n][n], column j
  * belongs to eigenvalue j and its largest-magnitude component is positive
  * (the conventions of ricmrcc_semicanonicalize).  stream: cudaStream_t (NULL
- * = legacy default); the call returns once the work is enqueued.
- * Returns EINVAL for NULL pointers, n < 1 or n > RICMRCC_NOALLOC_MAX_N, and
- * ECUDA if the device address of the working array cannot be obtained.
+ * = legacy default); the call returns once the work is enqueued.  The
+ * eigen-decomposition is a cyclic Jacobi iteration in one thread block
+ * (about n^3 work per sweep; measured on a GB300: 1.6 s per call at n = 300,
+ * 40 s at n = 1000, milliseconds for the blocks of a few dozen orbitals of
+ * the semi-canonicalisation).  If 40 sweeps leave the block unconverged, every eigenvalue is
+ * NaN: the call only enqueues work, so the outcome reaches the caller that
+ * way.  Returns EINVAL for NULL pointers, n < 1 or n > RICMRCC_NOALLOC_MAX_N,
+ * and ECUDA if the device address of the working array cannot be obtained or
+ * one of this call's own launches fails.
  *
  * The first call on each device looks up that device's address of the
  * working array (with the device current); make that first call before any

@@ -1510,7 +1510,17 @@ int ricmrcc_semicanonicalize(ricmrcc_t* h, double* U_out) {
     CK(cudaMemcpy2DAsync(blk, sizeof(double) * sz[b], h->F + (int64_t)off[b] * n + off[b],
                          sizeof(double) * n, sizeof(double) * sz[b], sz[b],
                          cudaMemcpyDeviceToDevice, h->s));
-    run_jacobi(blk, V, sz[b], U, n, off[b], h->d_sweeps, h->s);
+    CK(run_jacobi(blk, V, sz[b], U, n, off[b], h->d_sweeps, h->s));
+    int sweeps = 0;
+    CK(cudaMemcpyAsync(&sweeps, h->d_sweeps, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    if (sweeps < 0) {
+      cudaFree(U);
+      cudaFree(blk);
+      cudaFree(V);
+      cudaFree(tmp);
+      return fail(h, RICMRCC_NOT_CONVERGED, "Jacobi eigen-decomposition of a Fock block did not converge");
+    }
   }
   // rotations x' = U^T x U, one index at a time, with the contraction kernel
   auto rotate = [&](double* x, int nidx, int64_t lead, int dim, const double* u, int64_t ldu,

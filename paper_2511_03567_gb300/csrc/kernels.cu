@@ -470,6 +470,8 @@ void launch_extrapolate(double* T, const double* vecs, const double* coef, const
 // Semi-canonicalisation: cyclic Jacobi on one symmetric block (one CTA)
 // ---------------------------------------------------------------------------
 namespace {
+// *sweeps_done receives the sweeps performed, or -1 when max_sweeps sweeps
+// left the off-diagonal norm above tol (not converged).
 __global__ void k_jacobi(double* __restrict__ Ablk, double* __restrict__ V, int n, int max_sweeps,
                          double tol, int* sweeps_done) {
   // A (n x n, row-major) is overwritten; V accumulates rotations (V0 = I).
@@ -483,7 +485,7 @@ __global__ void k_jacobi(double* __restrict__ Ablk, double* __restrict__ V, int 
   if (threadIdx.x == 0) tots = tot;
   __syncthreads();
   int sw = 0;
-  for (; sw < max_sweeps; ++sw) {
+  for (;; ++sw) {
     double off = 0.0;
     for (int i = threadIdx.x; i < n * n; i += blockDim.x)
       if (i / n != i % n) off += Ablk[i] * Ablk[i];
@@ -491,6 +493,10 @@ __global__ void k_jacobi(double* __restrict__ Ablk, double* __restrict__ V, int 
     if (threadIdx.x == 0) offs = off;
     __syncthreads();
     if (offs <= tol * tol * tots) break;
+    if (sw == max_sweeps) {
+      sw = -1;
+      break;
+    }
     for (int p = 0; p < n - 1; ++p)
       for (int q = p + 1; q < n; ++q) {
         if (threadIdx.x == 0) {
@@ -551,12 +557,19 @@ __global__ void k_jacobi_finish(const double* __restrict__ Ablk, const double* _
 }
 }  // namespace
 
-int run_jacobi(double* Ablk, double* V, int n, double* U, int n_full, int off, int* d_sweeps,
-               cudaStream_t s) {
-  if (n == 0) return 0;
-  k_jacobi<<<1, 1024, 0, s>>>(Ablk, V, n, 40, 1e-15, d_sweeps);
-  k_jacobi_finish<<<1, 256, 0, s>>>(Ablk, V, n, U, n_full, off);
-  return 0;
+// Convergence target of the off-diagonal norm relative to the Frobenius norm:
+// 1e-15, loosened to n x 2.2e-16 for large blocks (the rounding floor of the
+// rotations grows with n).  Returns the launches' own status.
+cudaError_t run_jacobi(double* Ablk, double* V, int n, double* U, int n_full, int off, int* d_sweeps,
+                       cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  int max_sweeps = 40;
+  double tol = n * 2.2e-16 > 1e-15 ? n * 2.2e-16 : 1e-15;
+  void* a1[] = {&Ablk, &V, &n, &max_sweeps, &tol, &d_sweeps};
+  cudaError_t e = cudaLaunchKernel((const void*)k_jacobi, dim3(1), dim3(1024), a1, 0, s);
+  if (e != cudaSuccess) return e;
+  void* a2[] = {(void*)&Ablk, (void*)&V, &n, &U, &n_full, &off};
+  return cudaLaunchKernel((const void*)k_jacobi_finish, dim3(1), dim3(256), a2, 0, s);
 }
 
 namespace {

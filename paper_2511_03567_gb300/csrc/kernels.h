@@ -23,8 +23,11 @@ void launch_dots(double* dots, const double* enew, const double* hist, int64_t n
 void launch_diis_solve(const double* gram, double* coef, int m, int* status, cudaStream_t st);
 void launch_extrapolate(double* T, const double* vecs, const double* coef, const int* status,
                         int m, int newest, int64_t n, int64_t ld, cudaStream_t st);
-int run_jacobi(double* Ablk, double* V, int n, double* U, int n_full, int off, int* d_sweeps,
-               cudaStream_t s);
+// Cyclic Jacobi eigen-decomposition of one symmetric block (overwritten)
+// into columns of U at (off, off); *d_sweeps (device) receives the sweeps or
+// -1 if the sweep limit was reached unconverged.  Returns the launch status.
+cudaError_t run_jacobi(double* Ablk, double* V, int n, double* U, int n_full, int off, int* d_sweeps,
+                       cudaStream_t s);
 void launch_energy_out(double* out, const double* acc, double e0, cudaStream_t s);
 void launch_adj_y(const double* Lam, double* Yraw, double* Ytil, const double* eps, const Dims& d, double s,
                   cudaStream_t st);

@@ -48,9 +48,17 @@ int scratch_address(double** out) {
   return RICMRCC_OK;
 }
 
-// Eigenvalues in ascending order from the diagonal the sweeps converged to.
-__global__ void k_sorted_diagonal(const double* __restrict__ A, int n, double* __restrict__ w) {
+// Eigenvalues in ascending order from the diagonal the sweeps converged to;
+// all NaN when the sweeps stopped unconverged (*sweeps < 0), which is how an
+// enqueue-only call reports that outcome to its caller.
+__global__ void k_sorted_diagonal(const double* __restrict__ A, int n, const int* __restrict__ sweeps,
+                                  double* __restrict__ w) {
+  const bool failed = *sweeps < 0;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    if (failed) {
+      w[j] = __longlong_as_double(0x7ff8000000000000ll);
+      continue;
+    }
     const double x = A[(int64_t)j * n + j];
     int rank = 0;
     for (int k = 0; k < n; ++k) {
@@ -79,7 +87,10 @@ extern "C" int ricmrcc_block_eigh_noalloc(const double* A, int n, double* eigenv
   if (cudaMemcpyAsync(work, A, sizeof(double) * (size_t)n * n, cudaMemcpyDeviceToDevice, s) !=
       cudaSuccess)
     return RICMRCC_ECUDA;
-  run_jacobi(work, rot, n, eigenvectors, n, 0, sweeps, s);
-  k_sorted_diagonal<<<1, 256, 0, s>>>(work, n, eigenvalues);
-  return cudaGetLastError() == cudaSuccess ? RICMRCC_OK : RICMRCC_ECUDA;
+  // every status below is the one of this call's own launch
+  if (run_jacobi(work, rot, n, eigenvectors, n, 0, sweeps, s) != cudaSuccess) return RICMRCC_ECUDA;
+  void* args[] = {(void*)&work, &n, (void*)&sweeps, &eigenvalues};
+  if (cudaLaunchKernel((const void*)k_sorted_diagonal, dim3(1), dim3(256), args, 0, s) != cudaSuccess)
+    return RICMRCC_ECUDA;
+  return RICMRCC_OK;
 }
