@@ -114,8 +114,22 @@ typedef struct {
 /* Create a handle for one problem size (Table 1 spaces) and an auxiliary
  * basis of n_aux functions.  n_core, n_act, n_virt >= 0, n_aux >= 1.
  * n_act = 0 is a single-determinant reference.  Uses the current CUDA device.
+ * The many-body residual is RIC-MRCCSD's (RICMRCC_METHOD_RIC).
  * Errors: EINVAL (negative sizes), ENOMEM, ECUDA. */
 RICMRCC_API int ricmrcc_create(int n_core, int n_act, int n_virt, int n_aux, ricmrcc_t** out);
+
+/* method argument of ricmrcc_create_method */
+enum {
+  RICMRCC_METHOD_RIC = 0,  /* H + [H,T] + 1/2[[H,T],T] under the RIC neglect rules (Sec. 2.2) */
+  RICMRCC_METHOD_FULL = 1  /* the same expansion without them (cumulants up to lambda_3): the
+                              reference point of the neglect error; its term list is ~40 times
+                              longer (73 902 residual terms), meant for small systems */
+};
+/* ricmrcc_create with the residual of `method`.  Every call applies to both
+ * methods except ricmrcc_energy_backward (RIC only: ENOTSUP).  Errors as
+ * ricmrcc_create, EINVAL for an unknown method. */
+RICMRCC_API int ricmrcc_create_method(int n_core, int n_act, int n_virt, int n_aux, int method,
+                                      ricmrcc_t** out);
 
 /* Release every resource of the handle (NULL is ignored). */
 RICMRCC_API void ricmrcc_destroy(ricmrcc_t* h);

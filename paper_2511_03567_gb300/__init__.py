@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libricmrcc.so")
 OK, EINVAL, ENOMEM, ECUDA, NOT_CONVERGED, DIVERGED, ESTATE, ENOTSUP = range(8)
 RDM, CUMULANT = 0, 1
 FP64, MIXED = 0, 1
+METHOD_RIC, METHOD_FULL = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "NOT_CONVERGED",
                 5: "DIVERGED", 6: "ESTATE", 7: "ENOTSUP"}
 
@@ -114,6 +115,7 @@ def load_library():
     vp = ctypes.c_void_p
     sig = {
         "ricmrcc_create": ([ctypes.c_int] * 4 + [ctypes.POINTER(vp)], ctypes.c_int),
+        "ricmrcc_create_method": ([ctypes.c_int] * 5 + [ctypes.POINTER(vp)], ctypes.c_int),
         "ricmrcc_destroy": ([vp], None),
         "ricmrcc_last_error": ([vp], ctypes.c_char_p),
         "ricmrcc_set_stream": ([vp, vp], ctypes.c_int),
@@ -201,16 +203,17 @@ def _host(x):
 class RicMrcc:
     """One problem (sizes fixed at creation) on the current CUDA device."""
 
-    def __init__(self, n_core, n_act, n_virt, n_aux, _borrowed=None):
+    def __init__(self, n_core, n_act, n_virt, n_aux, _borrowed=None, method=METHOD_RIC):
         self.lib = load_library()
         self.dims = (n_core, n_act, n_virt, n_aux)
+        self.method = method
         self._owner = None
         if _borrowed is not None:
             # handle owned by a RicMrccBatch (kept alive through _owner)
             h, self._owner = _borrowed
         else:
             h = ctypes.c_void_p()
-            rc = self.lib.ricmrcc_create(n_core, n_act, n_virt, n_aux, ctypes.byref(h))
+            rc = self.lib.ricmrcc_create_method(n_core, n_act, n_virt, n_aux, int(method), ctypes.byref(h))
             if rc != OK:
                 raise RicMrccError(rc, "ricmrcc_create failed")
         self.h = h

@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 SOURCES = ["api.cu", "batch.cu", "planner.cu", "kernels.cu", "noalloc.cu", "tcgemm.cu", "grouped.cu", "schedule.cu", "ladder.cu"]
+HOST_SOURCES = ["full_terms.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 LIBNAME = "libricmrcc.so"
@@ -33,10 +34,27 @@ def _newer(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def cuda_include():
+    return os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
+
+
+def unpack_full_terms(force=False):
+    """csrc/ric_terms_full.inc.gz -> _build/ric_terms_full.inc (when newer)."""
+    import gzip
+    src = os.path.join(CSRC, "ric_terms_full.inc.gz")
+    dst = os.path.join(OUT, "ric_terms_full.inc")
+    if force or _newer(dst, [src]):
+        with gzip.open(src, "rb") as f, open(dst + ".tmp", "wb") as g:
+            g.write(f.read())
+        os.replace(dst + ".tmp", dst)
+    return dst
+
+
 def build(force=False, verbose=False):
     os.makedirs(OUT, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".inc"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "ricmrcc.h"))
+    full_inc = unpack_full_terms(force)
     objs = []
     jobs = []
     for src in SOURCES:
@@ -45,6 +63,15 @@ def build(force=False, verbose=False):
         objs.append(o)
         if force or _newer(o, [s] + headers):
             jobs.append([nvcc(), *ARCH, *FLAGS, "-c", s, "-o", o])
+    # the unfiltered term tables: data only, a host unit (g++ at -O0 keeps
+    # the 17 MB initializer quick to compile)
+    for src in HOST_SOURCES:
+        s = os.path.join(CSRC, src)
+        o = os.path.join(OUT, src.replace(".cpp", ".o"))
+        objs.append(o)
+        if force or _newer(o, [s, full_inc] + headers):
+            jobs.append(["g++", "-O0", "-std=c++17", "-fPIC", "-I", OUT, "-I", CSRC, "-I", cuda_include(),
+                         "-c", s, "-o", o])
 
     def run(cmd):
         if verbose:
@@ -54,7 +81,7 @@ def build(force=False, verbose=False):
             raise RuntimeError(f"nvcc failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
         return r
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with ThreadPoolExecutor(max_workers=len(SOURCES) + len(HOST_SOURCES)) as ex:
         list(ex.map(run, jobs))
     lib = os.path.join(OUT, LIBNAME)
     if force or jobs or not os.path.exists(lib):

@@ -152,10 +152,20 @@ int plan(ricmrcc_t* h) {
   // separate planners: the programs run at different times and each zeroes
   // the shared arena first, so they must not share intermediates
   Planner pl(d, tv, ov, h->scal + 3), pc(d, tv, ov, h->scal + 3);
-  for (const auto& t : kResidualTerms)
-    if (!pl.add_term(t, &h->res_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad residual term");
-  for (const auto& t : kEnergyTerms)
-    if (!pl.add_term(t, &h->res_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad energy term");
+  // the residual and energy terms of the handle's method: RIC (Sec. 2.2's
+  // neglect rules) or the unfiltered two-fold commutator expansion
+  size_t n_res = sizeof(kResidualTerms) / sizeof(kResidualTerms[0]);
+  size_t n_en = sizeof(kEnergyTerms) / sizeof(kEnergyTerms[0]);
+  const RicTermDesc* res_terms = kResidualTerms;
+  const RicTermDesc* en_terms = kEnergyTerms;
+  if (h->method == RICMRCC_METHOD_FULL) {
+    res_terms = ric_full_terms(0, &n_res);
+    en_terms = ric_full_terms(1, &n_en);
+  }
+  for (size_t i = 0; i < n_res; ++i)
+    if (!pl.add_term(res_terms[i], &h->res_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad residual term");
+  for (size_t i = 0; i < n_en; ++i)
+    if (!pl.add_term(en_terms[i], &h->res_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad energy term");
   for (const auto& t : kCumulant3Terms)
     if (!pc.add_term(t, &h->cum_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad cumulant term");
   h->arena_elems = std::max<int64_t>(std::max<int64_t>(pl.arena_size(), pc.arena_size()), 1);
@@ -703,11 +713,17 @@ extern "C" {
 static int create_impl(ricmrcc_t* h, int n_core, int n_act, int n_virt, int n_aux);
 
 int ricmrcc_create(int n_core, int n_act, int n_virt, int n_aux, ricmrcc_t** out) {
+  return ricmrcc_create_method(n_core, n_act, n_virt, n_aux, RICMRCC_METHOD_RIC, out);
+}
+
+int ricmrcc_create_method(int n_core, int n_act, int n_virt, int n_aux, int method, ricmrcc_t** out) {
   if (!out) return RICMRCC_EINVAL;
   *out = nullptr;
   if (n_core < 0 || n_act < 0 || n_virt < 0 || n_aux < 1 || n_core + n_act + n_virt < 1)
     return RICMRCC_EINVAL;
+  if (method != RICMRCC_METHOD_RIC && method != RICMRCC_METHOD_FULL) return RICMRCC_EINVAL;
   ricmrcc_t* h = new ricmrcc();
+  h->method = method;
   const int rc = create_impl(h, n_core, n_act, n_virt, n_aux);
   if (rc != RICMRCC_OK) {
     ricmrcc_destroy(h);
@@ -1697,6 +1713,8 @@ extern "C" {
 
 int ricmrcc_energy_backward(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds) {
   if (!h) return RICMRCC_EINVAL;
+  if (h->method != RICMRCC_METHOD_RIC)
+    return fail(h, RICMRCC_ENOTSUP, "energy_backward is generated for the RIC method only");
   if (!h->solved) return fail(h, RICMRCC_ESTATE, "energy_backward needs a converged ricmrcc_solve");
   TRY(enter(h));
   TRY(plan_adjoint(h));

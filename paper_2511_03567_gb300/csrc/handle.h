@@ -48,6 +48,7 @@ constexpr int kTcLanes = kLanes - kTcLane0;
 
 struct ricmrcc {
   Dims d{};
+  int method = 0;  // RICMRCC_METHOD_RIC or RICMRCC_METHOD_FULL
   std::string err;
   cudaStream_t user_stream = nullptr;
   cudaStream_t s = nullptr;  // internal work stream

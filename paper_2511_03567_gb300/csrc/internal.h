@@ -26,8 +26,12 @@ struct RicTermDesc {
   uint8_t nfac;
   uint8_t nlab;
   uint8_t mask[16];  // core=1 active=2 virtual=4
-  RicFactorDesc fac[7];
+  RicFactorDesc fac[8];  // the RIC tables use at most 7, the unfiltered ones 8
 };
+
+// Unfiltered BCH-2 ("FULL") term tables (full_terms.cpp, from the generated
+// csrc/ric_terms_full.inc.gz): which = 0 residual, 1 energy.
+const RicTermDesc* ric_full_terms(int which, size_t* count);
 
 enum TensorId { TF = 0, TV = 1, TT1 = 2, TT2 = 3, TG = 4, TE = 5, TD2 = 6, TD3 = 7, TY1 = 8, TY2 = 9, NTENSOR = 10 };
 enum OutId { OR1 = 0, OX2 = 1, OE = 2, OL3 = 3, OGT1 = 4, OGT2 = 5, OGF = 6, OGV = 7, NOUT = 8 };
