@@ -159,6 +159,13 @@ def fp32_peak_tflops(torch):
     return props.multi_processor_count * 128 * 2 * mhz * 1e6 / 1e12
 
 
+# DRAM bytes (read + write) of the grouped tensor-core launches of one Mid
+# residual, from the ncu capture named below (None until one was taken with
+# the current kernel)
+TC_TRAFFIC_PER_RESIDUAL = None
+TC_TRAFFIC_SOURCE = None
+
+
 def roofline(kind_ms, info, mixed, pk, fp64_peak, torch):
     """Dominant kernel of the serialised per-kernel profile against its roof."""
     c = int(np.argmax(kind_ms))
@@ -170,18 +177,20 @@ def roofline(kind_ms, info, mixed, pk, fp64_peak, torch):
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), of measured",
                 "work": "bytes: FP64 source read + BF16 hi and lo halves written, per packed buffer"}
     elif c == 4:
-        # the tensor-core GEMMs read every packed operand once and update every
-        # output in FP64: 3 x 2MNK BF16 FLOPs over these bytes is ~94 FLOP/B at
-        # the 8/8/120 size, below the machine balance (measured BF16 / HBM =
-        # 250 FLOP/B), so HBM is their roof
+        # the split-precision products run on the tensor cores: 3 BF16 MMAs
+        # (hi*hi, hi*lo, lo*hi) per product of the method, counted as stated;
+        # the byte view (packed operands once + FP64 read and write of every
+        # output per launched op) is kept beside it
         gb = getattr(info, "tc_gemm_bytes", 0.0)
-        roof = {"bound": "hbm", "achieved": gb / t / 1e9, "unit": "GB/s", "peak": pk.get("hbm_gbs", 6800.0),
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy), of measured",
-                "work": "bytes: packed operand buffers read once + 16 B (FP64 read+write) per output "
-                        "element per launched (merged) op",
-                "tensor_tflops": 3.0 * work / t / 1e12,
-                "tensor_frac": 3.0 * work / t / 1e12 / pk.get("bf16_tflops_sustained", 1700.0),
-                "tensor_peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured"}
+        roof = {"bound": "tensor", "achieved": 3.0 * work / t / 1e12, "unit": "TFLOP/s",
+                "peak": pk.get("bf16_tflops_sustained", 1700.0),
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained, of measured",
+                "work": "3 x 2 MNK BF16 FLOPs per tensor-core contraction (the split products counted)",
+                "frac_of_burst": 3.0 * work / t / 1e12 / pk.get("bf16_tflops", 1900.0),
+                "method_tflops": work / t / 1e12,
+                "bytes_view": {"achieved_gbs": gb / t / 1e9, "peak_gbs": pk.get("hbm_gbs", 6800.0),
+                               "bytes": "packed operand buffers read once + 16 B (FP64 read+write) per output "
+                                        "element per launched (merged) op"}}
     elif mixed:
         roof = {"bound": "alu", "achieved": work / t / 1e12, "unit": "TFLOP/s", "peak": fp32_peak_tflops(torch),
                 "peak_source": "nominal FP32 FMA rate: SMs x 128 x 2 x max SM clock (derived)",
@@ -192,9 +201,8 @@ def roofline(kind_ms, info, mixed, pk, fp64_peak, torch):
                 "work": "contraction FLOPs (FP64)"}
     roof["kernel"] = name
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
-    roof["traffic"] = None
-    roof["traffic_note"] = ("not captured at this size; on the 4/CAS(4,4)/64/200 case the tensor-core "
-                            "launches moved 0.86x their algorithmic bytes (profiles/tc_grouped_prof_full.md)")
+    roof["traffic"] = TC_TRAFFIC_PER_RESIDUAL if c == 4 else None
+    roof["traffic_source"] = TC_TRAFFIC_SOURCE if c == 4 else None
     roof["contractions_per_residual"] = int(info.kernel_ops[c])
     roof["ms_per_residual"] = float(kind_ms[c])
     roof["profile_ms_per_residual"] = {n: float(x) for n, x in zip(KERNEL_NAMES, kind_ms)}

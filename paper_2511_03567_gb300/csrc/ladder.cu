@@ -152,9 +152,11 @@ __global__ void __launch_bounds__(kLThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   float* etile = reinterpret_cast<float*>(smem + LSTAGES * kLStage);  // kLEpi x 32 x 33
-  uint64_t* full = reinterpret_cast<uint64_t*>(etile + kLEpi * 32 * 33);
-  uint64_t* empty = full + LSTAGES;
-  uint64_t* tfull = empty + LSTAGES;  // [2]
+  // each stage's four tiles travel in two groups with their own barriers:
+  // group 1 = {A_lo, B_hi}, group 2 = {A_hi, B_lo} (see the MMA issuer)
+  uint64_t* full = reinterpret_cast<uint64_t*>(etile + kLEpi * 32 * 33);  // [2][LSTAGES]
+  uint64_t* empty = full + 2 * LSTAGES;                                    // [2][LSTAGES]
+  uint64_t* tfull = empty + 2 * LSTAGES;  // [2]
   uint64_t* tempty = tfull + 2;       // [2]
   uint64_t* fin = tempty + 2;
   uint64_t* never = fin + 1;  // completed by nothing (error-path test)
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(kLThreads, 1)
   const int64_t total = (int64_t)tm.mt * tm.nt * tm.nchunk;
   const bool reduce = tm.nchunk > 1;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < LSTAGES; ++s) {
+    for (int s = 0; s < 2 * LSTAGES; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
@@ -187,31 +189,39 @@ __global__ void __launch_bounds__(kLThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // TMA producer: stage st, phase ph of the ring; load i goes to stage
-    // i % LSTAGES with phase (i / LSTAGES) & 1
+    // TMA producer: stage st, phase ph of the ring; group g of load i goes to
+    // stage i % LSTAGES with phase (i / LSTAGES) & 1.  Group 1 of a stage is
+    // released after the second product, group 2 after the third, so the
+    // next refill of a stage starts a third of its MMAs earlier.
     uint32_t st = 0, ph = 0;
-    int64_t issued = 0;
+    int64_t issued[2] = {0, 0};
     bool ok = true;
     const uint32_t s0 = smem_u32(smem), full0 = smem_u32(full);
+    constexpr uint32_t kGroup = kLA + kLB;
     const int lo_x = kt * LBK;
     for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
       int mi, ni, k0, k1;
       tm.item(t, &mi, &ni, &k0, &k1, kt);
       const int ya = ya0 + mi * LBM, yb = yb0 + ni * LBN;
-      for (int k = k0; k < k1; ++k) {
-        if (issued >= LSTAGES && !mbar_wait(empty + st, ph ^ 1u, err)) {
-          ok = false;
-          break;
-        }
-        const uint32_t fb = full0 + st * 8;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kLStage) : "memory");
+      for (int k = k0; k < k1 && ok; ++k) {
         const uint32_t sb = s0 + st * kLStage;
         const int x = k * LBK;
-        tma_load_2d_u(sb, &tmA, x, ya, fb);
-        tma_load_2d_u(sb + kLA, &tmA, lo_x + x, ya, fb);
-        tma_load_2d_u(sb + 2 * kLA, &tmB, x, yb, fb);
-        tma_load_2d_u(sb + 2 * kLA + kLB, &tmB, lo_x + x, yb, fb);
-        ++issued;
+        for (int g = 0; g < 2; ++g) {
+          if (issued[g] >= LSTAGES && !mbar_wait(empty + g * LSTAGES + st, ph ^ 1u, err)) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = full0 + (g * LSTAGES + st) * 8;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kGroup) : "memory");
+          if (g == 0) {
+            tma_load_2d_u(sb + kLA, &tmA, lo_x + x, ya, fb);       // A_lo
+            tma_load_2d_u(sb + 2 * kLA, &tmB, x, yb, fb);          // B_hi
+          } else {
+            tma_load_2d_u(sb, &tmA, x, ya, fb);                    // A_hi
+            tma_load_2d_u(sb + 2 * kLA + kLB, &tmB, lo_x + x, yb, fb);  // B_lo
+          }
+          ++issued[g];
+        }
         if (++st == LSTAGES) {
           st = 0;
           ph ^= 1u;
@@ -219,8 +229,9 @@ __global__ void __launch_bounds__(kLThreads, 1)
       }
     }
     // copies still in flight land before the CTA exits
-    for (int64_t i = issued > LSTAGES ? issued - LSTAGES : 0; i < issued; ++i)
-      mbar_wait_drain(full + i % LSTAGES, (uint32_t)(i / LSTAGES) & 1u, err);
+    for (int g = 0; g < 2; ++g)
+      for (int64_t i = issued[g] > LSTAGES ? issued[g] - LSTAGES : 0; i < issued[g]; ++i)
+        mbar_wait_drain(full + g * LSTAGES + i % LSTAGES, (uint32_t)(i / LSTAGES) & 1u, err);
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: per K block hi*hi, hi*lo, lo*hi into accumulator c & 1
     uint32_t st = 0, ph = 0, c = 0;
@@ -237,18 +248,29 @@ __global__ void __launch_bounds__(kLThreads, 1)
       int mi, ni, k0, k1;
       tm.item(t, &mi, &ni, &k0, &k1, kt);
       for (int k = k0; k < k1; ++k) {
+        const uint64_t ahi = desc0 + st * (kLStage >> 4), alo = ahi + (kLA >> 4);
+        const uint64_t bhi = ahi + ((2 * kLA) >> 4), blo = bhi + (kLB >> 4);
+        // lo*hi needs group 1 only; hi*hi and hi*lo need group 2 as well.
+        // Group 1 is released once hi*hi (the last user of B_hi) completes,
+        // group 2 after hi*lo.
         if (!mbar_wait(full + st, ph, err)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t ahi = desc0 + st * (kLStage >> 4), alo = ahi + (kLA >> 4);
-        const uint64_t bhi = ahi + ((2 * kLA) >> 4), blo = bhi + (kLB >> 4);
-        mma_kblock<BK>(acc, ahi, bhi, idesc, k > k0 ? 1u : 0u);
-        mma_kblock<BK>(acc, ahi, blo, idesc, 1u);
-        mma_kblock<BK>(acc, alo, bhi, idesc, 1u);
+        mma_kblock<BK>(acc, alo, bhi, idesc, k > k0 ? 1u : 0u);
+        if (!mbar_wait(full + LSTAGES + st, ph, err)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        mma_kblock<BK>(acc, ahi, bhi, idesc, 1u);
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          empty0 + st * 8)
+                     : "memory");
+        mma_kblock<BK>(acc, ahi, blo, idesc, 1u);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         empty0 + (LSTAGES + st) * 8)
                      : "memory");
         if (++st == LSTAGES) {
           st = 0;
@@ -329,7 +351,7 @@ __global__ void __launch_bounds__(kLThreads, 1)
 
 template <int BK>
 size_t gemm3_smem_bytes() {
-  return 1024 + (size_t)Ring<BK>::kStages * Ring<BK>::kStage + kLEpi * 32 * 33 * 4 + (2 * Ring<BK>::kStages + 6) * 8 +
+  return 1024 + (size_t)Ring<BK>::kStages * Ring<BK>::kStage + kLEpi * 32 * 33 * 4 + (4 * Ring<BK>::kStages + 6) * 8 +
          16;
 }
 
