@@ -296,6 +296,9 @@ RICMRCC_API int ricmrcc_run_largest_ops(ricmrcc_t* h, int count);
  * Requires the last ricmrcc_solve to have converged (else ESTATE); uses its
  * flow s and options.  Returns NOT_CONVERGED / DIVERGED for the multipliers. */
 RICMRCC_API int ricmrcc_energy_backward(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds);
+/* Same with device outputs (dE_ds a device double), written on the handle's
+ * stream; the multiplier iteration still synchronises with the host. */
+RICMRCC_API int ricmrcc_energy_backward_dev(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds);
 
 /* Copy the stored amplitudes out / in (flat class layout, host pointers);
  * set_amplitudes allows warm starts and resuming an interrupted solve.

@@ -141,6 +141,7 @@ def load_library():
         "ricmrcc_set_amplitudes": ([vp, vp, vp], ctypes.c_int),
         "ricmrcc_run_largest_ops": ([vp, ctypes.c_int], ctypes.c_int),
         "ricmrcc_energy_backward": ([vp, vp, vp, vp], ctypes.c_int),
+        "ricmrcc_energy_backward_dev": ([vp, vp, vp, vp], ctypes.c_int),
         "ricmrcc_gemm_bf16x3": ([vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, vp],
                                 ctypes.c_int),
@@ -387,6 +388,11 @@ def _energy_backward(self):
     return dh, dB, ds.value
 
 
+def _energy_backward_dev(self, dh, dB, ds):
+    """Device-output variant: CUDA float64 tensors [n,n], [n_aux,n,n], [1]."""
+    self._check(self.lib.ricmrcc_energy_backward_dev(self.h, _ptr(dh), _ptr(dB), _ptr(ds)))
+
+
 def _get_residual(self):
     """(R1, R2) flat class layout of the last residual evaluation."""
     r1 = np.zeros(self.layout.t1_size)
@@ -426,6 +432,7 @@ RicMrcc.set_tile_rule = _set_tile_rule
 RicMrcc.get_tile_rule = _get_tile_rule
 RicMrcc.tune = _tune
 RicMrcc.energy_backward = _energy_backward
+RicMrcc.energy_backward_dev = _energy_backward_dev
 RicMrcc.step = _step
 RicMrcc.plan_info = _plan_info
 RicMrcc.profile = _profile

@@ -1711,7 +1711,7 @@ int diis_step(ricmrcc_t* h, const double* vec, const double* err, double* target
 
 extern "C" {
 
-int ricmrcc_energy_backward(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds) {
+static int energy_backward_impl(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds, bool dev) {
   if (!h) return RICMRCC_EINVAL;
   if (h->method != RICMRCC_METHOD_RIC)
     return fail(h, RICMRCC_ENOTSUP, "energy_backward is generated for the RIC method only");
@@ -1797,12 +1797,24 @@ int ricmrcc_energy_backward(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* 
     CK(cudaStreamSynchronize(h->s));
     CK(cudaFree(dt));
   }
-  if (dE_dh) CK(cudaMemcpyAsync(dE_dh, h->gh, sizeof(double) * n2, cudaMemcpyDeviceToHost, h->s));
-  if (dE_dB) CK(cudaMemcpyAsync(dE_dB, h->gB, sizeof(double) * d.X * n2, cudaMemcpyDeviceToHost, h->s));
-  CK(cudaMemcpyAsync(h->host_scal + 5, h->scal + 5, sizeof(double), cudaMemcpyDeviceToHost, h->s));
-  CK(cudaStreamSynchronize(h->s));
-  if (dE_ds) *dE_ds = h->host_scal[5];
+  const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (dE_dh) CK(cudaMemcpyAsync(dE_dh, h->gh, sizeof(double) * n2, kind, h->s));
+  if (dE_dB) CK(cudaMemcpyAsync(dE_dB, h->gB, sizeof(double) * d.X * n2, kind, h->s));
+  if (dev) {
+    if (dE_ds) CK(cudaMemcpyAsync(dE_ds, h->scal + 5, sizeof(double), kind, h->s));
+  } else {
+    CK(cudaMemcpyAsync(h->host_scal + 5, h->scal + 5, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    if (dE_ds) *dE_ds = h->host_scal[5];
+  }
   return leave(h);
+}
+
+int ricmrcc_energy_backward(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds) {
+  return energy_backward_impl(h, dE_dh, dE_dB, dE_ds, false);
+}
+int ricmrcc_energy_backward_dev(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds) {
+  return energy_backward_impl(h, dE_dh, dE_dB, dE_ds, true);
 }
 
 }  // extern "C"

@@ -108,6 +108,35 @@ def test_autograd_function():
     assert abs(float(ts.grad) - ds) < 1e-12
 
 
+def test_device_outputs_equal_host_outputs():
+    import torch
+    g, h, B, rot = _setup(2, 4, 10, 48, 0)
+    _energy(g, h, B, 0.5)
+    dh, dB, ds = g.energy_backward()
+    n = h.shape[0]
+    ddh = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    ddB = torch.zeros(B.shape, dtype=torch.float64, device="cuda")
+    dds = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g.energy_backward_dev(ddh, ddB, dds)
+    torch.cuda.synchronize()
+    assert np.array_equal(ddh.cpu().numpy(), dh) and np.array_equal(ddB.cpu().numpy(), dB)
+    assert float(dds.item()) == ds
+
+
+def test_full_method_has_no_adjoint():
+    import paper_2511_03567_gb300 as ric
+    p = synthetic.make_problem(1, 2, 2, 12, None, 3)
+    _, *rot = o.semicanonicalize(1, 2, 2, p.h, p.B, p.G1, p.G2, p.G3)
+    g = ric.RicMrcc(1, 2, 2, 12, method=ric.METHOD_FULL)
+    g.set_integrals(rot[0], rot[1])
+    g.set_rdms(*rot[2:])
+    e, st = g.solve(0.5, **TIGHT)
+    assert st.converged == 1
+    with pytest.raises(ric.RicMrccError) as ei:
+        g.energy_backward()
+    assert ei.value.code == ric.ENOTSUP
+
+
 def test_backward_requires_converged_solve():
     import paper_2511_03567_gb300 as ric
     g, h, B, rot = _setup(2, 4, 10, 48, 0)
