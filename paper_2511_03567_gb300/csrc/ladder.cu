@@ -104,8 +104,17 @@ __device__ __forceinline__ void mma_kblock(uint32_t d, uint64_t ad, uint64_t bd,
 constexpr int kLEpi = 4;                           // epilogue warps (one per TMEM lane quarter)
 constexpr int kLThreads = 64 + 32 * kLEpi;
 // K products a tensor-core accumulation runs over before its FP32 sum is
-// added into the output (the rebuild GEMM's K, n_aux, stays below it)
-constexpr int kLadderChunk = 16384;
+// added into the output.  Short enough that one wave of CTAs (a 16 x ~9 block
+// of output tiles) reads ~90 MB of operands per chunk, which L2 holds while
+// the wave works through it: the CTAs sharing an operand tile then fetch it
+// from DRAM once.  (16384 let the CTAs of a wave drift apart over a chunk and
+// re-read their shared tiles from DRAM ~30 times over: 520 GB per ladder GEMM
+// at the Large sizes against 18 GB of operands.)
+constexpr int kLadderChunk = 4096;
+// n tiles per raster group of the ladder GEMMs (A tiles are re-read once per group)
+constexpr int kLadderGroup = 16;
+// work-item counters of one GEMM (one per K-chunk launch)
+constexpr int kMaxLaunchCounters = 1024;
 
 __device__ __forceinline__ uint32_t idesc_128x256() {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(LBN >> 3) << 17) | ((uint32_t)(LBM >> 4) << 24);
@@ -113,14 +122,16 @@ __device__ __forceinline__ uint32_t idesc_128x256() {
 
 struct TileMap {
   int mt, nt, group;
-  int kchunk, nchunk;  // K blocks per chunk, chunks per tile
+  int kchunk, nchunk;  // K blocks per chunk, chunks per tile in this launch
+  int kfirst;          // first K block of this launch
+  int reduce;          // add into D with FP32 reductions (else store)
   // work item t -> (tile, K chunk): chunk-major, so that the CTAs of one wave
   // work on the same K range of neighbouring tiles
   __device__ __forceinline__ void item(int64_t t, int* mi, int* ni, int* k0, int* k1, int kt) const {
     const int64_t tiles = (int64_t)mt * nt;
     const int ch = (int)(t / tiles);
     at(t - (int64_t)ch * tiles, mi, ni);
-    *k0 = ch * kchunk;
+    *k0 = kfirst + ch * kchunk;
     *k1 = min(kt, *k0 + kchunk);
   }
   __device__ __forceinline__ void at(int64_t t, int* mi, int* ni) const {
@@ -146,7 +157,8 @@ struct TileMap {
 template <int BK>
 __global__ void __launch_bounds__(kLThreads, 1)
     k_gemm3(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int ya0, int yb0,
-            int64_t M, int64_t N, int kt, float* __restrict__ D, int64_t ldd, TileMap tm, int* err) {
+            int64_t M, int64_t N, int kt, float* __restrict__ D, int64_t ldd, TileMap tm,
+            unsigned long long* __restrict__ ctr, int* err) {
   constexpr int LSTAGES = Ring<BK>::kStages, LBK = BK;
   constexpr uint32_t kLA = Ring<BK>::kA, kLB = Ring<BK>::kB, kLStage = Ring<BK>::kStage;
   extern __shared__ uint8_t smem_raw[];
@@ -160,11 +172,18 @@ __global__ void __launch_bounds__(kLThreads, 1)
   uint64_t* tempty = tfull + 2;       // [2]
   uint64_t* fin = tempty + 2;
   uint64_t* never = fin + 1;  // completed by nothing (error-path test)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
+  // work items: the producer claims them from the launch's counter (so the
+  // CTAs in flight always hold a contiguous window of items and share their
+  // operand tiles through L2) and hands each to the MMA issuer and the
+  // epilogue through a four-slot ring; -1 ends the sequence
+  uint64_t* ifull = never + 1;   // [4]
+  uint64_t* iempty = ifull + 4;  // [4]
+  int64_t* iring = reinterpret_cast<int64_t*>(iempty + 4);  // [4]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(iring + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t total = (int64_t)tm.mt * tm.nt * tm.nchunk;
-  const bool reduce = tm.nchunk > 1;
+  const bool reduce = tm.reduce != 0;
   if (threadIdx.x == 0) {
     for (int s = 0; s < 2 * LSTAGES; ++s) {
       mbar_init(full + s, 1);
@@ -176,6 +195,10 @@ __global__ void __launch_bounds__(kLThreads, 1)
     }
     mbar_init(fin, 1);
     mbar_init(never, 1);
+    for (int j = 0; j < 4; ++j) {
+      mbar_init(ifull + j, 1);
+      mbar_init(iempty + j, 1 + kLEpi);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -199,7 +222,18 @@ __global__ void __launch_bounds__(kLThreads, 1)
     const uint32_t s0 = smem_u32(smem), full0 = smem_u32(full);
     constexpr uint32_t kGroup = kLA + kLB;
     const int lo_x = kt * LBK;
-    for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+    uint32_t ic = 0;
+    for (int64_t t = ctr ? (int64_t)atomicAdd(ctr, 1ull) : (int64_t)blockIdx.x;; ) {
+      // publish the item (or the end) to the MMA issuer and the epilogue
+      const uint32_t j = ic & 3;
+      if (ic >= 4 && !mbar_wait(iempty + j, ((ic >> 2) - 1) & 1, err)) {
+        ok = false;
+        break;
+      }
+      iring[j] = t < total ? t : -1;
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(ifull + j)) : "memory");
+      ++ic;
+      if (t >= total) break;
       int mi, ni, k0, k1;
       tm.item(t, &mi, &ni, &k0, &k1, kt);
       const int ya = ya0 + mi * LBM, yb = yb0 + ni * LBN;
@@ -227,6 +261,8 @@ __global__ void __launch_bounds__(kLThreads, 1)
           ph ^= 1u;
         }
       }
+      if (!ok) break;
+      t = ctr ? (int64_t)atomicAdd(ctr, 1ull) : t + gridDim.x;
     }
     // copies still in flight land before the CTA exits
     for (int g = 0; g < 2; ++g)
@@ -240,7 +276,13 @@ __global__ void __launch_bounds__(kLThreads, 1)
     const uint32_t empty0 = smem_u32(empty);
     const uint32_t idesc = idesc_128x256();
     ok = stall_test_wait(never, err);
-    for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++c) {
+    for (uint32_t ic = 0; ok; ++c) {
+      const uint32_t j = ic & 3;
+      if (!mbar_wait(ifull + j, (ic >> 2) & 1, err)) break;
+      const int64_t t = iring[j];
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(iempty + j)) : "memory");
+      ++ic;
+      if (t < 0) break;
       const uint32_t b = c & 1;
       if (c >= 2 && !mbar_wait(tempty + b, ((c >> 1) - 1) & 1, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -293,7 +335,14 @@ __global__ void __launch_bounds__(kLThreads, 1)
     const int q = warp & 3;
     float* tile = etile + (warp - 2) * 32 * 33;
     uint32_t c = 0;
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++c) {
+    for (uint32_t ic = 0;; ++c) {
+      const uint32_t j = ic & 3;
+      if (!__all_sync(0xffffffffu, mbar_wait(ifull + j, (ic >> 2) & 1, err))) break;
+      const int64_t t = iring[j];
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(iempty + j)) : "memory");
+      ++ic;
+      if (t < 0) break;
       int mi, ni, k0, k1;
       tm.item(t, &mi, &ni, &k0, &k1, kt);
       const uint32_t b = c & 1;
@@ -352,7 +401,7 @@ __global__ void __launch_bounds__(kLThreads, 1)
 template <int BK>
 size_t gemm3_smem_bytes() {
   return 1024 + (size_t)Ring<BK>::kStages * Ring<BK>::kStage + kLEpi * 32 * 33 * 4 + (4 * Ring<BK>::kStages + 6) * 8 +
-         16;
+         (8 + 4) * 8 + 16;
 }
 
 // ---------------------------------------------------------------------------
@@ -643,6 +692,7 @@ struct ricmrcc_ladder {
   int2* tiles64 = nullptr;       // 64 x 64 tile pairs (symmetrisation)
   int ntiles64 = 0;
   int* d_err = nullptr;
+  unsigned long long* ctrs = nullptr;  // work-item counters, one per GEMM launch of a chunk sequence
   bool have_factor = false;
   std::vector<cudaEvent_t> ev;   // per slab: 5 boundaries (rebuild, symmetrise, ladder +, ladder -, unpack)
   cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // amplitude packing
@@ -664,27 +714,38 @@ int lfail(ricmrcc_ladder_t* L, int code, const std::string& m) {
   } while (0)
 
 // kt K blocks of BK; kchunk = 0 or >= kt: whole K per tile, D stored; else
-// chunks of kchunk K blocks reduced into D (which the caller has zeroed).
+// chunks of kchunk K blocks reduced into D (which the caller has zeroed), one
+// launch per chunk: the persistent CTAs of a launch cover the tiles of one K
+// range together, and the launch boundary keeps them from drifting apart
+// (CTAs that drift apart stop sharing their operand tiles through L2).
 template <int BK>
 int launch_gemm3(ricmrcc_ladder_t* L, const CUtensorMap& ma, const CUtensorMap& mb, int ya0, int yb0, int64_t M,
-                 int64_t N, int kt, float* D, int64_t ldd, int kchunk) {
+                 int64_t N, int kt, float* D, int64_t ldd, int kchunk, int group) {
   TileMap tm;
   tm.mt = (int)((M + LBM - 1) / LBM);
   tm.nt = (int)((N + LBN - 1) / LBN);
-  tm.group = std::min(tm.nt, 8);
+  tm.group = std::max(1, std::min(tm.nt, group));
   tm.kchunk = kchunk > 0 && kchunk < kt ? kchunk : kt;
-  tm.nchunk = (kt + tm.kchunk - 1) / tm.kchunk;
-  const int64_t total = (int64_t)tm.mt * tm.nt * tm.nchunk;
+  tm.nchunk = 1;
+  tm.reduce = tm.kchunk < kt ? 1 : 0;
+  const int64_t total = (int64_t)tm.mt * tm.nt;
   if (total <= 0 || kt <= 0) return RICMRCC_OK;
   const int grid = (int)std::min<int64_t>(total, L->sms);
-  k_gemm3<BK><<<grid, kLThreads, gemm3_smem_bytes<BK>(), L->s>>>(ma, mb, ya0, yb0, M, N, kt, D, ldd, tm, L->d_err);
-  LCK(cudaGetLastError());
+  const int nlaunch = (kt + tm.kchunk - 1) / tm.kchunk;
+  if (nlaunch > kMaxLaunchCounters) return lfail(L, RICMRCC_EINVAL, "too many K chunks");
+  LCK(cudaMemsetAsync(L->ctrs, 0, sizeof(unsigned long long) * nlaunch, L->s));
+  int c = 0;
+  for (tm.kfirst = 0; tm.kfirst < kt; tm.kfirst += tm.kchunk, ++c) {
+    k_gemm3<BK><<<grid, kLThreads, gemm3_smem_bytes<BK>(), L->s>>>(ma, mb, ya0, yb0, M, N, kt, D, ldd, tm,
+                                                                   L->ctrs + c, L->d_err);
+    LCK(cudaGetLastError());
+  }
   return RICMRCC_OK;
 }
 
 void free_all(ricmrcc_ladder_t* L) {
   for (void* p : {(void*)L->Bp, (void*)L->Tp, (void*)L->Tm, (void*)L->Wp, (void*)L->Wm, (void*)L->V, (void*)L->Dp,
-                  (void*)L->Dm, (void*)L->tiles, (void*)L->tiles64, (void*)L->d_err})
+                  (void*)L->Dm, (void*)L->tiles, (void*)L->tiles64, (void*)L->d_err, (void*)L->ctrs})
     if (p) cudaFree(p);
   for (cudaEvent_t e : L->ev) cudaEventDestroy(e);
   if (L->ev_t0) cudaEventDestroy(L->ev_t0);
@@ -792,6 +853,7 @@ int ricmrcc_ladder_create(int n_hole, int n_virt, int n_aux, int64_t slab_rows, 
   alloc((void**)&L->tiles, tp.size() * sizeof(int2), false);
   alloc((void**)&L->tiles64, tp64.size() * sizeof(int2), false);
   alloc((void**)&L->d_err, sizeof(int), true);
+  alloc((void**)&L->ctrs, sizeof(unsigned long long) * kMaxLaunchCounters, true);
   if (ok) ok = cudaMemcpy(L->tiles, tp.data(), tp.size() * sizeof(int2), cudaMemcpyHostToDevice) == cudaSuccess;
   if (ok)
     ok = cudaMemcpy(L->tiles64, tp64.data(), tp64.size() * sizeof(int2), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -895,7 +957,7 @@ int ricmrcc_ladder_apply_dev(ricmrcc_ladder_t* L, const double* T, double* R) {
     // 1. V[(a,e)][(b,f)] for a in the slab, b >= a0
     const int64_t ldv = pad_to((int64_t)(v - a0) * vp, 4);
     rc = launch_gemm3<32>(L, mB, mB256, a0 * vp, a0 * vp, (int64_t)(a1 - a0) * vp, (int64_t)(v - a0) * vp,
-                          (int)(L->kx / 32), L->V, ldv, 0);
+                          (int)(L->kx / 32), L->V, ldv, 0, 8);
     if (rc) return rc;
     LCK(cudaEventRecord(e[1], L->s));
     // 2. W+ / W- rows of the slab
@@ -908,12 +970,14 @@ int ricmrcc_ladder_apply_dev(ricmrcc_ladder_t* L, const double* T, double* R) {
         !packed_map(&mWm, L->Wm, 2 * L->Km, std::max<int64_t>(nm, 1), LBN, 64))
       return lfail(L, RICMRCC_ECUDA, "tensor map encoding failed");
     LCK(cudaMemsetAsync(L->Dp, 0, sizeof(float) * L->nkp * L->ldd, L->s));
-    rc = launch_gemm3<64>(L, mTp, mWp, 0, 0, L->nkp, np, (int)(L->Kp / 64), L->Dp, L->ldd, kLadderChunk / 64);
+    rc = launch_gemm3<64>(L, mTp, mWp, 0, 0, L->nkp, np, (int)(L->Kp / 64), L->Dp, L->ldd, kLadderChunk / 64,
+                          kLadderGroup);
     if (rc) return rc;
     LCK(cudaEventRecord(e[3], L->s));
     if (L->nkm > 0 && nm > 0) {
       LCK(cudaMemsetAsync(L->Dm, 0, sizeof(float) * L->nkm * L->ldd, L->s));
-      rc = launch_gemm3<64>(L, mTm, mWm, 0, 0, L->nkm, nm, (int)(L->Km / 64), L->Dm, L->ldd, kLadderChunk / 64);
+      rc = launch_gemm3<64>(L, mTm, mWm, 0, 0, L->nkm, nm, (int)(L->Km / 64), L->Dm, L->ldd, kLadderChunk / 64,
+                            kLadderGroup);
       if (rc) return rc;
     }
     LCK(cudaEventRecord(e[4], L->s));
