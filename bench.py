@@ -162,8 +162,9 @@ def fp32_peak_tflops(torch):
 # DRAM bytes (read + write) of the grouped tensor-core launches of one Mid
 # residual, from the ncu capture named below (None until one was taken with
 # the current kernel)
-TC_TRAFFIC_PER_RESIDUAL = None
-TC_TRAFFIC_SOURCE = None
+TC_TRAFFIC_PER_RESIDUAL = 8.919e9
+TC_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the five k_tc_grouped launches of one "
+                     "Mid residual (profiles/tc_grouped_mid_traffic.md)")
 
 
 def roofline(kind_ms, info, mixed, pk, fp64_peak, torch):

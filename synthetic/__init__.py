@@ -188,28 +188,34 @@ def _annihilate(dets, coef, so):
 def _annihilation_images(ci: CIVector, k):
     """Rows V[(s1..sk)] = a_{sk} ... a_{s1} |Psi> over ordered tuples of spin orbitals.
 
-    Returns (tuples array [ntup, k], dense matrix [ntup, ncol]).
+    Returns (tuples array [ntup, k], sparse matrix [ntup, ncol]): a row holds
+    at most one entry per determinant of the CI vector, so the matrix stays
+    small even where the image space is large (CAS(14,14) with 2048
+    determinants has ~7e5 distinct three-hole images).
     """
+    from scipy import sparse
     nso = 2 * ci.n_act
     tuples = list(itertools.product(range(nso), repeat=k))
-    rows = []
-    allcols = []
-    for tup in tuples:
+    rows, cols_d, vals = [], [], []
+    for r, tup in enumerate(tuples):
         if len(set(tup)) < k:
-            rows.append((np.zeros(0, np.int64), np.zeros(0)))
             continue
         d, c = ci.dets, ci.coef
         for so in tup:
             d, c = _annihilate(d, c, so)
             if d.size == 0:
                 break
-        rows.append((d, c))
-        allcols.append(d)
-    cols = np.unique(np.concatenate(allcols)) if allcols else np.zeros(0, np.int64)
-    mat = np.zeros((len(tuples), cols.size))
-    for r, (d, c) in enumerate(rows):
         if d.size:
-            mat[r, np.searchsorted(cols, d)] += c
+            rows.append(np.full(d.size, r, dtype=np.int64))
+            cols_d.append(d)
+            vals.append(c)
+    if not rows:
+        return np.array(tuples), sparse.csr_matrix((len(tuples), 0))
+    rows = np.concatenate(rows)
+    cols_d = np.concatenate(cols_d)
+    vals = np.concatenate(vals)
+    uniq, col = np.unique(cols_d, return_inverse=True)
+    mat = sparse.csr_matrix((vals, (rows, col)), shape=(len(tuples), uniq.size))
     return np.array(tuples), mat
 
 
@@ -220,7 +226,7 @@ def spin_orbital_rdm(ci: CIVector, k):
     """
     nso = 2 * ci.n_act
     _, v = _annihilation_images(ci, k)
-    g = v @ v.T
+    g = (v @ v.T).toarray()
     return g.reshape((nso,) * (2 * k))
 
 
