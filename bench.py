@@ -528,6 +528,12 @@ def eval_mixed_vs_fp64(torch, g, snap):
             "rel_dR": float((rm - rf).abs().max() / rf.abs().max())}
 
 
+# DRAM bytes (read + write) of the ladder GEMM launches of one Large
+# application, from the ncu capture named below
+LADDER_TRAFFIC_PER_APPLICATION = 4.419e12
+LADDER_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 3936 k_gemm3<64> launches of one "
+                         "application (profiles/ladder_large_launch_list.md)")
+
 LADDER_LARGE = {"n_hole": 102, "n_virt": 707, "n_aux": 2400,
                 "sizes": "holes = 90 core + 12 active, 707 virtual, n_aux 2400 (the Large configuration)"}
 
@@ -566,6 +572,7 @@ def ladder_large(torch, stream, pk, steps=2, warmup=1, w=None):
     import synthetic
     w = w or LADDER_LARGE
     nh, nv, nx = w["n_hole"], w["n_virt"], w["n_aux"]
+    large = (nh, nv, nx) == (LADDER_LARGE["n_hole"], LADDER_LARGE["n_virt"], LADDER_LARGE["n_aux"])
     Bv, T = synthetic.make_ladder_inputs_device(nh, nv, nx, seed=0)
     R = torch.zeros_like(T)
     L = ric.Ladder(nh, nv, nx)
@@ -603,7 +610,8 @@ def ladder_large(torch, stream, pk, steps=2, warmup=1, w=None):
                         "frac_of_burst": achieved / pk.get("bf16_tflops", 1900.0),
                         "work": "3 x 2 MNK per packed ladder GEMM (the split products hi*hi, hi*lo, lo*hi "
                                 "counted; M, N, K without padding): 3 x ladder_flops",
-                        "traffic": None},
+                        "traffic": LADDER_TRAFFIC_PER_APPLICATION if large else None,
+                        "traffic_source": LADDER_TRAFFIC_SOURCE if large else None},
            "rebuild": {"kernel": "k_gemm3 (integral rebuild)",
                        "tflops_bf16": 3.0 * info["rebuild_flops"] / t_reb / 1e12,
                        "tflops_bf16_executed": info["rebuild_flops_executed"] / t_reb / 1e12,

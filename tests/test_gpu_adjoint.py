@@ -119,8 +119,10 @@ def test_device_outputs_equal_host_outputs():
     dds = torch.zeros(1, dtype=torch.float64, device="cuda")
     g.energy_backward_dev(ddh, ddB, dds)
     torch.cuda.synchronize()
-    assert np.array_equal(ddh.cpu().numpy(), dh) and np.array_equal(ddB.cpu().numpy(), dB)
-    assert float(dds.item()) == ds
+    # a second multiplier solve: equal up to the order of the atomic accumulations
+    assert np.abs(ddh.cpu().numpy() - dh).max() < 1e-10 * max(1.0, np.abs(dh).max())
+    assert np.abs(ddB.cpu().numpy() - dB).max() < 1e-10 * max(1.0, np.abs(dB).max())
+    assert abs(float(dds.item()) - ds) < 1e-10 * max(1.0, abs(ds))
 
 
 def test_full_method_has_no_adjoint():
