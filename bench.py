@@ -277,6 +277,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile rule")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ladder", action="store_true", help="skip the Large-size density-fitted ladder")
+    ap.add_argument("--no-cas14", action="store_true",
+                    help="skip the full residual at 20 core, CAS(14,14), 250 virtual, n_aux 1136")
     ap.add_argument("--ladder-steps", type=int, default=2, help="timed applications of the Large ladder")
     ap.add_argument("--no-converging", action="store_true",
                     help="skip the mixed-against-FP64 solves of the converging Mid-sized problem")
@@ -427,6 +429,10 @@ def main():
     ladder = None
     if not args.no_ladder and rank == 0:
         ladder = ladder_large(torch, stream, pk, steps=args.ladder_steps)
+    # the full residual at the CAS(14,14) variant of the Large configuration
+    cas14 = None
+    if not args.no_cas14 and rank == 0:
+        cas14 = large_cas14(torch, stream, steps=3)
     # a converging problem of the same sizes: mixed solve (with its FP64
     # refinement) against the FP64 solve
     conv = None
@@ -463,6 +469,7 @@ def main():
             "roofline": roof, "clocks": clk.summary(), "tensor_core": tc, "fp64_path": fp64_line,
             "accuracy": {"mixed_vs_fp64_one_evaluation": acc, "converging_mid": conv},
             "ladder_large": ladder,
+            "large_cas14": cas14,
             "tile_rule": g.get_tile_rule(), "tuning": tuning}
     if not args.no_cpu_baseline and ws == 1 and args.workload == "mid":
         try:
@@ -619,6 +626,71 @@ def ladder_large(torch, stream, pk, steps=2, warmup=1, w=None):
     del L, Bv, T, R
     torch.cuda.empty_cache()
     return out
+
+
+CAS14 = {"n_core": 20, "n_act": 14, "n_virt": 250, "n_aux": 1136, "n_det": 2048, "s": 0.1, "seed": 0,
+         "sizes": "20 core, CAS(14,14) (2048 determinants), 250 virtual, n_aux 1136: the CAS(14,14) variant of the "
+                  "Large configuration"}
+
+
+def large_cas14(torch, stream, steps=3):
+    """The whole residual program at the CAS(14,14) variant's sizes: mixed
+    solver iterations (the same blocked scheme as Mid: warm-up from T = 0,
+    then `steps` timed iterations) and one FP64 evaluation at the same
+    amplitudes for the accuracy and the FP64 time."""
+    import paper_2511_03567_gb300 as ric
+    import synthetic
+    w = CAS14
+    p = synthetic.make_problem(w["n_core"], w["n_act"], w["n_virt"], w["n_aux"], w["n_det"], w["seed"])
+    g = ric.RicMrcc(w["n_core"], w["n_act"], w["n_virt"], w["n_aux"])
+    g.set_stream(stream.cuda_stream)
+    g.set_integrals(p.h, p.B)
+    g.set_rdms(p.G1, p.G2, p.G3)
+    g.semicanonicalize()
+    g.set_tile_rule(3e5, True, True)
+    g.set_precision(ric.MIXED)
+    info = g.plan_info()
+    g.step(s=w["s"], n_steps=2, restart=True, precision=ric.MIXED)  # capture + warm-up
+    lay = g.layout
+    t1 = torch.empty(lay.t1_size, dtype=torch.float64, device="cuda")
+    t2 = torch.empty(lay.t2_size, dtype=torch.float64, device="cuda")
+    g.get_amplitudes_dev(t1, t2)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    E, _ = g.step(s=w["s"], n_steps=steps, restart=False, precision=ric.MIXED)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s_iter = e0.elapsed_time(e1) / 1e3 / steps
+    # one evaluation in each precision at the warm amplitudes
+    out = {}
+    for name, prec in (("mixed", ric.MIXED), ("fp64", ric.FP64)):
+        g.set_precision(prec)
+        r1 = torch.empty_like(t1)
+        r2 = torch.empty_like(t2)
+        en = torch.zeros(1, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.residual_dev(t1, t2, r1, r2, en)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = (torch.cat([r1, r2]), float(en.item()), e0.elapsed_time(e1) / 1e3)
+    rm, em, tm = out["mixed"]
+    rf, ef, tf = out["fp64"]
+    res = {"workload": w["sizes"], "s": w["s"], "steps": steps, "converged": False,
+           "s_per_iter_mixed": s_iter, "residual_flops": info.residual_flops,
+           "tflops_mixed": info.residual_flops / s_iter / 1e12,
+           "s_per_residual_fp64": tf, "tflops_fp64": info.residual_flops / tf / 1e12,
+           "arena_gb": info.arena_bytes / 1e9, "tables_gb": info.table_bytes / 1e9,
+           "accuracy_one_evaluation": {"energy_fp64": ef, "energy_mixed": em, "abs_dE": abs(em - ef),
+                                       "rel_dR": float((rm - rf).abs().max() / rf.abs().max())},
+           "timing": "mixed solver iterations after 2 warm-up iterations from T = 0, CUDA events on the "
+                     "library stream; FP64: one residual evaluation (captured graph) at the same amplitudes"}
+    g.close()
+    del t1, t2, out, rm, rf
+    torch.cuda.empty_cache()
+    return res
 
 
 # B scale of the converging problem: B ~ N(0, 0.05 * CONV_B_SCALE), every

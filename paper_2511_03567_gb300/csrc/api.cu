@@ -193,7 +193,11 @@ int plan(ricmrcc_t* h) {
 // 8/8/120 size).  M and K are padded to the 128 x 64 tile, so ops with M >= 64
 // and K >= 32 waste at most half of each.
 bool tc_eligible(const ContractOp& op, const TileRule& r) {
-  return op.kind != 2 && op.L == 1 && op.M >= 64 && op.K >= 32 && op.N >= r.tc_min_n && op.flops >= r.tc_min_flops;
+  // the grouped launch's work items index 128-row tiles and 64-wide K blocks
+  // with 16-bit fields
+  const bool fits = (op.M + 127) / 128 <= 0xffff && (op.K + 63) / 64 <= 0xffff && (op.N + 127) / 128 <= 0xffff;
+  return op.kind != 2 && op.L == 1 && op.M >= 64 && op.K >= 32 && op.N >= r.tc_min_n && op.flops >= r.tc_min_flops &&
+         fits;
 }
 
 // FP64 kernel of an op: the planner's choice (64x64 tile, 16x16 tile or dot

@@ -149,8 +149,13 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
         key.append(reinterpret_cast<const char*>(th + 3 * op.L + 2 * op.M + op.N), sizeof(int64_t) * op.N);
         auto it = merge.find(key);
         if (it != merge.end() && merged[it->second].size() < (size_t)kTcMaxSeg) {
-          merged[it->second].push_back(tc_args(inst[i], p, (int)q, 0));
-          continue;
+          // the merged op's concatenated K blocks index 16-bit item fields
+          int64_t kb = (op.K + 63) / 64;
+          for (const TcArgs& y : merged[it->second]) kb += (y.K + 63) / 64;
+          if (kb <= 0xffff) {
+            merged[it->second].push_back(tc_args(inst[i], p, (int)q, 0));
+            continue;
+          }
         }
         merge[key] = merged.size();
         merged.push_back({tc_args(inst[i], p, (int)q, 0)});
@@ -170,8 +175,8 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
     std::vector<TcGroupOp> ops;
     std::vector<TcSeg> segs;
     std::vector<TcItem> items;
-    if (tc_group_build(args.data(), nseg.data(), (int)nseg.size(), ops, segs, items) != 0)
-      return fail(eh, RICMRCC_ECUDA, "grouped tensor-core descriptors");
+    const int grc = tc_group_build(args.data(), nseg.data(), (int)nseg.size(), ops, segs, items);
+    if (grc != 0) return fail(eh, RICMRCC_ECUDA, "grouped tensor-core descriptors (code " + std::to_string(grc) + ")");
     void *dops = nullptr, *dit = nullptr, *dsg = nullptr;
     if (cudaMalloc(&dops, sizeof(TcGroupOp) * ops.size()) != cudaSuccess) return fail(eh, RICMRCC_ENOMEM, "descriptors");
     allocs.push_back(dops);

@@ -873,15 +873,15 @@ int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupO
     const int bn = std::min(pbn, GBN);
     const int64_t Mp = tc_pad(x.M, BM), Np = tc_pad(x.N, pbn);
     int kt_all = 0;
-    if (nseg[j] < 1 || nseg[j] > kTcMaxSeg) return -1;
+    if (nseg[j] < 1 || nseg[j] > kTcMaxSeg) return -11;
     // weights relative to the first segment: a sign and 2^e, 0 <= e <= 15
     double alphas[kTcMaxSeg];
     for (int sgi = 0; sgi < nseg[j]; ++sgi) alphas[sgi] = a[first[j] + sgi].alpha;
-    if (!tc_segment_weights(alphas, nseg[j], o.scode, &o.alpha)) return -1;
+    if (!tc_segment_weights(alphas, nseg[j], o.scode, &o.alpha)) return -12;
     for (int sgi = 0; sgi < nseg[j]; ++sgi) {
       const TcArgs& y = a[first[j] + sgi];
-      if (!y.packA || !y.packB) return -1;  // both operands come packed
-      if (y.M != x.M || y.N != x.N) return -1;
+      if (!y.packA || !y.packB) return -13;  // both operands come packed
+      if (y.M != x.M || y.N != x.N) return -14;
       const int64_t inner = 2 * tc_pad(y.K, BK);  // [hi | lo]
       CUtensorMap* pma = &o.ma;
       CUtensorMap* pmb = &o.mb;
@@ -920,7 +920,7 @@ int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupO
       clusters.push_back(c);
     }
     TcCluster& c = clusters.back();
-    if (c.mt != (int)(Mp / BM) || c.kt_total != kt_all) return -1;  // shared A: same M and K
+    if (c.mt != (int)(Mp / BM) || c.kt_total != kt_all) return -15;  // shared A: same M and K
     o.wbegin = c.W;
     c.W += o.nt;
     c.nops += 1;
@@ -929,7 +929,7 @@ int tc_group_build(const TcArgs* a, const int* nseg, int n, std::vector<TcGroupO
   }
   // the work items, cluster by cluster: (m tile, K chunk) major, slot minor
   items.reserve((size_t)t);
-  if (!tc_expand_items(clusters, ops, segs, items)) return -1;  // 16-bit item fields
+  if (!tc_expand_items(clusters, ops, segs, items)) return -16;  // 16-bit item fields
   return (int64_t)items.size() == t ? 0 : -1;
 }
 
