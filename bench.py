@@ -10,11 +10,14 @@ events on the library's stream; inputs are larger than L2 (the integral
 tensor alone is 2.7 GB), so no flush is needed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision mixed|fp64] [--workload mid|prof|batched]
+                  [--precision mixed|fp64] [--workload mid|prof|batched|ladder|adjoint]
 
 `--workload batched` times one iteration of 48 independent instances of
 uneven sizes (core 2-10, CAS(4,4)-CAS(8,8), virtual 40-120, n_aux 4n) run
-as one batch: one graph of grouped launches per iteration.
+as one batch: one graph of grouped launches per iteration.  `--workload
+ladder` times the Large-size density-fitted vvvv ladder alone, `--workload
+adjoint` the energy gradient at the Adjoint configuration with
+finite-difference checks.
 """
 from __future__ import annotations
 
@@ -47,6 +50,10 @@ WORKLOADS["ladder"] = {"workload": "ladder", "n_hole": 102, "n_virt": 707, "n_au
                        "sizes": "holes = 90 core + 12 active, 707 virtual, n_aux 2400 (the Large configuration)"}
 WORKLOADS["ladder_prof"] = {"workload": "ladder_prof", "n_hole": 34, "n_virt": 300, "n_aux": 800,
                             "sizes": "34 holes, 300 virtual, n_aux 800 (profiling case)"}
+# Adjoint: 12 core, CAS(10,10), 160 virtual, n_aux 560, 2048 determinants,
+# with B scaled as in the converging Mid problem so that the solve converges
+WORKLOADS["adjoint"] = {"workload": "adjoint", "n_core": 12, "n_act": 10, "n_virt": 160, "n_aux": 560,
+                        "n_det": 2048, "s": 0.5, "seed": 0}
 WORKLOAD = WORKLOADS["mid"]
 METRIC = "RIC-MRCCSD s/iter (Mid, one GB300)"
 METRIC_BATCHED = "RIC-MRCCSD s/iter (Batched, 48 instances per iteration, one GB300)"
@@ -280,9 +287,15 @@ def main():
     ap.add_argument("--no-cas14", action="store_true",
                     help="skip the full residual at 20 core, CAS(14,14), 250 virtual, n_aux 1136")
     ap.add_argument("--ladder-steps", type=int, default=2, help="timed applications of the Large ladder")
+    ap.add_argument("--no-emulation", action="store_true",
+                    help="skip the emulated-FP64 GEMM against cuBLAS DGEMM")
     ap.add_argument("--no-converging", action="store_true",
                     help="skip the mixed-against-FP64 solves of the converging Mid-sized problem")
     ap.add_argument("--workload", default="mid", choices=sorted(WORKLOADS))
+    ap.add_argument("--fd-entries", type=int, default=8,
+                    help="adjoint workload: random h and B entries checked by central differences")
+    ap.add_argument("--no-fp64-adjoint", action="store_true",
+                    help="adjoint workload: skip the FP64-iterated adjoint beside the refined one")
     ap.add_argument("--ncu-largest", type=int, default=0,
                     help="profiler mode: one residual, then only the N largest contractions")
     ap.add_argument("--ncu-residual", type=int, default=0,
@@ -299,6 +312,8 @@ def main():
         return run_batched(args)
     if args.workload in ("ladder", "ladder_prof"):
         return run_ladder(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
 
     import torch
     dist, rank, ws, local = dist_init()
@@ -433,6 +448,10 @@ def main():
     cas14 = None
     if not args.no_cas14 and rank == 0:
         cas14 = large_cas14(torch, stream, steps=3)
+    # FP64-accurate GEMM emulated on the tensor cores against cuBLAS DGEMM
+    emu = None
+    if not args.no_emulation and rank == 0:
+        emu = fp64_emulation(torch, pk, fp64_peak)
     # a converging problem of the same sizes: mixed solve (with its FP64
     # refinement) against the FP64 solve
     conv = None
@@ -470,6 +489,7 @@ def main():
             "accuracy": {"mixed_vs_fp64_one_evaluation": acc, "converging_mid": conv},
             "ladder_large": ladder,
             "large_cas14": cas14,
+            "fp64_emulation": emu,
             "tile_rule": g.get_tile_rule(), "tuning": tuning}
     if not args.no_cpu_baseline and ws == 1 and args.workload == "mid":
         try:
@@ -565,6 +585,172 @@ def run_ladder(args):
             "config": {"workload": WORKLOAD["workload"], "sizes": WORKLOAD["sizes"],
                        "l2": "operands larger than L2, no flush"},
             "roofline": out["roofline"], "clocks": clk.summary(), "ladder": out}
+    print(json.dumps(line))
+    return 0
+
+
+def fp64_emulation(torch, pk, fp64_peak, n=8192, reps=3):
+    """C = A B^T at n^3 with ricmrcc_gemm_f64_emulated (default 11 digits,
+    66 BF16 digit products) against cuBLAS DGEMM (torch.matmul in float64):
+    CUDA-event times on the current stream, FP64-equivalent TFLOP/s, the
+    tensor-core rate of the digit products against the measured BF16 peak,
+    and the largest difference from DGEMM relative to |A||B|."""
+    import paper_2511_03567_gb300 as ric
+    g = torch.Generator(device="cuda").manual_seed(3)
+    A = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+    B = torch.randn((n, n), dtype=torch.float64, device="cuda", generator=g)
+    C = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, k):
+        ts = []
+        for _ in range(k):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        return float(np.median(ts))
+
+    emu = lambda: ric.gemm_f64_emulated(A, B, C, slices=0, stream=stream)
+    emu()
+    t_emu = timed(emu, reps)
+    C.zero_()
+    emu()
+    ref = torch.matmul(A, B.T)
+    t_dgemm = timed(lambda: torch.matmul(A, B.T), 2)
+    absab = torch.matmul(A.abs().float(), B.abs().float().T).double()
+    diff = float(((C - ref).abs() / absab).max())
+    del A, B, C, ref, absab
+    torch.cuda.empty_cache()
+    S = 11
+    flops = 2.0 * n ** 3
+    bf16 = S * (S + 1) / 2 * flops
+    peak = pk.get("bf16_tflops_sustained") or pk.get("bf16_tflops")
+    return {"size": f"{n}^3", "digits": S, "bf16_products": S * (S + 1) // 2, "emulated_s": t_emu,
+            "dgemm_s": t_dgemm, "emulated_fp64_tflops": flops / t_emu / 1e12,
+            "dgemm_tflops": flops / t_dgemm / 1e12, "speedup_vs_dgemm": t_dgemm / t_emu,
+            "tensor_tflops": bf16 / t_emu / 1e12,
+            "tensor_frac_of_bf16_sustained": (bf16 / t_emu / 1e12) / peak if peak else None,
+            "fp64_peak_tflops_measured": fp64_peak,
+            "max_abs_diff_vs_dgemm_over_absAB": diff,
+            "timing": "CUDA events on the current stream, median of the calls; the emulated time includes "
+                      "the digit slicing and its allocations"}
+
+
+ADJ_TOL = dict(e_tol=1e-11, t_tol=1e-10, max_iter=100)
+ADJ_STEP = 1e-5
+
+
+def run_adjoint(args):
+    """`--workload adjoint`: the Adjoint configuration.  Converge the mixed
+    solve (tensor-core iterations, FP64 refinement), then time
+    energy_backward (multipliers by mixed-precision iterative refinement;
+    dE/dh, dE/dB, dE/ds), optionally the FP64-iterated adjoint beside it, and
+    check entries of the gradient by central differences of converged FP64
+    energies (step 1e-5) warm-started from the converged amplitudes.  The
+    integrals are taken in the semi-canonical basis the handle computes, so
+    that perturbed and unperturbed energies share one basis."""
+    import torch
+    dist, rank, ws, local = dist_init()
+    torch.cuda.set_device(local)
+    import paper_2511_03567_gb300 as ric
+    import synthetic
+
+    w = WORKLOAD
+    nc, na, nv, nx = w["n_core"], w["n_act"], w["n_virt"], w["n_aux"]
+    n, s = nc + na + nv, w["s"]
+    p = synthetic.make_problem(nc, na, nv, nx, w["n_det"], w["seed"])
+    g = ric.RicMrcc(nc, na, nv, nx)
+    g.set_integrals(p.h, np.ascontiguousarray(p.B * CONV_B_SCALE))
+    g.set_rdms(p.G1, p.G2, p.G3)
+    U = g.semicanonicalize()
+    h = U.T @ p.h @ U
+    h = np.ascontiguousarray(0.5 * (h + h.T))
+    B = np.einsum("pi,Qpq,qj->Qij", U, p.B * CONV_B_SCALE, U, optimize=True)
+    B = np.ascontiguousarray(0.5 * (B + B.transpose(0, 2, 1)))
+    g.set_integrals(h, B)
+
+    with ClockSampler(local) as clk:
+        clk.mark("timed_start")
+        t = time.time()
+        e_mixed, st = g.solve(s, precision=ric.MIXED, refine_tol=1e-5, **ADJ_TOL)
+        fwd = {"energy": e_mixed, "converged": bool(st.converged), "iterations": st.iterations,
+               "mixed_iterations": st.mixed_iterations, "fp64_iterations": st.fp64_iterations,
+               "seconds": time.time() - t}
+        if not st.converged:
+            raise SystemExit(f"adjoint workload: the forward solve did not converge ({fwd})")
+        T0 = g.get_amplitudes()
+        t = time.time()
+        dh, dB, ds = g.energy_backward()
+        sec = time.time() - t
+        info = g.adjoint_info()
+        clk.mark("timed_end")
+    bwd = {"seconds": sec, "multiplier_seconds": info.seconds, "fp64_applications": info.fp64_applications,
+           "mixed_applications": info.mixed_applications, "dE_ds": ds}
+    fp64_adj = None
+    if not args.no_fp64_adjoint:
+        g.set_amplitudes(T0)
+        e64, st64 = g.solve(s, precision=ric.FP64, **ADJ_TOL)
+        t = time.time()
+        dh64, dB64, ds64 = g.energy_backward()
+        sec64 = time.time() - t
+        i64 = g.adjoint_info()
+        fp64_adj = {"energy": e64, "converged": bool(st64.converged), "seconds": sec64,
+                    "fp64_applications": i64.fp64_applications, "dE_ds": ds64,
+                    "max_abs_diff_dh": float(np.max(np.abs(dh64 - dh))),
+                    "max_abs_diff_dB": float(np.max(np.abs(dB64 - dB))),
+                    "abs_diff_ds": abs(ds64 - ds), "max_abs_dh": float(np.max(np.abs(dh64))),
+                    "max_abs_dB": float(np.max(np.abs(dB64)))}
+
+    def energy(hh, BB, ss):
+        g.set_integrals(hh, BB)
+        g.set_amplitudes(T0)
+        e, st = g.solve(ss, precision=ric.FP64, **ADJ_TOL)
+        if not st.converged:
+            raise SystemExit("adjoint workload: a finite-difference solve did not converge")
+        return e, st.iterations
+
+    rng = np.random.default_rng(w["seed"] + 100)
+    checks = []
+    t_fd = time.time()
+    (ep, ip), (em, im) = energy(h, B, s + ADJ_STEP), energy(h, B, s - ADJ_STEP)
+    checks.append({"param": "s", "fd": (ep - em) / (2 * ADJ_STEP), "adjoint": ds, "iterations": ip + im})
+    for k in range(args.fd_entries):
+        if k % 2 == 0:
+            a, b = (int(x) for x in rng.integers(0, n, size=2))
+            hp, hm = h.copy(), h.copy()
+            hp[a, b] += ADJ_STEP
+            hm[a, b] -= ADJ_STEP
+            (ep, ip), (em, im) = energy(hp, B, s), energy(hm, B, s)
+            checks.append({"param": f"h[{a},{b}]", "fd": (ep - em) / (2 * ADJ_STEP), "adjoint": float(dh[a, b]),
+                           "iterations": ip + im})
+        else:
+            Q = int(rng.integers(0, nx))
+            a, b = (int(x) for x in rng.integers(0, n, size=2))
+            Bp, Bm = B.copy(), B.copy()
+            Bp[Q, a, b] += ADJ_STEP
+            Bm[Q, a, b] -= ADJ_STEP
+            (ep, ip), (em, im) = energy(h, Bp, s), energy(h, Bm, s)
+            checks.append({"param": f"B[{Q},{a},{b}]", "fd": (ep - em) / (2 * ADJ_STEP),
+                           "adjoint": float(dB[Q, a, b]), "iterations": ip + im})
+    for c in checks:
+        c["abs_err"] = abs(c["fd"] - c["adjoint"])
+        c["ok"] = c["abs_err"] <= 1e-5 * max(1.0, abs(c["fd"]))
+    if rank != 0:
+        return 0
+    line = {"metric": "RIC-MRCCSD energy gradient (dE/dh, dE/dB, dE/ds), s per gradient (Adjoint, one GB300)",
+            "value": sec, "unit": "s/gradient", "n_gpus": ws, "steps": 1, "warmup": 0,
+            "ms_per_step": sec * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16x3+f64", "data": "synthetic",
+            "config": {"workload": "adjoint", "n_core": nc, "n_act": na, "n_virt": nv, "n_aux": nx,
+                       "n_det": w["n_det"], "s": s, "inputs": f"B scaled by {CONV_B_SCALE}, semi-canonical basis",
+                       "tolerances": ADJ_TOL},
+            "forward": fwd, "backward": bwd, "fp64_adjoint": fp64_adj,
+            "finite_differences": {"step": ADJ_STEP, "seconds": time.time() - t_fd, "checks": checks,
+                                   "all_ok": all(c["ok"] for c in checks)},
+            "clocks": clk.summary()}
     print(json.dumps(line))
     return 0
 

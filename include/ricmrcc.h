@@ -279,6 +279,31 @@ RICMRCC_API int ricmrcc_gemm_bf16x3(const double* A, int64_t lda, const double* 
                                     double* C, int64_t ldc, int64_t M, int64_t N, int64_t K,
                                     double alpha, void* stream);
 
+/* FP64-accurate GEMM emulated on the BF16 tensor cores (the Ozaki scheme of
+ * error-free slicing, Ozaki et al. 2012, in the tensor-core form of
+ * Mukunoki et al. 2020; the proposed FP64 route of the refinement steps):
+ *   C[m][n] += alpha * sum_k A[m][k] * B[n][k]
+ * A [M][lda], B [N][ldb], C [M][ldc]: row-major FP64 device arrays (lda,
+ * ldb >= K, ldc >= N).  Each row of alpha*A and of B is scaled by a power of
+ * two into (-1, 1) and cut into `slices` signed 5-bit digits (0 = the
+ * default RICMRCC_EMULATED_DEFAULT_SLICES, 55 bits; 1 .. MAX allowed); the
+ * digit products with i + j < slices run on tcgen05 tensor cores with exact
+ * FP32 sums (pieces of at most 8192 products) and are added into C with FP64
+ * reductions.  Error per element: at most 4 (slices + 1) 2^{-5 slices} K
+ * max_k |alpha A[m][k]| max_k |B[n][k]| from the dropped digits, plus the
+ * rounding of the FP64 additions (as in a plain FP64 GEMM).  Cost: slices (slices + 1) / 2 BF16 products.  The
+ * order of the FP64 additions varies between runs.  Allocates its own
+ * temporary device memory (about 2 slices (M + N) K bytes); synchronises
+ * `stream`.  Returns EINVAL (bad sizes or slices, non-finite alpha, or a
+ * non-finite entry in A or B, detected before C is touched), ENOMEM,
+ * ENOTSUP (no tensor-map support), ECUDA (launch failure or a timed-out
+ * pipeline wait). */
+#define RICMRCC_EMULATED_DEFAULT_SLICES 11
+#define RICMRCC_EMULATED_MAX_SLICES 13
+RICMRCC_API int ricmrcc_gemm_f64_emulated(const double* A, int64_t lda, const double* B, int64_t ldb,
+                                          double* C, int64_t ldc, int64_t M, int64_t N, int64_t K,
+                                          double alpha, int slices, void* stream);
+
 /* Launch only the `count` largest-FLOP contractions of the residual program
  * (largest first), reading the operands left by the last residual.  For
  * profilers that capture one representative launch; blocks until done. */
@@ -294,11 +319,31 @@ RICMRCC_API int ricmrcc_run_largest_ops(ricmrcc_t* h, int count);
  * dE_dh [n][n] and dE_dB [n_aux][n][n] with every entry treated as independent
  * (for the symmetric parameters add the transposed entry), dE_ds scalar.
  * Requires the last ricmrcc_solve to have converged (else ESTATE); uses its
- * flow s and options.  Returns NOT_CONVERGED / DIVERGED for the multipliers. */
+ * flow s and options.  The multiplier equations are linear in Lam.  After an
+ * FP64 solve they are iterated in FP64.  After a RICMRCC_MIXED solve they
+ * are solved by mixed-precision iterative refinement: each outer step takes
+ * the FP64 defect r = (dU/dT)^T Lam + dE/dT - Lam, solves the correction
+ * delta = (dU/dT)^T delta + r to 1e-3 of |r| with tensor-core (split-BF16,
+ * FP32-accumulated) applications of the multiplier terms, and adds delta.
+ * Both end at the same FP64 test: max |defect| below max(t_tol, 1e-11).
+ * If a refinement step fails to halve the defect, plain FP64 iterations
+ * finish.  Returns NOT_CONVERGED / DIVERGED for the multipliers, ECUDA for
+ * a timed-out tensor-core wait. */
 RICMRCC_API int ricmrcc_energy_backward(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds);
 /* Same with device outputs (dE_ds a device double), written on the handle's
  * stream; the multiplier iteration still synchronises with the host. */
 RICMRCC_API int ricmrcc_energy_backward_dev(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds);
+
+/* Work of the last energy_backward call: applications of the multiplier map
+ * in FP64 (every term; about 1.5 times the FLOPs of one residual) and in
+ * mixed precision (the multiplier terms only), and the wall-clock seconds of
+ * the multiplier solve. */
+typedef struct ricmrcc_adjoint_info {
+  int fp64_applications;
+  int mixed_applications;
+  double seconds;
+} ricmrcc_adjoint_info;
+RICMRCC_API int ricmrcc_get_adjoint_info(const ricmrcc_t* h, ricmrcc_adjoint_info* out);
 
 /* Copy the stored amplitudes out / in (flat class layout, host pointers);
  * set_amplitudes allows warm starts and resuming an interrupted solve.

@@ -89,6 +89,11 @@ class LadderInfo(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class AdjointInfo(ctypes.Structure):
+    _fields_ = [("fp64_applications", ctypes.c_int), ("mixed_applications", ctypes.c_int),
+                ("seconds", ctypes.c_double)]
+
+
 class RicMrccError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
@@ -142,9 +147,13 @@ def load_library():
         "ricmrcc_run_largest_ops": ([vp, ctypes.c_int], ctypes.c_int),
         "ricmrcc_energy_backward": ([vp, vp, vp, vp], ctypes.c_int),
         "ricmrcc_energy_backward_dev": ([vp, vp, vp, vp], ctypes.c_int),
+        "ricmrcc_get_adjoint_info": ([vp, ctypes.POINTER(AdjointInfo)], ctypes.c_int),
         "ricmrcc_gemm_bf16x3": ([vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
                                  ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, vp],
                                 ctypes.c_int),
+        "ricmrcc_gemm_f64_emulated": ([vp, ctypes.c_int64, vp, ctypes.c_int64, vp, ctypes.c_int64,
+                                       ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                       ctypes.c_int, vp], ctypes.c_int),
         "ricmrcc_block_eigh_noalloc": ([vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
         "ricmrcc_ladder_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.POINTER(vp)],
                                   ctypes.c_int),
@@ -393,6 +402,13 @@ def _energy_backward_dev(self, dh, dB, ds):
     self._check(self.lib.ricmrcc_energy_backward_dev(self.h, _ptr(dh), _ptr(dB), _ptr(ds)))
 
 
+def _adjoint_info(self):
+    """Applications of the multiplier map (FP64, mixed) and seconds of the last energy_backward."""
+    info = AdjointInfo()
+    self._check(self.lib.ricmrcc_get_adjoint_info(self.h, ctypes.byref(info)))
+    return info
+
+
 def _get_residual(self):
     """(R1, R2) flat class layout of the last residual evaluation."""
     r1 = np.zeros(self.layout.t1_size)
@@ -433,6 +449,7 @@ RicMrcc.get_tile_rule = _get_tile_rule
 RicMrcc.tune = _tune
 RicMrcc.energy_backward = _energy_backward
 RicMrcc.energy_backward_dev = _energy_backward_dev
+RicMrcc.adjoint_info = _adjoint_info
 RicMrcc.step = _step
 RicMrcc.plan_info = _plan_info
 RicMrcc.profile = _profile
@@ -590,6 +607,22 @@ class Ladder:
         info = LadderInfo()
         self._check(self.lib.ricmrcc_ladder_info(self.L, ctypes.byref(info)))
         return info.as_dict()
+
+
+def gemm_f64_emulated(A, B, C, alpha=1.0, slices=0, stream=None):
+    """C += alpha * A @ B.T on the tensor cores with FP64 accuracy (digit
+    slicing, see ricmrcc_gemm_f64_emulated).  A [M,K], B [N,K], C [M,N]:
+    CUDA float64 tensors with unit stride along the last axis."""
+    M, K = A.shape
+    N = B.shape[0]
+    assert B.shape[1] == K and tuple(C.shape) == (M, N)
+    for x in (A, B, C):
+        assert x.dtype.is_floating_point and x.element_size() == 8 and x.is_cuda and x.stride(1) == 1
+    rc = load_library().ricmrcc_gemm_f64_emulated(
+        A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0), C.data_ptr(), C.stride(0), M, N, K,
+        float(alpha), int(slices), None if stream is None else stream.cuda_stream)
+    if rc != OK:
+        raise RicMrccError(rc, "ricmrcc_gemm_f64_emulated failed")
 
 
 def set_wait_limit(seconds, stall_test=False):

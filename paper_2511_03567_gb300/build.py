@@ -15,7 +15,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "batch.cu", "planner.cu", "kernels.cu", "noalloc.cu", "tcgemm.cu", "grouped.cu", "schedule.cu", "ladder.cu"]
+SOURCES = ["api.cu", "batch.cu", "planner.cu", "kernels.cu", "noalloc.cu", "tcgemm.cu", "grouped.cu", "schedule.cu", "ladder.cu", "ozaki.cu"]
 HOST_SOURCES = ["full_terms.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]

@@ -985,7 +985,7 @@ int ricmrcc_set_wait_limit(double seconds, int stall_test) {
   if (!(seconds > 0.0) || !(seconds < 1e6)) return RICMRCC_EINVAL;
   const uint64_t ns = (uint64_t)(seconds * 1e9) > 0 ? (uint64_t)(seconds * 1e9) : 1;
   const int st = stall_test ? 1 : 0;
-  if (tc_set_wait_ns(ns, st) != 0 || ladder_set_wait_ns(ns, st) != 0) {
+  if (tc_set_wait_ns(ns, st) != 0 || ladder_set_wait_ns(ns, st) != 0 || ozaki_set_wait_ns(ns, st) != 0) {
     cudaGetLastError();
     return RICMRCC_ECUDA;
   }
@@ -1663,19 +1663,39 @@ int plan_adjoint(ricmrcc_t* h) {
   set(ov[OGF], h->gF, {DOM_G, DOM_G}, {n, 1});
   // d/dV[p,q,r,s] lands on d/d(pr|qs): the same permuted view as the input V
   set(ov[OGV], h->geri, {DOM_G, DOM_G, DOM_G, DOM_G}, {n * n * n, n, n * n, 1});
-  Planner pt(d, tv, ov, h->scal + 3), ph(d, tv, ov, h->scal + 3);
-  for (const auto& t : kGradTTerms)
+  Planner pt(d, tv, ov, h->scal + 3), ph(d, tv, ov, h->scal + 3), pl(d, tv, ov, h->scal + 3);
+  for (const auto& t : kGradTTerms) {
     if (!pt.add_term(t, &h->gradt_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad dT term");
+    bool multiplier = false;
+    for (int f = 0; f < t.nfac; ++f) multiplier |= t.fac[f].tensor == TY1 || t.fac[f].tensor == TY2;
+    if (multiplier && !pl.add_term(t, &h->gradl_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad dT term");
+  }
   for (const auto& t : kGradHTerms)
     if (!ph.add_term(t, &h->gradh_prog)) return fail(h, RICMRCC_EINVAL, "planner: bad d(F,V) term");
-  h->adj_arena_elems = std::max<int64_t>(std::max<int64_t>(pt.arena_size(), ph.arena_size()), 1);
+  h->adj_arena_elems =
+      std::max<int64_t>(std::max<int64_t>(std::max<int64_t>(pt.arena_size(), ph.arena_size()), pl.arena_size()), 1);
   TRY(dalloc(h, &h->adj_arena, h->adj_arena_elems));
   pt.finalize(&h->gradt_prog, h->adj_arena);
   ph.finalize(&h->gradh_prog, h->adj_arena);
-  for (Program* p : {&h->gradt_prog, &h->gradh_prog}) {
+  pl.finalize(&h->gradl_prog, h->adj_arena);
+  TRY(dalloc(h, &h->Dlt, h->ng));
+  TRY(dalloc(h, &h->Rdf, h->ng));
+  for (Program* p : {&h->gradt_prog, &h->gradh_prog, &h->gradl_prog}) {
     TRY(dalloc(h, &p->d_table, (int64_t)p->table.size()));
     CK(cudaMemcpyAsync(p->d_table, p->table.data(), sizeof(int64_t) * p->table.size(), cudaMemcpyHostToDevice,
                        h->s));
+  }
+  if (h->verbose) {
+    for (const Program* p : {&h->gradt_prog, &h->gradl_prog, &h->gradh_prog}) {
+      double tc = 0.0, batched = 0.0, dot = 0.0;
+      for (const ContractOp& op : p->ops) {
+        if (tc_eligible(op, h->rule)) tc += op.flops;
+        if (op.L > 1) batched += op.flops;
+        if (op.kind == 2) dot += op.flops;
+      }
+      fprintf(stderr, "ricmrcc adjoint program: %zu ops, %.4g flops (tensor-core eligible %.4g, batched %.4g, dot %.4g)\n",
+              p->ops.size(), p->flops, tc, batched, dot);
+    }
   }
   h->adj_planned = true;
   return RICMRCC_OK;
@@ -1715,6 +1735,134 @@ int diis_step(ricmrcc_t* h, const double* vec, const double* err, double* target
 
 extern "C" {
 
+namespace {
+
+// Tensor-core scratch for the multiplier-linear program: the packed operands
+// of its largest contraction that any tile rule could send to the tensor
+// cores (eligibility depends on the rule only through thresholds).
+int ensure_adj_tc(ricmrcc_t* h) {
+  if (h->adj_tc_scratch) return RICMRCC_OK;
+  const Program& p = h->gradl_prog;
+  size_t need = 0;
+  h->gradl_col.assign(p.ops.size(), 0);
+  for (size_t i = 0; i < p.ops.size(); ++i) {
+    const ContractOp& op = p.ops[i];
+    if (op.kind == 2 || op.L != 1 || op.M < 64 || op.K < 32) continue;
+    need = std::max(need, tc_scratch_bytes(op.M, op.N, op.K));
+    const int64_t* th = p.table.data() + op.tab;
+    const int64_t* tAM = th + 3;
+    const int64_t* tBN = tAM + 2 * op.M;
+    h->gradl_col[i] = (char)rows_fast(tBN + op.N, op.N, tAM + op.M, op.M);
+  }
+  char* buf = nullptr;
+  TRY(dalloc(h, &buf, (int64_t)std::max<size_t>(need, 16)));
+  h->adj_tc_scratch = buf;
+  h->adj_tc_bytes = std::max<size_t>(need, 16);
+  return RICMRCC_OK;
+}
+
+// One application of the multiplier map at `lam`:
+//   Tn = S[Delta Yraw + GT],  Err = Tn - lam,  *md = max |Err|,
+// with Yraw = phi Lam and GT = gt0 (zero if null) + the gradient program
+// `p` evaluated at Ytil(lam).  In mixed precision the contractions the tile
+// rule accepts run on the tensor cores (split BF16, FP32 accumulation).
+int adjoint_apply(ricmrcc_t* h, const double* lam, const Program& p, bool mixed, const double* gt0, double s,
+                  double* md) {
+  const Dims& d = h->d;
+  launch_adj_y(lam, h->Yraw, h->Ytil, h->eps, d, s, h->s);
+  if (gt0)
+    CK(cudaMemcpyAsync(h->GT, gt0, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
+  else
+    CK(cudaMemsetAsync(h->GT, 0, sizeof(double) * h->ng, h->s));
+  CK(cudaMemsetAsync(h->adj_arena, 0, sizeof(double) * h->adj_arena_elems, h->s));
+  if (!mixed) {
+    TRY(run_program(h, p));
+  } else {
+    for (size_t i = 0; i < p.ops.size(); ++i) {
+      const ContractOp& op = p.ops[i];
+      if (tc_eligible(op, h->rule) && op.M > 0 && op.N > 0 && op.K > 0) {
+        TcArgs a = tc_args(h, p, (int)i, 0);
+        a.scratch = h->adj_tc_scratch;
+        a.scratch_bytes = h->adj_tc_bytes;
+        a.col_lanes = h->gradl_col[i];
+        const int rc = tc_contract(a, h->s);
+        if (rc != 0)
+          return fail(h, RICMRCC_ECUDA, "tensor-core contraction launch failed (" + std::to_string(rc) + ")");
+      } else {
+        launch_contract(op, p.d_table, h->s);
+      }
+    }
+  }
+  CK(cudaMemsetAsync(h->scal + 2, 0, sizeof(double), h->s));
+  launch_adj_update(lam, h->Yraw, h->GT, h->Tn, h->Err, h->eps, d, h->scal + 2, h->s);
+  CK(cudaMemcpyAsync(h->host_scal + 2, h->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  if (mixed) TRY(check_tc_error(h));
+  *md = h->host_scal[2];
+  if (!isfinite(*md) || *md > 1e100) return fail(h, RICMRCC_DIVERGED, "adjoint iteration diverged");
+  return RICMRCC_OK;
+}
+
+// Mixed-precision iterative refinement of the multiplier equations, which
+// are linear: Lam = A(Lam) + c with c = S[dE/dT].  Each outer step takes the
+// defect r = F(Lam) - Lam in FP64, solves the correction equation
+// delta = A(delta) + r with DIIS-accelerated mixed-precision applications of
+// A (the multiplier terms only, so the rounding error scales with delta, not
+// with Lam) to kInnerRel of |r|, and sets Lam += delta.  Stops with *conv
+// when the FP64 defect is below tol; returns with *conv false (Lam kept) when
+// an outer step fails to halve the defect, so that plain FP64 iterations
+// finish from there.
+constexpr double kInnerRel = 1e-3;
+constexpr int kMaxOuter = 16;
+int adjoint_refined(ricmrcc_t* h, double s, double tol, int cap, bool* conv) {
+  const ricmrcc_opts& o = h->solved_opts;
+  *conv = false;
+  TRY(ensure_tc(h));
+  TRY(ensure_adj_tc(h));
+  double md_prev = HUGE_VAL;
+  for (int outer = 1; outer <= kMaxOuter; ++outer) {
+    double md = 0.0;
+    TRY(adjoint_apply(h, h->Lam, h->gradt_prog, false, nullptr, s, &md));
+    ++h->adj_fp64;
+    if (h->verbose) fprintf(stderr, "ricmrcc adjoint refinement %2d  FP64 defect %.3e\n", outer, md);
+    if (md < tol) {
+      CK(cudaMemcpyAsync(h->Lam, h->Tn, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
+      *conv = true;
+      return RICMRCC_OK;
+    }
+    if (!(md < 0.5 * md_prev)) return RICMRCC_OK;
+    md_prev = md;
+    CK(cudaMemcpyAsync(h->Rdf, h->Err, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
+    CK(cudaMemcpyAsync(h->Dlt, h->Err, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
+    reset_iteration_state(h);
+    double best = HUGE_VAL;
+    int worse = 0;
+    for (int j = 1; j <= std::max(o.max_iter, 1); ++j) {
+      double mi = 0.0;
+      TRY(adjoint_apply(h, h->Dlt, h->gradl_prog, true, h->Rdf, s, &mi));
+      ++h->adj_mixed;
+      if (h->verbose) fprintf(stderr, "ricmrcc adjoint   correction %3d  max|d delta| = %.3e\n", j, mi);
+      bool stop = mi < kInnerRel * md || mi < 0.1 * tol;
+      if (mi < best) {
+        best = mi;
+        worse = 0;
+      } else if (++worse >= 3) {
+        stop = true;  // at the mixed-precision floor
+      }
+      if (stop || o.diis_size == 0) {
+        CK(cudaMemcpyAsync(h->Dlt, h->Tn, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
+        if (stop) break;
+      } else {
+        TRY(diis_step(h, h->Tn, h->Err, h->Dlt, cap, j, o.diis_start));
+      }
+    }
+    launch_add(h->Lam, h->Dlt, h->ng, h->s);
+  }
+  return RICMRCC_OK;
+}
+
+}  // namespace
+
 static int energy_backward_impl(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds, bool dev) {
   if (!h) return RICMRCC_EINVAL;
   if (h->method != RICMRCC_METHOD_RIC)
@@ -1732,21 +1880,22 @@ static int energy_backward_impl(ricmrcc_t* h, double* dE_dh, double* dE_dB, doub
   TRY(residual_device(h, false));
   // multipliers: Lam = Delta (phi Lam) + d/dT [E + Ytil . X],  Y = phi Lam
   CK(cudaMemsetAsync(h->Lam, 0, sizeof(double) * h->ng, h->s));
-  reset_iteration_state(h);
   const double tol = std::max(o.t_tol, 1e-11);
   bool conv = false;
-  for (int it = 1; it <= 4 * o.max_iter; ++it) {
-    launch_adj_y(h->Lam, h->Yraw, h->Ytil, h->eps, d, s, h->s);
-    CK(cudaMemsetAsync(h->GT, 0, sizeof(double) * h->ng, h->s));
-    CK(cudaMemsetAsync(h->adj_arena, 0, sizeof(double) * h->adj_arena_elems, h->s));
-    TRY(run_program(h, h->gradt_prog));
-    CK(cudaMemsetAsync(h->scal + 2, 0, sizeof(double), h->s));
-    launch_adj_update(h->Lam, h->Yraw, h->GT, h->Tn, h->Err, h->eps, d, h->scal + 2, h->s);
-    CK(cudaMemcpyAsync(h->host_scal + 2, h->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
-    const double md = h->host_scal[2];
-    if (h->verbose) fprintf(stderr, "ricmrcc adjoint iter %3d  max|dLam| = %.3e\n", it, md);
-    if (!isfinite(md) || md > 1e100) return fail(h, RICMRCC_DIVERGED, "adjoint iteration diverged");
+  const auto t_adj = std::chrono::steady_clock::now();
+  h->adj_fp64 = h->adj_mixed = 0;
+  // after a mixed-precision solve: refine the multipliers from mixed-precision
+  // correction solves; after an FP64 solve (or if refinement stalls): plain
+  // FP64 iterations
+  if (o.precision == RICMRCC_MIXED) TRY(adjoint_refined(h, s, tol, cap, &conv));
+  reset_iteration_state(h);
+  for (int it = 1; !conv && it <= 4 * o.max_iter; ++it) {
+    double md = 0.0;
+    TRY(adjoint_apply(h, h->Lam, h->gradt_prog, false, nullptr, s, &md));
+    ++h->adj_fp64;
+    if (h->verbose)
+      fprintf(stderr, "ricmrcc adjoint iter %3d  max|dLam| = %.3e  %.3f s\n", it, md,
+              std::chrono::duration<double>(std::chrono::steady_clock::now() - t_adj).count());
     if (md < tol) {
       CK(cudaMemcpyAsync(h->Lam, h->Tn, sizeof(double) * h->ng, cudaMemcpyDeviceToDevice, h->s));
       conv = true;
@@ -1758,6 +1907,7 @@ static int energy_backward_impl(ricmrcc_t* h, double* dE_dh, double* dE_dB, doub
       TRY(diis_step(h, h->Tn, h->Err, h->Lam, cap, it, o.diis_start));
     }
   }
+  h->adj_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_adj).count();
   if (!conv) return fail(h, RICMRCC_NOT_CONVERGED, "adjoint (multiplier) equations did not converge");
   // parameter gradient: dL/dF, dL/dV through the terms, then epsilon, E0, Fock, B
   launch_adj_y(h->Lam, h->Yraw, h->Ytil, h->eps, d, s, h->s);
@@ -1819,6 +1969,13 @@ int ricmrcc_energy_backward(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* 
 }
 int ricmrcc_energy_backward_dev(ricmrcc_t* h, double* dE_dh, double* dE_dB, double* dE_ds) {
   return energy_backward_impl(h, dE_dh, dE_dB, dE_ds, true);
+}
+int ricmrcc_get_adjoint_info(const ricmrcc_t* h, ricmrcc_adjoint_info* out) {
+  if (!h || !out) return RICMRCC_EINVAL;
+  out->fp64_applications = h->adj_fp64;
+  out->mixed_applications = h->adj_mixed;
+  out->seconds = h->adj_seconds;
+  return RICMRCC_OK;
 }
 
 }  // extern "C"

@@ -101,6 +101,15 @@ struct ricmrcc {
   Program res_prog, cum_prog;
   // adjoint (energy_backward)
   Program gradt_prog, gradh_prog;
+  // the terms of gradt_prog that depend on the multipliers (the linear part of
+  // the multiplier equations), for the mixed-precision correction solves
+  Program gradl_prog;
+  std::vector<char> gradl_col;  // tensor-core epilogue lanes per op of gradl_prog
+  double *Dlt = nullptr, *Rdf = nullptr;  // correction and defect of the multipliers
+  void* adj_tc_scratch = nullptr;
+  size_t adj_tc_bytes = 0;
+  int adj_fp64 = 0, adj_mixed = 0;  // applications in the last energy_backward
+  double adj_seconds = 0.0;
   bool adj_planned = false, solved = false;
   double solved_s = 0.0;
   ricmrcc_opts solved_opts{};

@@ -750,6 +750,13 @@ __global__ void k_sym_pairs(double* __restrict__ g, int64_t n2) {
 }
 }  // namespace
 
+__global__ void k_add(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+void launch_add(double* y, const double* x, int64_t n, cudaStream_t st) {
+  k_add<<<grid_for(n), kThreads, 0, st>>>(y, x, n);
+}
 void launch_adj_y(const double* Lam, double* Yraw, double* Ytil, const double* eps, const Dims& d, double s,
                   cudaStream_t st) {
   const int64_t n = (int64_t)d.np * d.np * d.nh * d.nh + (int64_t)d.np * d.nh;

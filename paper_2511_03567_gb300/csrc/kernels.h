@@ -29,6 +29,8 @@ void launch_extrapolate(double* T, const double* vecs, const double* coef, const
 cudaError_t run_jacobi(double* Ablk, double* V, int n, double* U, int n_full, int off, int* d_sweeps,
                        cudaStream_t s);
 void launch_energy_out(double* out, const double* acc, double e0, cudaStream_t s);
+// y += x over n elements
+void launch_add(double* y, const double* x, int64_t n, cudaStream_t s);
 void launch_adj_y(const double* Lam, double* Yraw, double* Ytil, const double* eps, const Dims& d, double s,
                   cudaStream_t st);
 void launch_adj_update(const double* Lam, const double* Yraw, const double* GT, double* Ln, double* Err,

@@ -189,6 +189,8 @@ bool tc_available();
 int tc_set_wait_ns(uint64_t ns, int stall_test);
 // Same for the ladder kernels (ladder.cu).
 int ladder_set_wait_ns(uint64_t ns, int stall_test);
+// the same for the emulated-FP64 GEMM (ozaki.cu)
+int ozaki_set_wait_ns(uint64_t ns, int stall_test);
 int tc_pick_bn(int64_t N);  // N tile of the GEMM for an N extent
 int64_t tc_pad(int64_t x, int64_t m);
 // Gather X[xL + tR[r] + tK[k]] (r < rows, k < K) into the packed split-BF16

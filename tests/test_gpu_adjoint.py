@@ -148,21 +148,29 @@ def test_backward_requires_converged_solve():
 
 
 def test_adjoint_after_mixed_forward():
-    """BF16 forward with FP64 adjoint: a mixed-precision solve (every
-    GEMM-shaped contraction on the tensor cores, then FP64 refinement) ends at
-    the FP64 fixed point, so the FP64 adjoint taken there gives the gradients
-    of the FP64 forward solve."""
+    """BF16 forward with FP64 adjoint accumulation: a mixed-precision solve
+    (every GEMM-shaped contraction on the tensor cores, then FP64 refinement)
+    ends at the FP64 fixed point; its adjoint solves the multiplier equations
+    by iterative refinement (FP64 defects, tensor-core corrections) and must
+    give the gradients of the FP64 forward solve and FP64-iterated adjoint,
+    in fewer FP64 applications of the multiplier map."""
     import paper_2511_03567_gb300 as ric
     nc, na, nv, nx = 4, 4, 20, 112
     g, h, B, rot = _setup(nc, na, nv, nx, 1)
     e64 = _energy(g, h, B, 0.5)
     dh64, dB64, ds64 = g.energy_backward()
+    fp64_only = g.adjoint_info()
+    assert fp64_only.mixed_applications == 0 and fp64_only.fp64_applications > 0
     g.set_tile_rule(1e3, True, True)
     g.set_amplitudes(g.unpack(np.zeros(g.layout.t1_size), np.zeros(g.layout.t2_size)))  # from T = 0
     em, st = g.solve(0.5, precision=ric.MIXED, refine_tol=1e-4, **TIGHT)
     assert st.converged == 1 and st.mixed_iterations > 0
     assert g.plan_info().tc_contractions > 0
     dhm, dBm, dsm = g.energy_backward()
+    refined = g.adjoint_info()
+    assert refined.mixed_applications > 0
+    assert refined.fp64_applications < fp64_only.fp64_applications, (refined.fp64_applications,
+                                                                      fp64_only.fp64_applications)
     assert abs(em - e64) < 1e-9
     assert abs(dsm - ds64) < 1e-7 * max(1.0, abs(ds64))
     assert np.abs(dhm - dh64).max() < 1e-7 * max(1.0, np.abs(dh64).max())
