@@ -885,9 +885,12 @@ CONV_B_SCALE = 0.2
 
 def converging_mid(g, p, w):
     """Mid sizes with a smaller density-fitting factor, so that the iteration
-    converges: the mixed solve (tensor-core iterations, then FP64 refinement)
-    against the FP64 solve, energies and times.  Changes the handle's
-    integrals (run after everything else on the Mid workload)."""
+    converges: the FP64 solve, the mixed solve (tensor-core iterations, then
+    FP64 refinement) and the emulated solve (the same, with the refinement
+    iterations' large contractions as emulated-FP64 tensor-core products):
+    energies and times, and the seconds of one residual evaluation at each
+    arithmetic.  Changes the handle's integrals (run after everything else on
+    the Mid workload)."""
     import paper_2511_03567_gb300 as ric
     g.set_integrals(p.h, np.ascontiguousarray(p.B * CONV_B_SCALE))
     g.set_rdms(p.G1, p.G2, p.G3)  # the handle holds them in its rotated basis
@@ -895,7 +898,7 @@ def converging_mid(g, p, w):
     out = {"inputs": f"Mid workload with B scaled by {CONV_B_SCALE} (B ~ N(0, {0.05 * CONV_B_SCALE:g}))",
            "s": w["s"]}
     res = {}
-    for name, prec in (("fp64", ric.FP64), ("mixed", ric.MIXED)):
+    for name, prec in (("fp64", ric.FP64), ("mixed", ric.MIXED), ("emulated", ric.EMULATED)):
         g.set_precision(prec)
         g.step(s=w["s"], n_steps=0, restart=True, precision=prec)  # T = 0
         try:
@@ -909,6 +912,23 @@ def converging_mid(g, p, w):
     if "energy" in res.get("fp64", {}) and "energy" in res.get("mixed", {}):
         out["abs_dE_mixed_vs_fp64"] = abs(res["mixed"]["energy"] - res["fp64"]["energy"])
         out["within_1e-6"] = out["abs_dE_mixed_vs_fp64"] <= 1e-6
+    if "energy" in res.get("fp64", {}) and "energy" in res.get("emulated", {}):
+        out["abs_dE_emulated_vs_fp64"] = abs(res["emulated"]["energy"] - res["fp64"]["energy"])
+    # one residual evaluation at each arithmetic (wall clock of the call, at
+    # the converged amplitudes, after a warm-up evaluation)
+    T = g.get_amplitudes()
+    times = {}
+    for name, prec in (("fp64", ric.FP64), ("mixed", ric.MIXED), ("emulated", ric.EMULATED)):
+        g.set_precision(prec)
+        g.residual(T)
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            g.residual(T)
+            ts.append(time.perf_counter() - t0)
+        times[name] = float(np.median(ts))
+    out["residual_seconds"] = times
+    out["residual_timing"] = "wall clock of ricmrcc_residual (host amplitudes in, residual out), median of 3"
     g.set_precision(ric.MIXED)
     return out
 

@@ -69,9 +69,14 @@ enum { RICMRCC_RDM = 0, RICMRCC_CUMULANT = 1 };
 
 /* precision of the dense contractions (ricmrcc_set_precision) */
 enum {
-  RICMRCC_FP64 = 0,  /* every contraction in FP64 */
-  RICMRCC_MIXED = 1  /* large contractions on BF16 tensor cores (split-precision
-                        products, FP32 accumulation), FP64 everything else */
+  RICMRCC_FP64 = 0,    /* every contraction in FP64 */
+  RICMRCC_MIXED = 1,   /* large contractions on BF16 tensor cores (split-precision
+                          products, FP32 accumulation), FP64 everything else */
+  RICMRCC_EMULATED = 2 /* FP64 accuracy with the large contractions on the BF16
+                          tensor cores: the digit-slicing scheme of
+                          ricmrcc_gemm_f64_emulated (11 digits), FP64 everything
+                          else.  As a solver precision: RICMRCC_MIXED iterations
+                          until refine_tol, then iterations at this arithmetic */
 };
 
 typedef struct ricmrcc ricmrcc_t;
@@ -95,8 +100,9 @@ typedef struct {
   double t_tol;      /* max |t_new - t| threshold (default 1e-9) */
   int diis_size;     /* DIIS subspace size, 0 disables (default 8) */
   int diis_start;    /* first iteration that extrapolates (default 3) */
-  int precision;     /* RICMRCC_FP64 or RICMRCC_MIXED (default FP64) */
-  double refine_tol; /* mixed: switch to FP64 iterations once max|dt| < refine_tol */
+  int precision;     /* RICMRCC_FP64, RICMRCC_MIXED or RICMRCC_EMULATED (default FP64) */
+  double refine_tol; /* mixed / emulated: switch to FP64-accurate iterations (FP64,
+                        resp. emulated FP64) once max|dt| < refine_tol */
 } ricmrcc_opts;
 
 typedef struct {
@@ -140,7 +146,9 @@ RICMRCC_API const char* ricmrcc_last_error(const ricmrcc_t* h);
 /* Stream (cudaStream_t) used by every later call; NULL = legacy default. */
 RICMRCC_API int ricmrcc_set_stream(ricmrcc_t* h, void* stream);
 
-/* Select the arithmetic of the dense contractions (RICMRCC_FP64 / MIXED). */
+/* Select the arithmetic of the dense contractions of ricmrcc_residual and of
+ * ricmrcc_step when its options say RICMRCC_FP64 (RICMRCC_FP64 / MIXED /
+ * EMULATED). */
 RICMRCC_API int ricmrcc_set_precision(ricmrcc_t* h, int precision);
 
 /* One-electron integrals h[n][n] (symmetric) and the density-fitting factor
@@ -216,7 +224,9 @@ RICMRCC_API int ricmrcc_solve(ricmrcc_t* h, double s, const ricmrcc_opts* opts, 
  * calls.  restart != 0 first returns to the solver's initial guess: T = 0
  * and an empty DIIS history.  E_out / max_dt_out (nullable, host) receive
  * the energy at the last evaluated amplitudes and the last max |t_new - t|.
- * Returns OK or DIVERGED. */
+ * Every step uses opts->precision's arithmetic (RICMRCC_EMULATED: emulated
+ * FP64 throughout), or the handle's (ricmrcc_set_precision) when that is
+ * RICMRCC_FP64.  Returns OK or DIVERGED. */
 RICMRCC_API int ricmrcc_step(ricmrcc_t* h, const ricmrcc_opts* opts, int n_steps, int restart,
                              double* E_out, double* max_dt_out);
 
@@ -250,6 +260,8 @@ typedef struct {
    * with grouped launches */
   int64_t tc_grouped_ops;
   int64_t tc_weighted_ops;
+  int64_t oz_contractions;   /* contractions the RICMRCC_EMULATED path runs on tensor cores */
+  double oz_flops;           /* their FLOPs (FP64-equivalent) */
 } ricmrcc_plan_info_t;
 
 /* Sizes of the contraction program planned for this handle. */
@@ -378,12 +390,17 @@ RICMRCC_API int ricmrcc_get_residual(ricmrcc_t* h, double* R1, double* R2);
  *                 <= 1 admit every N); narrower contractions stay on the
  *                 CUDA-core tiles, where a 128-row MMA tile would be mostly
  *                 padding.
+ *   oz_max_pad    RICMRCC_EMULATED: of those, the contractions whose 128 x 256
+ *                 x 64 tile padding multiplies the work by at most this factor
+ *                 run as emulated-FP64 tensor-core products, the others on the
+ *                 FP64 tiles (values below 1 select the default, 4).
  * The result does not depend on the rule beyond rounding. */
 typedef struct {
   double tc_min_flops;
   int skinny;
   int tc_grouped;
   int tc_min_n;
+  double oz_max_pad;
 } ricmrcc_tile_rule;
 
 #define RICMRCC_TUNE_MAX 8

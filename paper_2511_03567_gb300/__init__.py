@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libricmrcc.so")
 
 OK, EINVAL, ENOMEM, ECUDA, NOT_CONVERGED, DIVERGED, ESTATE, ENOTSUP = range(8)
 RDM, CUMULANT = 0, 1
-FP64, MIXED = 0, 1
+FP64, MIXED, EMULATED = 0, 1, 2
 METHOD_RIC, METHOD_FULL = 0, 1
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "NOT_CONVERGED",
                 5: "DIVERGED", 6: "ESTATE", 7: "ENOTSUP"}
@@ -56,12 +56,13 @@ class PlanInfo(ctypes.Structure):
                 ("tc_pack_bytes", ctypes.c_double), ("graph_launches", ctypes.c_int64 * 2),
                 ("kernel_ops", ctypes.c_int64 * 8), ("kernel_work", ctypes.c_double * 8),
                 ("tc_gemm_bytes", ctypes.c_double), ("tc_grouped_ops", ctypes.c_int64),
-                ("tc_weighted_ops", ctypes.c_int64)]
+                ("tc_weighted_ops", ctypes.c_int64), ("oz_contractions", ctypes.c_int64),
+                ("oz_flops", ctypes.c_double)]
 
 
 class TileRule(ctypes.Structure):
     _fields_ = [("tc_min_flops", ctypes.c_double), ("skinny", ctypes.c_int), ("tc_grouped", ctypes.c_int),
-                ("tc_min_n", ctypes.c_int)]
+                ("tc_min_n", ctypes.c_int), ("oz_max_pad", ctypes.c_double)]
 
 
 TUNE_MAX = 8
@@ -417,8 +418,8 @@ def _get_residual(self):
     return r1, r2
 
 
-def _set_tile_rule(self, tc_min_flops=1e7, skinny=True, tc_grouped=True, tc_min_n=1):
-    r = TileRule(float(tc_min_flops), int(bool(skinny)), int(bool(tc_grouped)), int(tc_min_n))
+def _set_tile_rule(self, tc_min_flops=1e7, skinny=True, tc_grouped=True, tc_min_n=1, oz_max_pad=4.0):
+    r = TileRule(float(tc_min_flops), int(bool(skinny)), int(bool(tc_grouped)), int(tc_min_n), float(oz_max_pad))
     self._check(self.lib.ricmrcc_set_tile_rule(self.h, ctypes.byref(r)))
 
 
@@ -426,7 +427,7 @@ def _get_tile_rule(self):
     r = TileRule()
     self._check(self.lib.ricmrcc_get_tile_rule(self.h, ctypes.byref(r)))
     return {"tc_min_flops": r.tc_min_flops, "skinny": bool(r.skinny), "tc_grouped": bool(r.tc_grouped),
-            "tc_min_n": r.tc_min_n}
+            "tc_min_n": r.tc_min_n, "oz_max_pad": r.oz_max_pad}
 
 
 def _tuning_dict(t):

@@ -200,6 +200,18 @@ bool tc_eligible(const ContractOp& op, const TileRule& r) {
          fits;
 }
 
+// Contractions the emulated-FP64 path runs on the tensor cores: those of the
+// mixed path whose 128 x 256 x 64 tile padding multiplies the work by at most
+// the rule's oz_max_pad (4 by default: the 66 digit products take about 1/15
+// of the FP64 pipe's time per useful product, so more padded ones are cheaper
+// on the CUDA cores).
+bool oz_eligible(const ContractOp& op, const TileRule& r) {
+  if (!tc_eligible(op, r)) return false;
+  const double pad = (double)((op.M + 127) / 128 * 128) * (double)((op.N + 255) / 256 * 256) *
+                     (double)((op.K + 63) / 64 * 64) / ((double)op.M * (double)op.N * (double)op.K);
+  return pad <= r.oz_max_pad;
+}
+
 // FP64 kernel of an op: the planner's choice (64x64 tile, 16x16 tile or dot
 // reduction), with tall-skinny ops moved to the 128x16 / 64x32 tiles, whose
 // threads own one output column each and so write C rows contiguously.
@@ -370,7 +382,7 @@ void release_graphs(ricmrcc_t* h) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
-  h->graph_launches[0] = h->graph_launches[1] = 0;
+  h->graph_launches[0] = h->graph_launches[1] = h->graph_launches[2] = 0;
   for (void* p : h->group_allocs) cudaFree(p);
   h->group_allocs.clear();
 }
@@ -390,6 +402,12 @@ void release_tc(ricmrcc_t* h) {
   drop(h->tc_scratch);
   h->tc_scratch = nullptr;
   h->tc_scratch_bytes = 0;
+  drop(h->oz_scratch);  // sized by the rule's tensor-core contractions
+  h->oz_scratch = nullptr;
+  h->oz_slice = 0;
+  drop(h->adj_oz_scratch);
+  h->adj_oz_scratch = nullptr;
+  h->adj_oz_bytes = 0;
   h->tc_planned = false;
   h->tc_cache_valid = false;
 }
@@ -431,7 +449,7 @@ std::vector<TileRule> tune_candidates(const TileRule& cur, bool mixed) {
 
 int set_rule(ricmrcc_t* h, const TileRule& r) {
   if (r.tc_min_flops == h->rule.tc_min_flops && r.skinny == h->rule.skinny && r.tc_grouped == h->rule.tc_grouped &&
-      r.tc_min_n == h->rule.tc_min_n)
+      r.tc_min_n == h->rule.tc_min_n && r.oz_max_pad == h->rule.oz_max_pad)
     return RICMRCC_OK;
   CK(cudaStreamSynchronize(h->s));
   release_tc(h);
@@ -639,12 +657,13 @@ namespace {
 // launches per level, tensor-core packing and GEMMs in mixed precision) on the
 // handle's lanes.  Outputs accumulate atomically, so ops of one level need no
 // ordering; intermediates flow only to later levels.
-int capture_residual(ricmrcc_t* h, bool mixed) {
+int capture_residual(ricmrcc_t* h, int mode) {
+  const bool mixed = mode == 1, emulated = mode == 2;
   const std::vector<ricmrcc_t*> inst{h};
   const std::vector<char> live{1};
   Schedule sc;
   // descriptor arrays first (allocation is not allowed inside the capture)
-  TRY(build_schedule(h, inst, live, h->rule, mixed, h->group_allocs, &sc));
+  TRY(build_schedule(h, inst, live, h->rule, mixed, h->group_allocs, &sc, emulated));
   cudaStream_t s0 = h->lane[0];
   CK(cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal));
   auto fail_capture = [&](int rc) {
@@ -658,14 +677,14 @@ int capture_residual(ricmrcc_t* h, bool mixed) {
       cudaMemsetAsync(h->X, 0, sizeof(double) * h->ng, s0) != cudaSuccess ||
       cudaMemsetAsync(h->scal + 1, 0, sizeof(double), s0) != cudaSuccess)
     return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: memset"));
-  if (mixed && cudaMemsetAsync(h->d_err, 0, sizeof(int), s0) != cudaSuccess)
+  if ((mixed || emulated) && cudaMemsetAsync(h->d_err, 0, sizeof(int), s0) != cudaSuccess)
     return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: memset"));
   if (cudaMemsetAsync(sc.counters, 0, sizeof(unsigned long long) * sc.ncounters, s0) != cudaSuccess)
     return fail_capture(fail(h, RICMRCC_ECUDA, "graph capture: memset"));
   StreamTarget tgt(h->lane, h->lane_ev, h->tc_ev);
   int64_t launches = 0;
   const int rc = run_schedule(h, sc, inst, live, h->rule, mixed, tgt, h->tc_scratch, h->tc_scratch_bytes,
-                              h->d_err, &launches);
+                              h->d_err, &launches, emulated);
   if (rc != RICMRCC_OK) return fail_capture(rc);
   cudaGraph_t g = nullptr;
   CK(cudaStreamEndCapture(s0, &g));
@@ -676,20 +695,87 @@ int capture_residual(ricmrcc_t* h, bool mixed) {
     cudaGetLastError();
     return fail(h, RICMRCC_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
-  h->graph[mixed ? 1 : 0] = ex;
-  h->graph_launches[mixed ? 1 : 0] = launches;
+  h->graph[mode] = ex;
+  h->graph_launches[mode] = launches;
   return RICMRCC_OK;
 }
 
 }  // namespace
 
-int residual_device(ricmrcc_t* h, bool mixed) {
-  if (mixed) {
+OzArgs oz_args(ricmrcc_t* h, const Program& p, int op_index) {
+  const ContractOp& op = p.ops[op_index];
+  const int64_t* t = p.d_table + op.tab;
+  const int64_t* th = p.table.data() + op.tab;
+  OzArgs a;
+  a.A = op.A;
+  a.B = op.B;
+  a.C = op.C;
+  a.aL = th[0];
+  a.bL = th[1];
+  a.cL = th[2];
+  a.tAM = t + 3;
+  a.tCM = a.tAM + op.M;
+  a.tBN = a.tCM + op.M;
+  a.tCN = a.tBN + op.N;
+  a.tAK = a.tCN + op.N;
+  a.tBK = a.tAK + op.K;
+  a.M = op.M;
+  a.N = op.N;
+  a.K = op.K;
+  a.alpha = op.alpha;
+  a.slices = RICMRCC_EMULATED_DEFAULT_SLICES;
+  a.err = h->d_err;
+  // epilogue lanes along the output index that is contiguous more often
+  const int64_t* hCM = th + 3 + op.M;
+  const int64_t* hCN = hCM + op.M + op.N;
+  a.col_lanes = rows_fast(hCN, op.N, hCM, op.M);
+  return a;
+}
+
+// Scratch of the emulated-FP64 contractions of the residual graph: the first
+// tensor-core lane holds the largest one; the other lanes take contractions
+// of at most kOzSmallBytes (or the largest, if all are smaller).
+constexpr size_t kOzSmallBytes = (size_t)1 << 30;
+
+int ensure_oz(ricmrcc_t* h) {
+  if (h->oz_scratch) return RICMRCC_OK;
+  if (!oz_prepare()) return fail(h, RICMRCC_ENOTSUP, "emulated-FP64 kernels unavailable");
+  size_t need = 0, small = 0;
+  for (const ContractOp& op : h->res_prog.ops) {
+    if (!oz_eligible(op, h->rule)) continue;
+    const size_t b = oz_scratch_bytes(op.M, op.N, op.K, RICMRCC_EMULATED_DEFAULT_SLICES);
+    need = std::max(need, b);
+    if (b <= kOzSmallBytes) small = std::max(small, b);
+  }
+  auto round = [](size_t b) { return (std::max<size_t>(b, 256) + 255) / 256 * 256; };
+  need = round(need);
+  small = round(small);
+  char* buf = nullptr;
+  TRY(dalloc(h, &buf, (int64_t)(need + small * (kTcLanes - 1))));
+  h->oz_scratch = buf;
+  h->oz_slice = need;
+  h->oz_small = small;
+  return RICMRCC_OK;
+}
+
+void oz_lane_scratch(ricmrcc_t* h, size_t need, int j, int* lane, void** scratch, size_t* bytes) {
+  int l = j % kTcLanes;
+  if (need > h->oz_small) l = 0;
+  *lane = l;
+  char* base = static_cast<char*>(h->oz_scratch);
+  *scratch = l == 0 ? base : base + h->oz_slice + (size_t)(l - 1) * h->oz_small;
+  *bytes = l == 0 ? h->oz_slice : h->oz_small;
+}
+
+int residual_device(ricmrcc_t* h, int mode) {
+  if (mode == 1) {
     TRY(ensure_tc(h));
     TRY(refresh_tc_cache(h, h->s));
+  } else if (mode == 2) {
+    TRY(ensure_oz(h));
   }
-  cudaGraphExec_t& ex = h->graph[mixed ? 1 : 0];
-  if (!ex) TRY(capture_residual(h, mixed));
+  cudaGraphExec_t& ex = h->graph[mode];
+  if (!ex) TRY(capture_residual(h, mode));
   CK(cudaGraphLaunch(ex, h->s));
   return RICMRCC_OK;
 }
@@ -838,8 +924,8 @@ int ricmrcc_set_stream(ricmrcc_t* h, void* stream) {
 
 int ricmrcc_set_precision(ricmrcc_t* h, int precision) {
   if (!h) return RICMRCC_EINVAL;
-  if (precision != RICMRCC_FP64 && precision != RICMRCC_MIXED)
-    return fail(h, RICMRCC_EINVAL, "precision must be RICMRCC_FP64 or RICMRCC_MIXED");
+  if (precision != RICMRCC_FP64 && precision != RICMRCC_MIXED && precision != RICMRCC_EMULATED)
+    return fail(h, RICMRCC_EINVAL, "precision must be RICMRCC_FP64, RICMRCC_MIXED or RICMRCC_EMULATED");
   h->precision = precision;
   return RICMRCC_OK;
 }
@@ -952,9 +1038,9 @@ static int residual_impl(ricmrcc_t* h, const double* T1, const double* T2, doubl
     f2 = h->flat2;
   }
   scatter_amplitudes(h, f1, f2);
-  const bool mixed = h->precision == RICMRCC_MIXED;
-  TRY(residual_device(h, mixed));
-  if (mixed) TRY(check_tc_error(h));
+  const int mode = h->precision;  // RICMRCC_FP64 / MIXED / EMULATED = graph modes 0 / 1 / 2
+  TRY(residual_device(h, mode));
+  if (mode != 0) TRY(check_tc_error(h));
   double* r1 = dev ? R1 : h->rflat1;
   double* r2 = dev ? R2 : h->rflat2;
   launch_gather(r1, h->X + h->n2g, h->pack1, nullptr, h->t1_size, h->s);
@@ -1101,9 +1187,9 @@ int iter_finish(ricmrcc_t* h, const ricmrcc_opts& o) {
 
 namespace {
 
-int iterate(ricmrcc_t* h, const ricmrcc_opts& o, bool check, bool mixed, bool* conv, bool* diverged) {
-  TRY(residual_device(h, mixed));
-  if (mixed) TRY(check_tc_error(h));
+int iterate(ricmrcc_t* h, const ricmrcc_opts& o, bool check, int mode, bool* conv, bool* diverged) {
+  TRY(residual_device(h, mode));
+  if (mode != 0) TRY(check_tc_error(h));
   TRY(iter_update(h, o));
   CK(cudaStreamSynchronize(h->s));
   bool diis = false;
@@ -1119,8 +1205,8 @@ int check_opts(ricmrcc_t* h, const ricmrcc_opts& o) {
   if (!(o.s >= 0.0) || !isfinite(o.s) || o.max_iter < 1 || o.diis_size < 0 || o.diis_size > 16)
     return fail(h, RICMRCC_EINVAL, "bad options (s >= 0, max_iter >= 1, 0 <= diis_size <= 16)");
   if (!(h->have_ints && h->have_rdms)) return fail(h, RICMRCC_ESTATE, "integrals and RDMs first");
-  if (o.precision != RICMRCC_FP64 && o.precision != RICMRCC_MIXED)
-    return fail(h, RICMRCC_EINVAL, "precision must be RICMRCC_FP64 or RICMRCC_MIXED");
+  if (o.precision != RICMRCC_FP64 && o.precision != RICMRCC_MIXED && o.precision != RICMRCC_EMULATED)
+    return fail(h, RICMRCC_EINVAL, "precision must be RICMRCC_FP64, RICMRCC_MIXED or RICMRCC_EMULATED");
   return RICMRCC_OK;
 }
 
@@ -1141,10 +1227,13 @@ int ricmrcc_solve(ricmrcc_t* h, double s, const ricmrcc_opts* opts, double* E_ou
   bool converged = false, diverged = false;
   int it = 0, n_mixed = 0;
   // mixed precision: tensor-core iterations until max|dt| < refine_tol, then
-  // FP64 refinement iterations until the FP64 convergence test passes
-  bool mixed = o.precision == RICMRCC_MIXED;
+  // FP64-accurate refinement iterations until the convergence test passes:
+  // FP64 CUDA-core contractions (RICMRCC_MIXED) or emulated-FP64 tensor-core
+  // ones (RICMRCC_EMULATED)
+  bool mixed = o.precision != RICMRCC_FP64;
+  const int refine_mode = o.precision == RICMRCC_EMULATED ? 2 : 0;
   for (it = 1; it <= o.max_iter; ++it) {
-    TRY(iterate(h, o, !mixed, mixed, &converged, &diverged));
+    TRY(iterate(h, o, !mixed, mixed ? 1 : refine_mode, &converged, &diverged));
     if (mixed) {
       ++n_mixed;
       if (!diverged && h->last_dt < o.refine_tol) mixed = false;
@@ -1190,8 +1279,9 @@ int ricmrcc_step(ricmrcc_t* h, const ricmrcc_opts* opts, int n_steps, int restar
     h->solved = false;
   }
   bool conv = false, div = false;
-  const bool mixed = o.precision == RICMRCC_MIXED || h->precision == RICMRCC_MIXED;
-  for (int i = 0; i < n_steps && !div; ++i) TRY(iterate(h, o, false, mixed, &conv, &div));
+  // the steps' arithmetic: opts->precision, else the handle's
+  const int mode = o.precision != RICMRCC_FP64 ? o.precision : h->precision;
+  for (int i = 0; i < n_steps && !div; ++i) TRY(iterate(h, o, false, mode, &conv, &div));
   if (E_out) *E_out = h->last_E;
   if (max_dt_out) *max_dt_out = h->last_dt;
   TRY(leave(h));
@@ -1211,7 +1301,7 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
   out->graph_launches[1] = h->graph_launches[1];
   // launches of one solver iteration: the residual graph (once captured, else
   // one per contraction) + update, dots, DIIS solve, extrapolate
-  const int64_t gl = h->graph_launches[h->precision == RICMRCC_MIXED ? 1 : 0];
+  const int64_t gl = h->graph_launches[h->precision];
   out->step_launches = (gl ? gl : out->residual_launches) + 4;
   const bool mixed = h->precision == RICMRCC_MIXED;
   static const int slot[kGroupKinds] = {0, 1, 2, 5, 6, 7, 5};
@@ -1267,6 +1357,11 @@ int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out) {
   // tensor-core path is planned.
   out->tc_grouped_ops = (int64_t)weighted.size();
   for (char w : weighted) out->tc_weighted_ops += w;
+  for (const ContractOp& op : h->res_prog.ops)
+    if (oz_eligible(op, h->rule)) {
+      out->oz_contractions += 1;
+      out->oz_flops += op.flops;
+    }
   for (const PackedOperand& e : h->tc_cache) {
     out->tc_gemm_bytes += 4.0 * e.rows_pad * e.Kp;
     if (e.level < 0) continue;
@@ -1423,6 +1518,7 @@ int ricmrcc_set_tile_rule(ricmrcc_t* h, const ricmrcc_tile_rule* rule) {
   r.skinny = rule->skinny ? 1 : 0;
   r.tc_grouped = rule->tc_grouped ? 1 : 0;
   r.tc_min_n = rule->tc_min_n > 1 ? rule->tc_min_n : 1;
+  r.oz_max_pad = rule->oz_max_pad >= 1.0 ? rule->oz_max_pad : 4.0;
   return set_rule(h, r);
 }
 
@@ -1432,6 +1528,7 @@ int ricmrcc_get_tile_rule(const ricmrcc_t* h, ricmrcc_tile_rule* rule) {
   rule->skinny = h->rule.skinny;
   rule->tc_grouped = h->rule.tc_grouped;
   rule->tc_min_n = h->rule.tc_min_n;
+  rule->oz_max_pad = h->rule.oz_max_pad;
   return RICMRCC_OK;
 }
 
@@ -1464,6 +1561,7 @@ int ricmrcc_tune(ricmrcc_t* h, int precision, int reps, ricmrcc_tuning* out) {
     res.rule[c].skinny = cand[c].skinny;
     res.rule[c].tc_grouped = cand[c].tc_grouped;
     res.rule[c].tc_min_n = cand[c].tc_min_n;
+    res.rule[c].oz_max_pad = cand[c].oz_max_pad;
     res.ms[c] = ms / reps;
     if (res.ms[c] < best) {
       best = res.ms[c];
@@ -1744,15 +1842,10 @@ int ensure_adj_tc(ricmrcc_t* h) {
   if (h->adj_tc_scratch) return RICMRCC_OK;
   const Program& p = h->gradl_prog;
   size_t need = 0;
-  h->gradl_col.assign(p.ops.size(), 0);
   for (size_t i = 0; i < p.ops.size(); ++i) {
     const ContractOp& op = p.ops[i];
     if (op.kind == 2 || op.L != 1 || op.M < 64 || op.K < 32) continue;
     need = std::max(need, tc_scratch_bytes(op.M, op.N, op.K));
-    const int64_t* th = p.table.data() + op.tab;
-    const int64_t* tAM = th + 3;
-    const int64_t* tBN = tAM + 2 * op.M;
-    h->gradl_col[i] = (char)rows_fast(tBN + op.N, op.N, tAM + op.M, op.M);
   }
   char* buf = nullptr;
   TRY(dalloc(h, &buf, (int64_t)std::max<size_t>(need, 16)));
@@ -1761,13 +1854,67 @@ int ensure_adj_tc(ricmrcc_t* h) {
   return RICMRCC_OK;
 }
 
+// Serial run of an adjoint program: mode 0 every contraction in FP64 on the
+// CUDA cores; 1 the contractions the tile rule accepts on the tensor cores
+// (split BF16, FP32 accumulation); 2 those as emulated-FP64 tensor-core
+// contractions.
+int run_adjoint_program(ricmrcc_t* h, const Program& p, int mode) {
+  if (mode == 0) return run_program(h, p);
+  for (size_t i = 0; i < p.ops.size(); ++i) {
+    const ContractOp& op = p.ops[i];
+    const bool nonempty = op.M > 0 && op.N > 0 && op.K > 0;
+    const bool tc = tc_eligible(op, h->rule) && nonempty;
+    if (mode == 2 && nonempty && oz_eligible(op, h->rule)) {
+      OzArgs a = oz_args(h, p, (int)i);
+      a.scratch = h->adj_oz_scratch;
+      a.scratch_bytes = h->adj_oz_bytes;
+      const int rc = oz_contract(a, h->s);
+      if (rc != 0) return fail(h, RICMRCC_ECUDA, "emulated-FP64 launch failed (" + std::to_string(rc) + ")");
+    } else if (tc && mode == 1) {
+      TcArgs a = tc_args(h, p, (int)i, 0);
+      a.scratch = h->adj_tc_scratch;
+      a.scratch_bytes = h->adj_tc_bytes;
+      a.col_lanes = oz_args(h, p, (int)i).col_lanes;
+      const int rc = tc_contract(a, h->s);
+      if (rc != 0)
+        return fail(h, RICMRCC_ECUDA, "tensor-core contraction launch failed (" + std::to_string(rc) + ")");
+    } else {
+      launch_contract(op, p.d_table, h->s);
+    }
+  }
+  return RICMRCC_OK;
+}
+
+// Scratch of the adjoint programs' emulated-FP64 contractions (serial
+// launches): their largest tensor-core-eligible contraction.
+int ensure_adj_oz(ricmrcc_t* h) {
+  if (h->adj_oz_scratch) return RICMRCC_OK;
+  if (!oz_prepare()) return fail(h, RICMRCC_ENOTSUP, "emulated-FP64 kernels unavailable");
+  size_t need = 256;
+  for (const Program* p : {&h->gradt_prog, &h->gradl_prog})
+    for (const ContractOp& op : p->ops)
+      if (oz_eligible(op, h->rule))
+        need = std::max(need, oz_scratch_bytes(op.M, op.N, op.K, RICMRCC_EMULATED_DEFAULT_SLICES));
+  for (const ContractOp& op : h->gradh_prog.ops)
+    if (oz_eligible(op, h->rule))
+      need = std::max(need, oz_scratch_bytes(op.M, op.N, op.K, RICMRCC_EMULATED_DEFAULT_SLICES));
+  char* buf = nullptr;
+  TRY(dalloc(h, &buf, (int64_t)need));
+  h->adj_oz_scratch = buf;
+  h->adj_oz_bytes = need;
+  return RICMRCC_OK;
+}
+
 // One application of the multiplier map at `lam`:
 //   Tn = S[Delta Yraw + GT],  Err = Tn - lam,  *md = max |Err|,
 // with Yraw = phi Lam and GT = gt0 (zero if null) + the gradient program
-// `p` evaluated at Ytil(lam).  In mixed precision the contractions the tile
-// rule accepts run on the tensor cores (split BF16, FP32 accumulation).
-int adjoint_apply(ricmrcc_t* h, const double* lam, const Program& p, bool mixed, const double* gt0, double s,
+// `p` evaluated at Ytil(lam).  mode 0: every contraction in FP64 on the CUDA
+// cores; 1: the contractions the tile rule accepts on the tensor cores (split
+// BF16, FP32 accumulation); 2: those as emulated-FP64 tensor-core
+// contractions.
+int adjoint_apply(ricmrcc_t* h, const double* lam, const Program& p, int mode, const double* gt0, double s,
                   double* md) {
+  const bool mixed = mode != 0;
   const Dims& d = h->d;
   launch_adj_y(lam, h->Yraw, h->Ytil, h->eps, d, s, h->s);
   if (gt0)
@@ -1775,24 +1922,7 @@ int adjoint_apply(ricmrcc_t* h, const double* lam, const Program& p, bool mixed,
   else
     CK(cudaMemsetAsync(h->GT, 0, sizeof(double) * h->ng, h->s));
   CK(cudaMemsetAsync(h->adj_arena, 0, sizeof(double) * h->adj_arena_elems, h->s));
-  if (!mixed) {
-    TRY(run_program(h, p));
-  } else {
-    for (size_t i = 0; i < p.ops.size(); ++i) {
-      const ContractOp& op = p.ops[i];
-      if (tc_eligible(op, h->rule) && op.M > 0 && op.N > 0 && op.K > 0) {
-        TcArgs a = tc_args(h, p, (int)i, 0);
-        a.scratch = h->adj_tc_scratch;
-        a.scratch_bytes = h->adj_tc_bytes;
-        a.col_lanes = h->gradl_col[i];
-        const int rc = tc_contract(a, h->s);
-        if (rc != 0)
-          return fail(h, RICMRCC_ECUDA, "tensor-core contraction launch failed (" + std::to_string(rc) + ")");
-      } else {
-        launch_contract(op, p.d_table, h->s);
-      }
-    }
-  }
+  TRY(run_adjoint_program(h, p, mode));
   CK(cudaMemsetAsync(h->scal + 2, 0, sizeof(double), h->s));
   launch_adj_update(lam, h->Yraw, h->GT, h->Tn, h->Err, h->eps, d, h->scal + 2, h->s);
   CK(cudaMemcpyAsync(h->host_scal + 2, h->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, h->s));
@@ -1819,10 +1949,13 @@ int adjoint_refined(ricmrcc_t* h, double s, double tol, int cap, bool* conv) {
   *conv = false;
   TRY(ensure_tc(h));
   TRY(ensure_adj_tc(h));
+  // the defects in FP64 on the CUDA cores, or emulated FP64 after an emulated solve
+  const int defect_mode = o.precision == RICMRCC_EMULATED ? 2 : 0;
+  if (defect_mode == 2) TRY(ensure_adj_oz(h));
   double md_prev = HUGE_VAL;
   for (int outer = 1; outer <= kMaxOuter; ++outer) {
     double md = 0.0;
-    TRY(adjoint_apply(h, h->Lam, h->gradt_prog, false, nullptr, s, &md));
+    TRY(adjoint_apply(h, h->Lam, h->gradt_prog, defect_mode, nullptr, s, &md));
     ++h->adj_fp64;
     if (h->verbose) fprintf(stderr, "ricmrcc adjoint refinement %2d  FP64 defect %.3e\n", outer, md);
     if (md < tol) {
@@ -1839,7 +1972,7 @@ int adjoint_refined(ricmrcc_t* h, double s, double tol, int cap, bool* conv) {
     int worse = 0;
     for (int j = 1; j <= std::max(o.max_iter, 1); ++j) {
       double mi = 0.0;
-      TRY(adjoint_apply(h, h->Dlt, h->gradl_prog, true, h->Rdf, s, &mi));
+      TRY(adjoint_apply(h, h->Dlt, h->gradl_prog, 1, h->Rdf, s, &mi));
       ++h->adj_mixed;
       if (h->verbose) fprintf(stderr, "ricmrcc adjoint   correction %3d  max|d delta| = %.3e\n", j, mi);
       bool stop = mi < kInnerRel * md || mi < 0.1 * tol;
@@ -1887,11 +2020,11 @@ static int energy_backward_impl(ricmrcc_t* h, double* dE_dh, double* dE_dB, doub
   // after a mixed-precision solve: refine the multipliers from mixed-precision
   // correction solves; after an FP64 solve (or if refinement stalls): plain
   // FP64 iterations
-  if (o.precision == RICMRCC_MIXED) TRY(adjoint_refined(h, s, tol, cap, &conv));
+  if (o.precision != RICMRCC_FP64) TRY(adjoint_refined(h, s, tol, cap, &conv));
   reset_iteration_state(h);
   for (int it = 1; !conv && it <= 4 * o.max_iter; ++it) {
     double md = 0.0;
-    TRY(adjoint_apply(h, h->Lam, h->gradt_prog, false, nullptr, s, &md));
+    TRY(adjoint_apply(h, h->Lam, h->gradt_prog, o.precision == RICMRCC_EMULATED ? 2 : 0, nullptr, s, &md));
     ++h->adj_fp64;
     if (h->verbose)
       fprintf(stderr, "ricmrcc adjoint iter %3d  max|dLam| = %.3e  %.3f s\n", it, md,
@@ -1914,7 +2047,7 @@ static int energy_backward_impl(ricmrcc_t* h, double* dE_dh, double* dE_dB, doub
   CK(cudaMemsetAsync(h->gF, 0, sizeof(double) * n2, h->s));
   CK(cudaMemsetAsync(h->geri, 0, sizeof(double) * n2 * n2, h->s));
   CK(cudaMemsetAsync(h->adj_arena, 0, sizeof(double) * h->adj_arena_elems, h->s));
-  TRY(run_program(h, h->gradh_prog));
+  TRY(run_adjoint_program(h, h->gradh_prog, o.precision == RICMRCC_EMULATED ? 2 : 0));
   CK(cudaMemsetAsync(h->geps, 0, sizeof(double) * n, h->s));
   CK(cudaMemsetAsync(h->scal + 5, 0, sizeof(double), h->s));
   launch_adj_eps(h->Lam, h->T, h->X, h->eps, d, s, h->geps, h->scal + 5, h->s);
@@ -1947,7 +2080,39 @@ static int energy_backward_impl(ricmrcc_t* h, double* dE_dh, double* dE_dB, doub
     int64_t* dt = nullptr;
     CK(cudaMalloc(&dt, sizeof(int64_t) * t.size()));
     CK(cudaMemcpyAsync(dt, t.data(), sizeof(int64_t) * t.size(), cudaMemcpyHostToDevice, h->s));
-    launch_contract(op, dt, h->s);
+    // after an emulated solve: emulated FP64 on the tensor cores when its
+    // scratch can be had, else the FP64 CUDA-core kernel
+    bool done = false;
+    if (o.precision == RICMRCC_EMULATED && n2 >= 64 && d.X >= 1) {
+      OzArgs a;
+      a.A = op.A;
+      a.B = op.B;
+      a.C = op.C;
+      a.tAM = dt + 3;
+      a.tCM = a.tAM + n2;
+      a.tBN = a.tCM + n2;
+      a.tCN = a.tBN + d.X;
+      a.tAK = a.tCN + d.X;
+      a.tBK = a.tAK + n2;
+      a.M = n2;
+      a.N = d.X;
+      a.K = n2;
+      a.slices = RICMRCC_EMULATED_DEFAULT_SLICES;
+      a.err = h->d_err;
+      a.col_lanes = 0;  // output rows (pq) contiguous
+      a.scratch_bytes = oz_scratch_bytes(a.M, a.N, a.K, a.slices);
+      if (oz_prepare() && cudaMalloc(&a.scratch, a.scratch_bytes) == cudaSuccess) {
+        const int rc = oz_contract(a, h->s);
+        CK(cudaStreamSynchronize(h->s));
+        cudaFree(a.scratch);
+        if (rc != 0) return fail(h, RICMRCC_ECUDA, "emulated-FP64 launch failed (" + std::to_string(rc) + ")");
+        TRY(check_tc_error(h));
+        done = true;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    if (!done) launch_contract(op, dt, h->s);
     CK(cudaStreamSynchronize(h->s));
     CK(cudaFree(dt));
   }

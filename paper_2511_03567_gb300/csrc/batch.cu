@@ -496,6 +496,7 @@ int ricmrcc_batch_tune(ricmrcc_batch_t* b, int precision, int reps, ricmrcc_tuni
     res.rule[c].tc_min_n = cand[c].tc_min_n;
     res.rule[c].skinny = cand[c].skinny;
     res.rule[c].tc_grouped = cand[c].tc_grouped;
+    res.rule[c].oz_max_pad = cand[c].oz_max_pad;
     res.ms[c] = ms / reps;
     if (res.ms[c] < best) {
       best = res.ms[c];

@@ -11,6 +11,7 @@
 #include "../../include/ricmrcc.h"
 #include "grouped.h"
 #include "internal.h"
+#include "ozaki.h"
 #include "tcgemm.h"
 
 namespace ric {
@@ -23,6 +24,7 @@ struct TileRule {
   int skinny = 1;             // 1: tall-skinny ops (N < 32, M >= 64) use the 128x16 / 64x32 tiles
   int tc_grouped = 1;         // 1: one persistent tensor-core launch per level, 0: one per op
   int tc_min_n = 1;           // mixed precision: narrowest output (N) on the tensor cores
+  double oz_max_pad = 4.0;    // emulated FP64: largest tile-padding factor on the tensor cores
 };
 
 // A packed split-BF16 operand ([hi | lo] per row, either GEMM side) kept
@@ -82,8 +84,15 @@ struct ricmrcc {
   cudaStream_t lane[ric::kLanes] = {nullptr};
   cudaEvent_t lane_ev[ric::kLanes + 1] = {nullptr};  // [kLanes]: fork
   cudaEvent_t tc_ev[ric::kTcLanes] = {nullptr};      // tensor-core lanes meeting
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [fp64, mixed]
-  int64_t graph_launches[2] = {0, 0};              // kernel launches in each graph
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // [fp64, mixed, emulated fp64]
+  int64_t graph_launches[3] = {0, 0, 0};                    // kernel launches in each graph
+  // emulated-FP64 tensor-core contractions: scratch of the first tensor-core
+  // lane (oz_slice bytes, the largest contraction), then one slice of oz_small
+  // bytes per other lane (contractions needing at most oz_small bytes)
+  void* oz_scratch = nullptr;
+  size_t oz_slice = 0, oz_small = 0;
+  void* adj_oz_scratch = nullptr;  // one slice for the adjoint programs' serial launches
+  size_t adj_oz_bytes = 0;
   int sms = 152;
   std::vector<void*> group_allocs;  // grouped-launch descriptor arrays
   int* d_err = nullptr;
@@ -104,7 +113,6 @@ struct ricmrcc {
   // the terms of gradt_prog that depend on the multipliers (the linear part of
   // the multiplier equations), for the mixed-precision correction solves
   Program gradl_prog;
-  std::vector<char> gradl_col;  // tensor-core epilogue lanes per op of gradl_prog
   double *Dlt = nullptr, *Rdf = nullptr;  // correction and defect of the multipliers
   void* adj_tc_scratch = nullptr;
   size_t adj_tc_bytes = 0;
@@ -153,6 +161,8 @@ int leave(ricmrcc_t* h);
 // tile whose lanes follow its contiguous output index.
 int op_kind(const ContractOp& op, const TileRule& r, const int64_t* th = nullptr);
 bool tc_eligible(const ContractOp& op, const TileRule& r);
+// Contractions the emulated-FP64 path runs on the tensor cores.
+bool oz_eligible(const ContractOp& op, const TileRule& r);
 // Plan the tensor-core path (eligible ops, operand cache, scratch size) ...
 int ensure_tc_plan(ricmrcc_t* h);
 // ... and allocate its per-lane scratch.
@@ -164,13 +174,19 @@ void release_tc(ricmrcc_t* h);
 int set_rule(ricmrcc_t* h, const TileRule& r);
 // Rules the autotuner times (at most RICMRCC_TUNE_MAX).
 std::vector<TileRule> tune_candidates(const TileRule& cur, bool mixed);
-int residual_device(ricmrcc_t* h, bool mixed);
+// Residual graph launch: mode 0 FP64, 1 mixed (split BF16), 2 emulated FP64.
+int residual_device(ricmrcc_t* h, int mode);
 int check_tc_error(ricmrcc_t* h);
 // Pack (or refresh) the constant-operand cache of the residual's TC ops.
 int refresh_tc_cache(ricmrcc_t* h, cudaStream_t s);
 // Pack one operand buffer on stream s (0 on success).
 int pack_entry(const PackedOperand& e, cudaStream_t s);
 TcArgs tc_args(ricmrcc_t* h, const Program& p, int op_index, int lane);
+// Emulated-FP64 arguments of op `op_index` (scratch not set).
+OzArgs oz_args(ricmrcc_t* h, const Program& p, int op_index);
+// Lane (0 .. kTcLanes-1) and scratch of the j-th emulated contraction of a
+// level: contractions larger than oz_small bytes of scratch run on lane 0.
+void oz_lane_scratch(ricmrcc_t* h, size_t need, int j, int* lane, void** scratch, size_t* bytes);
 GroupOp group_op(const Program& p, const ContractOp& op);
 
 // Descriptor arrays of one grouped launch (device), kept for a graph's life.
@@ -247,13 +263,19 @@ struct ProfileTarget : ScheduleTarget {
 };
 // Group the FP64-path contractions of the live instances per level and tile
 // kind (descriptor arrays appended to `allocs`); errors are reported on eh.
+// With `emulated` (FP64 arithmetic, mixed off), the tensor-core-eligible
+// contractions are left out of the groups: run_schedule runs them as
+// emulated-FP64 tensor-core contractions (ozaki.cu).
 int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std::vector<char>& live,
-                   const TileRule& rule, bool mixed, std::vector<void*>& allocs, Schedule* out);
+                   const TileRule& rule, bool mixed, std::vector<void*>& allocs, Schedule* out,
+                   bool emulated = false);
 // Enqueue the schedule on `tgt` (tensor-core scratch: kTcLanes slices of
 // `slice` bytes at `scratch`; pipeline time-out flag `err`).
+// With `emulated`: the emulated-FP64 contractions use each instance's
+// oz_scratch (oz_lane_scratch).
 int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*>& inst,
                  const std::vector<char>& live, const TileRule& rule, bool mixed, ScheduleTarget& tgt,
-                 void* scratch, size_t slice, int* err, int64_t* launches);
+                 void* scratch, size_t slice, int* err, int64_t* launches, bool emulated = false);
 
 // Renormalised update + DIIS in three phases so that many instances can share
 // one host synchronisation per phase (each phase runs on h->s):

@@ -38,6 +38,7 @@
 #include <vector>
 
 #include "../../include/ricmrcc.h"
+#include "ozaki.h"
 #include "tc_ptx.h"
 
 using namespace tcptx;
@@ -53,11 +54,28 @@ constexpr int kOzEpi = 4;
 constexpr int kOzThreads = 64 + 32 * kOzEpi;
 constexpr int kOzGroup = 16;                     // n tiles per raster group
 
-// One accumulation piece of a tile: level d, positions [q0, q1) of the level's
-// K-block sequence (pair p = q / kt of digits (p, d - p), K block q % kt).
-struct OzPiece {
-  int d, q0, q1, pad;
-};
+// The accumulation pieces of one output tile, level by level: level d's
+// K-block sequence (pair p = q / kt of digits (p, d - p), K block q % kt,
+// for q < (d + 1) kt) is cut into pieces of at most kOzBlocks blocks.
+__host__ __device__ __forceinline__ int oz_level_pieces(int d, int kt) {
+  return ((d + 1) * kt + kOzBlocks - 1) / kOzBlocks;
+}
+__host__ __device__ __forceinline__ int oz_npieces(int S, int kt) {
+  int n = 0;
+  for (int d = 0; d < S; ++d) n += oz_level_pieces(d, kt);
+  return n;
+}
+__device__ __forceinline__ void oz_piece(int pc, int S, int kt, int* d, int* q0, int* q1) {
+  int l = 0;
+  for (; l < S - 1; ++l) {
+    const int np = oz_level_pieces(l, kt);
+    if (pc < np) break;
+    pc -= np;
+  }
+  *d = l;
+  *q0 = pc * kOzBlocks;
+  *q1 = min((l + 1) * kt, *q0 + kOzBlocks);
+}
 
 __device__ __forceinline__ uint32_t oz_idesc() {
   // D FP32, A and B BF16, K-major both, N = 256, M = 128
@@ -80,10 +98,11 @@ __device__ __forceinline__ void oz_item(int64_t t, int mt, int nt, int* mi, int*
 
 // value * 2^k for an exact FP32 integer value (normal or zero): the FP32
 // fields moved into an FP64 with the exponent shifted by k (ldexp when the
-// result leaves the normal range)
+// result leaves the normal range); infinities and NaNs pass unchanged
 __device__ __forceinline__ double shifted(float v, int k) {
   const uint32_t b = __float_as_uint(v);
   if ((b << 1) == 0) return 0.0;
+  if (((b >> 23) & 0xff) == 0xff) return (double)v;  // a non-finite operand entry reached this sum
   const int e = (int)((b >> 23) & 0xff) - 127 + 1023 + k;
   if (e >= 1 && e <= 2046)
     return __longlong_as_double((long long)(((uint64_t)(b >> 31) << 63) | ((uint64_t)e << 52) |
@@ -93,9 +112,9 @@ __device__ __forceinline__ double shifted(float v, int k) {
 
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_gemm_oz(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t M,
-              int64_t N, int Mp, int Np, int kt, const OzPiece* __restrict__ pieces, int npieces,
-              const int* __restrict__ ea, const int* __restrict__ eb, double* __restrict__ C, int64_t ldc,
-              unsigned long long* __restrict__ ctr, int* err) {
+              int64_t N, int Mp, int Np, int kt, int S, const int* __restrict__ ea, const int* __restrict__ eb,
+              double* __restrict__ C, int64_t cL, const int64_t* __restrict__ tCM, const int64_t* __restrict__ tCN,
+              int64_t ldc, int col_lanes, unsigned long long* __restrict__ ctr, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   float* etile = reinterpret_cast<float*>(smem + kOzStages * kOzStage);  // kOzEpi x 32 x 33
@@ -112,7 +131,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mt = Mp / OBM, nt = Np / OBN;
-  const int64_t total = (int64_t)mt * nt * npieces;
+  const int64_t total = (int64_t)mt * nt * oz_npieces(S, kt);
   if (threadIdx.x == 0) {
     for (int s = 0; s < kOzStages; ++s) {
       mbar_init(full + s, 1);
@@ -147,7 +166,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     bool ok = true;
     const uint32_t s0 = smem_u32(smem), full0 = smem_u32(full);
     uint32_t ic = 0;
-    for (int64_t t = (int64_t)atomicAdd(ctr, 1ull);;) {
+    for (int64_t t = ctr ? (int64_t)atomicAdd(ctr, 1ull) : (int64_t)blockIdx.x;;) {
       const uint32_t j = ic & 3;
       if (ic >= 4 && !mbar_wait(iempty + j, ((ic >> 2) - 1) & 1, err)) {
         ok = false;
@@ -157,10 +176,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(ifull + j)) : "memory");
       ++ic;
       if (t >= total) break;
-      int mi, ni, pc;
+      int mi, ni, pc, d, q0, q1;
       oz_item(t, mt, nt, &mi, &ni, &pc);
-      const OzPiece P = pieces[pc];
-      for (int q = P.q0; q < P.q1; ++q) {
+      oz_piece(pc, S, kt, &d, &q0, &q1);
+      for (int q = q0; q < q1; ++q) {
         const int p = q / kt, kb = q - p * kt;
         if (issued >= kOzStages && !mbar_wait(empty + st, ph ^ 1u, err)) {
           ok = false;
@@ -169,7 +188,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         const uint32_t sb = s0 + st * kOzStage, fb = full0 + st * 8;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kOzStage) : "memory");
         tma_load_2d_u(sb, &tmA, kb * OBK, p * Mp + mi * OBM, fb);
-        tma_load_2d_u(sb + kOzA, &tmB, kb * OBK, (P.d - p) * Np + ni * OBN, fb);
+        tma_load_2d_u(sb + kOzA, &tmB, kb * OBK, (d - p) * Np + ni * OBN, fb);
         ++issued;
         if (++st == kOzStages) {
           st = 0;
@@ -177,7 +196,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         }
       }
       if (!ok) break;
-      t = (int64_t)atomicAdd(ctr, 1ull);
+      t = ctr ? (int64_t)atomicAdd(ctr, 1ull) : t + gridDim.x;
     }
     // copies still in flight land before the CTA exits
     for (int64_t i = issued > kOzStages ? issued - kOzStages : 0; i < issued; ++i)
@@ -201,17 +220,17 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       if (c >= 2 && !mbar_wait(tempty + b, ((c >> 1) - 1) & 1, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t acc = tmem + b * OBN;
-      int mi, ni, pc;
+      int mi, ni, pc, d, q0, q1;
       oz_item(t, mt, nt, &mi, &ni, &pc);
-      const OzPiece P = pieces[pc];
-      for (int q = P.q0; q < P.q1; ++q) {
+      oz_piece(pc, S, kt, &d, &q0, &q1);
+      for (int q = q0; q < q1; ++q) {
         const uint64_t ad = desc0 + st * (kOzStage >> 4), bd = ad + (kOzA >> 4);
         if (!mbar_wait(full + st, ph, err)) {
           ok = false;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        mma_ktile(acc, ad, bd, idesc, q > P.q0 ? 1u : 0u);
+        mma_ktile(acc, ad, bd, idesc, q > q0 ? 1u : 0u);
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          empty0 + st * 8)
                      : "memory");
@@ -243,9 +262,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(iempty + j)) : "memory");
       ++ic;
       if (t < 0) break;
-      int mi, ni, pc;
+      int mi, ni, pc, d, q0, q1;
       oz_item(t, mt, nt, &mi, &ni, &pc);
-      const int shift = -kOzBits * (pieces[pc].d + 2);
+      oz_piece(pc, S, kt, &d, &q0, &q1);
+      const int shift = -kOzBits * (d + 2);
       const uint32_t b = c & 1;
       if (!__all_sync(0xffffffffu, mbar_wait(tfull + b, (c >> 1) & 1, err))) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -264,20 +284,44 @@ __global__ void __launch_bounds__(kOzThreads, 1)
               "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int64_t nc0 = (int64_t)ni * OBN + ch * 32;
+        if (!col_lanes) {
+          // lanes along rows: lane l adds row m0 + l's 32 values
+          const int64_t m = m0 + lane;
+          if (m < M) {
+            const int km = shift + ea[m];
+            const int64_t rowoff = tCM ? cL + tCM[m] : m * ldc;
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) tile[lane * 33 + jj] = __uint_as_float(r[jj]);
-        __syncwarp();
-        const int64_t n = (int64_t)ni * OBN + ch * 32 + lane;
-        if (n < N) {
-          const int kn = shift + eb[n];
+            for (int jj = 0; jj < 32; ++jj) {
+              const int64_t n = nc0 + jj;
+              if (n < N) {
+                const double v = shifted(__uint_as_float(r[jj]), km + eb[n]);
+                if (v != 0.0)
+                  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(
+                                   __cvta_generic_to_global(C + rowoff + (tCN ? tCN[n] : n))),
+                               "d"(v));
+              }
+            }
+          }
+        } else {
+          // lanes along columns, through the shared tile
+#pragma unroll
+          for (int jj = 0; jj < 32; ++jj) tile[lane * 33 + jj] = __uint_as_float(r[jj]);
+          __syncwarp();
+          const int64_t n = nc0 + lane;
+          if (n < N) {
+            const int kn = shift + eb[n];
+            const int64_t coloff = tCN ? tCN[n] : n;
 #pragma unroll 4
-          for (int rr = 0; rr < 32; ++rr) {
-            const int64_t m = m0 + rr;
-            if (m >= M) break;
-            const double v = shifted(tile[rr * 33 + lane], kn + ea[m]);
-            if (v != 0.0)
-              asm volatile("red.global.add.f64 [%0], %1;" ::"l"(__cvta_generic_to_global(C + m * ldc + n)),
-                           "d"(v));
+            for (int rr = 0; rr < 32; ++rr) {
+              const int64_t m = m0 + rr;
+              if (m >= M) break;
+              const double v = shifted(tile[rr * 33 + lane], kn + ea[m]);
+              if (v != 0.0)
+                asm volatile("red.global.add.f64 [%0], %1;" ::"l"(
+                                 __cvta_generic_to_global(C + (tCM ? cL + tCM[m] : m * ldc) + coloff)),
+                             "d"(v));
+            }
           }
         }
         __syncwarp();
@@ -299,46 +343,56 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 
 size_t oz_smem_bytes() { return 1024 + (size_t)kOzStages * kOzStage + kOzEpi * 32 * 33 * 4 + 256; }
 
-// e[r] = the exponent of max_k |scale X[r][k]| (max = f 2^e, f in [0.5, 1)),
-// 0 for an all-zero row; a non-finite entry sets *bad.  One warp per row.
-__global__ void k_oz_exponent(const double* __restrict__ X, int64_t ld, int64_t rows, int64_t K, double scale,
-                              int* __restrict__ e, int* bad) {
+// Digit planes of one operand, one warp per padded row r < rows_pad:
+//   x = scale X[r][k] 2^-e[r] for r < rows, k < K (zero elsewhere),
+//   out[(j rows_pad + r) Kp + k] = d_j(x)  (BF16),
+// X[r][k] = X[xL + (tR ? tR[r] : r ld) + (tK ? tK[k] : k)], e[r] the exponent
+// of max_k |scale X[r][k]| over the finite entries (max = f 2^e, f in [0.5,
+// 1); 0 for a zero row).  A non-finite entry goes into digit 0 unchanged (and
+// into no other digit), so that it reaches the result; *bad (if given) is set.
+__global__ void k_oz_pack(const double* __restrict__ X, int64_t xL, const int64_t* __restrict__ tR,
+                          const int64_t* __restrict__ tK, int64_t ld, int64_t rows, int64_t K, double scale, int S,
+                          int64_t rows_pad, int64_t Kp, int* __restrict__ e, __nv_bfloat16* __restrict__ out,
+                          int* bad) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = w; r < rows; r += nw) {
+  for (int64_t r = w; r < rows_pad; r += nw) {
+    const bool live = r < rows;
+    const double* row = live ? X + xL + (tR ? tR[r] : r * ld) : X;
     double mx = 0.0;
     bool fin = true;
-    for (int64_t k = lane; k < K; k += 32) {
-      const double x = scale * X[r * ld + k];
-      fin &= isfinite(x);
-      mx = fmax(mx, fabs(x));
+    if (live) {
+      for (int64_t k = lane; k < K; k += 32) {
+        const double x = scale * row[tK ? tK[k] : k];
+        if (isfinite(x))
+          mx = fmax(mx, fabs(x));
+        else
+          fin = false;
+      }
     }
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     const bool allfin = __all_sync(0xffffffffu, fin);
-    if (lane == 0) {
-      int ex = 0;
-      if (mx > 0.0) frexp(mx, &ex);
+    int ex = 0;
+    if (mx > 0.0) frexp(mx, &ex);
+    if (live && lane == 0) {
       e[r] = ex;
-      if (!allfin) atomicExch(bad, 1);
+      if (!allfin && bad) atomicExch(bad, 1);
     }
-  }
-}
-
-// Digit planes: out[(j rows_pad + r) Kp + k] = d_j of scale X[r][k] 2^-e[r]
-// (BF16; padding rows and columns stay zero from the buffer's clear).
-__global__ void k_oz_slice(const double* __restrict__ X, int64_t ld, int64_t rows, int64_t K, double scale,
-                           const int* __restrict__ e, int S, int64_t rows_pad, int64_t Kp,
-                           __nv_bfloat16* __restrict__ out) {
-  const int64_t n = rows * K;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / K, k = i - r * K;
-    double x = ldexp(scale * X[r * ld + k], -e[r]);
-    for (int j = 0; j < S; ++j) {
-      const double y = x * (double)(1 << kOzBits);
-      const double d = rint(y);
-      x = y - d;
-      out[((int64_t)j * rows_pad + r) * Kp + k] = __float2bfloat16_rn((float)d);
+    for (int64_t k = lane; k < Kp; k += 32) {
+      double x = (live && k < K) ? scale * row[tK ? tK[k] : k] : 0.0;
+      if (!isfinite(x)) {
+        out[r * Kp + k] = __float2bfloat16_rn((float)x);
+        for (int j = 1; j < S; ++j) out[((int64_t)j * rows_pad + r) * Kp + k] = __float2bfloat16_rn(0.f);
+        continue;
+      }
+      x = ldexp(x, -ex);
+      for (int j = 0; j < S; ++j) {
+        const double y = x * (double)(1 << kOzBits);
+        const double dg = rint(y);
+        x = y - dg;
+        out[((int64_t)j * rows_pad + r) * Kp + k] = __float2bfloat16_rn((float)dg);
+      }
     }
   }
 }
@@ -372,24 +426,83 @@ int64_t oz_pad(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 }  // namespace
 
-// The accumulation pieces of one output tile, level by level.
-static std::vector<OzPiece> oz_pieces(int S, int kt) {
-  std::vector<OzPiece> v;
-  for (int d = 0; d < S; ++d) {
-    const int len = (d + 1) * kt;
-    for (int q = 0; q < len; q += kOzBlocks) v.push_back({d, q, std::min(len, q + kOzBlocks), 0});
-  }
-  return v;
-}
-
-static uint64_t g_oz_wait_ns = kDefaultWaitNs;
-static int g_oz_stall = 0;
-
 int ozaki_set_wait_ns(uint64_t ns, int stall_test) {
-  g_oz_wait_ns = ns;
-  g_oz_stall = stall_test;
-  return 0;
+  return cudaMemcpyToSymbol(tcptx::g_wait_ns, &ns, sizeof(ns)) == cudaSuccess &&
+                 cudaMemcpyToSymbol(tcptx::g_stall_test, &stall_test, sizeof(int)) == cudaSuccess
+             ? 0
+             : -1;
 }
+
+namespace ric {
+
+// scratch: A digit planes | B digit planes | row exponents of A | of B
+size_t oz_scratch_bytes(int64_t M, int64_t N, int64_t K, int S) {
+  const int64_t Mp = oz_pad(M, OBM), Np = oz_pad(N, OBN), Kp = oz_pad(K, OBK);
+  return (size_t)S * (Mp + Np) * Kp * 2 + (size_t)oz_pad(M, 64) * 4 + (size_t)oz_pad(N, 64) * 4 + 256;
+}
+
+namespace {
+int g_oz_sms = 0;
+}  // namespace
+
+bool oz_prepare() {
+  static bool done = false;
+  if (done) return true;
+  if (!oz_encode()) return false;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&g_oz_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (g_oz_sms <= 0) g_oz_sms = 152;
+  if (cudaFuncSetAttribute(k_gemm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes()) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  done = true;
+  return true;
+}
+
+// pack (unless `packed`: the scratch already holds this call's digits) and
+// multiply; ctr (nullable, zeroed) hands out the work items dynamically
+int oz_launch(const OzArgs& a, unsigned long long* ctr, int* bad, bool packed, cudaStream_t s) {
+  const int S = a.slices;
+  if (a.M < 0 || a.N < 0 || a.K < 0 || S < 1 || S > RICMRCC_EMULATED_MAX_SLICES) return -1;
+  if (a.M == 0 || a.N == 0 || a.K == 0) return 0;
+  const int64_t Mp = oz_pad(a.M, OBM), Np = oz_pad(a.N, OBN), Kp = oz_pad(a.K, OBK);
+  // TMA row coordinates (digit plane x padded rows) and K-block positions are 32-bit
+  if ((int64_t)S * Mp > INT32_MAX || (int64_t)S * Np > INT32_MAX || Kp / OBK * S > INT32_MAX) return -1;
+  if (!oz_encode()) return -2;
+  if (oz_scratch_bytes(a.M, a.N, a.K, S) > a.scratch_bytes || !a.scratch) return -3;
+  if (!g_oz_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_oz_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_oz_sms <= 0) g_oz_sms = 152;
+  }
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(a.scratch) + 255) & ~(uintptr_t)255);
+  __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(base);
+  __nv_bfloat16* pb = pa + (size_t)S * Mp * Kp;
+  int* ea = reinterpret_cast<int*>(pb + (size_t)S * Np * Kp);
+  int* eb = ea + oz_pad(a.M, 64);
+  auto warps_grid = [&](int64_t rows) { return (int)std::min<int64_t>((rows + 7) / 8, 16 * (int64_t)g_oz_sms); };
+  if (!packed) {
+    k_oz_pack<<<warps_grid(Mp), 256, 0, s>>>(a.A, a.aL, a.tAM, a.tAK, a.lda, a.M, a.K, a.alpha, S, Mp, Kp, ea, pa,
+                                             bad);
+    k_oz_pack<<<warps_grid(Np), 256, 0, s>>>(a.B, a.bL, a.tBN, a.tBK, a.ldb, a.N, a.K, 1.0, S, Np, Kp, eb, pb, bad);
+  }
+  CUtensorMap ma, mb;
+  if (!oz_map(&ma, pa, Kp, (int64_t)S * Mp, OBM) || !oz_map(&mb, pb, Kp, (int64_t)S * Np, OBN)) return -4;
+  const int kt = (int)(Kp / OBK);
+  const int64_t items = (Mp / OBM) * (Np / OBN) * (int64_t)oz_npieces(S, kt);
+  const int grid = (int)std::min<int64_t>(items, g_oz_sms);
+  k_gemm_oz<<<grid, kOzThreads, oz_smem_bytes(), s>>>(ma, mb, a.M, a.N, (int)Mp, (int)Np, kt, S, ea, eb, a.C, a.cL,
+                                                       a.tCM, a.tCN, a.ldc, a.col_lanes, ctr, a.err);
+  return cudaGetLastError() == cudaSuccess ? 0 : -5;
+}
+
+int oz_contract(const OzArgs& a, cudaStream_t s) { return oz_launch(a, nullptr, nullptr, false, s); }
+
+}  // namespace ric
 
 extern "C" int ricmrcc_gemm_f64_emulated(const double* A, int64_t lda, const double* B, int64_t ldb, double* C,
                                          int64_t ldc, int64_t M, int64_t N, int64_t K, double alpha, int slices,
@@ -400,91 +513,68 @@ extern "C" int ricmrcc_gemm_f64_emulated(const double* A, int64_t lda, const dou
   if (M == 0 || N == 0 || K == 0 || alpha == 0.0) return RICMRCC_OK;
   if (!A || !B || !C || lda < K || ldb < K || ldc < N) return RICMRCC_EINVAL;
   const int64_t Mp = oz_pad(M, OBM), Np = oz_pad(N, OBN), Kp = oz_pad(K, OBK);
-  // TMA row coordinates (digit plane x padded rows) and K blocks are 32-bit
   if ((int64_t)S * Mp > INT32_MAX || (int64_t)S * Np > INT32_MAX || Kp / OBK * S > INT32_MAX) return RICMRCC_EINVAL;
-  if (!oz_encode()) return RICMRCC_ENOTSUP;
+  if (!ric::oz_prepare()) return RICMRCC_ENOTSUP;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int kt = (int)(Kp / OBK);
-  const std::vector<OzPiece> pieces = oz_pieces(S, kt);
-  __nv_bfloat16 *pa = nullptr, *pb = nullptr;
-  int *ea = nullptr, *eb = nullptr, *flags = nullptr;  // flags: [0] error, [1] non-finite input
-  OzPiece* dp = nullptr;
+  ric::OzArgs a;
+  a.A = A;
+  a.B = B;
+  a.C = C;
+  a.lda = lda;
+  a.ldb = ldb;
+  a.ldc = ldc;
+  a.M = M;
+  a.N = N;
+  a.K = K;
+  a.alpha = alpha;
+  a.slices = S;
+  a.scratch_bytes = ric::oz_scratch_bytes(M, N, K, S);
+  int* flags = nullptr;  // [0] pipeline timeout, [1] non-finite operand
   unsigned long long* ctr = nullptr;
-  const size_t bytesA = (size_t)S * Mp * Kp * 2, bytesB = (size_t)S * Np * Kp * 2;
-  int rc = RICMRCC_OK;
-  auto release = [&]() {
-    cudaFree(pa);
-    cudaFree(pb);
-    cudaFree(ea);
-    cudaFree(eb);
-    cudaFree(flags);
-    cudaFree(dp);
-    cudaFree(ctr);
-  };
-  if (cudaMalloc(&pa, bytesA) != cudaSuccess || cudaMalloc(&pb, bytesB) != cudaSuccess ||
-      cudaMalloc(&ea, sizeof(int) * M) != cudaSuccess || cudaMalloc(&eb, sizeof(int) * N) != cudaSuccess ||
-      cudaMalloc(&flags, sizeof(int) * 2) != cudaSuccess ||
-      cudaMalloc(&dp, sizeof(OzPiece) * pieces.size()) != cudaSuccess ||
+  if (cudaMalloc(&a.scratch, a.scratch_bytes) != cudaSuccess || cudaMalloc(&flags, sizeof(int) * 2) != cudaSuccess ||
       cudaMalloc(&ctr, sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
-    release();
+    cudaFree(a.scratch);
+    cudaFree(flags);
+    cudaFree(ctr);
     return RICMRCC_ENOMEM;
   }
-  static bool attr = false;
-  if (!attr) {
-    if (cudaFuncSetAttribute(k_gemm_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes()) !=
-        cudaSuccess) {
-      cudaGetLastError();
-      release();
-      return RICMRCC_ECUDA;
-    }
-    attr = true;
-  }
-  const uint64_t wait_ns = g_oz_wait_ns;
-  const int stall = g_oz_stall;
-  cudaMemcpyToSymbolAsync(g_wait_ns, &wait_ns, sizeof(wait_ns), 0, cudaMemcpyHostToDevice, s);
-  cudaMemcpyToSymbolAsync(g_stall_test, &stall, sizeof(stall), 0, cudaMemcpyHostToDevice, s);
-  cudaMemsetAsync(pa, 0, bytesA, s);
-  cudaMemsetAsync(pb, 0, bytesB, s);
+  a.err = flags;
+  int rc = RICMRCC_OK;
+  int hf[2] = {0, 0};
   cudaMemsetAsync(flags, 0, sizeof(int) * 2, s);
   cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s);
-  cudaMemcpyAsync(dp, pieces.data(), sizeof(OzPiece) * pieces.size(), cudaMemcpyHostToDevice, s);
-  int sms = 152, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  auto warps_grid = [&](int64_t rows) { return (int)std::min<int64_t>((rows + 7) / 8, 16 * (int64_t)sms); };
-  k_oz_exponent<<<warps_grid(M), 256, 0, s>>>(A, lda, M, K, alpha, ea, flags + 1);
-  k_oz_exponent<<<warps_grid(N), 256, 0, s>>>(B, ldb, N, K, 1.0, eb, flags + 1);
-  // refuse non-finite operands before C is touched
-  int hf[2] = {0, 0};
-  if (cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
-    cudaGetLastError();
-    release();
-    return RICMRCC_ECUDA;
+  // pack, and refuse non-finite operands before C is touched
+  {
+    char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(a.scratch) + 255) & ~(uintptr_t)255);
+    __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(base);
+    __nv_bfloat16* pb = pa + (size_t)S * Mp * Kp;
+    int* ea = reinterpret_cast<int*>(pb + (size_t)S * Np * Kp);
+    int* eb = ea + oz_pad(M, 64);
+    int sms = 152, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto warps_grid = [&](int64_t rows) { return (int)std::min<int64_t>((rows + 7) / 8, 16 * (int64_t)sms); };
+    k_oz_pack<<<warps_grid(Mp), 256, 0, s>>>(A, 0, nullptr, nullptr, lda, M, K, alpha, S, Mp, Kp, ea, pa,
+                                             flags + 1);
+    k_oz_pack<<<warps_grid(Np), 256, 0, s>>>(B, 0, nullptr, nullptr, ldb, N, K, 1.0, S, Np, Kp, eb, pb, flags + 1);
+    if (cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = RICMRCC_ECUDA;
+    else if (hf[1])
+      rc = RICMRCC_EINVAL;
   }
-  if (hf[1]) {
-    release();
-    return RICMRCC_EINVAL;
+  if (rc == RICMRCC_OK) {
+    const int lr = ric::oz_launch(a, ctr, nullptr, true, s);
+    if (lr == -2) rc = RICMRCC_ENOTSUP;
+    else if (lr != 0) rc = lr == -1 ? RICMRCC_EINVAL : RICMRCC_ECUDA;
+    if (cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+      rc = RICMRCC_ECUDA;
+    if (rc == RICMRCC_OK && hf[0]) rc = RICMRCC_ECUDA;  // a pipeline wait timed out
   }
-  const int sg = 8 * sms;
-  k_oz_slice<<<sg, 256, 0, s>>>(A, lda, M, K, alpha, ea, S, Mp, Kp, pa);
-  k_oz_slice<<<sg, 256, 0, s>>>(B, ldb, N, K, 1.0, eb, S, Np, Kp, pb);
-  CUtensorMap ma, mb;
-  if (!oz_map(&ma, pa, Kp, (int64_t)S * Mp, OBM) || !oz_map(&mb, pb, Kp, (int64_t)S * Np, OBN)) {
-    cudaStreamSynchronize(s);
-    release();
-    return RICMRCC_ECUDA;
-  }
-  const int64_t items = (Mp / OBM) * (Np / OBN) * (int64_t)pieces.size();
-  const int grid = (int)std::min<int64_t>(items, sms);
-  k_gemm_oz<<<grid, kOzThreads, oz_smem_bytes(), s>>>(ma, mb, M, N, (int)Mp, (int)Np, kt, dp, (int)pieces.size(),
-                                                       ea, eb, C, ldc, ctr, flags);
-  if (cudaGetLastError() != cudaSuccess) rc = RICMRCC_ECUDA;
-  if (cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
-    rc = RICMRCC_ECUDA;
-  if (rc == RICMRCC_OK && hf[0]) rc = RICMRCC_ECUDA;  // a pipeline wait timed out
-  release();
+  cudaFree(a.scratch);
+  cudaFree(flags);
+  cudaFree(ctr);
   return rc;
 }

@@ -1,0 +1,38 @@
+// FP64-accurate contractions emulated on the BF16 tensor cores (ozaki.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace ric {
+
+// C[cL + tCM[m] + tCN[n]] += alpha * sum_k A[aL + tAM[m] + tAK[k]] B[bL + tBN[n] + tBK[k]]
+// (device offset tables; a null row table means rows ld apart, a null K
+// table contiguous K, a null C table C[m ldc + n]).
+struct OzArgs {
+  const double* A = nullptr;
+  const double* B = nullptr;
+  double* C = nullptr;
+  int64_t aL = 0, bL = 0, cL = 0;
+  const int64_t *tAM = nullptr, *tAK = nullptr, *tBN = nullptr, *tBK = nullptr, *tCM = nullptr, *tCN = nullptr;
+  int64_t lda = 0, ldb = 0, ldc = 0;
+  int64_t M = 0, N = 0, K = 0;
+  double alpha = 1.0;
+  int slices = 11;
+  void* scratch = nullptr;  // oz_scratch_bytes(M, N, K, slices) bytes
+  size_t scratch_bytes = 0;
+  int* err = nullptr;       // device flag: set to 1 if a pipeline wait timed out
+  int col_lanes = 1;        // epilogue lanes along output columns (1) or rows (0)
+};
+
+size_t oz_scratch_bytes(int64_t M, int64_t N, int64_t K, int slices);
+// kernel attributes (outside any stream capture, before the first launch)
+bool oz_prepare();
+// packs both operands into the scratch and runs the digit products; no
+// allocation and no synchronisation (graph-capturable after oz_prepare).
+// Non-finite operand entries propagate into C as non-finite values.
+// Returns 0, -1 (bad sizes), -2 (no tensor-map support), -3 (scratch too
+// small), -4 (tensor map), -5 (launch).
+int oz_contract(const OzArgs& a, cudaStream_t s);
+
+}  // namespace ric

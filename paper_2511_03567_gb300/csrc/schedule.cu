@@ -22,11 +22,17 @@
 #include <vector>
 
 #include "handle.h"
+#include "ozaki.h"
 
 namespace ric {
 
 int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std::vector<char>& live,
-                   const TileRule& rule, bool mixed, std::vector<void*>& allocs, Schedule* out) {
+                   const TileRule& rule, bool mixed, std::vector<void*>& allocs, Schedule* out, bool emulated) {
+  // the contractions that leave the FP64 groups: to the split-BF16 tensor-core
+  // path (mixed) or to the emulated-FP64 one
+  auto routed = [&](const ContractOp& op) {
+    return mixed ? tc_eligible(op, rule) : emulated && oz_eligible(op, rule);
+  };
   out->max_level = 0;
   for (size_t i = 0; i < inst.size(); ++i)
     if (live[i]) out->max_level = std::max(out->max_level, inst[i]->res_prog.max_level);
@@ -44,7 +50,7 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
       for (const auto& op : p.ops) {
         if (op.level != lvl || op.L == 0 || op.M == 0 || op.N == 0 || op.K == 0) continue;
         out->flops += op.flops;
-        if (mixed && tc_eligible(op, rule)) {
+        if (routed(op)) {
           out->tc_contractions += 1;
           out->tc_flops += op.flops;
           continue;
@@ -201,7 +207,7 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
 
 int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*>& inst,
                  const std::vector<char>& live, const TileRule& rule, bool mixed, ScheduleTarget& tgt,
-                 void* scratch, size_t slice, int* err, int64_t* launches) {
+                 void* scratch, size_t slice, int* err, int64_t* launches, bool emulated) {
   static const int slot[kGroupKinds] = {0, 1, 2, 5, 6, 7, 5};  // profile kernel index per tile kind
   int64_t n = 0;
   auto grouped_fp = [&](int lvl) {
@@ -216,6 +222,30 @@ int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*
   for (int lvl = 0; lvl <= sc.max_level; ++lvl) {
     tgt.fork();
     if (!mixed) {
+      if (emulated) {
+        // FP64-accurate tensor-core contractions first (one-CTA-per-SM
+        // launches), spread over the tensor-core lanes, each lane with its own
+        // scratch (the largest contractions all on the first lane)
+        int j = 0;
+        for (size_t i = 0; i < inst.size(); ++i) {
+          if (!live[i]) continue;
+          ricmrcc_t* h = inst[i];
+          const Program& p = h->res_prog;
+          for (size_t q = 0; q < p.ops.size(); ++q) {
+            const ContractOp& op = p.ops[q];
+            if (op.level != lvl || !oz_eligible(op, rule)) continue;
+            if (op.L == 0 || op.M == 0 || op.N == 0 || op.K == 0) continue;
+            OzArgs a = oz_args(h, p, (int)q);
+            int s = 0;
+            oz_lane_scratch(h, oz_scratch_bytes(a.M, a.N, a.K, a.slices), j++, &s, &a.scratch, &a.scratch_bytes);
+            a.err = err;
+            tgt.mark(4);
+            const int rc = oz_contract(a, tgt.lane(kTcLane0 + s));
+            if (rc != 0) return fail(eh, RICMRCC_ECUDA, "emulated-FP64 launch (" + std::to_string(rc) + ")");
+            n += 3;
+          }
+        }
+      }
       grouped_fp(lvl);
       tgt.join();
       continue;
