@@ -273,8 +273,10 @@ RICMRCC_API int ricmrcc_plan_info(const ricmrcc_t* h, ricmrcc_plan_info_t* out);
  * the mean milliseconds per residual in kind_ms[RICMRCC_PROFILE_KINDS]
  * (host), per kernel: [0] 64x64 tile, [1] 16x16 tile, [2] dot reduction,
  * [3] tensor-core operand packing, [4] tcgen05 GEMM, [5] 128x16 tile,
- * [6] 64x32 tile, [7] small-output long-K reduction.  The tiles compute in FP64, or in FP32 with mixed != 0,
- * which also routes the large contractions to the tensor cores ([3], [4]).
+ * [6] 64x32 tile, [7] small-output long-K reduction.  The tiles compute in
+ * FP64, or in FP32 with mixed = 1, which also routes the large contractions
+ * to the tensor cores ([3], [4]).  mixed = 2: the RICMRCC_EMULATED schedule,
+ * FP64 tiles and the emulated-FP64 contractions (packing included) in [4].
  * Diagnostic: the events serialise the launches. */
 #define RICMRCC_PROFILE_KINDS 8
 RICMRCC_API int ricmrcc_profile(ricmrcc_t* h, int reps, int mixed, double* kind_ms);
@@ -311,7 +313,7 @@ RICMRCC_API int ricmrcc_gemm_bf16x3(const double* A, int64_t lda, const double* 
  * ENOTSUP (no tensor-map support), ECUDA (launch failure or a timed-out
  * pipeline wait). */
 #define RICMRCC_EMULATED_DEFAULT_SLICES 11
-#define RICMRCC_EMULATED_MAX_SLICES 13
+#define RICMRCC_EMULATED_MAX_SLICES 12
 RICMRCC_API int ricmrcc_gemm_f64_emulated(const double* A, int64_t lda, const double* B, int64_t ldb,
                                           double* C, int64_t ldc, int64_t M, int64_t N, int64_t K,
                                           double alpha, int slices, void* stream);

@@ -404,7 +404,7 @@ void release_tc(ricmrcc_t* h) {
   h->tc_scratch_bytes = 0;
   drop(h->oz_scratch);  // sized by the rule's tensor-core contractions
   h->oz_scratch = nullptr;
-  h->oz_slice = 0;
+  h->oz_bytes = 0;
   drop(h->adj_oz_scratch);
   h->adj_oz_scratch = nullptr;
   h->adj_oz_bytes = 0;
@@ -732,39 +732,29 @@ OzArgs oz_args(ricmrcc_t* h, const Program& p, int op_index) {
   return a;
 }
 
-// Scratch of the emulated-FP64 contractions of the residual graph: the first
-// tensor-core lane holds the largest one; the other lanes take contractions
-// of at most kOzSmallBytes (or the largest, if all are smaller).
-constexpr size_t kOzSmallBytes = (size_t)1 << 30;
+std::vector<std::vector<OzArgs>> oz_levels(ricmrcc_t* h) {
+  const Program& p = h->res_prog;
+  std::vector<std::vector<OzArgs>> lv(p.max_level + 1);
+  for (size_t i = 0; i < p.ops.size(); ++i) {
+    const ContractOp& op = p.ops[i];
+    if (op.L == 0 || op.M == 0 || op.N == 0 || op.K == 0 || !oz_eligible(op, h->rule)) continue;
+    lv[op.level].push_back(oz_args(h, p, (int)i));
+  }
+  return lv;
+}
 
+// Scratch of the emulated-FP64 contractions of the residual graph: the
+// digit planes of the largest level's contractions, side by side.
 int ensure_oz(ricmrcc_t* h) {
   if (h->oz_scratch) return RICMRCC_OK;
   if (!oz_prepare()) return fail(h, RICMRCC_ENOTSUP, "emulated-FP64 kernels unavailable");
-  size_t need = 0, small = 0;
-  for (const ContractOp& op : h->res_prog.ops) {
-    if (!oz_eligible(op, h->rule)) continue;
-    const size_t b = oz_scratch_bytes(op.M, op.N, op.K, RICMRCC_EMULATED_DEFAULT_SLICES);
-    need = std::max(need, b);
-    if (b <= kOzSmallBytes) small = std::max(small, b);
-  }
-  auto round = [](size_t b) { return (std::max<size_t>(b, 256) + 255) / 256 * 256; };
-  need = round(need);
-  small = round(small);
+  size_t need = 256;
+  for (const auto& lv : oz_levels(h)) need = std::max(need, oz_group_scratch(lv));
   char* buf = nullptr;
-  TRY(dalloc(h, &buf, (int64_t)(need + small * (kTcLanes - 1))));
+  TRY(dalloc(h, &buf, (int64_t)need));
   h->oz_scratch = buf;
-  h->oz_slice = need;
-  h->oz_small = small;
+  h->oz_bytes = need;
   return RICMRCC_OK;
-}
-
-void oz_lane_scratch(ricmrcc_t* h, size_t need, int j, int* lane, void** scratch, size_t* bytes) {
-  int l = j % kTcLanes;
-  if (need > h->oz_small) l = 0;
-  *lane = l;
-  char* base = static_cast<char*>(h->oz_scratch);
-  *scratch = l == 0 ? base : base + h->oz_slice + (size_t)(l - 1) * h->oz_small;
-  *bytes = l == 0 ? h->oz_slice : h->oz_small;
 }
 
 int residual_device(ricmrcc_t* h, int mode) {
@@ -1455,7 +1445,11 @@ int ricmrcc_profile(ricmrcc_t* h, int reps, int mixed, double* kind_ms) {
   TRY(enter(h));
   // the residual's launch schedule (as captured into the graph) replayed on
   // the work stream, one launch at a time, with events between launches
-  if (mixed) {
+  const bool emulated = mixed == 2;
+  if (emulated) {
+    TRY(ensure_oz(h));
+    mixed = 0;
+  } else if (mixed) {
     TRY(ensure_tc(h));
     TRY(refresh_tc_cache(h, h->s));
   }
@@ -1469,21 +1463,21 @@ int ricmrcc_profile(ricmrcc_t* h, int reps, int mixed, double* kind_ms) {
     }
   } cleanup{allocs};
   Schedule sc;
-  TRY(build_schedule(h, inst, live, h->rule, mixed != 0, allocs, &sc));
+  TRY(build_schedule(h, inst, live, h->rule, mixed != 0, allocs, &sc, emulated));
   for (int k = 0; k < RICMRCC_PROFILE_KINDS; ++k) kind_ms[k] = 0.0;
   for (int r = 0; r < reps; ++r) {
     CK(cudaMemsetAsync(h->arena, 0, sizeof(double) * h->arena_elems, h->s));
     CK(cudaMemsetAsync(h->X, 0, sizeof(double) * h->ng, h->s));
     CK(cudaMemsetAsync(h->scal + 1, 0, sizeof(double), h->s));
-    if (mixed) CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
+    if (mixed || emulated) CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
     CK(cudaMemsetAsync(sc.counters, 0, sizeof(unsigned long long) * sc.ncounters, h->s));
     ProfileTarget tgt(h->s);
     TRY(run_schedule(h, sc, inst, live, h->rule, mixed != 0, tgt, h->tc_scratch, h->tc_scratch_bytes, h->d_err,
-                     nullptr));
+                     nullptr, emulated));
     if (!tgt.accumulate(kind_ms, 1.0 / reps)) return fail(h, RICMRCC_ECUDA, "profile events");
   }
   CK(cudaStreamSynchronize(h->s));
-  if (mixed) TRY(check_tc_error(h));
+  if (mixed || emulated) TRY(check_tc_error(h));
   return leave(h);
 }
 

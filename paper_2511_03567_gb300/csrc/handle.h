@@ -86,11 +86,10 @@ struct ricmrcc {
   cudaEvent_t tc_ev[ric::kTcLanes] = {nullptr};      // tensor-core lanes meeting
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // [fp64, mixed, emulated fp64]
   int64_t graph_launches[3] = {0, 0, 0};                    // kernel launches in each graph
-  // emulated-FP64 tensor-core contractions: scratch of the first tensor-core
-  // lane (oz_slice bytes, the largest contraction), then one slice of oz_small
-  // bytes per other lane (contractions needing at most oz_small bytes)
+  // emulated-FP64 tensor-core contractions of the residual graph: the digit
+  // planes of one dependency level's contractions side by side
   void* oz_scratch = nullptr;
-  size_t oz_slice = 0, oz_small = 0;
+  size_t oz_bytes = 0;
   void* adj_oz_scratch = nullptr;  // one slice for the adjoint programs' serial launches
   size_t adj_oz_bytes = 0;
   int sms = 152;
@@ -184,9 +183,8 @@ int pack_entry(const PackedOperand& e, cudaStream_t s);
 TcArgs tc_args(ricmrcc_t* h, const Program& p, int op_index, int lane);
 // Emulated-FP64 arguments of op `op_index` (scratch not set).
 OzArgs oz_args(ricmrcc_t* h, const Program& p, int op_index);
-// Lane (0 .. kTcLanes-1) and scratch of the j-th emulated contraction of a
-// level: contractions larger than oz_small bytes of scratch run on lane 0.
-void oz_lane_scratch(ricmrcc_t* h, size_t need, int j, int* lane, void** scratch, size_t* bytes);
+// The emulated-FP64 contractions of the residual program, per dependency level.
+std::vector<std::vector<OzArgs>> oz_levels(ricmrcc_t* h);
 GroupOp group_op(const Program& p, const ContractOp& op);
 
 // Descriptor arrays of one grouped launch (device), kept for a graph's life.
@@ -224,6 +222,9 @@ struct Schedule {
   int64_t ncounters = 0;
   std::vector<std::array<Group, kGroupKinds>> groups;  // per level and tile kind
   std::vector<TcLevel> tc;                             // per level (grouped tensor-core launches)
+  // per level, emulated FP64: the grouped launch and its device descriptors
+  std::vector<OzGroup> oz;
+  std::vector<const void*> oz_desc;
   double flops = 0.0, tc_flops = 0.0;
   int64_t tc_contractions = 0;
 };
@@ -271,8 +272,8 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
                    bool emulated = false);
 // Enqueue the schedule on `tgt` (tensor-core scratch: kTcLanes slices of
 // `slice` bytes at `scratch`; pipeline time-out flag `err`).
-// With `emulated`: the emulated-FP64 contractions use each instance's
-// oz_scratch (oz_lane_scratch).
+// With `emulated`: the emulated-FP64 contractions of a level run as one
+// grouped launch in the first instance's oz_scratch (single-instance use).
 int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*>& inst,
                  const std::vector<char>& live, const TileRule& rule, bool mixed, ScheduleTarget& tgt,
                  void* scratch, size_t slice, int* err, int64_t* launches, bool emulated = false);

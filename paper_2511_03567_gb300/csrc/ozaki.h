@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace ric {
 
 // C[cL + tCM[m] + tCN[n]] += alpha * sum_k A[aL + tAM[m] + tAK[k]] B[bL + tBN[n] + tBK[k]]
@@ -34,5 +36,20 @@ bool oz_prepare();
 // Returns 0, -1 (bad sizes), -2 (no tensor-map support), -3 (scratch too
 // small), -4 (tensor map), -5 (launch).
 int oz_contract(const OzArgs& a, cudaStream_t s);
+
+// Grouped form: every contraction of a dependency level in one packing launch
+// and one persistent GEMM launch, their digit planes side by side in one
+// scratch buffer (at most oz_group_scratch bytes).  oz_group_build encodes the
+// device descriptors (opaque, `desc_bytes` bytes) for the given scratch;
+// the caller uploads them and passes the device copy to oz_group_launch.
+struct OzGroup {
+  std::vector<unsigned char> desc;  // [ops | packs] as uploaded
+  int nops = 0, npacks = 0;
+  int64_t items = 0, pack_rows = 0;
+  size_t ops_bytes = 0;             // offset of the pack descriptors in desc
+};
+size_t oz_group_scratch(const std::vector<OzArgs>& ops);
+int oz_group_build(const std::vector<OzArgs>& ops, void* scratch, size_t scratch_bytes, OzGroup* out);
+int oz_group_launch(const OzGroup& g, const void* d_desc, int* err, cudaStream_t s);
 
 }  // namespace ric

@@ -95,6 +95,26 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
   for (int lvl = 0; lvl <= out->max_level; ++lvl)
     for (int k = 0; k < kGroupKinds; ++k) out->groups[lvl][k].ctr = out->counters + lvl * kGroupKinds + k;
   out->tc.assign(out->max_level + 1, {});
+  if (emulated) {
+    // one grouped launch per level, descriptors for the first instance's scratch
+    ricmrcc_t* h = inst[0];
+    const auto lv = oz_levels(h);
+    out->oz.assign(out->max_level + 1, {});
+    out->oz_desc.assign(out->max_level + 1, nullptr);
+    for (size_t l = 0; l < lv.size() && (int)l <= out->max_level; ++l) {
+      std::vector<OzArgs> ops = lv[l];
+      for (OzArgs& a : ops) a.err = h->d_err;
+      const int rc = oz_group_build(ops, h->oz_scratch, h->oz_bytes, &out->oz[l]);
+      if (rc != 0) return fail(eh, RICMRCC_ECUDA, "emulated-FP64 descriptors (" + std::to_string(rc) + ")");
+      if (!out->oz[l].nops) continue;
+      void* d = nullptr;
+      if (cudaMalloc(&d, out->oz[l].desc.size()) != cudaSuccess) return fail(eh, RICMRCC_ENOMEM, "descriptors");
+      allocs.push_back(d);
+      if (cudaMemcpy(d, out->oz[l].desc.data(), out->oz[l].desc.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(eh, RICMRCC_ECUDA, "descriptor upload");
+      out->oz_desc[l] = d;
+    }
+  }
   if (!mixed) return RICMRCC_OK;
   // grouped packing launches (one per level)
   for (int lvl = 0; lvl <= out->max_level; ++lvl) {
@@ -222,29 +242,14 @@ int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*
   for (int lvl = 0; lvl <= sc.max_level; ++lvl) {
     tgt.fork();
     if (!mixed) {
-      if (emulated) {
-        // FP64-accurate tensor-core contractions first (one-CTA-per-SM
-        // launches), spread over the tensor-core lanes, each lane with its own
-        // scratch (the largest contractions all on the first lane)
-        int j = 0;
-        for (size_t i = 0; i < inst.size(); ++i) {
-          if (!live[i]) continue;
-          ricmrcc_t* h = inst[i];
-          const Program& p = h->res_prog;
-          for (size_t q = 0; q < p.ops.size(); ++q) {
-            const ContractOp& op = p.ops[q];
-            if (op.level != lvl || !oz_eligible(op, rule)) continue;
-            if (op.L == 0 || op.M == 0 || op.N == 0 || op.K == 0) continue;
-            OzArgs a = oz_args(h, p, (int)q);
-            int s = 0;
-            oz_lane_scratch(h, oz_scratch_bytes(a.M, a.N, a.K, a.slices), j++, &s, &a.scratch, &a.scratch_bytes);
-            a.err = err;
-            tgt.mark(4);
-            const int rc = oz_contract(a, tgt.lane(kTcLane0 + s));
-            if (rc != 0) return fail(eh, RICMRCC_ECUDA, "emulated-FP64 launch (" + std::to_string(rc) + ")");
-            n += 3;
-          }
-        }
+      if (emulated && (size_t)lvl < sc.oz.size() && sc.oz[lvl].nops) {
+        // the level's FP64-accurate tensor-core contractions first (one
+        // grouped packing launch, one persistent GEMM launch), beside the
+        // FP64 tiles of the rest
+        tgt.mark(4);
+        const int rc = oz_group_launch(sc.oz[lvl], sc.oz_desc[lvl], err, tgt.lane(kTcLane0));
+        if (rc != 0) return fail(eh, RICMRCC_ECUDA, "emulated-FP64 launch (" + std::to_string(rc) + ")");
+        n += 2;
       }
       grouped_fp(lvl);
       tgt.join();
