@@ -278,7 +278,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "emulated"],
+                    help="arithmetic of the timed iterations; emulated (emulated-FP64 tensor-core contractions) "
+                         "with --ncu-residual only")
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip timing the FP64 path beside the mixed one")
     ap.add_argument("--no-tune", action="store_true", help="keep the default tile rule")
@@ -329,7 +331,9 @@ def main():
     g.set_integrals(p.h, p.B)
     g.set_rdms(p.G1, p.G2, p.G3)
     g.semicanonicalize()
-    prec = ric.MIXED if args.precision == "mixed" else ric.FP64
+    prec = {"mixed": ric.MIXED, "fp64": ric.FP64, "emulated": ric.EMULATED}[args.precision]
+    if prec == ric.EMULATED and not args.ncu_residual:
+        raise SystemExit("--precision emulated: profiler mode only (--ncu-residual N)")
     tuning = None
     if args.tile_rule is not None:
         g.set_tile_rule(args.tile_rule, True, True)
@@ -344,6 +348,7 @@ def main():
         print(json.dumps({"ncu_residual": args.ncu_residual, "workload": w["workload"], "precision": args.precision,
                           "tile_rule": g.get_tile_rule(), "energy": E,
                           "graph_launches": int(info.graph_launches[1 if prec == ric.MIXED else 0]),
+                          "oz_contractions": int(info.oz_contractions), "oz_flops": info.oz_flops,
                           "tc_gemm_bytes": info.tc_gemm_bytes, "tc_flops": info.tc_flops,
                           "tc_grouped_ops": int(info.tc_grouped_ops),
                           "tc_weighted_ops": int(info.tc_weighted_ops)}))
@@ -949,6 +954,8 @@ def run_batched(args):
         g.set_integrals(p.h, p.B)
         g.set_rdms(p.G1, p.G2, p.G3)
         g.semicanonicalize()
+    if args.precision == "emulated":
+        raise SystemExit("--precision emulated: not for the batched workload")
     prec = ric.MIXED if args.precision == "mixed" else ric.FP64
     tuning = None
     if not args.no_tune:
