@@ -156,12 +156,16 @@ __device__ __forceinline__ OzWork oz_work(const OzOp& single, const OzOp* ops, i
   return w;
 }
 
-// Work items are handed out statically (t = blockIdx.x, + gridDim.x, ...):
-// piece-major inside each op, so that the CTAs of a wave work on the same
-// piece (same length) of neighbouring tiles.
+// Work items run piece-major inside each op, so that the CTAs of a wave work
+// on the same piece (same length) of neighbouring tiles.  With a counter
+// (zeroed) the producer claims them one by one, so that the CTAs in flight
+// hold a contiguous window of items and share their digit tiles through L2;
+// without one they are striped (t = blockIdx.x, + gridDim.x, ...).  The
+// producer hands each item to the MMA issuer and the epilogue through a
+// four-slot ring; -1 ends the sequence.
 __global__ void __launch_bounds__(kOzThreads, 1)
     k_gemm_oz(const __grid_constant__ OzOp single, const OzOp* __restrict__ ops, int nops, int64_t total,
-              int* err) {
+              unsigned long long* __restrict__ ctr, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   float* etile = reinterpret_cast<float*>(smem + kOzStages * kOzStage);  // kOzEpi x 32 x 33
@@ -171,7 +175,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   uint64_t* tempty = tfull + 2;         // [2]
   uint64_t* fin = tempty + 2;
   uint64_t* never = fin + 1;  // completed by nothing (error-path test)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
+  uint64_t* ifull = never + 1;   // [4]
+  uint64_t* iempty = ifull + 4;  // [4]
+  int64_t* iring = reinterpret_cast<int64_t*>(iempty + 4);  // [4]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(iring + 4);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -185,6 +192,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     }
     mbar_init(fin, 1);
     mbar_init(never, 1);
+    for (int j = 0; j < 4; ++j) {
+      mbar_init(ifull + j, 1);
+      mbar_init(iempty + j, 1 + kOzEpi);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -203,7 +214,18 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     int64_t issued = 0;
     bool ok = true;
     const uint32_t s0 = smem_u32(smem), full0 = smem_u32(full);
-    for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x) {
+    uint32_t ic = 0;
+    for (int64_t t = ctr ? (int64_t)atomicAdd(ctr, 1ull) : (int64_t)blockIdx.x;;) {
+      // publish the item (or the end) to the MMA issuer and the epilogue
+      const uint32_t j = ic & 3;
+      if (ic >= 4 && !mbar_wait(iempty + j, ((ic >> 2) - 1) & 1, err)) {
+        ok = false;
+        break;
+      }
+      iring[j] = t < total ? t : -1;
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(ifull + j)) : "memory");
+      ++ic;
+      if (t >= total) break;
       const OzWork w = oz_work(single, ops, nops, t);
       const OzOp& op = *w.op;
       for (int q = w.q0; q < w.q1; ++q) {
@@ -222,6 +244,8 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           ph ^= 1u;
         }
       }
+      if (!ok) break;
+      t = ctr ? (int64_t)atomicAdd(ctr, 1ull) : t + gridDim.x;
     }
     // copies still in flight land before the CTA exits
     for (int64_t i = issued > kOzStages ? issued - kOzStages : 0; i < issued; ++i)
@@ -234,7 +258,13 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const uint32_t empty0 = smem_u32(empty);
     const uint32_t idesc = oz_idesc();
     ok = stall_test_wait(never, err);
-    for (int64_t t = blockIdx.x; t < total && ok; t += gridDim.x, ++c) {
+    for (uint32_t ic = 0; ok; ++c) {
+      const uint32_t j = ic & 3;
+      if (!mbar_wait(ifull + j, (ic >> 2) & 1, err)) break;
+      const int64_t t = iring[j];
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(iempty + j)) : "memory");
+      ++ic;
+      if (t < 0) break;
       const OzWork w = oz_work(single, ops, nops, t);
       const uint32_t b = c & 1;
       if (c >= 2 && !mbar_wait(tempty + b, ((c >> 1) - 1) & 1, err)) break;
@@ -271,7 +301,14 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     const int qw = warp & 3;
     float* tile = etile + (warp - 2) * 32 * 33;
     uint32_t c = 0;
-    for (int64_t t = blockIdx.x; t < total; t += gridDim.x, ++c) {
+    for (uint32_t ic = 0;; ++c) {
+      const uint32_t j = ic & 3;
+      if (!__all_sync(0xffffffffu, mbar_wait(ifull + j, (ic >> 2) & 1, err))) break;
+      const int64_t t = iring[j];
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(iempty + j)) : "memory");
+      ++ic;
+      if (t < 0) break;
       const OzWork w = oz_work(single, ops, nops, t);
       const OzOp& op = *w.op;
       const int shift = -kOzBits * (w.d + 2);
@@ -640,8 +677,8 @@ int oz_describe(const OzArgs& a, char* base, int64_t item0, int64_t row0, OzOp* 
 int oz_warps_grid(int64_t rows) { return (int)std::min<int64_t>((rows + 7) / 8, 16 * (int64_t)g_oz_sms); }
 
 // pack (unless `packed`: the scratch already holds this call's digits) and
-// multiply, one contraction
-int oz_launch(const OzArgs& a, int* bad, bool packed, cudaStream_t s) {
+// multiply, one contraction (ctr: a zeroed work-item counter, or null)
+int oz_launch(const OzArgs& a, int* bad, bool packed, unsigned long long* ctr, cudaStream_t s) {
   if (oz_check(a)) return -1;
   if (a.M == 0 || a.N == 0 || a.K == 0) return 0;
   if (!oz_prepare()) return -2;
@@ -657,11 +694,11 @@ int oz_launch(const OzArgs& a, int* bad, bool packed, cudaStream_t s) {
     k_oz_pack<<<oz_warps_grid(pb.rows_pad), 256, 0, s>>>(pb, bad);
   }
   const int grid = (int)std::min<int64_t>(items, g_oz_sms);
-  k_gemm_oz<<<grid, kOzThreads, oz_smem_bytes(), s>>>(op, nullptr, 1, items, a.err);
+  k_gemm_oz<<<grid, kOzThreads, oz_smem_bytes(), s>>>(op, nullptr, 1, items, ctr, a.err);
   return cudaGetLastError() == cudaSuccess ? 0 : -5;
 }
 
-int oz_contract(const OzArgs& a, cudaStream_t s) { return oz_launch(a, nullptr, false, s); }
+int oz_contract(const OzArgs& a, cudaStream_t s) { return oz_launch(a, nullptr, false, nullptr, s); }
 
 size_t oz_group_scratch(const std::vector<OzArgs>& ops) {
   size_t b = 256;
@@ -706,7 +743,7 @@ int oz_group_build(const std::vector<OzArgs>& ops, void* scratch, size_t scratch
   return 0;
 }
 
-int oz_group_launch(const OzGroup& g, const void* d_desc, int* err, cudaStream_t s) {
+int oz_group_launch(const OzGroup& g, const void* d_desc, unsigned long long* ctr, int* err, cudaStream_t s) {
   if (!g.nops) return 0;
   const OzOp* ops = static_cast<const OzOp*>(d_desc);
   const OzPack* packs = reinterpret_cast<const OzPack*>(static_cast<const char*>(d_desc) + g.ops_bytes);
@@ -714,7 +751,7 @@ int oz_group_launch(const OzGroup& g, const void* d_desc, int* err, cudaStream_t
   OzOp none;
   memset(&none, 0, sizeof(none));
   const int grid = (int)std::min<int64_t>(g.items, g_oz_sms);
-  k_gemm_oz<<<grid, kOzThreads, oz_smem_bytes(), s>>>(none, ops, g.nops, g.items, err);
+  k_gemm_oz<<<grid, kOzThreads, oz_smem_bytes(), s>>>(none, ops, g.nops, g.items, ctr, err);
   return cudaGetLastError() == cudaSuccess ? 0 : -5;
 }
 
@@ -745,16 +782,20 @@ extern "C" int ricmrcc_gemm_f64_emulated(const double* A, int64_t lda, const dou
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   a.scratch_bytes = ric::oz_scratch_bytes(M, N, K, S);
   int* flags = nullptr;  // [0] pipeline timeout, [1] non-finite operand
-  if (cudaMalloc(&a.scratch, a.scratch_bytes) != cudaSuccess || cudaMalloc(&flags, sizeof(int) * 2) != cudaSuccess) {
+  unsigned long long* ctr = nullptr;
+  if (cudaMalloc(&a.scratch, a.scratch_bytes) != cudaSuccess || cudaMalloc(&flags, sizeof(int) * 2) != cudaSuccess ||
+      cudaMalloc(&ctr, sizeof(unsigned long long)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(a.scratch);
     cudaFree(flags);
+    cudaFree(ctr);
     return RICMRCC_ENOMEM;
   }
   a.err = flags;
   int rc = RICMRCC_OK;
   int hf[2] = {0, 0};
   cudaMemsetAsync(flags, 0, sizeof(int) * 2, s);
+  cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s);
   // pack, and refuse non-finite operands before C is touched
   {
     char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(a.scratch) + 255) & ~(uintptr_t)255);
@@ -774,7 +815,7 @@ extern "C" int ricmrcc_gemm_f64_emulated(const double* A, int64_t lda, const dou
     }
   }
   if (rc == RICMRCC_OK) {
-    const int lr = ric::oz_launch(a, nullptr, true, s);
+    const int lr = ric::oz_launch(a, nullptr, true, ctr, s);
     if (lr == -2)
       rc = RICMRCC_ENOTSUP;
     else if (lr != 0)
@@ -786,5 +827,6 @@ extern "C" int ricmrcc_gemm_f64_emulated(const double* A, int64_t lda, const dou
   }
   cudaFree(a.scratch);
   cudaFree(flags);
+  cudaFree(ctr);
   return rc;
 }

@@ -50,6 +50,7 @@ struct OzGroup {
 };
 size_t oz_group_scratch(const std::vector<OzArgs>& ops);
 int oz_group_build(const std::vector<OzArgs>& ops, void* scratch, size_t scratch_bytes, OzGroup* out);
-int oz_group_launch(const OzGroup& g, const void* d_desc, int* err, cudaStream_t s);
+// ctr: a work-item counter zeroed before the launch (or null: striped items)
+int oz_group_launch(const OzGroup& g, const void* d_desc, unsigned long long* ctr, int* err, cudaStream_t s);
 
 }  // namespace ric

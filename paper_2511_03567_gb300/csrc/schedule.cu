@@ -85,8 +85,9 @@ int build_schedule(ricmrcc_t* eh, const std::vector<ricmrcc_t*>& inst, const std
         if (g.nseg > 1 || k == 5) group_split(g, k);
     for (int k = 0; k < kGroupKinds; ++k) TRY(make_group(eh, allocs, by_kind[k], k, &out->groups[lvl][k]));
   }
-  // one work-item counter per grouped launch
-  out->ncounters = (int64_t)(out->max_level + 1) * kGroupKinds;
+  // one work-item counter per grouped launch (per level: the tile kinds, then
+  // the emulated-FP64 launch)
+  out->ncounters = (int64_t)(out->max_level + 1) * (kGroupKinds + 1);
   void* dc = nullptr;
   if (cudaMalloc(&dc, sizeof(unsigned long long) * out->ncounters) != cudaSuccess)
     return fail(eh, RICMRCC_ENOMEM, "work counters");
@@ -247,7 +248,8 @@ int run_schedule(ricmrcc_t* eh, const Schedule& sc, const std::vector<ricmrcc_t*
         // grouped packing launch, one persistent GEMM launch), beside the
         // FP64 tiles of the rest
         tgt.mark(4);
-        const int rc = oz_group_launch(sc.oz[lvl], sc.oz_desc[lvl], err, tgt.lane(kTcLane0));
+        unsigned long long* ctr = sc.counters + (int64_t)(sc.max_level + 1) * kGroupKinds + lvl;
+        const int rc = oz_group_launch(sc.oz[lvl], sc.oz_desc[lvl], ctr, err, tgt.lane(kTcLane0));
         if (rc != 0) return fail(eh, RICMRCC_ECUDA, "emulated-FP64 launch (" + std::to_string(rc) + ")");
         n += 2;
       }
