@@ -451,7 +451,9 @@ RICMRCC_API int ricmrcc_batch_set_rdms(ricmrcc_batch_t* b, int i, const double* 
  * `precision` (RICMRCC_FP64 / RICMRCC_MIXED).  E_out: host [count], nullable;
  * read the residuals with ricmrcc_get_residual on the instances. */
 RICMRCC_API int ricmrcc_batch_residual(ricmrcc_batch_t* b, int precision, double* E_out);
-/* Solve all instances with one set of options (precision, flow s, ...).  In
+/* Solve all instances with one set of options (precision, flow s, ...;
+ * RICMRCC_FP64 or RICMRCC_MIXED, RICMRCC_EMULATED is refused with EINVAL, as
+ * in ricmrcc_batch_step).  In
  * RICMRCC_MIXED every instance iterates on the tensor-core path until all
  * unconverged instances reach max|dt| < refine_tol, then the batch refines in
  * FP64.  Converged instances stop updating; the graph drops them once half of

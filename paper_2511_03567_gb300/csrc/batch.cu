@@ -226,6 +226,9 @@ int batch_iterate(ricmrcc_batch_t* b, const std::vector<ricmrcc_opts>& oi, const
 }
 
 int check_batch_opts(ricmrcc_batch_t* b, const ricmrcc_opts& o) {
+  // the batch schedule has the FP64 and split-BF16 arithmetics only
+  if (o.precision == RICMRCC_EMULATED)
+    return bfail(b, RICMRCC_EINVAL, "batches run RICMRCC_FP64 or RICMRCC_MIXED");
   for (int i = 0; i < b->count; ++i) ITRY(i, check_opts(b->inst[i], o));
   return RICMRCC_OK;
 }
@@ -394,6 +397,7 @@ static int batch_solve_impl(ricmrcc_batch_t* b, const ricmrcc_opts* opts, const 
   std::vector<ricmrcc_opts> oi(n, o);
   if (s_each)
     for (int i = 0; i < n; ++i) oi[i].s = s_each[i];
+  if (o.precision == RICMRCC_EMULATED) return bfail(b, RICMRCC_EINVAL, "batches run RICMRCC_FP64 or RICMRCC_MIXED");
   for (int i = 0; i < n; ++i) ITRY(i, check_opts(b->inst[i], oi[i]));
   const auto t0 = std::chrono::steady_clock::now();
   for (ricmrcc_t* h : b->inst) reset_iteration_state(h);

@@ -134,6 +134,11 @@ def test_batch_errors():
     with pytest.raises(ric.RicMrccError) as ei:
         b.residual(7)
     assert ei.value.code == ric.EINVAL
+    # the batch schedule has no emulated-FP64 arithmetic
+    for call in (lambda: b.solve(0.5, precision=ric.EMULATED), lambda: b.step(0.5, 1, precision=ric.EMULATED)):
+        with pytest.raises(ric.RicMrccError) as ei:
+            call()
+        assert ei.value.code == ric.EINVAL
     with pytest.raises(ric.RicMrccError):
         ric.RicMrccBatch([(2, 4, 10, 0)])
 
