@@ -253,6 +253,8 @@ def run_reference(args):
     for i in range(args.steps):
         smp.run(smp.schedule(i))
     secs = time.perf_counter() - t0
+    if not any(smp.row_times.values()):
+        smp.run(cheapest)  # one step sampled the energy only: one row, outside the timed steps
     per_iter, desc = smp.estimate()
     host = sampled.host_description()
     line = {"metric": METRIC, "value": per_iter, "unit": "s/iter", "n_gpus": args.gpus,
