@@ -9,8 +9,8 @@
 // entries lie in (-1, 1), then written as S signed base-2^5 digits:
 //   a = sum_{j<S} d_j 2^{-5(j+1)} + r,  d_j integer, |d_0| <= 32, |d_j| <= 16 (j > 0),
 //   |r| <= 2^{-5S-1},
-// the balanced base-32 digits of the integer rint(a 2^{5S}) (an exponent
-// shift, one conversion, then integer arithmetic).
+// the balanced base-32 digits of the integer rint(a 2^{5S}), all from
+// integer arithmetic on the FP64 bit fields (the FP64 pipe is narrow).
 // The digits are small integers, exact in BF16, and so is every product
 // d_i d'_j (|.| <= 2^10) in the MMA's FP32 accumulator.  The product is the
 // sum over digit pairs (i, j) of 2^{-5(i+j+2)} (D_i D'_j^T); pairs with
@@ -21,14 +21,18 @@
 // integer below 2^23 and the FP32 accumulation is exact).  Each piece's sum
 // is scaled by 2^{e_m + e_n - 5(d+2)} (an exponent shift of an exact integer)
 // and added into C with FP64 reductions: the only roundings are those FP64
-// additions, as in a plain FP64 GEMM.  alpha is folded into A's slicing.
+// additions, as in a plain FP64 GEMM.  alpha is folded into A's slicing
+// (an exponent shift when it is a power of two).
 //
 // Kernel layout: the persistent tcgen05 GEMM of the ladder (one TMA producer
 // warp, one MMA-issuing warp, four epilogue warps; 128 x 256 output tiles,
 // two TMEM accumulators, four 48 KB shared-memory stages of one 64-wide
 // K block of an A digit plane and a B digit plane; work items claimed from
-// an atomic counter and handed on through a four-slot ring).  Every wait is
-// bounded (tc_ptx.h).
+// an atomic counter, or striped without one, and handed on through a
+// four-slot ring).  One launch can cover many contractions (a dependency
+// level of the residual): their descriptors, tensor maps included, sit in
+// global memory, sorted by first work item.  Every wait is bounded
+// (tc_ptx.h).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
