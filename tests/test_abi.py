@@ -53,3 +53,48 @@ def test_argument_errors_without_gpu(lib_path):
     o = ric.Opts()
     assert lib.ricmrcc_opts_default(ctypes.byref(o)) == ric.OK
     assert o.s == 0.5 and o.max_iter == 100 and o.diis_size == 8
+
+
+STRUCTS = [("ricmrcc_layout", "Layout"), ("ricmrcc_opts", "Opts"), ("ricmrcc_stats", "Stats"),
+           ("ricmrcc_plan_info_t", "PlanInfo"), ("ricmrcc_tile_rule", "TileRule"), ("ricmrcc_tuning", "Tuning"),
+           ("ricmrcc_batch_info_t", "BatchInfo"), ("ricmrcc_ladder_info_t", "LadderInfo"),
+           ("ricmrcc_adjoint_info", "AdjointInfo")]
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """sizeof of every ABI struct (C compiler, the header as shipped) equals
+    the ctypes layout the binding passes."""
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    here = os.path.dirname(os.path.abspath(__file__))
+    inc = os.path.join(os.path.dirname(here), "include")
+    src = tmp_path / "sizes.c"
+    body = "".join(f'  printf("{c} %zu\\n", sizeof({c}));\n' for c, _ in STRUCTS)
+    src.write_text("#include <stdio.h>\n#include \"ricmrcc.h\"\nint main(void) {\n" + body + "  return 0;\n}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    sizes = dict(zip(out[0::2], (int(x) for x in out[1::2])))
+    for c, py in STRUCTS:
+        assert sizes[c] == ctypes.sizeof(getattr(ric, py)), (c, sizes[c], ctypes.sizeof(getattr(ric, py)))
+
+
+def test_emulated_gemm_and_adjoint_info_argument_errors(lib_path):
+    """Refused before any device work."""
+    lib = ric.load_library()
+    f = lib.ricmrcc_gemm_f64_emulated
+    assert f(None, 1, None, 1, None, 1, -1, 1, 1, 1.0, 0, None) == ric.EINVAL
+    assert f(None, 1, None, 1, None, 1, 1, 1, 1, 1.0, ric_max_slices() + 1, None) == ric.EINVAL
+    assert f(None, 1, None, 1, None, 1, 1, 1, 1, float("nan"), 0, None) == ric.EINVAL
+    assert f(None, 1, None, 1, None, 1, 4, 4, 4, 1.0, 0, None) == ric.EINVAL  # null operands
+    assert f(None, 1, None, 1, None, 1, 0, 4, 4, 1.0, 0, None) == ric.OK     # empty: nothing to do
+    assert lib.ricmrcc_get_adjoint_info(None, None) == ric.EINVAL
+
+
+def ric_max_slices():
+    import re
+    here = os.path.dirname(os.path.abspath(__file__))
+    text = open(os.path.join(os.path.dirname(here), "include", "ricmrcc.h")).read()
+    return int(re.search(r"#define RICMRCC_EMULATED_MAX_SLICES (\d+)", text).group(1))
