@@ -353,6 +353,13 @@ class RicMrcc:
         return o
 
     def solve(self, s=0.5, **kw):
+        """Converge the amplitudes at flow s; keyword options as ricmrcc_opts
+        (max_iter, e_tol, t_tol, diis_size, diis_start, precision, refine_tol).
+        precision FP64: every iteration in FP64; MIXED: split-BF16 tensor-core
+        iterations until max|dt| < refine_tol, then FP64 refinement;
+        EMULATED: the same, with the refinement's large contractions as
+        emulated-FP64 tensor-core products.  Returns (energy, Stats); a
+        NOT_CONVERGED outcome is reported in Stats, other failures raise."""
         o = self.default_opts(s=s, **kw)
         st = Stats()
         e = ctypes.c_double()
